@@ -1,0 +1,127 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module holds workload definitions (mesh sizes, coefficient parameters,
+step counts) and seeded random-number recipes only.  It contains none of the
+method's arithmetic, and neither the oracle nor the CUDA path is imported
+here.
+
+Workloads (the paper has no datasets; every input is defined by formulas):
+
+* ``bm1d_drift``           -- 1D Brownian motion with drift b = 0.5, sigma = 1
+                              on (-1, 1), T = 1, 201 nodes, 8 Gauss-Hermite
+                              points, dt = 1e-3 (1000 steps), FP64, terminal
+                              field chi (Sec. 4.1 with drift).
+* ``cellular_1025x513``    -- passive tracer in the time-periodic cellular
+                              flow psi = A sin(pi x) sin(pi y)
+                              + eps sin(omega t) sin(2 pi x) sin(pi y), A = 1,
+                              eps = 0.2, omega = 2 pi, D = 1e-3, box
+                              [0,2] x [0,1], 1025 x 513 nodes, 6 x 6 points,
+                              dt = 1e-3, 2000 steps (T = 2), FP32 (Sec. 4.2
+                              family, our stream-function form).
+* ``cellular_4097x2049``   -- the same flow, 4097 x 2049, 8 x 8 points,
+                              dt = 5e-4, 4000 steps, FP32 and FP64.
+* ``cellular_autonomous_2049x1025`` -- eps = 0, 2049 x 1025, 8 x 8 points,
+                              dt = 5e-4, 4000 steps, assembled-CSR path.
+* ``batched_64``           -- 64 instances: nx odd uniform in [257, 2049],
+                              ny = (nx+1)/2, D = 10^U[-4,-2], A ~ U[0.5, 2],
+                              eps = 0.2, omega = 2 pi, 6 x 6 points,
+                              dt = 1e-3, 1000 steps, FP32, fixed seed.
+* ``adjoint_1025x513``     -- the 1025 x 513 workload differentiated with
+                              respect to A, eps, D and the terminal field.
+
+Values in every workload are probabilities in [0, 1] that start from the 0/1
+indicator chi with a sharp ramp at the boundary; ``random_field`` draws
+fields of that kind for single-step checks.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+TWO_PI = 2.0 * math.pi
+
+WORKLOADS = {
+    "bm1d_drift": dict(n=(201,), lo=(-1.0,), hi=(1.0,), family="const_drift",
+                       params=(0.5, 0.0, 0.0, 1.0), q=8, dt=1e-3, n_steps=1000,
+                       precision="fp64"),
+    "cellular_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
+                              family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
+                              q=6, dt=1e-3, n_steps=2000, precision="fp32"),
+    "cellular_4097x2049": dict(n=(4097, 2049), lo=(0.0, 0.0), hi=(2.0, 1.0),
+                               family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
+                               q=8, dt=5e-4, n_steps=4000, precision="fp32"),
+    "cellular_autonomous_2049x1025": dict(n=(2049, 1025), lo=(0.0, 0.0), hi=(2.0, 1.0),
+                                          family="cellular_flow",
+                                          params=(1.0, 0.0, TWO_PI, 1e-3), q=8, dt=5e-4,
+                                          n_steps=4000, precision="fp32", path="csr"),
+    "adjoint_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
+                             family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
+                             q=6, dt=1e-3, n_steps=2000, precision="fp32"),
+}
+
+BATCH_SEED = 20240214
+
+
+def workload(name: str, **override) -> dict:
+    w = dict(WORKLOADS[name])
+    w.setdefault("path", "matrix_free")
+    w.update(override)
+    return w
+
+
+def batched_instances(count: int = 64, seed: int = BATCH_SEED, nx_range=(257, 2049)):
+    """Grids and parameters of the batched sweep: nx odd and uniform in
+    nx_range, ny = (nx+1)/2 (square cells on [0,2] x [0,1]), D log-uniform in
+    [1e-4, 1e-2], A uniform in [0.5, 2]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    lo_h, hi_h = (nx_range[0] - 1) // 2, (nx_range[1] - 1) // 2
+    for _ in range(count):
+        nx = 2 * int(rng.integers(lo_h, hi_h + 1)) + 1
+        ny = (nx + 1) // 2
+        D = 10.0 ** rng.uniform(-4.0, -2.0)
+        A = rng.uniform(0.5, 2.0)
+        out.append(dict(n=(nx, ny), lo=(0.0, 0.0), hi=(2.0, 1.0), family="cellular_flow",
+                        params=(A, 0.2, TWO_PI, D), q=6, dt=1e-3, n_steps=1000,
+                        precision="fp32"))
+    return out
+
+
+def random_field(shape, seed: int, modes: int = 6, boundary_one: bool = True) -> np.ndarray:
+    """A smooth seeded field with values in [0, 1]: a random combination of
+    low Fourier modes passed through a logistic squash, boundary nodes set to
+    1 (as every march state has), plus a few sharp ramps."""
+    rng = np.random.default_rng(seed)
+    grids = np.meshgrid(*[np.linspace(0.0, 1.0, s) for s in shape], indexing="ij")
+    f = np.zeros(shape)
+    for _ in range(modes):
+        k = rng.integers(1, 6, size=len(shape))
+        ph = rng.uniform(0, 2 * math.pi, size=len(shape))
+        term = np.ones(shape)
+        for g, kk, pp in zip(grids, k, ph):
+            term = term * np.cos(math.pi * kk * g + pp)
+        f += rng.normal() * term
+    f = 1.0 / (1.0 + np.exp(-2.0 * f))
+    if boundary_one:
+        for ax in range(len(shape)):
+            sl = [slice(None)] * len(shape)
+            sl[ax] = 0
+            f[tuple(sl)] = 1.0
+            sl[ax] = -1
+            f[tuple(sl)] = 1.0
+    return f
+
+
+def sample_nodes(shape, count: int, seed: int) -> np.ndarray:
+    """Seeded flat node indices, always including the corners and the
+    nodes next to the boundary."""
+    rng = np.random.default_rng(seed)
+    J = int(np.prod(shape))
+    pick = set(rng.integers(0, J, size=count).tolist())
+    if len(shape) == 2:
+        ny, nx = shape
+        for k in (0, 1, ny // 2, ny - 2, ny - 1):
+            for i in (0, 1, nx // 2, nx - 2, nx - 1):
+                pick.add(k * nx + i)
+    return np.array(sorted(pick), dtype=np.int64)

@@ -1,0 +1,395 @@
+/*
+ * FP64 CPU oracle for the Feynman-Kac exit-probability march
+ * (Yang, Zhang, del-Castillo-Negrete, Stoyanov, arXiv 2104.14561).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no
+ * code with the CUDA path and is written to be checked against the paper
+ * by eye: every query point is evaluated on its own, in the order Scheme 1
+ * states, with no blocking, fusion or factorisation.
+ *
+ * What it computes (Sec. 3.1, Scheme 1), for n = n_from-1 down to n_to:
+ *   Step 4 of the previous step / the terminal field: nodal slopes of u^{n+1}
+ *          by the PCHIP rule Eq. (e300), one grid line at a time, with the
+ *          end rule stated right after Eq. (e300);
+ *   Step 1: z_{jq} = x_j + b(t_n,x_j) dt + sigma(t_n,x_j) sqrt(2 dt) a_q,
+ *          Eq. (e31), over the tensor Gauss-Hermite rule of Eq. (quad);
+ *   Step 2: the PCHIP interpolant of Eq. (Lag11) at z_{jq}; its 1D cell
+ *          formula is the cubic Hermite formula of Sec. 3.1.2 and its
+ *          multi-dimensional form the tensor product of that formula with
+ *          nodal values and first partials only (the columns of Psi in
+ *          Eq. (e34)); a query outside the closed box takes the exit value 1
+ *          (Eq. (e24): the exit event contributes probability 1);
+ *   Step 3: u^n_j = sum_q w_q u^{n+1,J}(z_{jq}), Eq. (e304);
+ *   boundary nodes take u^n = 1 (Eq. (e3), Dirichlet value 1 on the boundary).
+ *
+ * Readings where the paper is silent or garbled are documented next to the
+ * code that takes them.  Coefficient time is the left end t_n = n dt
+ * (Eq. (ref-X)).  Every floating-point value is IEEE binary64; the library
+ * is built with -ffp-contract=off so that the host compiler does not fuse
+ * multiply-adds behind the reader's back.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define FKO_MAXDIM 3
+#define FKO_CONST_DRIFT 0
+#define FKO_CELLULAR_FLOW 1
+
+static const double FKO_PI = 3.14159265358979323846264338327950288;
+
+typedef struct fko_grid {
+  int dim;
+  int n[FKO_MAXDIM];
+  double lo[FKO_MAXDIM];
+  double hi[FKO_MAXDIM];
+} fko_grid;
+
+/* ---------------------------------------------------------------- grid -- */
+
+static int64_t grid_size(const fko_grid *g) {
+  int64_t J = 1;
+  for (int m = 0; m < g->dim; ++m) J *= g->n[m];
+  return J;
+}
+
+static double grid_h(const fko_grid *g, int m) {
+  return (g->hi[m] - g->lo[m]) / (double)(g->n[m] - 1);
+}
+
+/* Mesh S of Sec. 3.1.2: uniform per axis, x_i = lo + i h. */
+static double grid_x(const fko_grid *g, int m, int i) {
+  return g->lo[m] + (double)i * grid_h(g, m);
+}
+
+static int64_t grid_stride(const fko_grid *g, int m) {
+  int64_t s = 1;
+  for (int k = 0; k < m; ++k) s *= g->n[k];
+  return s;
+}
+
+/* Multi-index of the scalar node number j (x fastest). */
+static void grid_unflatten(const fko_grid *g, int64_t j, int *idx) {
+  for (int m = 0; m < g->dim; ++m) {
+    idx[m] = (int)(j % g->n[m]);
+    j /= g->n[m];
+  }
+}
+
+static int grid_is_boundary(const fko_grid *g, const int *idx) {
+  for (int m = 0; m < g->dim; ++m)
+    if (idx[m] == 0 || idx[m] == g->n[m] - 1) return 1;
+  return 0;
+}
+
+static int grid_check(const fko_grid *g) {
+  if (g->dim < 1 || g->dim > FKO_MAXDIM) return 1;
+  for (int m = 0; m < g->dim; ++m) {
+    if (g->n[m] < 3) return 1;
+    if (!(g->hi[m] > g->lo[m])) return 1;
+  }
+  return 0;
+}
+
+/* -------------------------------------------------------- coefficients -- */
+
+/*
+ * Drift b(t,x) and diffusion matrix sigma(t,x) (d x d, row-major) of the
+ * SDE Eq. (e1).
+ *
+ * FKO_CONST_DRIFT, p = (b_1, ..., b_d, s) with p[3] = s: b constant,
+ *   sigma = s I.  (Sec. 4.1 is the case d = 1, b = 0, s = 1.)
+ * FKO_CELLULAR_FLOW (d = 2), p = (A, eps, omega, D): the passive tracer of
+ *   Sec. 4.2 in the stream-function form
+ *     psi = A sin(pi x) sin(pi y) + eps sin(omega t) sin(2 pi x) sin(pi y),
+ *   velocity b = (-d psi/dy, d psi/dx) (the orientation of the paper's
+ *   cellular-flow velocity), and sigma = sqrt(2 D) I, so that the generator
+ *   is b.grad + D Laplacian.
+ */
+void fko_coefficients(int family, const double *p, int dim, double t,
+                      const double *x, double *b, double *sig) {
+  for (int i = 0; i < dim * dim; ++i) sig[i] = 0.0;
+  if (family == FKO_CONST_DRIFT) {
+    for (int m = 0; m < dim; ++m) {
+      b[m] = p[m];
+      sig[m * dim + m] = p[3];
+    }
+    return;
+  }
+  /* FKO_CELLULAR_FLOW */
+  {
+    double A = p[0], eps = p[1], omega = p[2], D = p[3];
+    double f = sin(omega * t);
+    double X = x[0], Y = x[1];
+    double dpsi_dy = FKO_PI * cos(FKO_PI * Y) *
+                     (A * sin(FKO_PI * X) + eps * f * sin(2.0 * FKO_PI * X));
+    double dpsi_dx = sin(FKO_PI * Y) * (A * FKO_PI * cos(FKO_PI * X) +
+                                        eps * f * 2.0 * FKO_PI * cos(2.0 * FKO_PI * X));
+    b[0] = -dpsi_dy;
+    b[1] = dpsi_dx;
+    sig[0] = sqrt(2.0 * D);
+    sig[3] = sqrt(2.0 * D);
+  }
+}
+
+static int family_check(int family, int dim, const double *p) {
+  if (family == FKO_CONST_DRIFT) return !(p[3] >= 0.0);
+  if (family == FKO_CELLULAR_FLOW) return dim != 2 || !(p[3] >= 0.0);
+  return 1;
+}
+
+/* ---------------------------------------------------------- PCHIP (F) -- */
+
+/*
+ * Eq. (e300): the nodal derivative is 0 when the two neighbouring divided
+ * differences have opposite signs, else their harmonic mean
+ * 2 / (1/delta_{j-1} + 1/delta_j).  The paper does not say what happens when
+ * one of them is zero; we read "opposite signs" as delta_{j-1} delta_j <= 0,
+ * which is also the limit of the harmonic mean as either difference tends
+ * to zero.
+ */
+static double pchip_rule(double d_left, double d_right) {
+  if (d_left * d_right <= 0.0) return 0.0;
+  return 2.0 / (1.0 / d_left + 1.0 / d_right);
+}
+
+/*
+ * Nodal slopes of u along axis m for every node.  Interior nodes use
+ * (delta_{i-1}, delta_i); the first node uses (delta_1, delta_2) and the
+ * last node (delta_{J-1}, delta_{J-2}) in the paper's 1-based numbering of
+ * the divided differences, i.e. (delta_0, delta_1) and (delta_{n-2},
+ * delta_{n-3}) in 0-based numbering.
+ */
+static void slopes_axis(const fko_grid *g, int m, const double *u, double *du) {
+  int64_t J = grid_size(g);
+  int64_t st = grid_stride(g, m);
+  int nm = g->n[m];
+  double h = grid_h(g, m);
+  int idx[FKO_MAXDIM];
+  for (int64_t j = 0; j < J; ++j) {
+    grid_unflatten(g, j, idx);
+    int i = idx[m];
+    int64_t base = j - (int64_t)i * st; /* node 0 of this grid line */
+#define U_(k) u[base + (int64_t)(k) * st]
+#define DELTA(k) ((U_((k) + 1) - U_(k)) / h)
+    double d;
+    if (i == 0)
+      d = pchip_rule(DELTA(0), DELTA(1));
+    else if (i == nm - 1)
+      d = pchip_rule(DELTA(nm - 2), DELTA(nm - 3));
+    else
+      d = pchip_rule(DELTA(i - 1), DELTA(i));
+#undef DELTA
+#undef U_
+    du[j] = d;
+  }
+}
+
+void fko_slopes(const fko_grid *g, const double *u, double *du) {
+  int64_t J = grid_size(g);
+  for (int m = 0; m < g->dim; ++m) slopes_axis(g, m, u, du + (int64_t)m * J);
+}
+
+/*
+ * The 1D cubic Hermite cell formula of Sec. 3.1.2 on [x_c, x_c + h] with
+ * s = z - x_c, written as the four basis functions that multiply
+ * u_c, u_{c+1}, u'_c, u'_{c+1}.
+ */
+static void hermite_basis(double s, double h, double *phi0, double *phi1,
+                          double *psi0, double *psi1) {
+  double h3 = h * h * h, h2 = h * h;
+  *phi1 = (3.0 * h * s * s - 2.0 * s * s * s) / h3;
+  *phi0 = (h3 - 3.0 * h * s * s + 2.0 * s * s * s) / h3;
+  *psi1 = s * s * (s - h) / h2;
+  *psi0 = s * (s - h) * (s - h) / h2;
+}
+
+/*
+ * u^{n,J}(z) of Eq. (Lag11) for z in the closed box: the tensor product of
+ * the 1D Hermite formula, carrying the nodal value and the d first partials
+ * at each of the 2^d corners of the cell that contains z.  The cell is
+ * floor((z - lo)/h) clamped to [0, n-2]; the interpolant is C^1 across cell
+ * faces, so a point on a face gets the same value from either side.
+ */
+static double interpolate(const fko_grid *g, const double *u, const double *du,
+                          const double *z) {
+  int64_t J = grid_size(g);
+  int c[FKO_MAXDIM];
+  double phi[FKO_MAXDIM][2], psi[FKO_MAXDIM][2];
+  for (int m = 0; m < g->dim; ++m) {
+    double h = grid_h(g, m);
+    int cm = (int)floor((z[m] - g->lo[m]) / h);
+    if (cm < 0) cm = 0;
+    if (cm > g->n[m] - 2) cm = g->n[m] - 2;
+    c[m] = cm;
+    double s = z[m] - grid_x(g, m, cm);
+    hermite_basis(s, h, &phi[m][0], &phi[m][1], &psi[m][0], &psi[m][1]);
+  }
+  double value = 0.0;
+  for (int corner = 0; corner < (1 << g->dim); ++corner) {
+    int64_t node = 0;
+    for (int m = 0; m < g->dim; ++m) {
+      int bit = (corner >> m) & 1;
+      node += (int64_t)(c[m] + bit) * grid_stride(g, m);
+    }
+    /* value basis: product of phi over all axes */
+    double wv = 1.0;
+    for (int m = 0; m < g->dim; ++m) wv *= phi[m][(corner >> m) & 1];
+    value += wv * u[node];
+    /* derivative basis along axis m: psi on axis m, phi on the others */
+    for (int m = 0; m < g->dim; ++m) {
+      double wd = 1.0;
+      for (int k = 0; k < g->dim; ++k) {
+        int bit = (corner >> k) & 1;
+        wd *= (k == m) ? psi[k][bit] : phi[k][bit];
+      }
+      value += wd * du[(int64_t)m * J + node];
+    }
+  }
+  return value;
+}
+
+/* --------------------------------------------------------- one node ---- */
+
+/*
+ * Steps 1-3 of Scheme 1 for one node: the tensor Gauss-Hermite sum of the
+ * interpolant at the shifted points, exit value 1 outside the closed box.
+ * a[], w[] hold the 1D rule normalised to the density pi^{-1/2} exp(-xi^2)
+ * (Eq. (expec)), so the tensor weights are products of w and sum to 1.
+ */
+static double node_update(const fko_grid *g, int family, const double *p,
+                          int nq, const double *a, const double *w, double dt,
+                          double tn, const double *u, const double *du,
+                          const int *idx) {
+  int d = g->dim;
+  double x[FKO_MAXDIM], b[FKO_MAXDIM], sig[FKO_MAXDIM * FKO_MAXDIM];
+  for (int m = 0; m < d; ++m) x[m] = grid_x(g, m, idx[m]);
+  fko_coefficients(family, p, d, tn, x, b, sig);
+  double sq = sqrt(2.0 * dt);
+  int64_t nqd = 1;
+  for (int m = 0; m < d; ++m) nqd *= nq;
+  double sum = 0.0;
+  for (int64_t qq = 0; qq < nqd; ++qq) {
+    int q[FKO_MAXDIM];
+    int64_t r = qq;
+    double wq = 1.0;
+    for (int m = 0; m < d; ++m) {
+      q[m] = (int)(r % nq);
+      r /= nq;
+      wq *= w[q[m]];
+    }
+    double z[FKO_MAXDIM];
+    int outside = 0;
+    for (int m = 0; m < d; ++m) {
+      double noise = 0.0;
+      for (int k = 0; k < d; ++k) noise += sig[m * d + k] * a[q[k]];
+      z[m] = x[m] + b[m] * dt + noise * sq;
+      if (z[m] < g->lo[m] || z[m] > g->hi[m]) outside = 1;
+    }
+    double val = outside ? 1.0 : interpolate(g, u, du, z);
+    sum += wq * val;
+  }
+  return sum;
+}
+
+/* ------------------------------------------------------------ public --- */
+
+/*
+ * Backward march of Scheme 1 from u^{n_from} (u_in) to u^{n_to} (u_out),
+ * n_to < n_from, coefficients at t_n = n dt.  boundary_rule = 1 holds the
+ * boundary nodes at 1 (the Dirichlet condition of Eq. (e3)); 0 is a test
+ * hook that treats boundary nodes like interior ones.  Returns 0 on success.
+ */
+int fko_march(const fko_grid *g, int family, const double *p, int nq,
+              const double *a, const double *w, double dt, int n_from,
+              int n_to, const double *u_in, double *u_out, int nthreads,
+              int boundary_rule) {
+  if (grid_check(g) || family_check(family, g->dim, p)) return 1;
+  if (nq < 1 || !(dt > 0.0) || n_to > n_from || n_to < 0) return 1;
+  int64_t J = grid_size(g);
+  double *cur = (double *)malloc(sizeof(double) * J);
+  double *nxt = (double *)malloc(sizeof(double) * J);
+  double *du = (double *)malloc(sizeof(double) * J * g->dim);
+  if (!cur || !nxt || !du) {
+    free(cur); free(nxt); free(du);
+    return 2;
+  }
+  memcpy(cur, u_in, sizeof(double) * J);
+  for (int n = n_from - 1; n >= n_to; --n) {
+    double tn = (double)n * dt;
+    fko_slopes(g, cur, du);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t j = 0; j < J; ++j) {
+      int idx[FKO_MAXDIM];
+      grid_unflatten(g, j, idx);
+      if (boundary_rule && grid_is_boundary(g, idx))
+        nxt[j] = 1.0;
+      else
+        nxt[j] = node_update(g, family, p, nq, a, w, dt, tn, cur, du, idx);
+    }
+    double *t = cur; cur = nxt; nxt = t;
+  }
+  memcpy(u_out, cur, sizeof(double) * J);
+  free(cur); free(nxt); free(du);
+  (void)nthreads;
+  return 0;
+}
+
+/*
+ * One step n (u^{n+1} -> u^n) evaluated only at the listed nodes; used to
+ * check sampled outputs of very large grids.
+ */
+int fko_step_nodes(const fko_grid *g, int family, const double *p, int nq,
+                   const double *a, const double *w, double dt, int n,
+                   const double *u_next, int64_t count, const int64_t *nodes,
+                   double *out, int nthreads, int boundary_rule) {
+  if (grid_check(g) || family_check(family, g->dim, p)) return 1;
+  int64_t J = grid_size(g);
+  double *du = (double *)malloc(sizeof(double) * J * g->dim);
+  if (!du) return 2;
+  fko_slopes(g, u_next, du);
+  double tn = (double)n * dt;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t k = 0; k < count; ++k) {
+    int idx[FKO_MAXDIM];
+    grid_unflatten(g, nodes[k], idx);
+    if (boundary_rule && grid_is_boundary(g, idx))
+      out[k] = 1.0;
+    else
+      out[k] = node_update(g, family, p, nq, a, w, dt, tn, u_next, du, idx);
+  }
+  free(du);
+  (void)nthreads;
+  return 0;
+}
+
+/* The interpolant of Eq. (Lag11) alone, at points inside the closed box. */
+int fko_interp(const fko_grid *g, const double *u, int64_t npts,
+               const double *pts, double *out) {
+  if (grid_check(g)) return 1;
+  int64_t J = grid_size(g);
+  double *du = (double *)malloc(sizeof(double) * J * g->dim);
+  if (!du) return 2;
+  fko_slopes(g, u, du);
+  for (int64_t k = 0; k < npts; ++k)
+    out[k] = interpolate(g, u, du, pts + k * g->dim);
+  free(du);
+  return 0;
+}
+
+int fko_has_openmp(void) {
+#ifdef _OPENMP
+  return 1;
+#else
+  return 0;
+#endif
+}
