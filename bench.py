@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the Feynman-Kac exit-probability march on GB300.
+
+One step = one whole march (fk_solve) of the workload: for the default
+``cellular_1025x513`` that is Scheme 1 over 2000 time steps on a 1025 x 513
+mesh with 6 x 6 Gauss-Hermite points, FP32.  The metric is
+node-quadrature updates per second: interior nodes x Q^2 x time steps per
+second of march, summed over all ranks (each rank marches its own instance:
+independent problems, weak scaling, no collective on the data path).
+
+Printed (rank 0, one JSON line): value (inputs resident on the device),
+e2e (the same through the public API with host buffers and host<->device
+copies inside the timed region), roofline of the dominant kernel, the CPU
+oracle timed on the host cores (cpu_baseline), clocks sampled during the
+timed region, and the number of our kernel launches in the timed region.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(bounded samples of the same workload); it never touches the GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fk_inputs  # noqa: E402
+
+METRIC = "node-quadrature updates/s & HBM GB/s (2D, 36-pt GH, FP32/FP64); adjoint/forward"
+UNIT = "node-quadrature updates/s"
+L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+FLOP_PER_UPDATE = 26                # see the design doc: 13 multiply-adds per query
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+PROFILE_JSON = os.path.join(ROOT, "profiles", "k_step2d_cellular_1025x513.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cellular_1025x513")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def units_per_solve(w) -> float:
+    interior = 1
+    for n in w["n"]:
+        interior *= n - 2
+    return float(interior) * (w["q"] ** len(w["n"])) * w["n_steps"]
+
+
+def hbm_bytes_per_solve(w) -> float:
+    """Algorithmic HBM traffic of the march: read u^{n+1} and write u^n once
+    per time step (the matrix-free path keeps no other per-node array)."""
+    J = 1
+    for n in w["n"]:
+        J *= n
+    elem = 4 if w["precision"] == "fp32" else 8
+    return 2.0 * J * elem * w["n_steps"]
+
+
+# ------------------------------------------------------------- clocks ----
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle -----
+def oracle_rate(w, max_seconds: float = 20.0):
+    """FP64 CPU oracle on the host cores over a bounded sample of the
+    workload's march (consecutive time steps from the terminal field)."""
+    from oracle import fk_oracle as O
+    fam = {"const_drift": O.CONST_DRIFT, "cellular_flow": O.CELLULAR_FLOW}[w["family"]]
+    g = O.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]))
+    cores = os.cpu_count() or 1
+    per_step = units_per_solve(w) / w["n_steps"]
+    t = time.perf_counter()
+    O.march(g, fam, list(w["params"]), w["q"], w["dt"], w["n_steps"], w["n_steps"] - 1,
+            nthreads=cores)
+    one = time.perf_counter() - t
+    k = max(1, min(w["n_steps"] - 1, int(max_seconds / max(one, 1e-6))))
+    t = time.perf_counter()
+    O.march(g, fam, list(w["params"]), w["q"], w["dt"], w["n_steps"], w["n_steps"] - k,
+            nthreads=cores)
+    dt = time.perf_counter() - t
+    return {"value": per_step * k / dt, "unit": UNIT, "cores": cores if O.has_openmp() else 1,
+            "kind": "oracle",
+            "sample": f"{k} of {w['n_steps']} time steps of {w['n'][0]}x{w['n'][1] if len(w['n']) > 1 else 1}"
+                      f", FP64, OpenMP over nodes ({dt:.1f} s)"}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    w = fk_inputs.workload(args.workload)
+    from oracle import fk_oracle as O
+    O.build()
+    fam = {"const_drift": O.CONST_DRIFT, "cellular_flow": O.CELLULAR_FLOW}[w["family"]]
+    g = O.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]))
+    cores = os.cpu_count() or 1
+    per_step = units_per_solve(w) / w["n_steps"]
+    # one benchmark step of the reference arm = one time step of the march
+    # (a bounded sample of the workload), so that K + W steps take seconds
+    u = None
+    times = []
+    for s in range(args.warmup + args.steps):
+        n = w["n_steps"] - s
+        t = time.perf_counter()
+        u = O.march(g, fam, list(w["params"]), w["q"], w["dt"], n, n - 1, u, nthreads=cores)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t)
+    sec = sum(times) / len(times)
+    value = per_step / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "grid": list(w["n"]), "q_per_dim": w["q"],
+                       "dt": w["dt"], "step": "one time step of the march per benchmark step"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores if O.has_openmp() else 1,
+                             "sample": f"{args.steps} time steps of {w['n'][0]}x{w['n'][1]}, FP64",
+                             "value": value, "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    try:
+        prof = json.load(open(PROFILE_JSON))
+        src = os.path.join(ROOT, "paper_2104_14561_gb300", "csrc", "fk_march.cu")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if prof.get("source_sha256") != h:
+            return None
+        return prof.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------- ours ----
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+    import paper_2104_14561_gb300 as fk
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = fk_inputs.workload(args.workload)
+    spec = fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
+                       params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
+                       precision=w["precision"], path=w["path"])
+    plan = fk.Plan(spec)
+    stream = torch.cuda.Stream(device=dev)
+    out = plan.empty()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    units = units_per_solve(w)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.solve(None, out, stream=stream)
+    stream.synchronize()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))                 # evict L2 before each timed march
+            starts[i].record(stream)
+            plan.solve(None, out, stream=stream)
+            ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_step = sum(ms) / len(ms)
+    if plan.last_device_error() != 0:
+        raise RuntimeError("device-side range check fired during the benchmark")
+    t_max = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_step_max = float(t_max.item())
+    value = units * world / (ms_step_max * 1e-3)
+
+    # end to end through the public API: pinned host in -> device -> march -> host out
+    host_in = torch.zeros(plan.shape, dtype=plan.dtype).pin_memory()
+    host_in[0, :] = 1.0
+    host_in[-1, :] = 1.0
+    host_in[:, 0] = 1.0
+    host_in[:, -1] = 1.0
+    host_out = torch.empty(plan.shape, dtype=plan.dtype).pin_memory()
+    dev_in = plan.empty()
+    e_ms = []
+    with torch.cuda.stream(stream):
+        for i in range(max(args.warmup, 1) + args.steps):
+            flush.fill_(float(i))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dev_in.copy_(host_in, non_blocking=True)
+            plan.solve(dev_in, out, stream=stream)
+            host_out.copy_(out, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            if i >= max(args.warmup, 1):
+                e_ms.append(a.elapsed_time(b))
+    e2e_t = torch.tensor([sum(e_ms) / len(e_ms)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = units * world / (float(e2e_t.item()) * 1e-3)
+    field_bytes = int(host_in.numel() * host_in.element_size())
+
+    if rank != 0:
+        return
+    info = plan.info()
+    launch_ms = ms_step / w["n_steps"]  # graph of back-to-back step kernels
+    flops_launch = FLOP_PER_UPDATE * units / w["n_steps"]
+    peak_flops = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6
+    achieved = flops_launch / (launch_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if w["precision"] == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": list(w["n"]), "q_per_dim": w["q"],
+                   "time_steps": w["n_steps"], "dt": w["dt"], "path": w["path"],
+                   "tile": info["tile"][:2], "halo": info["halo"][:2],
+                   "l2": "flushed (512 MB write) before every timed march; the 2 MB field "
+                         "stays L2-resident across the 2000 time steps of one march",
+                   "parallelism": f"{world} independent instances (one per GPU)"},
+        "hbm_gbs_algorithmic": hbm_bytes_per_solve(w) * world / (ms_step_max * 1e-3) / 1e9,
+        "roofline": {"kernel": "k_step2d", "bound": "alu", "achieved": achieved / 1e12,
+                     "peak": peak_flops / 1e12, "unit": "TFLOP/s", "frac": achieved / peak_flops,
+                     "traffic": profile_traffic(),
+                     "flop_per_launch": flops_launch,
+                     "launch_ms": launch_ms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,
+                "d2h_bytes_per_step": field_bytes},
+        "gpu_launches": args.steps * (w["n_steps"] + 1),
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+    if not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = oracle_rate(w)
+        except Exception as exc:  # the oracle is optional for the GPU number
+            line["cpu_baseline"] = {"value": None, "error": repr(exc)}
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * fk.h -- C ABI of a GB300 (sm_103a) library for the Feynman-Kac backward
+ * march that computes exit-time probabilities of SDEs (Yang, Zhang,
+ * del-Castillo-Negrete, Stoyanov, "A Feynman-Kac based numerical method for
+ * the exit time probability of a class of transport problems",
+ * arXiv 2104.14561).
+ *
+ * The method (Sec. 3.1, Scheme 1).  For the SDE dX = b(t,X) dt +
+ * sigma(t,X) dW (Eq. (e1)) in an open box D (Sec. 2), the exit probability
+ * P(T,x) = u(0,x) (Eq. (e5)) is approximated on a Cartesian mesh S by
+ * marching backward from the terminal field u^N, n = N-1, ..., 0:
+ *
+ *   u^n_j = sum_q w_q Itilde[u^{n+1}](x_j + b(t_n,x_j) dt
+ *                                      + sigma(t_n,x_j) sqrt(2 dt) a_q)
+ *
+ * with the tensor Gauss-Hermite rule (a_q, w_q) of Eq. (quad) normalised to
+ * the density pi^{-d/2} exp(-|xi|^2) of Eq. (expec), the piecewise cubic
+ * Hermite interpolant Itilde of Eq. (Lag11) whose nodal derivatives follow
+ * the PCHIP rule Eq. (e300), the exit value 1 for a shifted point outside
+ * the closed box (Eq. (e24)), and boundary nodes held at 1 (Eq. (e3)).
+ *
+ * Conventions for every call:
+ *  - Fields are dense arrays of the plan's precision (float for FK_FP32,
+ *    double for FK_FP64) with one value per mesh node, x fastest:
+ *    u[(k * n[1] + j) * n[0] + i] for node (i, j, k).  Node i on axis m sits
+ *    at lo[m] + i * (hi[m] - lo[m]) / (n[m] - 1).
+ *  - "Device pointer" means memory of the plan's CUDA device (cudaMalloc,
+ *    a PyTorch CUDA tensor, ...).  The caller owns every buffer it passes;
+ *    the library never frees or retains caller memory after a call returns.
+ *  - Calls that take a cudaStream_t are asynchronous on that stream; they
+ *    return after enqueueing.  A plan must not be used from two host
+ *    threads at once.
+ *  - Every call returns an fk_status; no C++ exception crosses the ABI.
+ *    Arguments are validated before any CUDA call is made.
+ */
+#ifndef FK_H
+#define FK_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fk_status {
+  FK_OK = 0,
+  FK_ERR_INVALID_ARG = 1, /* a NULL, out-of-range or inconsistent argument */
+  FK_ERR_UNSUPPORTED = 2, /* valid, but not a case this build implements  */
+  FK_ERR_OOM = 3,         /* device allocation failed                     */
+  FK_ERR_CUDA = 4,        /* a CUDA runtime call failed                   */
+  FK_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up           */
+  FK_ERR_DEVICE = 6       /* a device-side range check fired              */
+} fk_status;
+
+typedef enum fk_precision { FK_FP32 = 0, FK_FP64 = 1 } fk_precision;
+
+/* FK_PATH_MATRIX_FREE recomputes shifted points and interpolation weights
+ * in every step (one fused kernel per step).  FK_PATH_CSR assembles the
+ * product Q Psi of Eq. (e36) once as a sparse matrix and applies it every
+ * step; it needs coefficients that do not depend on t. */
+typedef enum fk_path { FK_PATH_MATRIX_FREE = 0, FK_PATH_CSR = 1 } fk_path;
+
+/* Coefficient families (b, sigma of Eq. (e1)):
+ *  FK_CONST_DRIFT     p = {b_1, b_2, b_3, s}: b constant, sigma = s I
+ *                     (Sec. 4.1 is d = 1, b = 0, s = 1).  d = 1 or 2.
+ *  FK_CELLULAR_FLOW   p = {A, eps, omega, D}, d = 2: the time-periodic
+ *                     cellular flow of Sec. 4.2 written with the stream
+ *                     function psi = A sin(pi x) sin(pi y)
+ *                       + eps sin(omega t) sin(2 pi x) sin(pi y),
+ *                     b = (-d psi/dy, d psi/dx), sigma = sqrt(2 D) I. */
+enum { FK_CONST_DRIFT = 0, FK_CELLULAR_FLOW = 1 };
+
+/* Uniform Cartesian mesh S (Sec. 3.1.2): n[m] >= 3 nodes on [lo[m], hi[m]]
+ * for m < dim; entries for m >= dim are ignored. */
+typedef struct fk_grid {
+  int dim;
+  int n[3];
+  double lo[3];
+  double hi[3];
+} fk_grid;
+
+/* Which faces of the box absorb (exit value 1).  Bit 2m is the lower face
+ * of axis m, bit 2m+1 the upper face.  Only "all faces absorbing" is
+ * implemented; any other mask gives FK_ERR_UNSUPPORTED. */
+typedef struct fk_region {
+  unsigned absorbing_faces;
+} fk_region;
+#define FK_ALL_FACES_ABSORBING 0x3Fu
+
+typedef struct fk_coeffs {
+  int family;
+  double p[8];
+} fk_coeffs;
+
+typedef struct fk_plan fk_plan;
+
+/* Read-only description of a plan (fk_plan_get_info). */
+typedef struct fk_plan_info {
+  int64_t n_nodes;          /* J                                        */
+  int64_t n_interior;       /* nodes strictly inside the box            */
+  int dim, q_per_dim, n_steps, precision, path;
+  int halo[3];              /* halo of a tile, in cells, per axis       */
+  int tile[3];              /* output nodes per tile, per axis          */
+  double reach_cells[3];    /* bound on |shift| in cells, per axis      */
+  int64_t csr_nnz;          /* stored entries of Q Psi (FK_PATH_CSR)    */
+  int64_t workspace_bytes;  /* device memory owned by the plan          */
+} fk_plan_info;
+
+/* ------------------------------------------------------------------------
+ * fk_plan_create -- validate a problem and prepare everything a march needs.
+ * Problem statement: Eq. (e1) (b, sigma), Sec. 2 (the box D), Sec. 3.1.2
+ * (mesh S), Eq. (quad) (q_per_dim Gauss-Hermite points per axis, so Q =
+ * q_per_dim^dim shifted points per node), Sec. 3.1.1 (uniform time step dt,
+ * N = n_steps steps, T = N dt, coefficients evaluated at t_n = n dt).
+ *   out        receives the new plan (set to NULL on failure).
+ *   q_per_dim  1..8 for dim = 2, 1..16 for dim = 1.
+ *   dt > 0, n_steps >= 1.
+ *   path       FK_PATH_CSR needs a family whose coefficients do not depend
+ *              on t (FK_CONST_DRIFT, or FK_CELLULAR_FLOW with eps = 0),
+ *              else FK_ERR_UNSUPPORTED.
+ * The plan allocates its own device workspace on the current CUDA device
+ * (coefficient tables, one scratch field, for FK_PATH_CSR the assembled
+ * matrix, which is built here).  Errors: FK_ERR_INVALID_ARG,
+ * FK_ERR_UNSUPPORTED, FK_ERR_OOM, FK_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+fk_status fk_plan_create(fk_plan **out, const fk_grid *grid,
+                         const fk_region *region, const fk_coeffs *coeffs,
+                         int q_per_dim, double dt, int n_steps,
+                         fk_precision prec, fk_path path);
+
+/* Release a plan and all device memory it owns (NULL is a no-op).  Waits
+ * for the plan's own work to finish. */
+fk_status fk_plan_destroy(fk_plan *plan);
+
+/* Copy the plan's description into *info. */
+fk_status fk_plan_get_info(const fk_plan *plan, fk_plan_info *info);
+
+/* ------------------------------------------------------------------------
+ * fk_gauss_hermite -- the 1D rule the plans use: q nodes a[] (ascending) and
+ * weights w[] for the density pi^{-1/2} exp(-xi^2) of Eq. (expec), so that
+ * sum w = 1.  Host arrays of length q, 1 <= q <= 16.  Host-only call.
+ * ---------------------------------------------------------------------- */
+fk_status fk_gauss_hermite(int q, double *a, double *w);
+
+/* ------------------------------------------------------------------------
+ * fk_solve -- Scheme 1 from n = N to n = 0: u_out <- u^0 = P(T, x_j).
+ *   u_terminal  device pointer to u^N, or NULL for the terminal indicator
+ *               chi of Sec. 3.2 (0 inside, 1 on the boundary).  Read only.
+ *               May equal u_out.
+ *   u_out       device pointer, receives u^0.
+ *   snapshots   NULL, or a device buffer of floor(N / snapshot_stride)
+ *               fields: field m receives u^{N - (m+1) snapshot_stride}.
+ *               For coefficients that do not depend on t this is
+ *               P((m+1) snapshot_stride dt, x): the whole time history
+ *               (Sec. 3.2) from one march.
+ *   stream      CUDA stream; the march is enqueued as one CUDA graph.
+ * ---------------------------------------------------------------------- */
+fk_status fk_solve(fk_plan *plan, const void *u_terminal, void *u_out,
+                   void *snapshots, int snapshot_stride, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * fk_march -- the steps n = n_from-1, ..., n_to of Scheme 1 only:
+ * u_out <- u^{n_to} given u_in = u^{n_from}, 0 <= n_to <= n_from <= N.
+ * The march is Markov in (n, u^n), so this is also checkpoint / resume.
+ * u_in may equal u_out.  Device pointers.  n_to == n_from copies.
+ * ---------------------------------------------------------------------- */
+fk_status fk_march(fk_plan *plan, int n_from, int n_to, const void *u_in,
+                   void *u_out, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * fk_solve_batched -- fk_solve for n independent plans (same precision,
+ * dim = 2, FK_PATH_MATRIX_FREE, same q_per_dim and n_steps) in ONE
+ * persistent kernel: the tiles of every instance share one work list and
+ * the steps are separated by a bounded grid barrier (Sec. 5 of the paper's
+ * conclusion notes that batches parallelise directly).
+ *   plans[i], u_terminal[i] (NULL = chi), u_out[i] (device) per instance.
+ * Returns FK_ERR_TIMEOUT (after the kernel has stopped) if a device-side
+ * barrier wait exceeded its bound.
+ * ---------------------------------------------------------------------- */
+fk_status fk_solve_batched(int n, fk_plan *const *plans,
+                           const void *const *u_terminal, void *const *u_out,
+                           cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * fk_adjoint -- reverse-mode derivative of the scalar L = <g, u^0>, where
+ * u^0 = S_0(S_1(...S_{N-1}(u^N))) is the march and g = cotangent_u0 (FP64
+ * device array, one value per node).  Each step S_n is differentiated
+ * exactly: the transpose of the interpolation-and-quadrature map of
+ * Eqs. (e34)-(e36) applied to [u; du], the transpose of the slope map F
+ * (Eq. (e300), derivative taken on its active branch), and the derivative
+ * of the shifted points of Eq. (e31) with respect to the coefficients.
+ *   u_terminal      device pointer to u^N or NULL (= chi).
+ *   dtheta          device FP64 array of 4 entries, receives
+ *                   dL/d(p[0..3]) of the coefficient family (for
+ *                   FK_CELLULAR_FLOW: A, eps, omega, D).  May be NULL.
+ *   du_terminal     device array of the plan's precision, receives dL/du^N.
+ *                   May be NULL.
+ *   checkpoint_every K >= 1: u is stored every K steps on the forward pass
+ *                   and each segment is recomputed in reverse.
+ * Only dim = 2, FK_PATH_MATRIX_FREE plans.  Gradients are accumulated in
+ * FP64 whatever the march precision.
+ * ---------------------------------------------------------------------- */
+fk_status fk_adjoint(fk_plan *plan, const void *u_terminal,
+                     const double *cotangent_u0, double *dtheta,
+                     void *du_terminal, int checkpoint_every,
+                     cudaStream_t stream);
+
+/* Text for a status code (static storage). */
+const char *fk_status_string(fk_status status);
+
+/* Synchronise with the plan's device and report (then clear) the plan's
+ * device-side error word: FK_OK, FK_ERR_DEVICE (a range check fired) or
+ * FK_ERR_TIMEOUT (a bounded wait gave up). */
+fk_status fk_last_device_error(fk_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FK_H */

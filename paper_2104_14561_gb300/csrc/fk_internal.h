@@ -1,0 +1,134 @@
+// Internal declarations shared by the translation units of libfk_gb300.
+// Nothing here is part of the C ABI (include/fk.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "fk.h"
+
+#define FK_MAXQ 16      // largest 1D rule a plan accepts (dim = 1)
+#define FK_MAXQ_2D 8    // largest rule per axis for dim = 2
+#define FK_THREADS 256  // threads per CTA of the march kernels
+
+// Device error word bits (fk_last_device_error).
+#define FK_DEVERR_RANGE 1u    // a shifted point fell outside its tile halo
+#define FK_DEVERR_TIMEOUT 2u  // a bounded grid-barrier wait gave up
+
+// Two- and four-component records aligned for single vector shared-memory
+// accesses (16 B for float4-like, 32 B for double4-like).
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+  T x, y, z, w;
+};
+template <typename T>
+struct alignas(2 * sizeof(T)) V2 {
+  T x, y;
+};
+
+// Everything one 2D step kernel needs, passed by value.  All lengths are in
+// cells of the uniform mesh ("index space"): node i sits at lo + i h, and a
+// shifted point is i + delta with delta = b dt / h + sigma sqrt(2 dt) a / h.
+template <typename T>
+struct Step2D {
+  const T* u_in;   // u^{n+1}
+  T* u_out;        // u^n
+  T* snap;         // optional second copy of u^n (snapshot), or nullptr
+  int nx, ny;
+  int tx, ty;      // output tile (interior nodes) per CTA
+  int hx, hy;      // halo in cells
+  int lx, ly;      // staged value tile: tx + 2 hx + 2, ty + 2 hy + 2
+  int lyr;         // column pitch (records) of the column-major record tiles, odd
+  int family;
+  // drift in cells: cellular flow  dx = kx cos(pi y)(A sin(pi x) + e1 sin(2 pi x))
+  //                                dy = ky sin(pi y)(A cos(pi x) + e2 cos(2 pi x))
+  //                 constant drift dx = cdx, dy = cdy
+  T kx, ky, A, e1, e2, cdx, cdy;
+  const T* col_tab;  // per column i: sin(pi x), sin(2 pi x), cos(pi x), cos(2 pi x)
+  const T* row_tab;  // per row k: cos(pi y), sin(pi y)
+  T gx[FK_MAXQ_2D], gy[FK_MAXQ_2D], w[FK_MAXQ_2D];  // sigma sqrt(2dt) a_q / h, w_q
+  unsigned* err;
+};
+
+template <typename T>
+struct Step1D {
+  const T* u_in;
+  T* u_out;
+  T* snap;
+  int nx;
+  int tx;   // output nodes per CTA
+  int hx;   // halo in cells
+  int lx;   // tx + 2 hx + 2
+  T cdx;    // b dt / h
+  T g[FK_MAXQ], w[FK_MAXQ];
+  unsigned* err;
+};
+
+// Shared memory bytes of one 2D step CTA.
+size_t fk_step2d_smem(int lx, int ly, int lyr, int elem);
+size_t fk_step1d_smem(int lx, int elem);
+
+// Launchers (fk_march.cu).  Return cudaGetLastError().
+template <typename T>
+cudaError_t fk_launch_step2d(const Step2D<T>& a, int q, cudaStream_t s);
+template <typename T>
+cudaError_t fk_launch_step1d(const Step1D<T>& a, int q, cudaStream_t s);
+// Opt the step kernels of this (dim, q, precision) into large dynamic shared
+// memory; called once at plan creation, never during stream capture.
+cudaError_t fk_prepare_step_kernels(int dim, int q, int elem);
+cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s);
+cudaError_t fk_launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
+
+struct fk_plan {
+  fk_grid grid;
+  fk_region region;
+  fk_coeffs coeffs;
+  int q;
+  double dt;
+  int n_steps;
+  fk_precision prec;
+  fk_path path;
+  int device;
+  int elem;          // 4 or 8
+  int64_t J, J_int;
+  double h[3];
+  double reach[3];
+  int halo[3], tile[3];
+  double gh_a[FK_MAXQ], gh_w[FK_MAXQ];
+  // device memory owned by the plan
+  void* scratch;     // one field
+  void* col_tab;     // 4 * nx values of the plan precision
+  void* row_tab;     // 2 * ny values
+  unsigned* d_err;
+  int64_t workspace_bytes;
+  cudaStream_t cap_stream;  // private stream used for graph capture
+  // CUDA graph cache for fk_solve
+  cudaGraphExec_t graph;
+  const void* g_in;
+  void* g_out;
+  void* g_snap;
+  int g_stride;
+  // CSR path (fk_csr.cu)
+  int64_t csr_nnz;
+  int* csr_rowptr;   // J + 1
+  int* csr_col;      // nnz, column in the stacked vector [u; Dx; Dy]
+  void* csr_val;     // nnz
+  void* csr_c;       // J: exit weight constant per row
+  void* stack;       // 3 J: [u; Dx; Dy] for the CSR product
+};
+
+// Step launchers that fill the argument struct from the plan (fk_plan.cu).
+fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void* snap,
+                          cudaStream_t s);
+void fk_fill_step2d_f32(const fk_plan* p, int n, Step2D<float>* a);
+void fk_fill_step2d_f64(const fk_plan* p, int n, Step2D<double>* a);
+
+// Device allocation through the plan's accounting.
+fk_status fk_dev_alloc(fk_plan* p, void** ptr, size_t bytes);
+void fk_dev_free(void* ptr);
+
+// CSR path (fk_csr.cu).
+fk_status fk_csr_assemble(fk_plan* p, cudaStream_t s);
+fk_status fk_csr_step(fk_plan* p, const void* u_in, void* u_out, void* snap, cudaStream_t s);

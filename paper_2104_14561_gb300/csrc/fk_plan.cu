@@ -1,0 +1,560 @@
+// Plan object, argument validation, Gauss-Hermite rule and the march driver
+// of the C ABI (include/fk.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "fk_internal.h"
+
+namespace {
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+// ---------------------------------------------------------- quadrature --
+// Polynomials orthonormal for the probability density pi^{-1/2} exp(-x^2)
+// satisfy x p_k = b_{k+1} p_{k+1} + b_k p_{k-1} with b_k = sqrt(k/2),
+// p_0 = 1.  The Gauss nodes are the zeros of p_q; they are bracketed by a
+// sign scan over (-sqrt(2q+1), sqrt(2q+1)) (a bound on the zeros of the
+// Hermite polynomials) and refined by bisection to the last bit.  The
+// weight of node x is the Christoffel number 1 / sum_{k<q} p_k(x)^2, so the
+// weights of the probability measure sum to 1 (Eq. (expec)).
+double orthonormal_hermite(int q, double x, double* sum_sq) {
+  double pm = 0.0, p = 1.0, s = 1.0;
+  for (int k = 0; k < q; ++k) {
+    const double bk = sqrt(0.5 * k), bk1 = sqrt(0.5 * (k + 1));
+    const double pn = (x * p - bk * pm) / bk1;
+    pm = p;
+    p = pn;
+    if (k + 1 < q) s += p * p;
+  }
+  if (sum_sq) *sum_sq = s;
+  return p;
+}
+
+bool gauss_hermite(int q, double* a, double* w) {
+  if (q < 1 || q > FK_MAXQ) return false;
+  const double lim = sqrt(2.0 * q + 1.0);
+  const int scan = 4000 * q;
+  int found = 0;
+  double xl = -lim, fl = orthonormal_hermite(q, xl, nullptr);
+  for (int s = 1; s <= scan && found < q; ++s) {
+    const double xr = -lim + 2.0 * lim * s / scan;
+    const double fr = orthonormal_hermite(q, xr, nullptr);
+    if (fr == 0.0) {
+      a[found++] = xr;
+    } else if ((fl < 0.0) != (fr < 0.0) && fl != 0.0) {
+      double lo = xl, hi = xr, flo = fl;
+      for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        const double fm = orthonormal_hermite(q, mid, nullptr);
+        if (fm == 0.0) {
+          lo = hi = mid;
+          break;
+        }
+        if ((fm < 0.0) == (flo < 0.0)) {
+          lo = mid;
+          flo = fm;
+        } else {
+          hi = mid;
+        }
+      }
+      a[found++] = 0.5 * (lo + hi);
+    }
+    xl = xr;
+    fl = fr;
+  }
+  if (found != q) return false;
+  // symmetrise (the rule is symmetric about 0)
+  for (int i = 0; i < q / 2; ++i) {
+    const double m = 0.5 * (a[q - 1 - i] - a[i]);
+    a[i] = -m;
+    a[q - 1 - i] = m;
+  }
+  if (q % 2) a[q / 2] = 0.0;
+  double tot = 0.0;
+  for (int i = 0; i < q; ++i) {
+    double s;
+    orthonormal_hermite(q, a[i], &s);
+    w[i] = 1.0 / s;
+    tot += w[i];
+  }
+  (void)tot;
+  return true;
+}
+
+bool finite(double v) { return v == v && v - v == 0.0; }
+
+// Largest |b| over the box (drift bound used to size the tile halo).
+void drift_bound(const fk_coeffs* c, int dim, double* bmax) {
+  for (int m = 0; m < 3; ++m) bmax[m] = 0.0;
+  if (c->family == FK_CONST_DRIFT) {
+    for (int m = 0; m < dim; ++m) bmax[m] = fabs(c->p[m]);
+  } else {
+    const double A = fabs(c->p[0]), e = fabs(c->p[1]);
+    bmax[0] = kPi * (A + e);
+    bmax[1] = kPi * (A + 2.0 * e);
+  }
+}
+
+double sigma_of(const fk_coeffs* c) {
+  return c->family == FK_CONST_DRIFT ? c->p[3] : sqrt(2.0 * c->p[3]);
+}
+
+fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int q, double dt,
+                   int n_steps, fk_precision prec, fk_path path) {
+  if (!g || !c) return FK_ERR_INVALID_ARG;
+  if (g->dim < 1 || g->dim > 3) return FK_ERR_INVALID_ARG;
+  for (int m = 0; m < g->dim; ++m) {
+    if (g->n[m] < 3) return FK_ERR_INVALID_ARG;
+    if (!finite(g->lo[m]) || !finite(g->hi[m]) || !(g->hi[m] > g->lo[m])) return FK_ERR_INVALID_ARG;
+  }
+  if (!(dt > 0.0) || !finite(dt) || n_steps < 1) return FK_ERR_INVALID_ARG;
+  if (prec != FK_FP32 && prec != FK_FP64) return FK_ERR_INVALID_ARG;
+  if (path != FK_PATH_MATRIX_FREE && path != FK_PATH_CSR) return FK_ERR_INVALID_ARG;
+  if (c->family != FK_CONST_DRIFT && c->family != FK_CELLULAR_FLOW) return FK_ERR_INVALID_ARG;
+  for (int k = 0; k < 8; ++k)
+    if (!finite(c->p[k])) return FK_ERR_INVALID_ARG;
+  if (c->family == FK_CONST_DRIFT && !(c->p[3] >= 0.0)) return FK_ERR_INVALID_ARG;
+  if (c->family == FK_CELLULAR_FLOW && !(c->p[3] >= 0.0)) return FK_ERR_INVALID_ARG;
+  if (g->dim == 3) return FK_ERR_UNSUPPORTED;
+  if (c->family == FK_CELLULAR_FLOW && g->dim != 2) return FK_ERR_INVALID_ARG;
+  if (q < 1 || q > (g->dim == 1 ? FK_MAXQ : FK_MAXQ_2D)) return FK_ERR_UNSUPPORTED;
+  if (r && r->absorbing_faces != FK_ALL_FACES_ABSORBING) return FK_ERR_UNSUPPORTED;
+  if (path == FK_PATH_CSR) {
+    if (g->dim != 2) return FK_ERR_UNSUPPORTED;
+    if (c->family == FK_CELLULAR_FLOW && c->p[1] != 0.0) return FK_ERR_UNSUPPORTED;
+  }
+  int64_t J = 1;
+  for (int m = 0; m < g->dim; ++m) J *= g->n[m];
+  if (J > ((int64_t)1 << 31) - 1) return FK_ERR_UNSUPPORTED;
+  return FK_OK;
+}
+
+fk_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return FK_OK;
+  if (e == cudaErrorMemoryAllocation) return FK_ERR_OOM;
+  return FK_ERR_CUDA;
+}
+
+template <typename T>
+fk_status upload_tables(fk_plan* p) {
+  const int nx = p->grid.n[0], ny = p->grid.dim == 2 ? p->grid.n[1] : 1;
+  T* ct = (T*)malloc(sizeof(T) * 4 * nx);
+  T* rt = (T*)malloc(sizeof(T) * 2 * ny);
+  if (!ct || !rt) {
+    free(ct);
+    free(rt);
+    return FK_ERR_OOM;
+  }
+  for (int i = 0; i < nx; ++i) {
+    const double x = p->grid.lo[0] + i * p->h[0];
+    ct[4 * i + 0] = (T)sin(kPi * x);
+    ct[4 * i + 1] = (T)sin(2.0 * kPi * x);
+    ct[4 * i + 2] = (T)cos(kPi * x);
+    ct[4 * i + 3] = (T)cos(2.0 * kPi * x);
+  }
+  for (int k = 0; k < ny; ++k) {
+    const double y = p->grid.dim == 2 ? p->grid.lo[1] + k * p->h[1] : 0.0;
+    rt[2 * k + 0] = (T)cos(kPi * y);
+    rt[2 * k + 1] = (T)sin(kPi * y);
+  }
+  fk_status st = fk_dev_alloc(p, &p->col_tab, sizeof(T) * 4 * nx);
+  if (st == FK_OK) st = fk_dev_alloc(p, &p->row_tab, sizeof(T) * 2 * ny);
+  if (st == FK_OK) st = cuda_status(cudaMemcpy(p->col_tab, ct, sizeof(T) * 4 * nx, cudaMemcpyHostToDevice));
+  if (st == FK_OK) st = cuda_status(cudaMemcpy(p->row_tab, rt, sizeof(T) * 2 * ny, cudaMemcpyHostToDevice));
+  free(ct);
+  free(rt);
+  return st;
+}
+
+template <typename T>
+void fill2d(const fk_plan* p, int n, Step2D<T>* a) {
+  memset(a, 0, sizeof(*a));
+  a->nx = p->grid.n[0];
+  a->ny = p->grid.n[1];
+  a->tx = p->tile[0];
+  a->ty = p->tile[1];
+  a->hx = p->halo[0];
+  a->hy = p->halo[1];
+  a->lx = a->tx + 2 * a->hx + 2;
+  a->ly = a->ty + 2 * a->hy + 2;
+  a->lyr = a->ly | 1;
+  a->family = p->coeffs.family;
+  const double dt = p->dt, tn = n * dt;
+  if (p->coeffs.family == FK_CELLULAR_FLOW) {
+    const double A = p->coeffs.p[0], eps = p->coeffs.p[1], om = p->coeffs.p[2];
+    const double st = sin(om * tn);
+    a->kx = (T)(-kPi * dt / p->h[0]);
+    a->ky = (T)(kPi * dt / p->h[1]);
+    a->A = (T)A;
+    a->e1 = (T)(eps * st);
+    a->e2 = (T)(2.0 * eps * st);
+  } else {
+    a->cdx = (T)(p->coeffs.p[0] * dt / p->h[0]);
+    a->cdy = (T)(p->coeffs.p[1] * dt / p->h[1]);
+  }
+  a->col_tab = (const T*)p->col_tab;
+  a->row_tab = (const T*)p->row_tab;
+  const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * dt);
+  for (int q = 0; q < p->q; ++q) {
+    a->gx[q] = (T)(sg * p->gh_a[q] / p->h[0]);
+    a->gy[q] = (T)(sg * p->gh_a[q] / p->h[1]);
+    a->w[q] = (T)p->gh_w[q];
+  }
+  a->err = p->d_err;
+}
+
+template <typename T>
+void fill1d(const fk_plan* p, Step1D<T>* a) {
+  memset(a, 0, sizeof(*a));
+  a->nx = p->grid.n[0];
+  a->tx = p->tile[0];
+  a->hx = p->halo[0];
+  a->lx = a->tx + 2 * a->hx + 2;
+  a->cdx = (T)(p->coeffs.p[0] * p->dt / p->h[0]);
+  const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * p->dt);
+  for (int q = 0; q < p->q; ++q) {
+    a->g[q] = (T)(sg * p->gh_a[q] / p->h[0]);
+    a->w[q] = (T)p->gh_w[q];
+  }
+  a->err = p->d_err;
+}
+
+// Choose the output tile and check the shared-memory budget.
+fk_status choose_tiles(fk_plan* p) {
+  int dev_smem = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+  if (e != cudaSuccess) return FK_ERR_CUDA;
+  if (p->grid.dim == 1) {
+    p->tile[0] = 1024;
+    const int lx = p->tile[0] + 2 * p->halo[0] + 2;
+    if (fk_step1d_smem(lx, p->elem) > (size_t)dev_smem) return FK_ERR_UNSUPPORTED;
+    return FK_OK;
+  }
+  // 2D: 32 x 16 output nodes per CTA (two per thread); grow the tile when the
+  // halo dominates, shrink it when the staged tile would not fit.
+  static const int cand[][2] = {{32, 16}, {64, 32}, {64, 16}, {32, 32}, {32, 8}, {32, 4}};
+  int best = -1;
+  double best_cost = 1e300;
+  for (int c = 0; c < 6; ++c) {
+    const int tx = cand[c][0], ty = cand[c][1];
+    const int lx = tx + 2 * p->halo[0] + 2, ly = ty + 2 * p->halo[1] + 2;
+    const size_t smem = fk_step2d_smem(lx, ly, ly | 1, p->elem);
+    if (smem > (size_t)dev_smem) continue;
+    // staged records per output node, penalised when few CTAs fit per SM
+    const int per_sm = (int)((228 * 1024) / (smem + 1024));
+    const double cost = (double)lx * ly / (tx * ty) + (per_sm < 2 ? 1.0 : 0.0) + (c == 0 ? -0.05 : 0.0);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = c;
+    }
+  }
+  if (best < 0) return FK_ERR_UNSUPPORTED;
+  p->tile[0] = cand[best][0];
+  p->tile[1] = cand[best][1];
+  return FK_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ internal --
+
+fk_status fk_dev_alloc(fk_plan* p, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) return FK_OK;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? FK_ERR_OOM : FK_ERR_CUDA;
+  }
+  p->workspace_bytes += (int64_t)bytes;
+  return FK_OK;
+}
+
+void fk_dev_free(void* ptr) {
+  if (ptr) cudaFree(ptr);
+}
+
+void fk_fill_step2d_f32(const fk_plan* p, int n, Step2D<float>* a) { fill2d<float>(p, n, a); }
+void fk_fill_step2d_f64(const fk_plan* p, int n, Step2D<double>* a) { fill2d<double>(p, n, a); }
+
+fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void* snap,
+                          cudaStream_t s) {
+  if (p->path == FK_PATH_CSR) return fk_csr_step(p, u_in, u_out, snap, s);
+  cudaError_t e;
+  if (p->grid.dim == 2) {
+    if (p->prec == FK_FP32) {
+      Step2D<float> a;
+      fill2d<float>(p, n, &a);
+      a.u_in = (const float*)u_in;
+      a.u_out = (float*)u_out;
+      a.snap = (float*)snap;
+      e = fk_launch_step2d<float>(a, p->q, s);
+    } else {
+      Step2D<double> a;
+      fill2d<double>(p, n, &a);
+      a.u_in = (const double*)u_in;
+      a.u_out = (double*)u_out;
+      a.snap = (double*)snap;
+      e = fk_launch_step2d<double>(a, p->q, s);
+    }
+  } else {
+    if (p->prec == FK_FP32) {
+      Step1D<float> a;
+      fill1d<float>(p, &a);
+      a.u_in = (const float*)u_in;
+      a.u_out = (float*)u_out;
+      a.snap = (float*)snap;
+      e = fk_launch_step1d<float>(a, p->q, s);
+    } else {
+      Step1D<double> a;
+      fill1d<double>(p, &a);
+      a.u_in = (const double*)u_in;
+      a.u_out = (double*)u_out;
+      a.snap = (double*)snap;
+      e = fk_launch_step1d<double>(a, p->q, s);
+    }
+  }
+  return cuda_status(e);
+}
+
+namespace {
+
+// Steps n_from-1 .. n_to from u_in (NULL = chi) into u_out, ping-ponging
+// between u_out and the plan's scratch field so that the last step lands in
+// u_out; snapshots as documented for fk_solve when snaps != NULL.
+fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void* u_out,
+                        void* snaps, int stride, cudaStream_t s) {
+  const int64_t bytes = p->J * p->elem;
+  const int steps = n_from - n_to;
+  if (steps == 0) {
+    if (!u_in) return cuda_status(fk_launch_fill_chi(u_out, p->grid.dim, p->grid.n[0],
+                                                      p->grid.n[1], p->elem, s));
+    if (u_in != u_out) return cuda_status(fk_launch_copy(u_out, u_in, bytes, s));
+    return FK_OK;
+  }
+  const bool first_to_out = ((steps - 1) % 2) == 0;  // does step 1 write u_out?
+  const void* src = u_in;
+  if (!src) {
+    void* buf = first_to_out ? p->scratch : u_out;
+    fk_status st = cuda_status(fk_launch_fill_chi(buf, p->grid.dim, p->grid.n[0], p->grid.n[1],
+                                                  p->elem, s));
+    if (st != FK_OK) return st;
+    src = buf;
+  } else if (src == u_out && first_to_out) {
+    fk_status st = cuda_status(fk_launch_copy(p->scratch, src, bytes, s));
+    if (st != FK_OK) return st;
+    src = p->scratch;
+  }
+  for (int m = 1; m <= steps; ++m) {
+    const int n = n_from - m;
+    void* dst = ((steps - m) % 2 == 0) ? u_out : p->scratch;
+    void* snap = nullptr;
+    if (snaps && stride > 0 && (m % stride) == 0)
+      snap = (char*)snaps + (int64_t)(m / stride - 1) * bytes;
+    fk_status st = fk_enqueue_step(p, n, src, dst, snap, s);
+    if (st != FK_OK) return st;
+    src = dst;
+  }
+  return FK_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- the ABI --
+
+extern "C" {
+
+const char* fk_status_string(fk_status s) {
+  switch (s) {
+    case FK_OK: return "FK_OK";
+    case FK_ERR_INVALID_ARG: return "FK_ERR_INVALID_ARG: invalid argument";
+    case FK_ERR_UNSUPPORTED: return "FK_ERR_UNSUPPORTED: case not implemented";
+    case FK_ERR_OOM: return "FK_ERR_OOM: device allocation failed";
+    case FK_ERR_CUDA: return "FK_ERR_CUDA: CUDA runtime error";
+    case FK_ERR_TIMEOUT: return "FK_ERR_TIMEOUT: bounded device wait expired";
+    case FK_ERR_DEVICE: return "FK_ERR_DEVICE: device-side range check fired";
+  }
+  return "unknown fk_status";
+}
+
+fk_status fk_gauss_hermite(int q, double* a, double* w) {
+  if (!a || !w || q < 1 || q > FK_MAXQ) return FK_ERR_INVALID_ARG;
+  return gauss_hermite(q, a, w) ? FK_OK : FK_ERR_INVALID_ARG;
+}
+
+fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* region,
+                         const fk_coeffs* coeffs, int q_per_dim, double dt, int n_steps,
+                         fk_precision prec, fk_path path) {
+  if (!out) return FK_ERR_INVALID_ARG;
+  *out = nullptr;
+  fk_status st = validate(grid, region, coeffs, q_per_dim, dt, n_steps, prec, path);
+  if (st != FK_OK) return st;
+  fk_plan* p = new (std::nothrow) fk_plan;
+  if (!p) return FK_ERR_OOM;
+  memset(p, 0, sizeof(*p));
+  p->grid = *grid;
+  for (int m = grid->dim; m < 3; ++m) {
+    p->grid.n[m] = 1;
+    p->grid.lo[m] = 0.0;
+    p->grid.hi[m] = 0.0;
+  }
+  p->region.absorbing_faces = FK_ALL_FACES_ABSORBING;
+  p->coeffs = *coeffs;
+  p->q = q_per_dim;
+  p->dt = dt;
+  p->n_steps = n_steps;
+  p->prec = prec;
+  p->path = path;
+  p->elem = prec == FK_FP32 ? 4 : 8;
+  if (!gauss_hermite(q_per_dim, p->gh_a, p->gh_w)) {
+    delete p;
+    return FK_ERR_INVALID_ARG;
+  }
+  p->J = 1;
+  p->J_int = 1;
+  for (int m = 0; m < grid->dim; ++m) {
+    p->J *= grid->n[m];
+    p->J_int *= grid->n[m] - 2;
+    p->h[m] = (grid->hi[m] - grid->lo[m]) / (grid->n[m] - 1);
+  }
+  // halo: every shifted point of an interior node stays within
+  // [i - halo + 1, i + halo - 1] cells, so its cell and the cell's right
+  // node are staged, and so are their slope stencils.
+  double bmax[3];
+  drift_bound(coeffs, grid->dim, bmax);
+  const double amax = fabs(p->gh_a[0]);
+  const double sg = sigma_of(coeffs) * sqrt(2.0 * dt);
+  for (int m = 0; m < grid->dim; ++m) {
+    p->reach[m] = (bmax[m] * dt + sg * amax) / p->h[m];
+    const double r = p->reach[m] * (1.0 + 1e-6) + 1e-3;
+    if (r > 4096.0) {
+      delete p;
+      return FK_ERR_UNSUPPORTED;
+    }
+    p->halo[m] = (int)ceil(r) + 1;
+  }
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return FK_ERR_CUDA;
+  }
+  st = choose_tiles(p);
+  if (st == FK_OK && path == FK_PATH_MATRIX_FREE)
+    st = cuda_status(fk_prepare_step_kernels(grid->dim, q_per_dim, p->elem));
+  if (st == FK_OK) st = fk_dev_alloc(p, (void**)&p->d_err, sizeof(unsigned));
+  if (st == FK_OK) st = cuda_status(cudaMemset(p->d_err, 0, sizeof(unsigned)));
+  if (st == FK_OK) st = fk_dev_alloc(p, &p->scratch, (size_t)(p->J * p->elem));
+  if (st == FK_OK) st = (prec == FK_FP32) ? upload_tables<float>(p) : upload_tables<double>(p);
+  if (st == FK_OK) st = cuda_status(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  if (st == FK_OK && path == FK_PATH_CSR) {
+    st = fk_csr_assemble(p, p->cap_stream);
+    if (st == FK_OK) st = cuda_status(cudaStreamSynchronize(p->cap_stream));
+  }
+  if (st != FK_OK) {
+    fk_plan_destroy(p);
+    return st;
+  }
+  *out = p;
+  return FK_OK;
+}
+
+fk_status fk_plan_destroy(fk_plan* p) {
+  if (!p) return FK_OK;
+  cudaDeviceSynchronize();
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  fk_dev_free(p->scratch);
+  fk_dev_free(p->col_tab);
+  fk_dev_free(p->row_tab);
+  fk_dev_free(p->d_err);
+  fk_dev_free(p->csr_rowptr);
+  fk_dev_free(p->csr_col);
+  fk_dev_free(p->csr_val);
+  fk_dev_free(p->csr_c);
+  fk_dev_free(p->stack);
+  delete p;
+  return FK_OK;
+}
+
+fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
+  if (!p || !info) return FK_ERR_INVALID_ARG;
+  memset(info, 0, sizeof(*info));
+  info->n_nodes = p->J;
+  info->n_interior = p->J_int;
+  info->dim = p->grid.dim;
+  info->q_per_dim = p->q;
+  info->n_steps = p->n_steps;
+  info->precision = p->prec;
+  info->path = p->path;
+  for (int m = 0; m < 3; ++m) {
+    info->halo[m] = p->halo[m];
+    info->tile[m] = p->tile[m];
+    info->reach_cells[m] = p->reach[m];
+  }
+  info->csr_nnz = p->csr_nnz;
+  info->workspace_bytes = p->workspace_bytes;
+  return FK_OK;
+}
+
+fk_status fk_march(fk_plan* p, int n_from, int n_to, const void* u_in, void* u_out,
+                   cudaStream_t stream) {
+  if (!p || !u_in || !u_out) return FK_ERR_INVALID_ARG;
+  if (n_to < 0 || n_from < n_to || n_from > p->n_steps) return FK_ERR_INVALID_ARG;
+  return enqueue_march(p, n_from, n_to, u_in, u_out, nullptr, 0, stream);
+}
+
+fk_status fk_solve(fk_plan* p, const void* u_terminal, void* u_out, void* snapshots,
+                   int snapshot_stride, cudaStream_t stream) {
+  if (!p || !u_out) return FK_ERR_INVALID_ARG;
+  if (snapshots && snapshot_stride < 1) return FK_ERR_INVALID_ARG;
+  if (!snapshots) snapshot_stride = 0;
+  const bool hit = p->graph && p->g_in == u_terminal && p->g_out == u_out &&
+                   p->g_snap == snapshots && p->g_stride == snapshot_stride;
+  if (!hit) {
+    if (p->graph) {
+      cudaGraphExecDestroy(p->graph);
+      p->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return FK_ERR_CUDA;
+    fk_status st = enqueue_march(p, p->n_steps, 0, u_terminal, u_out, snapshots,
+                                 snapshot_stride, p->cap_stream);
+    e = cudaStreamEndCapture(p->cap_stream, &g);
+    if (st != FK_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return FK_ERR_CUDA;
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_status(e);
+    p->graph = ex;
+    p->g_in = u_terminal;
+    p->g_out = u_out;
+    p->g_snap = snapshots;
+    p->g_stride = snapshot_stride;
+  }
+  return cuda_status(cudaGraphLaunch(p->graph, stream));
+}
+
+fk_status fk_last_device_error(fk_plan* p) {
+  if (!p) return FK_ERR_INVALID_ARG;
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpy(&h, p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return FK_ERR_CUDA;
+  if (h) cudaMemset(p->d_err, 0, sizeof(unsigned));
+  if (h & FK_DEVERR_TIMEOUT) return FK_ERR_TIMEOUT;
+  if (h & FK_DEVERR_RANGE) return FK_ERR_DEVICE;
+  return FK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+"""PyTorch binding of the fk_* C ABI (include/fk.h).
+
+PyTorch supplies device memory and streams; every step of the march runs
+in libfk_gb300's CUDA kernels.  Fields are tensors of shape (n[1], n[0])
+in 2D (x fastest) or (n[0],) in 1D, dtype float32 or float64 matching the
+plan's precision, on the plan's CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+_DTYPE = {"fp32": torch.float32, "fp64": torch.float64}
+_PREC = {"fp32": L.FK_FP32, "fp64": L.FK_FP64}
+_PATH = {"matrix_free": L.FK_PATH_MATRIX_FREE, "csr": L.FK_PATH_CSR}
+_FAMILY = {"const_drift": L.FK_CONST_DRIFT, "cellular_flow": L.FK_CELLULAR_FLOW}
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def gauss_hermite(q: int):
+    """The library's 1D Gauss-Hermite rule (density pi^{-1/2} exp(-x^2))."""
+    lib = L.load()
+    a = (ctypes.c_double * q)()
+    w = (ctypes.c_double * q)()
+    L.check("fk_gauss_hermite", lib.fk_gauss_hermite(q, a, w))
+    return list(a), list(w)
+
+
+@dataclass
+class PlanSpec:
+    n: tuple
+    lo: tuple
+    hi: tuple
+    family: str
+    params: tuple
+    q: int
+    dt: float
+    n_steps: int
+    precision: str = "fp32"
+    path: str = "matrix_free"
+
+
+class Plan:
+    """Owner of an fk_plan.  Create once per problem; solve many times."""
+
+    def __init__(self, spec: PlanSpec):
+        self.spec = spec
+        self._lib = L.load()
+        g = L.Grid()
+        g.dim = len(spec.n)
+        for m in range(g.dim):
+            g.n[m] = int(spec.n[m])
+            g.lo[m] = float(spec.lo[m])
+            g.hi[m] = float(spec.hi[m])
+        r = L.Region(L.FK_ALL_FACES_ABSORBING)
+        c = L.Coeffs()
+        c.family = _FAMILY[spec.family]
+        for k, v in enumerate(spec.params):
+            c.p[k] = float(v)
+        h = ctypes.c_void_p()
+        L.check("fk_plan_create",
+                self._lib.fk_plan_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(r),
+                                         ctypes.byref(c), int(spec.q), float(spec.dt),
+                                         int(spec.n_steps), _PREC[spec.precision],
+                                         _PATH[spec.path]))
+        self._h = h
+        self.dtype = _DTYPE[spec.precision]
+        self.shape = tuple(reversed(spec.n))
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    # ---------------------------------------------------------------- info
+    def info(self) -> dict:
+        i = L.PlanInfo()
+        L.check("fk_plan_get_info", self._lib.fk_plan_get_info(self._h, ctypes.byref(i)))
+        return {"n_nodes": i.n_nodes, "n_interior": i.n_interior, "dim": i.dim,
+                "q_per_dim": i.q_per_dim, "n_steps": i.n_steps, "halo": list(i.halo),
+                "tile": list(i.tile), "reach_cells": list(i.reach_cells),
+                "csr_nnz": i.csr_nnz, "workspace_bytes": i.workspace_bytes}
+
+    def _check_field(self, t: torch.Tensor, name: str):
+        if t.dtype != self.dtype or t.device.type != "cuda" or tuple(t.shape) != self.shape \
+                or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous {self.dtype} CUDA tensor of shape "
+                             f"{self.shape}, got {t.dtype} {tuple(t.shape)} on {t.device}")
+
+    def empty(self) -> torch.Tensor:
+        return torch.empty(self.shape, dtype=self.dtype, device=self.device)
+
+    # --------------------------------------------------------------- march
+    def solve(self, u_terminal: torch.Tensor | None = None, out: torch.Tensor | None = None,
+              snapshots: torch.Tensor | None = None, snapshot_stride: int = 0,
+              stream=None) -> torch.Tensor:
+        """u^0 of Scheme 1 (P(T, x) when u_terminal is None = chi)."""
+        if u_terminal is not None:
+            self._check_field(u_terminal, "u_terminal")
+        if out is None:
+            out = self.empty()
+        self._check_field(out, "out")
+        if snapshots is not None:
+            m = self.spec.n_steps // snapshot_stride
+            if snapshots.dtype != self.dtype or tuple(snapshots.shape) != (m,) + self.shape \
+                    or not snapshots.is_contiguous():
+                raise ValueError("snapshots: wrong dtype/shape")
+        L.check("fk_solve", self._lib.fk_solve(self._h, _ptr(u_terminal), _ptr(out),
+                                               _ptr(snapshots), int(snapshot_stride),
+                                               _stream(stream)))
+        return out
+
+    def march(self, n_from: int, n_to: int, u_in: torch.Tensor,
+              out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Steps n_from-1 .. n_to (resume from a checkpoint u^{n_from})."""
+        self._check_field(u_in, "u_in")
+        if out is None:
+            out = self.empty()
+        self._check_field(out, "out")
+        L.check("fk_march", self._lib.fk_march(self._h, int(n_from), int(n_to), _ptr(u_in),
+                                               _ptr(out), _stream(stream)))
+        return out
+
+    def adjoint(self, cotangent_u0: torch.Tensor, u_terminal: torch.Tensor | None = None,
+                checkpoint_every: int = 50, want_dtheta: bool = True,
+                want_du_terminal: bool = True, stream=None):
+        """dL/dtheta (4 FP64 values) and dL/du^N for L = <cotangent_u0, u^0>."""
+        if cotangent_u0.dtype != torch.float64 or tuple(cotangent_u0.shape) != self.shape:
+            raise ValueError("cotangent_u0 must be a float64 field")
+        if u_terminal is not None:
+            self._check_field(u_terminal, "u_terminal")
+        dtheta = torch.zeros(4, dtype=torch.float64, device=self.device) if want_dtheta else None
+        du = self.empty() if want_du_terminal else None
+        L.check("fk_adjoint", self._lib.fk_adjoint(self._h, _ptr(u_terminal),
+                                                   _ptr(cotangent_u0.contiguous()), _ptr(dtheta),
+                                                   _ptr(du), int(checkpoint_every),
+                                                   _stream(stream)))
+        return dtheta, du
+
+    def last_device_error(self) -> int:
+        return self._lib.fk_last_device_error(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fk_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batched(plans, u_terminals=None, outs=None, stream=None):
+    """fk_solve_batched over independent plans (one persistent launch)."""
+    lib = L.load()
+    n = len(plans)
+    if u_terminals is None:
+        u_terminals = [None] * n
+    if outs is None:
+        outs = [p.empty() for p in plans]
+    for p, u, o in zip(plans, u_terminals, outs):
+        if u is not None:
+            p._check_field(u, "u_terminal")
+        p._check_field(o, "out")
+    H = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+    U = (ctypes.c_void_p * n)(*[None if u is None else u.data_ptr() for u in u_terminals])
+    O = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    L.check("fk_solve_batched", lib.fk_solve_batched(n, H, U, O, _stream(stream)))
+    return outs

@@ -1,0 +1,111 @@
+"""The C-ABI library loads, exports every symbol include/fk.h declares, and
+rejects invalid arguments on the host before any CUDA call (no GPU needed:
+none of these calls launches work)."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2104_14561_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2104_14561_gb300.build import build
+        build()
+    _lib.load()
+    return _lib
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "fk.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fk_[a-z_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(L):
+    lib = L.load()
+    names = _declared()
+    assert set(names) == set(L.EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _args(L, **kw):
+    g = L.Grid()
+    g.dim = kw.get("dim", 2)
+    n = kw.get("n", (33, 17))
+    for m in range(len(n)):
+        g.n[m] = n[m]
+        g.lo[m] = 0.0
+        g.hi[m] = (2.0, 1.0, 1.0)[m]
+    r = L.Region(kw.get("faces", L.FK_ALL_FACES_ABSORBING))
+    c = L.Coeffs()
+    c.family = kw.get("family", L.FK_CELLULAR_FLOW)
+    for k, v in enumerate(kw.get("p", (1.0, 0.2, 2 * math.pi, 1e-3))):
+        c.p[k] = v
+    return g, r, c
+
+
+CASES = [
+    (dict(dim=0), 1),
+    (dict(dim=4), 1),
+    (dict(n=(2, 17)), 1),
+    (dict(dt=0.0), 1),
+    (dict(dt=-1e-3), 1),
+    (dict(dt=float("nan")), 1),
+    (dict(n_steps=0), 1),
+    (dict(prec=7), 1),
+    (dict(path=9), 1),
+    (dict(family=5), 1),
+    (dict(p=(1.0, float("inf"), 1.0, 1e-3)), 1),
+    (dict(p=(1.0, 0.2, 1.0, -1e-3)), 1),
+    (dict(q=0), 2),
+    (dict(q=9), 2),
+    (dict(faces=0x3), 2),
+    (dict(path=1), 2),             # CSR with a time-dependent drift
+    (dict(dim=3, n=(5, 5, 5)), 2),
+    (dict(dim=1, n=(33,)), 1),     # the cellular flow is two-dimensional
+]
+
+
+@pytest.mark.parametrize("kw,status", CASES)
+def test_plan_create_rejects(L, kw, status):
+    lib = L.load()
+    g, r, c = _args(L, **kw)
+    h = ctypes.c_void_p()
+    st = lib.fk_plan_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(r), ctypes.byref(c),
+                            kw.get("q", 6), kw.get("dt", 1e-3), kw.get("n_steps", 10),
+                            kw.get("prec", 0), kw.get("path", 0))
+    assert st == status
+    assert h.value is None
+
+
+def test_null_arguments(L):
+    lib = L.load()
+    g, r, c = _args(L)
+    assert lib.fk_plan_create(None, ctypes.byref(g), ctypes.byref(r), ctypes.byref(c), 6, 1e-3,
+                              10, 0, 0) == 1
+    h = ctypes.c_void_p()
+    assert lib.fk_plan_create(ctypes.byref(h), None, ctypes.byref(r), ctypes.byref(c), 6, 1e-3,
+                              10, 0, 0) == 1
+    assert lib.fk_solve(None, None, None, None, 0, None) == 1
+    assert lib.fk_march(None, 1, 0, None, None, None) == 1
+    assert lib.fk_plan_get_info(None, None) == 1
+    assert lib.fk_last_device_error(None) == 1
+    assert lib.fk_plan_destroy(None) == 0
+    a = (ctypes.c_double * 4)()
+    assert lib.fk_gauss_hermite(0, a, a) == 1
+    assert lib.fk_gauss_hermite(17, a, a) == 1
+    assert lib.fk_gauss_hermite(4, None, a) == 1
+
+
+def test_status_strings(L):
+    lib = L.load()
+    for code, name in L.STATUS.items():
+        assert lib.fk_status_string(code).decode().startswith(name)
+    assert b"unknown" in lib.fk_status_string(99)

@@ -1,0 +1,241 @@
+"""GPU parity of the matrix-free march (libfk_gb300 through the C ABI) with
+the FP64 CPU oracle, on the same seeded inputs.
+
+Tolerances (max-abs over every node): 1e-12 for the FP64 path, 1e-5 for
+the FP32 path against the FP64 oracle.  Small meshes span several CTA tiles
+and a ragged last tile; the full-size workloads are checked over the whole
+march where the oracle finishes in tens of seconds, else over a few steps
+on the whole mesh and one step on sampled nodes.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import fk_inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+NCPU = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def fk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2104_14561_gb300 as fk
+    fk.load()
+    return fk
+
+
+def _spec(fk, w):
+    return fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
+                       params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
+                       precision=w.get("precision", "fp32"), path=w.get("path", "matrix_free"))
+
+
+def _oracle_grid(oracle, w):
+    return oracle.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]))
+
+
+FAM = {"const_drift": 0, "cellular_flow": 1}
+
+
+def _oracle_march(oracle, w, n_from, n_to, u_in=None):
+    g = _oracle_grid(oracle, w)
+    return oracle.march(g, FAM[w["family"]], list(w["params"]), w["q"], w["dt"], n_from, n_to,
+                        u_in, nthreads=NCPU)
+
+
+def _gpu_solve(fk, w, u_terminal=None):
+    import torch
+    plan = fk.Plan(_spec(fk, w))
+    ut = None if u_terminal is None else torch.tensor(u_terminal, dtype=plan.dtype, device="cuda")
+    out = plan.solve(ut)
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    res = out.double().cpu().numpy()
+    plan.close()
+    return res
+
+
+def _small2d(q, precision, family="cellular_flow", n_steps=20, n=(77, 41)):
+    w = fk_inputs.workload("cellular_1025x513", n=n, q=q, n_steps=n_steps,
+                           precision=precision, params=(1.0, 0.2, 2 * math.pi, 0.02))
+    if family == "const_drift":
+        w.update(family="const_drift", params=(0.7, -0.4, 0.0, 0.3))
+    return w
+
+
+def test_gauss_hermite_matches_oracle(fk, oracle):
+    for q in range(1, 17):
+        a, w = fk.gauss_hermite(q)
+        ao, wo = oracle.gauss_hermite(q)
+        np.testing.assert_allclose(a, ao, atol=2e-14)
+        np.testing.assert_allclose(w, wo, atol=2e-15)
+
+
+def test_bm1d_drift_fp64_full_march(fk, oracle):
+    w = fk_inputs.workload("bm1d_drift")
+    got = _gpu_solve(fk, w)
+    want = _oracle_march(oracle, w, w["n_steps"], 0)
+    assert np.abs(got - want).max() <= TOL64
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_small2d_fp64_all_q(fk, oracle, q):
+    w = _small2d(q, "fp64")
+    got = _gpu_solve(fk, w)
+    want = _oracle_march(oracle, w, w["n_steps"], 0)
+    assert np.abs(got - want).max() <= TOL64
+
+
+@pytest.mark.parametrize("q", [3, 6, 8])
+def test_small2d_fp32(fk, oracle, q):
+    w = _small2d(q, "fp32", n_steps=200)
+    got = _gpu_solve(fk, w)
+    want = _oracle_march(oracle, w, w["n_steps"], 0)
+    assert np.abs(got - want).max() <= TOL32
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_small2d_const_drift(fk, oracle, precision, tol):
+    w = _small2d(4, precision, family="const_drift", n_steps=60)
+    got = _gpu_solve(fk, w)
+    want = _oracle_march(oracle, w, w["n_steps"], 0)
+    assert np.abs(got - want).max() <= tol
+
+
+@pytest.mark.parametrize("q", [1, 3, 8, 12, 16])
+def test_1d_random_field_fp64(fk, oracle, q):
+    w = fk_inputs.workload("bm1d_drift", n=(1500,), q=q, n_steps=7)
+    u0 = fk_inputs.random_field((1500,), seed=q)
+    got = _gpu_solve(fk, w, u0)
+    want = _oracle_march(oracle, w, w["n_steps"], 0, u0)
+    assert np.abs(got - want).max() <= TOL64
+
+
+def test_random_terminal_field_2d(fk, oracle):
+    w = _small2d(6, "fp64", n=(101, 67), n_steps=5)
+    u0 = fk_inputs.random_field((67, 101), seed=3)
+    got = _gpu_solve(fk, w, u0)
+    want = _oracle_march(oracle, w, w["n_steps"], 0, u0)
+    assert np.abs(got - want).max() <= TOL64
+
+
+def test_cellular_1025x513_fp32_full_march(fk):
+    """The benchmark workload itself: 2000 FP32 steps against the FP64
+    oracle's u^0 at 20k+ sampled nodes (all nodes next to the boundary
+    included), written by tests/golden/make_oracle_golden.py."""
+    import torch
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden",
+                                "cellular_1025x513_oracle_u0.npz"))
+    w = fk_inputs.workload("cellular_1025x513")
+    assert tuple(gold["n"]) == tuple(w["n"]) and int(gold["n_steps"]) == w["n_steps"]
+    plan = fk.Plan(_spec(fk, w))
+    out = plan.solve()
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    got = out.double().reshape(-1).cpu().numpy()[gold["nodes"]]
+    plan.close()
+    err = np.abs(got - gold["u0"]).max()
+    print(f"cellular_1025x513 fp32 vs fp64 oracle, 2000 steps: max-abs {err:.3e}")
+    assert err <= TOL32
+
+
+def test_cellular_1025x513_fp64_60_steps(fk, oracle):
+    w = fk_inputs.workload("cellular_1025x513", precision="fp64", n_steps=60)
+    got = _gpu_solve(fk, w)
+    want = _oracle_march(oracle, w, w["n_steps"], 0)
+    assert np.abs(got - want).max() <= TOL64
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", 2e-6)])
+def test_cellular_4097x2049_sampled_step(fk, oracle, precision, tol):
+    """One step at full size from a seeded field, checked on sampled nodes."""
+    import torch
+    w = fk_inputs.workload("cellular_4097x2049", precision=precision)
+    shape = (w["n"][1], w["n"][0])
+    u1 = fk_inputs.random_field(shape, seed=7)
+    plan = fk.Plan(_spec(fk, w))
+    n = 1234
+    ut = torch.tensor(u1, dtype=plan.dtype, device="cuda")
+    out = plan.march(n + 1, n, ut)
+    torch.cuda.synchronize()
+    nodes = fk_inputs.sample_nodes(shape, 4000, seed=11)
+    got = out.double().reshape(-1)[torch.tensor(nodes, device="cuda")].cpu().numpy()
+    g = _oracle_grid(oracle, w)
+    want = oracle.step_nodes(g, 1, list(w["params"]), w["q"], w["dt"], n, u1, nodes, nthreads=NCPU)
+    assert plan.last_device_error() == 0
+    plan.close()
+    assert np.abs(got - want).max() <= tol
+
+
+def test_cellular_4097x2049_fp64_two_steps(fk, oracle):
+    w = fk_inputs.workload("cellular_4097x2049", precision="fp64", n_steps=2)
+    got = _gpu_solve(fk, w)
+    want = _oracle_march(oracle, w, 2, 0)
+    assert np.abs(got - want).max() <= TOL64
+
+
+def test_snapshots_and_resume(fk):
+    """Snapshots equal the states reached by marching in chunks (fk_march)."""
+    import torch
+    w = _small2d(5, "fp64", n_steps=40)
+    plan = fk.Plan(_spec(fk, w))
+    snaps = torch.empty((4,) + plan.shape, dtype=plan.dtype, device="cuda")
+    u0 = plan.solve(None, snapshots=snaps, snapshot_stride=10)
+    chi = torch.tensor(fk_inputs_chi(plan.shape), dtype=plan.dtype, device="cuda")
+    u = chi
+    for m in range(4):
+        u = plan.march(40 - 10 * m, 40 - 10 * (m + 1), u)
+        assert torch.equal(u, snaps[m])
+    assert torch.equal(u, u0)
+    plan.close()
+
+
+def fk_inputs_chi(shape):
+    chi = np.zeros(shape)
+    chi[0, :] = chi[-1, :] = 1.0
+    chi[:, 0] = chi[:, -1] = 1.0
+    return chi
+
+
+@pytest.mark.parametrize("n_steps", [1, 2, 5, 6])
+def test_in_place_terminal(fk, n_steps):
+    import torch
+    w = _small2d(4, "fp64", n_steps=n_steps)
+    plan = fk.Plan(_spec(fk, w))
+    u0 = torch.tensor(fk_inputs.random_field(plan.shape, seed=1), dtype=plan.dtype, device="cuda")
+    ref = plan.solve(u0.clone())
+    buf = u0.clone()
+    plan.solve(buf, out=buf)
+    assert torch.equal(buf, ref)
+    plan.close()
+
+
+@pytest.mark.parametrize("n,q,params", [
+    ((3, 3), 3, (1.0, 0.2, 2 * math.pi, 0.01)),
+    ((4, 3), 2, (1.0, 0.2, 2 * math.pi, 0.01)),
+    ((9, 5), 8, (2.0, 0.5, 2 * math.pi, 0.5)),   # reach of many cells: halo wider than the mesh
+    ((40, 3), 6, (1.0, 0.2, 2 * math.pi, 0.001)),
+    ((3, 40), 6, (1.0, 0.2, 2 * math.pi, 0.001)),
+])
+def test_degenerate_meshes(fk, oracle, n, q, params):
+    w = fk_inputs.workload("cellular_1025x513", n=n, q=q, n_steps=9, precision="fp64",
+                           params=params, dt=0.01)
+    got = _gpu_solve(fk, w)
+    want = _oracle_march(oracle, w, 9, 0)
+    assert np.abs(got - want).max() <= TOL64
+
+
+def test_1d_minimal_and_wide_reach(fk, oracle):
+    for n, dt in ((3, 1e-3), (11, 0.5)):
+        w = fk_inputs.workload("bm1d_drift", n=(n,), n_steps=4, dt=dt)
+        got = _gpu_solve(fk, w)
+        want = _oracle_march(oracle, w, 4, 0)
+        assert np.abs(got - want).max() <= TOL64
