@@ -214,6 +214,43 @@ const char *fk_status_string(fk_status status);
  * FK_ERR_TIMEOUT (a bounded wait gave up). */
 fk_status fk_last_device_error(fk_plan *plan);
 
+/* ------------------------------------------------------------------------
+ * fk_solve_static -- the same march as fk_solve for a 2D FK_PATH_MATRIX_FREE
+ * problem, for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this exists only for such callers: applications whose own
+ * pool allocator owns all device memory and forbids libraries from calling
+ * cudaMalloc beside it, code that enqueues work while a stream is being
+ * captured into a CUDA graph (where an allocation is refused or breaks the
+ * capture), and latency-bound loops that cannot afford the device-wide
+ * synchronisation of cudaMalloc / cudaFree.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine, host or
+ * device.  Everything besides the caller's buffers (one scratch field, the
+ * coefficient tables, an error word) lives in one static device array of
+ * 16 MiB, which every GPU that loads this library holds until the process
+ * exits.
+ *   grid, coeffs, q_per_dim, dt, n_steps, prec  as for fk_plan_create, with
+ *               grid->dim = 2 (else FK_ERR_UNSUPPORTED).
+ *   u_terminal  device pointer to u^N, or NULL for chi; may equal u_out.
+ *   u_out       device pointer, receives u^0.
+ * Size limit: 256 + 4 n[0] e + 2 n[1] e + n[0] n[1] e bytes (e = 4 for FP32,
+ * 8 for FP64; each of the three tables rounded up to 256 B) must fit in
+ * 16 MiB -- about 4.1 million nodes in FP32, 2.09 million in FP64.  Larger
+ * problems get FK_ERR_INVALID_ARG before anything is enqueued.
+ * The first call on each device does a one-time set-up on that device (it
+ * looks up the device address of the static array and opts the step kernels
+ * into large shared memory); make that first call before any stream
+ * capture.  Every call on a device uses the same array and overwrites what
+ * the previous call left there: calls whose work overlaps on the GPU (two
+ * streams, two host threads) race and corrupt each other's results.  The
+ * device error word is cleared by each call but not reported; use a plan
+ * and fk_last_device_error to see range checks.
+ * ---------------------------------------------------------------------- */
+fk_status fk_solve_static(const fk_grid *grid, const fk_coeffs *coeffs,
+                          int q_per_dim, double dt, int n_steps,
+                          fk_precision prec, const void *u_terminal,
+                          void *u_out, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

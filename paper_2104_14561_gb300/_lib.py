@@ -23,7 +23,7 @@ FK_ALL_FACES_ABSORBING = 0x3F
 # every symbol include/fk.h declares
 EXPORTS = ("fk_plan_create", "fk_plan_destroy", "fk_plan_get_info", "fk_gauss_hermite",
            "fk_solve", "fk_march", "fk_solve_batched", "fk_adjoint", "fk_status_string",
-           "fk_last_device_error")
+           "fk_last_device_error", "fk_solve_static")
 
 
 class FkError(RuntimeError):
