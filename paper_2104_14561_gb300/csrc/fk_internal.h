@@ -37,7 +37,8 @@ struct Step2D {
   T* u_out;        // u^n
   T* snap;         // optional second copy of u^n (snapshot), or nullptr
   int nx, ny;
-  int tx, ty;      // output tile (interior nodes) per CTA
+  int tx, ty;      // output tile (interior nodes) per CTA: tx = 32, ty = 8 m
+  int variant;     // register-budget variant (FP32: 0 -> 4 CTAs/SM, 1 -> 3)
   int hx, hy;      // halo in cells
   int lx, ly;      // staged value tile: tx + 2 hx + 2, ty + 2 hy + 2
   int lyr;         // column pitch (records) of the column-major record tiles, odd
@@ -96,6 +97,7 @@ struct fk_plan {
   double h[3];
   double reach[3];
   int halo[3], tile[3];
+  int variant;       // register-budget variant of the 2D step kernel
   double gh_a[FK_MAXQ], gh_w[FK_MAXQ];
   // device memory owned by the plan
   void* scratch;     // one field

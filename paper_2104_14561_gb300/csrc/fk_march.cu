@@ -71,82 +71,134 @@ __device__ __forceinline__ bool locate(int k, T d, int n, int* cell, T* t) {
   return out;
 }
 
-template <typename T, int Q>
-__global__ void __launch_bounds__(FK_THREADS) k_step2d(const Step2D<T> a) {
+// Slope of Eq. (e300) from two neighbouring differences, in the FP32 path
+// with a fast reciprocal (the slope feeds an O(h) correction term, so a
+// 2-ulp quotient is far inside the 1e-5 parity budget); FP64 divides exactly.
+template <typename T>
+__device__ __forceinline__ T pchip_fast(T dl, T dr) { return pchip_scaled(dl, dr); }
+template <>
+__device__ __forceinline__ float pchip_fast<float>(float dl, float dr) {
+  const float p = dl * dr;
+  return p > 0.f ? __fdividef(2.f * p, dl + dr) : 0.f;
+}
+template <typename T>
+__device__ __forceinline__ T slope_fast(const T* u, int l, int stride, int g, int n) {
+  if (g < 0 || g >= n) return T(0);
+  const T* c = u + l * stride;
+  if (g == 0) return pchip_fast(c[stride] - c[0], c[2 * stride] - c[stride]);
+  if (g == n - 1) return pchip_fast(c[0] - c[-stride], c[-stride] - c[-2 * stride]);
+  return pchip_fast(c[0] - c[-stride], c[stride] - c[0]);
+}
+
+// MINB = CTAs of 256 threads per SM that the register budget is sized for
+// (4 -> <= 64 registers, 3 -> <= 85, 2 -> <= 128); the plan's autotuner
+// picks the variant together with the tile height.
+
+// Tiles are 32 nodes wide (one warp per tile row) and a multiple of 8 rows
+// high (ty = 8 * passes); every staging loop walks rows by warp and columns
+// by lane, so no index needs an integer division.
+template <typename T, int Q, int MINB>
+__global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lx = a.lx, ly = a.ly, lyr = a.lyr;
   V4<T>* R = reinterpret_cast<V4<T>*>(smem);
   V2<T>* S = reinterpret_cast<V2<T>*>(R + lx * lyr);
   T* U = reinterpret_cast<T*>(S + lx * lyr);
+  T* DX = U + lx * ly;
+  T* DY = DX + lx * ly;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  const int i0 = 1 + blockIdx.x * a.tx;  // first interior output node of the tile
+  const int i0 = 1 + blockIdx.x * 32;  // first interior output node of the tile
   const int k0 = 1 + blockIdx.y * a.ty;
   const int gi0 = i0 - a.hx - 1;  // global node of staged column 0
   const int gk0 = k0 - a.hy - 1;
 
-  // 1. stage u^{n+1}
-  for (int e = threadIdx.x; e < lx * ly; e += blockDim.x) {
-    const int li = e % lx, lk = e / lx;
-    const int gi = gi0 + li, gk = gk0 + lk;
-    T v = T(0);
-    if (gi >= 0 && gi < a.nx && gk >= 0 && gk < a.ny) v = a.u_in[(int64_t)gk * a.nx + gi];
-    U[e] = v;
+  // 1. stage u^{n+1} (zero outside the mesh; never read there)
+  for (int lk = warp; lk < ly; lk += FK_THREADS / 32) {
+    const int gk = gk0 + lk;
+    const bool rowin = gk >= 0 && gk < a.ny;
+    const T* src = a.u_in + (int64_t)gk * a.nx;
+    for (int li = lane; li < lx; li += 32) {
+      const int gi = gi0 + li;
+      U[lk * lx + li] = (rowin && gi >= 0 && gi < a.nx) ? src[gi] : T(0);
+    }
   }
   __syncthreads();
 
-  // 2. slopes and packed cell records, columns lc in [1, lx-3], rows lk in [1, ly-2]
-  const int ncx = lx - 3, ncy = ly - 2;
-  for (int e = threadIdx.x; e < ncx * ncy; e += blockDim.x) {
-    const int lc = 1 + e % ncx, lk = 1 + e / ncx;
-    const int gi = gi0 + lc, gk = gk0 + lk;
+  // 2. scaled PCHIP slopes h u_x, h u_y of the staged nodes 1..lx-2, 1..ly-2
+  for (int lk = 1 + warp; lk <= ly - 2; lk += FK_THREADS / 32) {
+    const int gk = gk0 + lk;
     const T* row = U + lk * lx;
-    const T u0 = row[lc], u1 = row[lc + 1];
-    const T dx0 = slope_line(row, lc, 1, gi, a.nx);
-    const T dx1 = slope_line(row, lc + 1, 1, gi + 1, a.nx);
-    const T dy0 = slope_line(U + lc, lk, lx, gk, a.ny);
-    const T dy1 = slope_line(U + lc + 1, lk, lx, gk, a.ny);
-    V4<T> r;
-    r.x = u0; r.y = u1 - u0; r.z = dx0; r.w = dx1;
-    V2<T> s;
-    s.x = dy0; s.y = dy1 - dy0;
-    R[lc * lyr + lk] = r;
-    S[lc * lyr + lk] = s;
+    for (int li = 1 + lane; li <= lx - 2; li += 32) {
+      DX[lk * lx + li] = slope_fast(row, li, 1, gi0 + li, a.nx);
+      DY[lk * lx + li] = slope_fast(U + li, lk, lx, gk, a.ny);
+    }
   }
   __syncthreads();
 
-  // 3. one output node per thread and pass
-  for (int e = threadIdx.x; e < a.tx * a.ty; e += blockDim.x) {
-    const int i = i0 + e % a.tx, k = k0 + e / a.tx;
-    if (i > a.nx - 2 || k > a.ny - 2) continue;
-    const int li = i - gi0, lk = k - gk0;
+  // 3. packed cell records (column-major, odd pitch: conflict-free)
+  for (int lk = 1 + warp; lk <= ly - 2; lk += FK_THREADS / 32) {
+    for (int lc = 1 + lane; lc <= lx - 3; lc += 32) {
+      const int o = lk * lx + lc;
+      const T u0 = U[o], u1 = U[o + 1];
+      V4<T> r;
+      r.x = u0; r.y = u1 - u0; r.z = DX[o]; r.w = DX[o + 1];
+      V2<T> s;
+      s.x = DY[o]; s.y = DY[o + 1] - DY[o];
+      R[lc * lyr + lk] = r;
+      S[lc * lyr + lk] = s;
+    }
+  }
+  __syncthreads();
+
+  // 4. one output node per thread and pass: column i0 + lane, row k0 + warp + 8 m
+  const int i = i0 + lane;
+  const int li = i - gi0;
+  const bool colok = i <= a.nx - 2;
+  T cx0 = T(0), cx1 = T(0), cx2 = T(0), cx3 = T(0);
+  if (a.family == FK_CELLULAR_FLOW && colok) {
+    const T* ct = a.col_tab + 4 * (int64_t)i;
+    cx0 = ct[0]; cx1 = ct[1]; cx2 = ct[2]; cx3 = ct[3];
+  }
+  const T nlo_x = T(-i), nhi_x = T(a.nx - 1 - i);
+  unsigned bad = 0;
+  for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
+    const int k = k0 + ty;
+    if (!colok || k > a.ny - 2) continue;
+    const int lk = k - gk0;
     const T uj = R[li * lyr + lk].x;
     T dx, dy;
     if (a.family == FK_CELLULAR_FLOW) {
-      const T* ct = a.col_tab + 4 * (int64_t)i;
       const T* rt = a.row_tab + 2 * (int64_t)k;
-      dx = a.kx * rt[0] * (a.A * ct[0] + a.e1 * ct[1]);
-      dy = a.ky * rt[1] * (a.A * ct[2] + a.e2 * ct[3]);
+      dx = a.kx * rt[0] * (a.A * cx0 + a.e1 * cx1);
+      dy = a.ky * rt[1] * (a.A * cx2 + a.e2 * cx3);
     } else {
       dx = a.cdx;
       dy = a.cdy;
     }
     // y factors of every query row, weights folded in
+    const T nlo_y = T(-k), nhi_y = T(a.ny - 1 - k);
     int rq[Q];
     T w0[Q], w1[Q], w2[Q], w3[Q];
     T exit_y = T(0);
-    unsigned bad = 0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      int c;
-      T t;
-      const bool out = locate(k, dy + a.gy[q], a.ny, &c, &t);
+      const T d = dy + a.gy[q];
+      const bool out = (d < nlo_y) || (d > nhi_y);
+      const T fl = floor(d);
+      int c = k + (int)fl;
+      T t = d - fl;
+      if (c > a.ny - 2) {
+        c = a.ny - 2;
+        t = T(1);
+      }
       int lc = c - gk0;
-      if (lc < 1 || lc > ly - 3) {
+      if ((unsigned)(lc - 1) > (unsigned)(ly - 4)) {
         bad |= out ? 0u : 1u;
         lc = lk;
       }
       const T wq = out ? T(0) : a.w[q];
-      exit_y += out ? a.w[q] : T(0);
+      exit_y += a.w[q] - wq;
       rq[q] = out ? lk : lc;
       const T t2 = t * t, omt = T(1) - t;
       w0[q] = wq;
@@ -158,15 +210,20 @@ __global__ void __launch_bounds__(FK_THREADS) k_step2d(const Step2D<T> a) {
     T acc = T(0);
 #pragma unroll 1
     for (int p = 0; p < Q; ++p) {
-      int c;
-      T t;
-      const bool out = locate(i, dx + a.gx[p], a.nx, &c, &t);
-      if (out) {
+      const T d = dx + a.gx[p];
+      if ((d < nlo_x) || (d > nhi_x)) {
         acc += a.w[p] * om;
         continue;
       }
+      const T fl = floor(d);
+      int c = i + (int)fl;
+      T t = d - fl;
+      if (c > a.nx - 2) {
+        c = a.nx - 2;
+        t = T(1);
+      }
       int lc = c - gi0;
-      if (lc < 1 || lc > lx - 3) {
+      if ((unsigned)(lc - 1) > (unsigned)(lx - 4)) {
         bad |= 1u;
         lc = li;
       }
@@ -185,16 +242,18 @@ __global__ void __launch_bounds__(FK_THREADS) k_step2d(const Step2D<T> a) {
         const T a1 = (r1.x - uj) + h01 * r1.y + h10 * r1.z + h11 * r1.w;
         const T b0 = s0.x + h01 * s0.y;
         const T b1 = s1.x + h01 * s1.y;
-        accp += w0[q] * a0 + w1[q] * (a1 - a0) + w2[q] * b0 + w3[q] * b1;
+        accp += w0[q] * a0;
+        accp += w1[q] * (a1 - a0);
+        accp += w2[q] * b0;
+        accp += w3[q] * b1;
       }
       acc += a.w[p] * accp;
     }
-    if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
     const T un = uj + acc;
     const int64_t nx = a.nx;
     a.u_out[(int64_t)k * nx + i] = un;
     if (a.snap) a.snap[(int64_t)k * nx + i] = un;
-    // 4. boundary nodes adjacent to this interior node hold 1 (Eq. (e3))
+    // 5. boundary nodes adjacent to this interior node hold 1 (Eq. (e3))
     const bool L = (i == 1), Rt = (i == a.nx - 2), B = (k == 1), Tp = (k == a.ny - 2);
     if (L | Rt | B | Tp) {
       // On a mesh with 3 nodes along an axis the single interior line is
@@ -214,6 +273,7 @@ __global__ void __launch_bounds__(FK_THREADS) k_step2d(const Step2D<T> a) {
       if (Rt & Tp) one(top + nx - 1);
     }
   }
+  if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
 
 // 1D step: same structure with a record {u_c, u_{c+1}-u_c, h u'_c, h u'_{c+1}}
@@ -304,17 +364,31 @@ __global__ void k_copy16(uint4* dst, const uint4* src, int64_t n16) {
     dst[j] = src[j];
 }
 
-template <typename T, int Q>
+template <typename T, int Q, int MINB>
 cudaError_t launch2d_q(const Step2D<T>& a, cudaStream_t s) {
   const size_t smem = fk_step2d_smem(a.lx, a.ly, a.lyr, (int)sizeof(T));
-  dim3 grid((a.nx - 2 + a.tx - 1) / a.tx, (a.ny - 2 + a.ty - 1) / a.ty);
-  k_step2d<T, Q><<<grid, FK_THREADS, smem, s>>>(a);
+  dim3 grid((a.nx - 2 + 31) / 32, (a.ny - 2 + a.ty - 1) / a.ty);
+  k_step2d<T, Q, MINB><<<grid, FK_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int Q>
+template <typename T, int Q, int MINB>
 cudaError_t attr2d_q() {
-  return cudaFuncSetAttribute(k_step2d<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return cudaFuncSetAttribute(k_step2d<T, Q, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              227 * 1024);
+}
+
+// Register-budget variants per precision: FP32 {4, 3} CTAs/SM, FP64 {2}.
+template <typename T, int Q>
+cudaError_t launch2d_var(const Step2D<T>& a, cudaStream_t s) {
+  if (sizeof(T) == 8) return launch2d_q<T, Q, 2>(a, s);
+  return a.variant == 1 ? launch2d_q<T, Q, 3>(a, s) : launch2d_q<T, Q, 4>(a, s);
+}
+template <typename T, int Q>
+cudaError_t attr2d_var() {
+  if (sizeof(T) == 8) return attr2d_q<T, Q, 2>();
+  cudaError_t e = attr2d_q<T, Q, 4>();
+  return e != cudaSuccess ? e : attr2d_q<T, Q, 3>();
 }
 
 template <typename T, int Q>
@@ -333,7 +407,7 @@ cudaError_t attr1d_q() {
 }  // namespace
 
 size_t fk_step2d_smem(int lx, int ly, int lyr, int elem) {
-  return (size_t)lx * lyr * (6 * elem) + (size_t)lx * ly * elem;
+  return (size_t)lx * lyr * (6 * elem) + (size_t)3 * lx * ly * elem;
 }
 
 size_t fk_step1d_smem(int lx, int elem) { return (size_t)lx * (4 * elem) + (size_t)lx * elem; }
@@ -341,14 +415,14 @@ size_t fk_step1d_smem(int lx, int elem) { return (size_t)lx * (4 * elem) + (size
 template <typename T>
 cudaError_t fk_launch_step2d(const Step2D<T>& a, int q, cudaStream_t s) {
   switch (q) {
-    case 1: return launch2d_q<T, 1>(a, s);
-    case 2: return launch2d_q<T, 2>(a, s);
-    case 3: return launch2d_q<T, 3>(a, s);
-    case 4: return launch2d_q<T, 4>(a, s);
-    case 5: return launch2d_q<T, 5>(a, s);
-    case 6: return launch2d_q<T, 6>(a, s);
-    case 7: return launch2d_q<T, 7>(a, s);
-    case 8: return launch2d_q<T, 8>(a, s);
+    case 1: return launch2d_var<T, 1>(a, s);
+    case 2: return launch2d_var<T, 2>(a, s);
+    case 3: return launch2d_var<T, 3>(a, s);
+    case 4: return launch2d_var<T, 4>(a, s);
+    case 5: return launch2d_var<T, 5>(a, s);
+    case 6: return launch2d_var<T, 6>(a, s);
+    case 7: return launch2d_var<T, 7>(a, s);
+    case 8: return launch2d_var<T, 8>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -380,7 +454,7 @@ cudaError_t fk_prepare_step_kernels(int dim, int q, int elem) {
   if (dim == 2) {
     switch (q) {
 #define FK_CASE(Q) \
-  case Q: return elem == 4 ? attr2d_q<float, Q>() : attr2d_q<double, Q>();
+  case Q: return elem == 4 ? attr2d_var<float, Q>() : attr2d_var<double, Q>();
       FK_CASE(1) FK_CASE(2) FK_CASE(3) FK_CASE(4) FK_CASE(5) FK_CASE(6) FK_CASE(7) FK_CASE(8)
 #undef FK_CASE
       default: return cudaErrorInvalidValue;

@@ -6,7 +6,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <stdio.h>
+
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "fk_internal.h"
 
@@ -179,6 +183,7 @@ void fill2d(const fk_plan* p, int n, Step2D<T>* a) {
   a->ny = p->grid.n[1];
   a->tx = p->tile[0];
   a->ty = p->tile[1];
+  a->variant = p->variant;
   a->hx = p->halo[0];
   a->hy = p->halo[1];
   a->lx = a->tx + 2 * a->hx + 2;
@@ -225,6 +230,21 @@ void fill1d(const fk_plan* p, Step1D<T>* a) {
   a->err = p->d_err;
 }
 
+// Candidate tiles of the 2D step kernel: 32 columns x ty rows, ty = 8 m,
+// times the FP32 register-budget variants.  The first entry that fits is
+// the default when no timing is done.
+struct TileCand {
+  int ty, variant;
+};
+const TileCand kCands[] = {{16, 0}, {8, 0}, {24, 0}, {32, 0}, {40, 0}, {48, 0}, {64, 0},
+                           {16, 1}, {8, 1},  {24, 1}, {32, 1}, {48, 1}};
+
+bool cand_fits(const fk_plan* p, const TileCand& c, int dev_smem) {
+  if (p->elem == 8 && c.variant != 0) return false;
+  const int lx = 32 + 2 * p->halo[0] + 2, ly = c.ty + 2 * p->halo[1] + 2;
+  return fk_step2d_smem(lx, ly, ly | 1, p->elem) <= (size_t)dev_smem;
+}
+
 // Choose the output tile and check the shared-memory budget.
 fk_status choose_tiles(fk_plan* p) {
   int dev_smem = 0;
@@ -236,28 +256,98 @@ fk_status choose_tiles(fk_plan* p) {
     if (fk_step1d_smem(lx, p->elem) > (size_t)dev_smem) return FK_ERR_UNSUPPORTED;
     return FK_OK;
   }
-  // 2D: 32 x 16 output nodes per CTA (two per thread); grow the tile when the
-  // halo dominates, shrink it when the staged tile would not fit.
-  static const int cand[][2] = {{32, 16}, {64, 32}, {64, 16}, {32, 32}, {32, 8}, {32, 4}};
-  int best = -1;
-  double best_cost = 1e300;
-  for (int c = 0; c < 6; ++c) {
-    const int tx = cand[c][0], ty = cand[c][1];
-    const int lx = tx + 2 * p->halo[0] + 2, ly = ty + 2 * p->halo[1] + 2;
-    const size_t smem = fk_step2d_smem(lx, ly, ly | 1, p->elem);
-    if (smem > (size_t)dev_smem) continue;
-    // staged records per output node, penalised when few CTAs fit per SM
-    const int per_sm = (int)((228 * 1024) / (smem + 1024));
-    const double cost = (double)lx * ly / (tx * ty) + (per_sm < 2 ? 1.0 : 0.0) + (c == 0 ? -0.05 : 0.0);
-    if (cost < best_cost) {
-      best_cost = cost;
-      best = c;
+  for (const TileCand& c : kCands) {
+    if (cand_fits(p, c, dev_smem)) {
+      p->tile[0] = 32;
+      p->tile[1] = c.ty;
+      p->variant = c.variant;
+      return FK_OK;
     }
   }
-  if (best < 0) return FK_ERR_UNSUPPORTED;
-  p->tile[0] = cand[best][0];
-  p->tile[1] = cand[best][1];
-  return FK_OK;
+  return FK_ERR_UNSUPPORTED;
+}
+
+// Autotuner: time one step of every fitting candidate on this device (from
+// the terminal indicator) and keep the fastest.  Results are cached per
+// problem shape for the life of the process.
+struct TuneEntry {
+  int dev, nx, ny, q, elem, hx, hy, family;
+  int ty, variant;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune_cache;
+
+fk_status autotune(fk_plan* p) {
+  if (p->grid.dim != 2 || p->path != FK_PATH_MATRIX_FREE) return FK_OK;
+  if (p->J_int < 16384) return FK_OK;  // small meshes: launch-bound, keep the default
+  TuneEntry key = {p->device, p->grid.n[0], p->grid.n[1], p->q, p->elem, p->halo[0], p->halo[1],
+                   p->coeffs.family, 0, 0};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const TuneEntry& t : g_tune_cache) {
+      if (t.dev == key.dev && t.nx == key.nx && t.ny == key.ny && t.q == key.q &&
+          t.elem == key.elem && t.hx == key.hx && t.hy == key.hy && t.family == key.family) {
+        p->tile[1] = t.ty;
+        p->variant = t.variant;
+        return FK_OK;
+      }
+    }
+  }
+  int dev_smem = 0;
+  if (cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) !=
+      cudaSuccess)
+    return FK_ERR_CUDA;
+  void* tmp = nullptr;
+  if (cudaMalloc(&tmp, (size_t)(p->J * p->elem)) != cudaSuccess) {
+    cudaGetLastError();
+    return FK_OK;  // keep the default tile
+  }
+  cudaStream_t s = p->cap_stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fk_status st = cuda_status(fk_launch_fill_chi(p->scratch, 2, p->grid.n[0], p->grid.n[1], p->elem, s));
+  const bool log = getenv("FK_TUNE_LOG") != nullptr;
+  float best = 1e30f;
+  int best_ty = p->tile[1], best_var = p->variant;
+  for (const TileCand& c : kCands) {
+    if (st != FK_OK) break;
+    if (!cand_fits(p, c, dev_smem)) continue;
+    p->tile[1] = c.ty;
+    p->variant = c.variant;
+    st = fk_enqueue_step(p, p->n_steps - 1, p->scratch, tmp, nullptr, s);  // warm-up
+    if (st != FK_OK) break;
+    cudaEventRecord(e0, s);
+    const int reps = 4;
+    for (int r = 0; r < reps && st == FK_OK; ++r)
+      st = fk_enqueue_step(p, p->n_steps - 1, p->scratch, tmp, nullptr, s);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) st = FK_ERR_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (log) fprintf(stderr, "fk autotune %dx%d q=%d elem=%d: ty=%d variant=%d  %.2f us\n",
+                     p->grid.n[0], p->grid.n[1], p->q, p->elem, c.ty, c.variant, ms * 1e3f);
+    if (ms < best) {
+      best = ms;
+      best_ty = c.ty;
+      best_var = c.variant;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  p->tile[1] = best_ty;
+  p->variant = best_var;
+  cudaMemset(p->d_err, 0, sizeof(unsigned));
+  if (st == FK_OK) {
+    key.ty = best_ty;
+    key.variant = best_var;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.push_back(key);
+  }
+  return st;
 }
 
 }  // namespace
@@ -453,6 +543,7 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   if (st == FK_OK) st = fk_dev_alloc(p, &p->scratch, (size_t)(p->J * p->elem));
   if (st == FK_OK) st = (prec == FK_FP32) ? upload_tables<float>(p) : upload_tables<double>(p);
   if (st == FK_OK) st = cuda_status(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  if (st == FK_OK) st = autotune(p);
   if (st == FK_OK && path == FK_PATH_CSR) {
     st = fk_csr_assemble(p, p->cap_stream);
     if (st == FK_OK) st = cuda_status(cudaStreamSynchronize(p->cap_stream));
