@@ -41,6 +41,28 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FLOP_PER_UPDATE = 26                # see the design doc: 13 multiply-adds per query
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 PROFILE_JSON = os.path.join(ROOT, "profiles", "k_step2d_cellular_1025x513.json")
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s, else the fallback."""
+    try:
+        v = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        return v, "measured"
+    except (OSError, ValueError, KeyError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def csr_bytes_per_step(w, nnz: int) -> float:
+    """Algorithmic HBM bytes of one CSR step: the matrix stream (column index
+    + value per stored entry), row offsets, exit constants, the stacked
+    vector [u; h u_x; h u_y] written by the slope pass and read once, u^{n+1}
+    read and u^n written."""
+    J = 1
+    for n in w["n"]:
+        J *= n
+    e = 4 if w["precision"] == "fp32" else 8
+    return nnz * (4 + e) + 8.0 * (J + 1) + e * J * (1 + 3 + 3 + 1 + 1)
 
 
 def parse():
@@ -285,9 +307,23 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         return
     info = plan.info()
     launch_ms = ms_step / w["n_steps"]  # graph of back-to-back step kernels
-    flops_launch = FLOP_PER_UPDATE * units / w["n_steps"]
-    peak_flops = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6
-    achieved = flops_launch / (launch_ms * 1e-3)
+    if w["path"] == "csr":
+        peak, peak_kind = hbm_peak()
+        bytes_step = csr_bytes_per_step(w, info["csr_nnz"])
+        achieved = bytes_step / (launch_ms * 1e-3) / 1e9
+        roofline = {"kernel": "k_csr_slopes + k_csr_spmv (one time step)", "bound": "hbm",
+                    "achieved": achieved, "peak": peak, "peak_source": peak_kind,
+                    "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                    "bytes_per_launch": bytes_step, "launch_ms": launch_ms,
+                    "csr_nnz": info["csr_nnz"]}
+    else:
+        flops_launch = FLOP_PER_UPDATE * units / w["n_steps"]
+        peak_flops = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6
+        achieved = flops_launch / (launch_ms * 1e-3)
+        roofline = {"kernel": "k_step2d", "bound": "alu", "achieved": achieved / 1e12,
+                    "peak": peak_flops / 1e12, "unit": "TFLOP/s", "frac": achieved / peak_flops,
+                    "traffic": profile_traffic(), "flop_per_launch": flops_launch,
+                    "launch_ms": launch_ms}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
@@ -300,14 +336,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                          "stays L2-resident across the 2000 time steps of one march",
                    "parallelism": f"{world} independent instances (one per GPU)"},
         "hbm_gbs_algorithmic": hbm_bytes_per_solve(w) * world / (ms_step_max * 1e-3) / 1e9,
-        "roofline": {"kernel": "k_step2d", "bound": "alu", "achieved": achieved / 1e12,
-                     "peak": peak_flops / 1e12, "unit": "TFLOP/s", "frac": achieved / peak_flops,
-                     "traffic": profile_traffic(),
-                     "flop_per_launch": flops_launch,
-                     "launch_ms": launch_ms},
+        "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,
                 "d2h_bytes_per_step": field_bytes},
-        "gpu_launches": args.steps * (w["n_steps"] + 1),
+        "gpu_launches": args.steps * ((2 if w["path"] == "csr" else 1) * w["n_steps"] + 1),
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }

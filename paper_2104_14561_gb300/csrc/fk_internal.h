@@ -114,7 +114,7 @@ struct fk_plan {
   int g_stride;
   // CSR path (fk_csr.cu)
   int64_t csr_nnz;
-  int* csr_rowptr;   // J + 1
+  int64_t* csr_rowptr;  // J + 1 row offsets, multiples of 4
   int* csr_col;      // nnz, column in the stacked vector [u; Dx; Dy]
   void* csr_val;     // nnz
   void* csr_c;       // J: exit weight constant per row

@@ -547,6 +547,9 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   if (st == FK_OK && path == FK_PATH_CSR) {
     st = fk_csr_assemble(p, p->cap_stream);
     if (st == FK_OK) st = cuda_status(cudaStreamSynchronize(p->cap_stream));
+    unsigned h = 0;
+    if (st == FK_OK) st = cuda_status(cudaMemcpy(&h, p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st == FK_OK && h) st = FK_ERR_DEVICE;
   }
   if (st != FK_OK) {
     fk_plan_destroy(p);
