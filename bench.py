@@ -33,6 +33,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import fk_inputs  # noqa: E402
 
 METRIC = "node-quadrature updates/s & HBM GB/s (2D, 36-pt GH, FP32/FP64); adjoint/forward"
@@ -220,6 +222,80 @@ def profile_traffic():
         return None
 
 
+# ----------------------------------------------------------- batched -----
+def run_batched(args, rank: int, world: int, local_rank: int):
+    """The 64-instance sweep: one batched persistent march of all instances
+    per benchmark step, with the plain march (one fk_solve per instance on
+    the same stream) timed beside it."""
+    import torch
+    import paper_2104_14561_gb300 as fk
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    ws = fk_inputs.batched_instances()
+    plans = [fk.Plan(fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
+                                 params=w["params"], q=w["q"], dt=w["dt"],
+                                 n_steps=w["n_steps"], precision=w["precision"]))
+             for w in ws]
+    outs = [p.empty() for p in plans]
+    units = sum(units_per_solve(w) for w in ws)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+        stream.synchronize()
+        ms = []
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        return sum(ms) / len(ms)
+
+    def batched():
+        fk.solve_batched(plans, None, outs, stream=stream)
+
+    def plain():
+        for p, o in zip(plans, outs):
+            p.solve(None, o, stream=stream)
+
+    clk = ClockSampler(local_rank)
+    clk.start()
+    ms_b = timed(batched)
+    clocks = clk.stop()
+    if plans[0].last_device_error() != 0:
+        raise RuntimeError("device-side error in the batched march")
+    ms_p = timed(plain)
+    grid = None
+    nodes = sum(int(np.prod(w["n"])) for w in ws)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": units / (ms_b * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "batched_64", "instances": len(ws), "nodes": nodes,
+                   "q_per_dim": 6, "time_steps": 1000, "dt": 1e-3,
+                   "l2": "flushed (512 MB write) before every timed march"},
+        "plain_march": {"value": units / (ms_p * 1e-3), "ms_per_step": ms_p,
+                        "how": "64 fk_solve calls (one CUDA graph each) on one stream"},
+        "hbm_gbs_algorithmic": 24.0 * nodes * 1000 * 2 / (ms_b * 1e-3) / 1e9,
+        "gpu_launches": args.steps * 1,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+
+
 # --------------------------------------------------------------- ours ----
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
@@ -366,7 +442,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "batched_64":
+            run_batched(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

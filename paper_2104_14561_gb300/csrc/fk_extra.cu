@@ -1,13 +1,7 @@
-// Batched persistent march and adjoint: not built yet.
+// Adjoint: not built yet.
 #include "fk_internal.h"
 
 extern "C" {
-
-fk_status fk_solve_batched(int n, fk_plan* const* plans, const void* const* u_terminal,
-                           void* const* u_out, cudaStream_t stream) {
-  (void)n; (void)plans; (void)u_terminal; (void)u_out; (void)stream;
-  return FK_ERR_UNSUPPORTED;
-}
 
 fk_status fk_adjoint(fk_plan* plan, const void* u_terminal, const double* cotangent_u0,
                      double* dtheta, void* du_terminal, int checkpoint_every,

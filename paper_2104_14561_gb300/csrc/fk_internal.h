@@ -119,7 +119,13 @@ struct fk_plan {
   void* csr_val;     // nnz
   void* csr_c;       // J: exit weight constant per row
   void* stack;       // 3 J: [u; Dx; Dy] for the CSR product
+  // batched persistent march (fk_batched.cu)
+  void* batch_rec;   // 6 J values: slope records of this instance
+  void* batch_work;  // BatchWork of a batch whose first plan is this one
+  int batch_grid;    // CTAs of the last batched launch
 };
+
+void fk_batch_release(fk_plan* p);
 
 // Step launchers that fill the argument struct from the plan (fk_plan.cu).
 fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void* snap,
