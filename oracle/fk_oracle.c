@@ -393,3 +393,244 @@ int fko_has_openmp(void) {
   return 0;
 #endif
 }
+
+/* ------------------------------------------------------------- adjoint --- */
+
+/*
+ * Reverse-mode derivative of the march above, for the scalar
+ * L = sum_j g_j u^0_j (g = cot_u0).  Each step S_n maps u^{n+1} to u^n
+ * through the slopes F (Eq. (e300)), the interpolant at the shifted points
+ * (Eq. (Lag11), (e31)) and the quadrature (Eq. (e304)); its transpose is
+ * applied query by query:
+ *   lambda^{n+1} = (dS_n/du^{n+1})^T lambda^n,
+ *   dL/dtheta   += lambda^n . dS_n/dtheta,
+ * with dS_n/dtheta through the shifted points z = x + b dt + sigma
+ * sqrt(2 dt) a (the exit set changes only on a null set and contributes
+ * nothing), and dS_n/du through the value/derivative basis and the chain
+ * rule of the slope rule (derivative of the active branch; 0 on the zero
+ * branch, also when a difference is exactly 0).  Boundary rows (u = 1 for
+ * n < N) depend on nothing.  theta = p[0..3] of the family: for the
+ * cellular flow (A, eps, omega, D), for constant drift (b_1, b_2, b_3, s).
+ * All u^n are kept in memory (test sizes only).  Single-threaded.
+ */
+
+/* d b / d theta_k (dim entries per k, k < 4) and d sigma / d theta_k */
+static void drift_derivs(int family, const double *p, int dim, double t,
+                         const double *x, double db[4][FKO_MAXDIM], double ds[4]) {
+  for (int k = 0; k < 4; ++k) {
+    ds[k] = 0.0;
+    for (int m = 0; m < FKO_MAXDIM; ++m) db[k][m] = 0.0;
+  }
+  if (family == FKO_CONST_DRIFT) {
+    for (int m = 0; m < dim; ++m) db[m][m] = 1.0;
+    ds[3] = 1.0;
+    return;
+  }
+  {
+    double eps = p[1], omega = p[2], D = p[3];
+    double f = sin(omega * t), df = t * cos(omega * t); /* d f / d omega */
+    double X = x[0], Y = x[1];
+    double cy = cos(FKO_PI * Y), sy = sin(FKO_PI * Y);
+    /* b_x = -pi cos(pi y) (A sin(pi x) + eps f sin(2 pi x)) */
+    /* b_y =  pi sin(pi y) (A cos(pi x) + 2 eps f cos(2 pi x)) */
+    db[0][0] = -FKO_PI * cy * sin(FKO_PI * X);
+    db[0][1] = FKO_PI * sy * cos(FKO_PI * X);
+    db[1][0] = -FKO_PI * cy * f * sin(2.0 * FKO_PI * X);
+    db[1][1] = FKO_PI * sy * 2.0 * f * cos(2.0 * FKO_PI * X);
+    db[2][0] = -FKO_PI * cy * eps * df * sin(2.0 * FKO_PI * X);
+    db[2][1] = FKO_PI * sy * 2.0 * eps * df * cos(2.0 * FKO_PI * X);
+    ds[3] = 1.0 / sqrt(2.0 * D); /* sigma = sqrt(2 D) */
+  }
+}
+
+/* derivatives of the four cell basis functions with respect to s */
+static void hermite_basis_ds(double s, double h, double *dphi0, double *dphi1,
+                             double *dpsi0, double *dpsi1) {
+  double h3 = h * h * h, h2 = h * h;
+  *dphi0 = (-6.0 * h * s + 6.0 * s * s) / h3;
+  *dphi1 = (6.0 * h * s - 6.0 * s * s) / h3;
+  *dpsi0 = (s - h) * (3.0 * s - h) / h2;
+  *dpsi1 = s * (3.0 * s - 2.0 * h) / h2;
+}
+
+/* partial derivatives of the PCHIP rule 2/(1/dl + 1/dr) (0 off its branch) */
+static void pchip_rule_grad(double dl, double dr, double *gl, double *gr) {
+  if (dl * dr <= 0.0) {
+    *gl = 0.0;
+    *gr = 0.0;
+    return;
+  }
+  double s = dl + dr;
+  *gl = 2.0 * dr * dr / (s * s);
+  *gr = 2.0 * dl * dl / (s * s);
+}
+
+/* lam_u[i] += sum_j mu[j] d(slope_j)/d u_i along axis m (transpose of F) */
+static void slopes_axis_transpose(const fko_grid *g, int m, const double *u,
+                                  const double *mu, double *lam_u) {
+  int64_t J = grid_size(g);
+  int64_t st = grid_stride(g, m);
+  int nm = g->n[m];
+  double h = grid_h(g, m);
+  int idx[FKO_MAXDIM];
+  for (int64_t j = 0; j < J; ++j) {
+    if (mu[j] == 0.0) continue;
+    grid_unflatten(g, j, idx);
+    int i = idx[m];
+    int64_t base = j - (int64_t)i * st;
+    /* the two differences used at node i, as (upper, lower) node pairs */
+    int l1, l0, r1, r0;
+    if (i == 0) {
+      l1 = 1; l0 = 0; r1 = 2; r0 = 1;
+    } else if (i == nm - 1) {
+      l1 = nm - 1; l0 = nm - 2; r1 = nm - 2; r0 = nm - 3;
+    } else {
+      l1 = i; l0 = i - 1; r1 = i + 1; r0 = i;
+    }
+    double dl = (u[base + (int64_t)l1 * st] - u[base + (int64_t)l0 * st]) / h;
+    double dr = (u[base + (int64_t)r1 * st] - u[base + (int64_t)r0 * st]) / h;
+    double gl, gr;
+    pchip_rule_grad(dl, dr, &gl, &gr);
+    lam_u[base + (int64_t)l1 * st] += mu[j] * gl / h;
+    lam_u[base + (int64_t)l0 * st] -= mu[j] * gl / h;
+    lam_u[base + (int64_t)r1 * st] += mu[j] * gr / h;
+    lam_u[base + (int64_t)r0 * st] -= mu[j] * gr / h;
+  }
+}
+
+int fko_adjoint(const fko_grid *g, int family, const double *p, int nq,
+                const double *a, const double *w, double dt, int n_steps,
+                const double *u_terminal, const double *cot_u0,
+                double *dtheta, double *du_terminal) {
+  if (grid_check(g) || family_check(family, g->dim, p)) return 1;
+  if (nq < 1 || !(dt > 0.0) || n_steps < 1) return 1;
+  int d = g->dim;
+  int64_t J = grid_size(g);
+  double *us = (double *)malloc(sizeof(double) * J * (size_t)(n_steps + 1));
+  double *du = (double *)malloc(sizeof(double) * J * d);
+  double *lam = (double *)malloc(sizeof(double) * J);
+  double *lam_next = (double *)malloc(sizeof(double) * J);
+  double *mu_u = (double *)malloc(sizeof(double) * J);
+  double *mu_d = (double *)malloc(sizeof(double) * J * d);
+  if (!us || !du || !lam || !lam_next || !mu_u || !mu_d) {
+    free(us); free(du); free(lam); free(lam_next); free(mu_u); free(mu_d);
+    return 2;
+  }
+  /* forward: us + n J holds u^n */
+  memcpy(us + (int64_t)n_steps * J, u_terminal, sizeof(double) * J);
+  for (int n = n_steps - 1; n >= 0; --n)
+    fko_march(g, family, p, nq, a, w, dt, n + 1, n, us + (int64_t)(n + 1) * J,
+              us + (int64_t)n * J, 1, 1);
+  for (int k = 0; k < 4; ++k) dtheta[k] = 0.0;
+  memcpy(lam, cot_u0, sizeof(double) * J);
+  double sq = sqrt(2.0 * dt);
+  int64_t nqd = 1;
+  for (int m = 0; m < d; ++m) nqd *= nq;
+  for (int n = 0; n < n_steps; ++n) {
+    const double *u = us + (int64_t)(n + 1) * J; /* input of step n */
+    double tn = (double)n * dt;
+    fko_slopes(g, u, du);
+    memset(mu_u, 0, sizeof(double) * J);
+    memset(mu_d, 0, sizeof(double) * J * d);
+    for (int64_t j = 0; j < J; ++j) {
+      int idx[FKO_MAXDIM];
+      grid_unflatten(g, j, idx);
+      if (grid_is_boundary(g, idx) || lam[j] == 0.0) continue;
+      double x[FKO_MAXDIM], b[FKO_MAXDIM], sig[FKO_MAXDIM * FKO_MAXDIM];
+      double db[4][FKO_MAXDIM], ds[4];
+      for (int m = 0; m < d; ++m) x[m] = grid_x(g, m, idx[m]);
+      fko_coefficients(family, p, d, tn, x, b, sig);
+      drift_derivs(family, p, d, tn, x, db, ds);
+      for (int64_t qq = 0; qq < nqd; ++qq) {
+        int q[FKO_MAXDIM];
+        int64_t r = qq;
+        double wq = 1.0;
+        for (int m = 0; m < d; ++m) {
+          q[m] = (int)(r % nq);
+          r /= nq;
+          wq *= w[q[m]];
+        }
+        double z[FKO_MAXDIM];
+        int outside = 0;
+        for (int m = 0; m < d; ++m) {
+          double noise = 0.0;
+          for (int k = 0; k < d; ++k) noise += sig[m * d + k] * a[q[k]];
+          z[m] = x[m] + b[m] * dt + noise * sq;
+          if (z[m] < g->lo[m] || z[m] > g->hi[m]) outside = 1;
+        }
+        if (outside) continue; /* the exit value 1 depends on nothing */
+        double W = lam[j] * wq;
+        int c[FKO_MAXDIM];
+        double phi[FKO_MAXDIM][2], psi[FKO_MAXDIM][2];
+        double dphi[FKO_MAXDIM][2], dpsi[FKO_MAXDIM][2];
+        for (int m = 0; m < d; ++m) {
+          double h = grid_h(g, m);
+          int cm = (int)floor((z[m] - g->lo[m]) / h);
+          if (cm < 0) cm = 0;
+          if (cm > g->n[m] - 2) cm = g->n[m] - 2;
+          c[m] = cm;
+          double s = z[m] - grid_x(g, m, cm);
+          hermite_basis(s, h, &phi[m][0], &phi[m][1], &psi[m][0], &psi[m][1]);
+          hermite_basis_ds(s, h, &dphi[m][0], &dphi[m][1], &dpsi[m][0], &dpsi[m][1]);
+        }
+        double grad[FKO_MAXDIM] = {0.0, 0.0, 0.0}; /* d Itilde / d z_m */
+        for (int corner = 0; corner < (1 << d); ++corner) {
+          int64_t node = 0;
+          for (int m = 0; m < d; ++m)
+            node += (int64_t)(c[m] + ((corner >> m) & 1)) * grid_stride(g, m);
+          /* value term */
+          double wv = 1.0;
+          for (int m = 0; m < d; ++m) wv *= phi[m][(corner >> m) & 1];
+          mu_u[node] += W * wv;
+          for (int k = 0; k < d; ++k) {
+            double gv = 1.0;
+            for (int m = 0; m < d; ++m) {
+              int bit = (corner >> m) & 1;
+              gv *= (m == k) ? dphi[m][bit] : phi[m][bit];
+            }
+            grad[k] += gv * u[node];
+          }
+          /* derivative terms */
+          for (int m = 0; m < d; ++m) {
+            double wd = 1.0;
+            for (int k = 0; k < d; ++k) {
+              int bit = (corner >> k) & 1;
+              wd *= (k == m) ? psi[k][bit] : phi[k][bit];
+            }
+            mu_d[(int64_t)m * J + node] += W * wd;
+            for (int kk = 0; kk < d; ++kk) {
+              double gd = 1.0;
+              for (int k = 0; k < d; ++k) {
+                int bit = (corner >> k) & 1;
+                double f;
+                if (k == m)
+                  f = (k == kk) ? dpsi[k][bit] : psi[k][bit];
+                else
+                  f = (k == kk) ? dphi[k][bit] : phi[k][bit];
+                gd *= f;
+              }
+              grad[kk] += gd * du[(int64_t)m * J + node];
+            }
+          }
+        }
+        /* dz_m / dtheta_k = db_k,m dt + dsigma_k sqrt(2 dt) (sigma-scaled noise) */
+        for (int k = 0; k < 4; ++k) {
+          double dz = 0.0;
+          for (int m = 0; m < d; ++m) {
+            double noise_m = 0.0;
+            for (int kk = 0; kk < d; ++kk) noise_m += (kk == m ? 1.0 : 0.0) * a[q[kk]];
+            dz += grad[m] * (db[k][m] * dt + ds[k] * noise_m * sq);
+          }
+          dtheta[k] += W * dz;
+        }
+      }
+    }
+    /* lambda^{n+1} = mu_u + F^T mu_d */
+    memcpy(lam_next, mu_u, sizeof(double) * J);
+    for (int m = 0; m < d; ++m) slopes_axis_transpose(g, m, u, mu_d + (int64_t)m * J, lam_next);
+    double *t = lam; lam = lam_next; lam_next = t;
+  }
+  memcpy(du_terminal, lam, sizeof(double) * J);
+  free(us); free(du); free(lam); free(lam_next); free(mu_u); free(mu_d);
+  return 0;
+}

@@ -89,6 +89,8 @@ def _load():
         lib.fko_coefficients.argtypes = [ctypes.c_int, dp, ctypes.c_int,
                                          ctypes.c_double, dp, dp, dp]
         lib.fko_coefficients.restype = None
+        lib.fko_adjoint.argtypes = [gp, ctypes.c_int, dp, ctypes.c_int, dp, dp, ctypes.c_double,
+                                    ctypes.c_int, dp, dp, dp, dp]
         _lib = lib
     return _lib
 
@@ -247,6 +249,26 @@ def step_nodes(grid: Grid, family: int, params, q: int, dt: float, n: int,
     if rc:
         raise ValueError(f"fko_step_nodes failed ({rc})")
     return out
+
+
+def adjoint(grid: Grid, family: int, params, q: int, dt: float, n_steps: int,
+            cot_u0: np.ndarray, u_terminal: np.ndarray | None = None):
+    """Reverse-mode derivative of L = <cot_u0, u^0> over the whole march:
+    returns (dL/dp[0..3], dL/du^N).  Keeps every u^n (small grids only)."""
+    lib = _load()
+    a, w = gauss_hermite(q)
+    if u_terminal is None:
+        u_terminal = terminal_indicator(grid)
+    ut = np.ascontiguousarray(u_terminal, dtype=np.float64).reshape(-1)
+    g = np.ascontiguousarray(cot_u0, dtype=np.float64).reshape(-1)
+    dth = np.zeros(4)
+    dut = np.zeros(grid.size)
+    p = _params(params)
+    rc = lib.fko_adjoint(ctypes.byref(grid._c()), family, _dp(p), q, _dp(a), _dp(w), float(dt),
+                         int(n_steps), _dp(ut), _dp(g), _dp(dth), _dp(dut))
+    if rc:
+        raise ValueError(f"fko_adjoint failed ({rc})")
+    return dth, dut.reshape(grid.shape)
 
 
 # ------------------------------------------------------- closed forms ----
