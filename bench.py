@@ -296,6 +296,73 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         p.close()
 
 
+# ----------------------------------------------------------- adjoint -----
+def run_adjoint(args, rank: int, world: int, local_rank: int):
+    """Adjoint workload: dL/d(A, eps, omega, D) and dL/du^N of the mean exit
+    probability at T = 2 on 1025 x 513 (2000 FP32 steps, FP64 reduction),
+    checkpoint every 50 steps.  One step = one fk_adjoint call (forward pass
+    with checkpoints, segment recompute, backward pass); the forward march
+    is timed beside it."""
+    import torch
+    import paper_2104_14561_gb300 as fk
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = fk_inputs.workload("adjoint_1025x513")
+    plan = fk.Plan(fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
+                               params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
+                               precision=w["precision"]))
+    ny, nx = plan.shape
+    cot = torch.zeros(plan.shape, dtype=torch.float64, device=dev)
+    cot[1:-1, 1:-1] = 1.0 / ((nx - 2) * (ny - 2))
+    out = plan.empty()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    units = units_per_solve(w)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+        stream.synchronize()
+        ms = []
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        return sum(ms) / len(ms)
+
+    clk = ClockSampler(local_rank)
+    clk.start()
+    ms_adj = timed(lambda: plan.adjoint(cot, None, checkpoint_every=50, stream=stream))
+    clocks = clk.stop()
+    ms_fwd = timed(lambda: plan.solve(None, out, stream=stream))
+    dth, _ = plan.adjoint(cot, None, checkpoint_every=50)
+    torch.cuda.synchronize()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": units / (ms_adj * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_adj,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "adjoint_1025x513", "grid": list(w["n"]), "q_per_dim": w["q"],
+                   "time_steps": w["n_steps"], "checkpoint_every": 50,
+                   "objective": "mean of u^0 over interior nodes",
+                   "l2": "flushed (512 MB write) before every timed call"},
+        "forward_ms": ms_fwd, "adjoint_over_forward": ms_adj / ms_fwd,
+        "dtheta": [float(v) for v in dth.cpu()],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 # --------------------------------------------------------------- ours ----
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
@@ -444,6 +511,8 @@ def main():
     try:
         if args.workload == "batched_64":
             run_batched(args, rank, world, local_rank)
+        elif args.workload == "adjoint_1025x513":
+            run_adjoint(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

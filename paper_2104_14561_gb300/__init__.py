@@ -3,5 +3,6 @@
 The compute path is libfk_gb300.so (CUDA kernels behind the C ABI of
 include/fk.h); this package only marshals PyTorch tensors into it.
 """
-from .fk import Plan, PlanSpec, gauss_hermite, solve_batched  # noqa: F401
+from .fk import (ExitProbability, Plan, PlanSpec, exit_probability, gauss_hermite,  # noqa: F401
+                 solve_batched)
 from ._lib import FkError, load  # noqa: F401

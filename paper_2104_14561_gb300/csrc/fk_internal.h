@@ -123,6 +123,10 @@ struct fk_plan {
   void* batch_rec;   // 6 J values: slope records of this instance
   void* batch_work;  // BatchWork of a batch whose first plan is this one
   int batch_grid;    // CTAs of the last batched launch
+  // adjoint (fk_adjoint.cu): checkpoints, segment, lambda, mu, dtheta
+  void* adj_ws;
+  int64_t adj_bytes;
+  void* adj_mu;      // 3 J accumulators inside adj_ws
 };
 
 void fk_batch_release(fk_plan* p);

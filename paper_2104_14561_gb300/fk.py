@@ -177,3 +177,42 @@ def solve_batched(plans, u_terminals=None, outs=None, stream=None):
     O = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
     L.check("fk_solve_batched", lib.fk_solve_batched(n, H, U, O, _stream(stream)))
     return outs
+
+
+class ExitProbability(torch.autograd.Function):
+    """u^0 = P(T, x) as a differentiable function of the coefficient
+    parameters theta = p[0..3] (cellular flow: A, eps, omega, D) and of the
+    terminal field.  Forward is fk_solve; backward is fk_adjoint (checkpoint
+    interval `checkpoint_every`), with the parameter gradient reduced in FP64.
+    """
+
+    @staticmethod
+    def forward(ctx, theta, u_terminal, spec, checkpoint_every):
+        params = tuple(float(v) for v in theta.detach().cpu().tolist())
+        s = PlanSpec(**{**spec.__dict__, "params": params})
+        plan = Plan(s)
+        ut = None if u_terminal is None else u_terminal.detach().contiguous()
+        u0 = plan.solve(ut)
+        ctx.plan = plan
+        ctx.theta_device, ctx.theta_dtype = theta.device, theta.dtype
+        ctx.ut = ut
+        ctx.k = checkpoint_every
+        ctx.has_ut = u_terminal is not None
+        return u0
+
+    @staticmethod
+    def backward(ctx, grad_u0):
+        plan = ctx.plan
+        dth, du = plan.adjoint(grad_u0.detach().double().contiguous(), ctx.ut,
+                               checkpoint_every=ctx.k)
+        torch.cuda.current_stream().synchronize()
+        plan.close()
+        return (dth.to(ctx.theta_device, ctx.theta_dtype), (du if ctx.has_ut else None),
+                None, None)
+
+
+def exit_probability(spec: PlanSpec, theta: torch.Tensor, u_terminal: torch.Tensor | None = None,
+                     checkpoint_every: int = 50) -> torch.Tensor:
+    """Differentiable P(T, x) on the mesh of `spec` (its params are replaced
+    by theta, a float64 tensor of 4 values)."""
+    return ExitProbability.apply(theta, u_terminal, spec, checkpoint_every)
