@@ -75,7 +75,21 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cellular_1025x513")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # profiling aids: a smaller case of the same workload (not a benchmark line)
+    ap.add_argument("--time-steps", type=int, default=None,
+                    help="override the workload's number of time steps")
+    ap.add_argument("--grid", type=int, nargs=2, default=None, metavar=("NX", "NY"),
+                    help="override the workload's mesh")
     return ap.parse_args()
+
+
+def workload_of(args):
+    over = {}
+    if args.time_steps:
+        over["n_steps"] = args.time_steps
+    if args.grid:
+        over["n"] = tuple(args.grid)
+    return fk_inputs.workload(args.workload, **over)
 
 
 def units_per_solve(w) -> float:
@@ -232,6 +246,8 @@ def run_batched(args, rank: int, world: int, local_rank: int):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     ws = fk_inputs.batched_instances()
+    if args.time_steps:
+        ws = [dict(x, n_steps=args.time_steps) for x in ws]
     plans = [fk.Plan(fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
                                  params=w["params"], q=w["q"], dt=w["dt"],
                                  n_steps=w["n_steps"], precision=w["precision"]))
@@ -283,11 +299,11 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "batched_64", "instances": len(ws), "nodes": nodes,
-                   "q_per_dim": 6, "time_steps": 1000, "dt": 1e-3,
+                   "q_per_dim": 6, "time_steps": ws[0]["n_steps"], "dt": 1e-3,
                    "l2": "flushed (512 MB write) before every timed march"},
         "plain_march": {"value": units / (ms_p * 1e-3), "ms_per_step": ms_p,
                         "how": "64 fk_solve calls (one CUDA graph each) on one stream"},
-        "hbm_gbs_algorithmic": 24.0 * nodes * 1000 * 2 / (ms_b * 1e-3) / 1e9,
+        "hbm_gbs_algorithmic": 24.0 * nodes * ws[0]["n_steps"] * 2 / (ms_b * 1e-3) / 1e9,
         "gpu_launches": args.steps * 1,
         "clocks": clocks,
     }
@@ -307,7 +323,7 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
     import paper_2104_14561_gb300 as fk
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    w = fk_inputs.workload("adjoint_1025x513")
+    w = workload_of(args)
     plan = fk.Plan(fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
                                params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
                                precision=w["precision"]))
@@ -372,7 +388,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    w = fk_inputs.workload(args.workload)
+    w = workload_of(args)
     spec = fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
                        params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
                        precision=w["precision"], path=w["path"])

@@ -51,6 +51,11 @@ struct Step2D {
   const T* row_tab;  // per row k: cos(pi y), sin(pi y)
   T gx[FK_MAXQ_2D], gy[FK_MAXQ_2D], w[FK_MAXQ_2D];  // sigma sqrt(2dt) a_q / h, w_q
   unsigned* err;
+  // row split between the direct and the window kernel (win > 0): the
+  // window kernel takes rows [row_lo, row_hi), the direct kernel (mode 1)
+  // the bands [1, row_lo) and [row_hi, ny-1), nb_lo tiles for the lower one
+  int mode, win, row_lo, row_hi, nb_lo;
+  int wm[FK_MAXQ_2D];  // floor(gy_q - gy_0): y-cell offset of point q in the window
 };
 
 template <typename T>
@@ -79,6 +84,8 @@ cudaError_t fk_launch_step1d(const Step1D<T>& a, int q, cudaStream_t s);
 // Opt the step kernels of this (dim, q, precision) into large dynamic shared
 // memory; called once at plan creation, never during stream capture.
 cudaError_t fk_prepare_step_kernels(int dim, int q, int elem);
+// Whether a window kernel with W rows exists for rule size q (FP32 only).
+bool fk_window_available(int q, int w);
 cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s);
 cudaError_t fk_launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
 
@@ -98,6 +105,10 @@ struct fk_plan {
   double reach[3];
   int halo[3], tile[3];
   int variant;       // register-budget variant of the 2D step kernel
+  int win;           // rows of the window kernel in use (0: direct kernel only)
+  int win_max;       // rows the window kernel needs (0: not eligible)
+  int win_row_lo, win_row_hi;
+  int wm[FK_MAXQ_2D];
   double gh_a[FK_MAXQ], gh_w[FK_MAXQ];
   // device memory owned by the plan
   void* scratch;     // one field

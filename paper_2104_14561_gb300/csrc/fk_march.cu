@@ -90,6 +90,37 @@ __device__ __forceinline__ T slope_fast(const T* u, int l, int stride, int g, in
   return pchip_fast(c[0] - c[-stride], c[stride] - c[0]);
 }
 
+// Record loads with explicit 32-bit shared-memory byte addresses: one add per
+// query for the R and one for the S record, the second row at an immediate
+// offset.  The compute phase only reads shared memory (it is written before
+// the last __syncthreads), so the loads carry no ordering constraint.
+__device__ __forceinline__ void lds_rec(uint32_t a, float& x, float& y, float& z, float& w) {
+  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a));
+}
+__device__ __forceinline__ void lds_rec_next(uint32_t a, float& x, float& y, float& z, float& w) {
+  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+16];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a));
+}
+__device__ __forceinline__ void lds_s(uint32_t a, float& x, float& y) {
+  asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a));
+}
+__device__ __forceinline__ void lds_s_next(uint32_t a, float& x, float& y) {
+  asm("ld.shared.v2.f32 {%0, %1}, [%2+8];" : "=f"(x), "=f"(y) : "r"(a));
+}
+__device__ __forceinline__ void lds_rec(uint32_t a, double& x, double& y, double& z, double& w) {
+  asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "r"(a));
+  asm("ld.shared.v2.f64 {%0, %1}, [%2+16];" : "=d"(z), "=d"(w) : "r"(a));
+}
+__device__ __forceinline__ void lds_rec_next(uint32_t a, double& x, double& y, double& z, double& w) {
+  asm("ld.shared.v2.f64 {%0, %1}, [%2+32];" : "=d"(x), "=d"(y) : "r"(a));
+  asm("ld.shared.v2.f64 {%0, %1}, [%2+48];" : "=d"(z), "=d"(w) : "r"(a));
+}
+__device__ __forceinline__ void lds_s(uint32_t a, double& x, double& y) {
+  asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "r"(a));
+}
+__device__ __forceinline__ void lds_s_next(uint32_t a, double& x, double& y) {
+  asm("ld.shared.v2.f64 {%0, %1}, [%2+16];" : "=d"(x), "=d"(y) : "r"(a));
+}
+
 // MINB = CTAs of 256 threads per SM that the register budget is sized for
 // (4 -> <= 64 registers, 3 -> <= 85, 2 -> <= 128); the plan's autotuner
 // picks the variant together with the tile height.
@@ -97,34 +128,33 @@ __device__ __forceinline__ T slope_fast(const T* u, int l, int stride, int g, in
 // Tiles are 32 nodes wide (one warp per tile row) and a multiple of 8 rows
 // high (ty = 8 * passes); every staging loop walks rows by warp and columns
 // by lane, so no index needs an integer division.
-template <typename T, int Q, int MINB>
-__global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// Phases 1-3 of a step CTA: stage u^{n+1} over the tile plus halo, compute
+// the scaled PCHIP slopes, pack the cell records.  gi0/gk0 are the global
+// node indices of staged column / row 0.
+template <typename T>
+__device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* S, T* U, int gi0,
+                                           int gk0, int warp, int lane) {
   const int lx = a.lx, ly = a.ly, lyr = a.lyr;
-  V4<T>* R = reinterpret_cast<V4<T>*>(smem);
-  V2<T>* S = reinterpret_cast<V2<T>*>(R + lx * lyr);
-  T* U = reinterpret_cast<T*>(S + lx * lyr);
   T* DX = U + lx * ly;
   T* DY = DX + lx * ly;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  const int i0 = 1 + blockIdx.x * 32;  // first interior output node of the tile
-  const int k0 = 1 + blockIdx.y * a.ty;
-  const int gi0 = i0 - a.hx - 1;  // global node of staged column 0
-  const int gk0 = k0 - a.hy - 1;
-
-  // 1. stage u^{n+1} (zero outside the mesh; never read there)
+  // 1. stage u^{n+1} with asynchronous copies, all in flight at once (zero
+  // fill outside the mesh; those entries are never read)
+  const uint32_t sU = (uint32_t)__cvta_generic_to_shared(U);
   for (int lk = warp; lk < ly; lk += FK_THREADS / 32) {
     const int gk = gk0 + lk;
     const bool rowin = gk >= 0 && gk < a.ny;
-    const T* src = a.u_in + (int64_t)gk * a.nx;
+    const T* src = a.u_in + (int64_t)(rowin ? gk : 0) * a.nx;
     for (int li = lane; li < lx; li += 32) {
       const int gi = gi0 + li;
-      U[lk * lx + li] = (rowin && gi >= 0 && gi < a.nx) ? src[gi] : T(0);
+      const bool in = rowin && gi >= 0 && gi < a.nx;
+      const T* g = in ? src + gi : a.u_in;
+      const uint32_t d = sU + (uint32_t)(lk * lx + li) * (uint32_t)sizeof(T);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(g),
+                   "n"(sizeof(T)), "r"(in ? (int)sizeof(T) : 0));
     }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-
   // 2. scaled PCHIP slopes h u_x, h u_y of the staged nodes 1..lx-2, 1..ly-2
   for (int lk = 1 + warp; lk <= ly - 2; lk += FK_THREADS / 32) {
     const int gk = gk0 + lk;
@@ -135,7 +165,6 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) 
     }
   }
   __syncthreads();
-
   // 3. packed cell records (column-major, odd pitch: conflict-free)
   for (int lk = 1 + warp; lk <= ly - 2; lk += FK_THREADS / 32) {
     for (int lc = 1 + lane; lc <= lx - 3; lc += 32) {
@@ -150,6 +179,59 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) 
     }
   }
   __syncthreads();
+}
+
+// Boundary nodes adjacent to interior node (i, k) hold 1 (Eq. (e3)).  On a
+// mesh with 3 nodes along an axis the single interior line is next to both
+// faces of that axis, so every flag is tested on its own.
+template <typename T>
+__device__ __forceinline__ void write_adjacent_boundary(const Step2D<T>& a, int i, int k) {
+  const int64_t nx = a.nx;
+  const bool L = (i == 1), Rt = (i == a.nx - 2), B = (k == 1), Tp = (k == a.ny - 2);
+  if (L | Rt | B | Tp) {
+    const int64_t top = (int64_t)(a.ny - 1) * nx, row = (int64_t)k * nx;
+    auto one = [&](int64_t j) {
+      a.u_out[j] = T(1);
+      if (a.snap) a.snap[j] = T(1);
+    };
+    if (L) one(row);
+    if (Rt) one(row + nx - 1);
+    if (B) one(i);
+    if (Tp) one(top + i);
+    if (L & B) one(0);
+    if (Rt & B) one(nx - 1);
+    if (L & Tp) one(top);
+    if (Rt & Tp) one(top + nx - 1);
+  }
+}
+
+// The direct kernel.  mode 0: all interior rows.  mode 1: only the two row
+// bands next to the y faces, [1, row_lo) and [row_hi, ny-1), whose shifted
+// points may leave the box (the rows between go to the window kernel).
+template <typename T, int Q, int MINB>
+__global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lx = a.lx, ly = a.ly, lyr = a.lyr;
+  V4<T>* R = reinterpret_cast<V4<T>*>(smem);
+  V2<T>* S = reinterpret_cast<V2<T>*>(R + lx * lyr);
+  T* U = reinterpret_cast<T*>(S + lx * lyr);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  const int i0 = 1 + blockIdx.x * 32;  // first interior output node of the tile
+  int k0, k_end;
+  if (a.mode == 0) {
+    k0 = 1 + blockIdx.y * a.ty;
+    k_end = a.ny - 1;
+  } else if ((int)blockIdx.y < a.nb_lo) {
+    k0 = 1 + blockIdx.y * a.ty;
+    k_end = a.row_lo;
+  } else {
+    k0 = a.row_hi + (blockIdx.y - a.nb_lo) * a.ty;
+    k_end = a.ny - 1;
+  }
+  const int gi0 = i0 - a.hx - 1;  // global node of staged column 0
+  const int gk0 = k0 - a.hy - 1;
+  stage_tile(a, R, S, U, gi0, gk0, warp, lane);
 
   // 4. one output node per thread and pass: column i0 + lane, row k0 + warp + 8 m
   const int i = i0 + lane;
@@ -161,10 +243,12 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) 
     cx0 = ct[0]; cx1 = ct[1]; cx2 = ct[2]; cx3 = ct[3];
   }
   const T nlo_x = T(-i), nhi_x = T(a.nx - 1 - i);
+  const uint32_t sR = (uint32_t)__cvta_generic_to_shared(R);
+  const uint32_t sS = (uint32_t)__cvta_generic_to_shared(S);
   unsigned bad = 0;
   for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
     const int k = k0 + ty;
-    if (!colok || k > a.ny - 2) continue;
+    if (!colok || k >= k_end) continue;
     const int lk = k - gk0;
     const T uj = R[li * lyr + lk].x;
     T dx, dy;
@@ -178,7 +262,7 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) 
     }
     // y factors of every query row, weights folded in
     const T nlo_y = T(-k), nhi_y = T(a.ny - 1 - k);
-    int rq[Q];
+    uint32_t rq[Q];  // byte offset of the query's lower row within a column of records
     T w0[Q], w1[Q], w2[Q], w3[Q];
     T exit_y = T(0);
 #pragma unroll
@@ -199,7 +283,7 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) 
       }
       const T wq = out ? T(0) : a.w[q];
       exit_y += a.w[q] - wq;
-      rq[q] = out ? lk : lc;
+      rq[q] = (uint32_t)(out ? lk : lc) * (uint32_t)sizeof(V2<T>);  // S stride; R stride is 2x
       const T t2 = t * t, omt = T(1) - t;
       w0[q] = wq;
       w1[q] = wq * (t2 * (T(3) - T(2) * t));  // h01
@@ -229,15 +313,18 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) 
       }
       const T t2 = t * t, omt = T(1) - t;
       const T h01 = t2 * (T(3) - T(2) * t), h10 = t * omt * omt, h11 = -(t2 * omt);
-      const V4<T>* Rc = R + lc * lyr;
-      const V2<T>* Sc = S + lc * lyr;
+      const uint32_t baseS = sS + (uint32_t)(lc * lyr) * (uint32_t)sizeof(V2<T>);
+      const uint32_t baseR = sR + (uint32_t)(lc * lyr) * (uint32_t)sizeof(V4<T>);
       T accp = exit_y * om;
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const V4<T> r0 = Rc[rq[q]];
-        const V4<T> r1 = Rc[rq[q] + 1];
-        const V2<T> s0 = Sc[rq[q]];
-        const V2<T> s1 = Sc[rq[q] + 1];
+        V4<T> r0, r1;
+        V2<T> s0, s1;
+        const uint32_t aR = baseR + 2 * rq[q], aS = baseS + rq[q];
+        lds_rec(aR, r0.x, r0.y, r0.z, r0.w);
+        lds_rec_next(aR, r1.x, r1.y, r1.z, r1.w);
+        lds_s(aS, s0.x, s0.y);
+        lds_s_next(aS, s1.x, s1.y);
         const T a0 = (r0.x - uj) + h01 * r0.y + h10 * r0.z + h11 * r0.w;
         const T a1 = (r1.x - uj) + h01 * r1.y + h10 * r1.z + h11 * r1.w;
         const T b0 = s0.x + h01 * s0.y;
@@ -250,28 +337,185 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) 
       acc += a.w[p] * accp;
     }
     const T un = uj + acc;
-    const int64_t nx = a.nx;
-    a.u_out[(int64_t)k * nx + i] = un;
-    if (a.snap) a.snap[(int64_t)k * nx + i] = un;
-    // 5. boundary nodes adjacent to this interior node hold 1 (Eq. (e3))
-    const bool L = (i == 1), Rt = (i == a.nx - 2), B = (k == 1), Tp = (k == a.ny - 2);
-    if (L | Rt | B | Tp) {
-      // On a mesh with 3 nodes along an axis the single interior line is
-      // next to both faces of that axis, so every flag is tested on its own.
-      const int64_t top = (int64_t)(a.ny - 1) * nx, row = (int64_t)k * nx;
-      auto one = [&](int64_t j) {
-        a.u_out[j] = T(1);
-        if (a.snap) a.snap[j] = T(1);
-      };
-      if (L) one(row);
-      if (Rt) one(row + nx - 1);
-      if (B) one(i);
-      if (Tp) one(top + i);
-      if (L & B) one(0);
-      if (Rt & B) one(nx - 1);
-      if (L & Tp) one(top);
-      if (Rt & Tp) one(top + nx - 1);
+    const int64_t j = (int64_t)k * a.nx + i;
+    a.u_out[j] = un;
+    if (a.snap) a.snap[j] = un;
+    write_adjacent_boundary(a, i, k);
+  }
+  if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
+}
+
+// Record loads at a compile-time row offset from a per-x-point base address.
+template <int OFF>
+__device__ __forceinline__ void lds_rec_at(uint32_t a, float& x, float& y, float& z, float& w) {
+  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
+      : "=f"(x), "=f"(y), "=f"(z), "=f"(w)
+      : "r"(a), "n"(OFF));
+}
+template <int OFF>
+__device__ __forceinline__ void lds_s_at(uint32_t a, float& x, float& y) {
+  asm("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(x), "=f"(y) : "r"(a), "n"(OFF));
+}
+
+template <int W, int R>
+struct WinRows {
+  // acc += sum over rows r >= R of Phi_r (row value - u_j) + Psi_r (row slope)
+  __device__ __forceinline__ static void run(uint32_t aR, uint32_t aS, float uj, float h01,
+                                             float h10, float h11, const float* phi,
+                                             const float* psi, float& acc0, float& acc1) {
+    float4 r;
+    float2 s;
+    lds_rec_at<16 * R>(aR, r.x, r.y, r.z, r.w);
+    lds_s_at<8 * R>(aS, s.x, s.y);
+    const float rb = (r.x - uj) + h01 * r.y + h10 * r.z + h11 * r.w;
+    const float sb = s.x + h01 * s.y;
+    acc0 += phi[R] * rb;
+    acc1 += psi[R] * sb;
+    WinRows<W, R + 1>::run(aR, aS, uj, h01, h10, h11, phi, psi, acc0, acc1);
+  }
+};
+template <int W>
+struct WinRows<W, W> {
+  __device__ __forceinline__ static void run(uint32_t, uint32_t, float, float, float, float,
+                                             const float*, const float*, float&, float&) {}
+};
+
+// Adds (v0, v1, v2) to rows (m, m+1, m+2) of a register window; m is the
+// same for every thread of the launch (a plan constant), so the switch is a
+// uniform branch and the window stays in registers.
+template <int W, int M>
+struct WinAdd {
+  __device__ __forceinline__ static void run(int m, float* f, float v0, float v1, float v2) {
+    if (m == M) {
+      f[M] += v0;
+      f[M + 1] += v1;
+      f[M + 2] += v2;
+    } else {
+      WinAdd<W, M + 1>::run(m, f, v0, v1, v2);
     }
+  }
+};
+template <int W>
+struct WinAdd<W, W - 2> {
+  __device__ __forceinline__ static void run(int, float*, float, float, float) {}
+};
+
+// The window kernel (FP32), for interior rows [row_lo, row_hi) whose
+// shifted points all stay strictly inside the box along y.  Per node the
+// y-points q of the tensor rule fall in cells c_q = c_0 + o_q with
+// o_q = m_q + beta_q, m_q = floor(gy_q - gy_0) a plan constant and
+// beta_q in {0, 1}; the sum over q of the y-Hermite weights is collected
+// per cell row into Phi_r (value basis) and Psi_r (slope basis), r < W.
+// Then for every x-point p each of the W rows is read once (24 bytes) and
+//   sum_q w_q (Itilde(x_p, y_q) - u_j) = sum_r Phi_r (row_r(x_p) - u_j)
+//                                            + Psi_r slope_r(x_p),
+// exactly the direct form's sum (zero-twist bicubic: Itilde is linear in
+// the row values, and sum_r Phi_r = sum_q w_q = 1), with W row reads
+// instead of 2Q per x-point.
+template <int Q, int W>
+__global__ void __launch_bounds__(FK_THREADS, 4) k_step2dw(const Step2D<float> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using T = float;
+  const int lx = a.lx, ly = a.ly, lyr = a.lyr;
+  V4<T>* R = reinterpret_cast<V4<T>*>(smem);
+  V2<T>* S = reinterpret_cast<V2<T>*>(R + lx * lyr);
+  T* U = reinterpret_cast<T*>(S + lx * lyr);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = 1 + blockIdx.x * 32;
+  const int k0 = a.row_lo + blockIdx.y * a.ty;
+  const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;
+  stage_tile(a, R, S, U, gi0, gk0, warp, lane);
+
+  const int i = i0 + lane;
+  const int li = i - gi0;
+  const bool colok = i <= a.nx - 2;
+  T cx0 = T(0), cx1 = T(0), cx2 = T(0), cx3 = T(0);
+  if (a.family == FK_CELLULAR_FLOW && colok) {
+    const T* ct = a.col_tab + 4 * (int64_t)i;
+    cx0 = ct[0]; cx1 = ct[1]; cx2 = ct[2]; cx3 = ct[3];
+  }
+  const T nlo_x = T(-i), nhi_x = T(a.nx - 1 - i);
+  const uint32_t sR = (uint32_t)__cvta_generic_to_shared(R);
+  const uint32_t sS = (uint32_t)__cvta_generic_to_shared(S);
+  unsigned bad = 0;
+  for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
+    const int k = k0 + ty;
+    if (!colok || k >= a.row_hi) continue;
+    const int lk = k - gk0;
+    const T uj = R[li * lyr + lk].x;
+    T dx, dy;
+    if (a.family == FK_CELLULAR_FLOW) {
+      const T* rt = a.row_tab + 2 * (int64_t)k;
+      dx = a.kx * rt[0] * (a.A * cx0 + a.e1 * cx1);
+      dy = a.ky * rt[1] * (a.A * cx2 + a.e2 * cx3);
+    } else {
+      dx = a.cdx;
+      dy = a.cdy;
+    }
+    // y window: rows c_0 .. c_0 + W - 1 relative to the staged tile
+    const int c0 = (int)floor(dy + a.gy[0]);
+    int lrow0 = k + c0 - gk0;
+    if (lrow0 < 1 || lrow0 + W - 1 > ly - 2) {
+      bad |= 1u;
+      lrow0 = 1;
+    }
+    T phi[W], psi[W];
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      phi[r] = T(0);
+      psi[r] = T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const T d = dy + a.gy[q];
+      const T fl = floor(d);
+      const T t = d - fl;
+      const int beta = (int)fl - c0 - a.wm[q];
+      if ((unsigned)beta > 1u) bad |= 1u;
+      const T t2 = t * t, omt = T(1) - t;
+      const T wq = a.w[q];
+      const T w01 = wq * (t2 * (T(3) - T(2) * t)), w00 = wq - w01;
+      const T w10 = wq * (t * omt * omt), w11 = -wq * (t2 * omt);
+      const bool b1 = beta == 1;
+      WinAdd<W, 0>::run(a.wm[q], phi, b1 ? T(0) : w00, b1 ? w00 : w01, b1 ? w01 : T(0));
+      WinAdd<W, 0>::run(a.wm[q], psi, b1 ? T(0) : w10, b1 ? w10 : w11, b1 ? w11 : T(0));
+    }
+    const T om = T(1) - uj;
+    const uint32_t rowR = (uint32_t)lrow0 * (uint32_t)sizeof(V4<T>);
+    const uint32_t rowS = (uint32_t)lrow0 * (uint32_t)sizeof(V2<T>);
+    T acc = T(0);
+#pragma unroll 1
+    for (int p = 0; p < Q; ++p) {
+      const T d = dx + a.gx[p];
+      if ((d < nlo_x) || (d > nhi_x)) {
+        acc += a.w[p] * om;
+        continue;
+      }
+      const T fl = floor(d);
+      int c = i + (int)fl;
+      T t = d - fl;
+      if (c > a.nx - 2) {
+        c = a.nx - 2;
+        t = T(1);
+      }
+      int lc = c - gi0;
+      if ((unsigned)(lc - 1) > (unsigned)(lx - 4)) {
+        bad |= 1u;
+        lc = li;
+      }
+      const T t2 = t * t, omt = T(1) - t;
+      const T h01 = t2 * (T(3) - T(2) * t), h10 = t * omt * omt, h11 = -(t2 * omt);
+      const uint32_t colR = sR + (uint32_t)(lc * lyr) * (uint32_t)sizeof(V4<T>) + rowR;
+      const uint32_t colS = sS + (uint32_t)(lc * lyr) * (uint32_t)sizeof(V2<T>) + rowS;
+      T acc0 = T(0), acc1 = T(0);
+      WinRows<W, 0>::run(colR, colS, uj, h01, h10, h11, phi, psi, acc0, acc1);
+      acc += a.w[p] * (acc0 + acc1);
+    }
+    const T un = uj + acc;
+    const int64_t j = (int64_t)k * a.nx + i;
+    a.u_out[j] = un;
+    if (a.snap) a.snap[j] = un;
+    write_adjacent_boundary(a, i, k);
   }
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
@@ -367,9 +611,54 @@ __global__ void k_copy16(uint4* dst, const uint4* src, int64_t n16) {
 template <typename T, int Q, int MINB>
 cudaError_t launch2d_q(const Step2D<T>& a, cudaStream_t s) {
   const size_t smem = fk_step2d_smem(a.lx, a.ly, a.lyr, (int)sizeof(T));
-  dim3 grid((a.nx - 2 + 31) / 32, (a.ny - 2 + a.ty - 1) / a.ty);
+  int gy;
+  if (a.mode == 0)
+    gy = (a.ny - 2 + a.ty - 1) / a.ty;
+  else
+    gy = a.nb_lo + (a.ny - 1 - a.row_hi + a.ty - 1) / a.ty;
+  if (gy <= 0) return cudaSuccess;
+  dim3 grid((a.nx - 2 + 31) / 32, gy);
   k_step2d<T, Q, MINB><<<grid, FK_THREADS, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// The window kernel stages one extra halo row in y: its window can reach
+// one row past the cells the points use (a row of weight 0).
+inline Step2D<float> window_args(const Step2D<float>& a) {
+  Step2D<float> w = a;
+  w.hy = a.hy + 1;
+  w.ly = w.ty + 2 * w.hy + 2;
+  w.lyr = w.ly | 1;
+  return w;
+}
+
+template <int Q, int W>
+cudaError_t launchw(const Step2D<float>& a, cudaStream_t s) {
+  const Step2D<float> w = window_args(a);
+  const size_t smem = fk_step2d_smem(w.lx, w.ly, w.lyr, 4);
+  dim3 grid((w.nx - 2 + 31) / 32, (w.row_hi - w.row_lo + w.ty - 1) / w.ty);
+  k_step2dw<Q, W><<<grid, FK_THREADS, smem, s>>>(w);
+  return cudaGetLastError();
+}
+template <int Q, int W>
+cudaError_t attrw() {
+  return cudaFuncSetAttribute(k_step2dw<Q, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              227 * 1024);
+}
+
+// (Q, W) pairs with a window kernel: Q in {4, 6, 8}, 3 <= W <= 2Q - 1.
+#define FK_WIN_LIST(X)                                                                     \
+  X(4, 3) X(4, 4) X(4, 5) X(4, 6) X(4, 7)                                                  \
+  X(6, 3) X(6, 4) X(6, 5) X(6, 6) X(6, 7) X(6, 8) X(6, 9) X(6, 10) X(6, 11)                \
+  X(8, 3) X(8, 4) X(8, 5) X(8, 6) X(8, 7) X(8, 8) X(8, 9) X(8, 10) X(8, 11) X(8, 12)       \
+  X(8, 13) X(8, 14) X(8, 15)
+
+cudaError_t launch_window(const Step2D<float>& a, int q, cudaStream_t s) {
+#define FK_W(QQ, WW) \
+  if (q == QQ && a.win == WW) return launchw<QQ, WW>(a, s);
+  FK_WIN_LIST(FK_W)
+#undef FK_W
+  return cudaErrorInvalidValue;
 }
 
 template <typename T, int Q, int MINB>
@@ -381,14 +670,20 @@ cudaError_t attr2d_q() {
 // Register-budget variants per precision: FP32 {4, 3} CTAs/SM, FP64 {2}.
 template <typename T, int Q>
 cudaError_t launch2d_var(const Step2D<T>& a, cudaStream_t s) {
-  if (sizeof(T) == 8) return launch2d_q<T, Q, 2>(a, s);
-  return a.variant == 1 ? launch2d_q<T, Q, 3>(a, s) : launch2d_q<T, Q, 4>(a, s);
+  if constexpr (sizeof(T) == 8) {
+    return launch2d_q<T, Q, 2>(a, s);
+  } else {
+    return a.variant == 1 ? launch2d_q<T, Q, 3>(a, s) : launch2d_q<T, Q, 4>(a, s);
+  }
 }
 template <typename T, int Q>
 cudaError_t attr2d_var() {
-  if (sizeof(T) == 8) return attr2d_q<T, Q, 2>();
-  cudaError_t e = attr2d_q<T, Q, 4>();
-  return e != cudaSuccess ? e : attr2d_q<T, Q, 3>();
+  if constexpr (sizeof(T) == 8) {
+    return attr2d_q<T, Q, 2>();
+  } else {
+    cudaError_t e = attr2d_q<T, Q, 4>();
+    return e != cudaSuccess ? e : attr2d_q<T, Q, 3>();
+  }
 }
 
 template <typename T, int Q>
@@ -412,8 +707,23 @@ size_t fk_step2d_smem(int lx, int ly, int lyr, int elem) {
 
 size_t fk_step1d_smem(int lx, int elem) { return (size_t)lx * (4 * elem) + (size_t)lx * elem; }
 
+bool fk_window_available(int q, int w) {
+#define FK_W(QQ, WW) \
+  if (q == QQ && w == WW) return true;
+  FK_WIN_LIST(FK_W)
+#undef FK_W
+  return false;
+}
+
 template <typename T>
 cudaError_t fk_launch_step2d(const Step2D<T>& a, int q, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (a.win > 0) {
+      cudaError_t e = launch_window(a, q, s);
+      if (e != cudaSuccess) return e;
+      // the direct kernel takes the bands next to the y faces (mode 1)
+    }
+  }
   switch (q) {
     case 1: return launch2d_var<T, 1>(a, s);
     case 2: return launch2d_var<T, 2>(a, s);
@@ -451,6 +761,15 @@ cudaError_t fk_launch_step1d(const Step1D<T>& a, int q, cudaStream_t s) {
 }
 
 cudaError_t fk_prepare_step_kernels(int dim, int q, int elem) {
+  if (dim == 2 && elem == 4) {
+#define FK_W(QQ, WW)                     \
+  if (q == QQ) {                         \
+    cudaError_t e = attrw<QQ, WW>();     \
+    if (e != cudaSuccess) return e;      \
+  }
+    FK_WIN_LIST(FK_W)
+#undef FK_W
+  }
   if (dim == 2) {
     switch (q) {
 #define FK_CASE(Q) \

@@ -212,6 +212,14 @@ void fill2d(const fk_plan* p, int n, Step2D<T>* a) {
     a->w[q] = (T)p->gh_w[q];
   }
   a->err = p->d_err;
+  a->win = (sizeof(T) == 4) ? p->win : 0;
+  a->mode = a->win > 0 ? 1 : 0;
+  if (a->win > 0) {
+    a->row_lo = p->win_row_lo;
+    a->row_hi = p->win_row_hi;
+    a->nb_lo = (a->row_lo - 1 + a->ty - 1) / a->ty;
+    for (int q = 0; q < p->q; ++q) a->wm[q] = p->wm[q];
+  }
 }
 
 template <typename T>
@@ -239,10 +247,40 @@ struct TileCand {
 const TileCand kCands[] = {{16, 0}, {8, 0}, {24, 0}, {32, 0}, {40, 0}, {48, 0}, {64, 0},
                            {16, 1}, {8, 1},  {24, 1}, {32, 1}, {48, 1}};
 
-bool cand_fits(const fk_plan* p, const TileCand& c, int dev_smem) {
+bool cand_fits(const fk_plan* p, const TileCand& c, int dev_smem, bool window = false) {
   if (p->elem == 8 && c.variant != 0) return false;
-  const int lx = 32 + 2 * p->halo[0] + 2, ly = c.ty + 2 * p->halo[1] + 2;
+  const int hy = p->halo[1] + (window ? 1 : 0);
+  const int lx = 32 + 2 * p->halo[0] + 2, ly = c.ty + 2 * hy + 2;
   return fk_step2d_smem(lx, ly, ly | 1, p->elem) <= (size_t)dev_smem;
+}
+
+// The window kernel (FP32, 2D, matrix-free) evaluates each cell row once per
+// x-point.  It needs: a rule size it is built for; the y-cell offsets
+// m_q = floor(gy_q - gy_0) of the points robustly integral-part-stable (the
+// fractional part of gy_q - gy_0 away from 0 and 1, so that the actual cell
+// offset of point q is m_q or m_q + 1 for every drift); fewer window rows
+// W = m_{Q-1} + 3 than the direct form's 2Q row reads; and a non-empty band
+// of rows whose points all stay strictly inside the box along y.
+void window_eligibility(fk_plan* p) {
+  p->win_max = 0;
+  if (p->grid.dim != 2 || p->prec != FK_FP32 || p->path != FK_PATH_MATRIX_FREE) return;
+  const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * p->dt);
+  float gy[FK_MAXQ_2D];
+  for (int q = 0; q < p->q; ++q) gy[q] = (float)(sg * p->gh_a[q] / p->h[1]);
+  p->wm[0] = 0;  // point 0 defines the window origin
+  for (int q = 1; q < p->q; ++q) {
+    const double d = (double)gy[q] - (double)gy[0];
+    const double f = d - floor(d);
+    if (f < 1e-4 || f > 1.0 - 1e-4) return;
+    p->wm[q] = (int)floor(d);
+  }
+  const int W = p->wm[p->q - 1] + 3;
+  if (W >= 2 * p->q || !fk_window_available(p->q, W)) return;
+  const int band = (int)ceil(p->reach[1] * (1.0 + 1e-6) + 1e-3) + 1;
+  p->win_row_lo = band;
+  p->win_row_hi = p->grid.n[1] - 1 - band;
+  if (p->win_row_hi - p->win_row_lo < 8) return;
+  p->win_max = W;
 }
 
 // Choose the output tile and check the shared-memory budget.
@@ -272,7 +310,7 @@ fk_status choose_tiles(fk_plan* p) {
 // problem shape for the life of the process.
 struct TuneEntry {
   int dev, nx, ny, q, elem, hx, hy, family;
-  int ty, variant;
+  int ty, variant, win;
 };
 std::mutex g_tune_mu;
 std::vector<TuneEntry> g_tune_cache;
@@ -281,7 +319,7 @@ fk_status autotune(fk_plan* p) {
   if (p->grid.dim != 2 || p->path != FK_PATH_MATRIX_FREE) return FK_OK;
   if (p->J_int < 16384) return FK_OK;  // small meshes: launch-bound, keep the default
   TuneEntry key = {p->device, p->grid.n[0], p->grid.n[1], p->q, p->elem, p->halo[0], p->halo[1],
-                   p->coeffs.family, 0, 0};
+                   p->coeffs.family, 0, 0, 0};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     for (const TuneEntry& t : g_tune_cache) {
@@ -289,6 +327,7 @@ fk_status autotune(fk_plan* p) {
           t.elem == key.elem && t.hx == key.hx && t.hy == key.hy && t.family == key.family) {
         p->tile[1] = t.ty;
         p->variant = t.variant;
+        p->win = t.win > 0 ? p->win_max : 0;
         return FK_OK;
       }
     }
@@ -308,13 +347,19 @@ fk_status autotune(fk_plan* p) {
   cudaEventCreate(&e1);
   fk_status st = cuda_status(fk_launch_fill_chi(p->scratch, 2, p->grid.n[0], p->grid.n[1], p->elem, s));
   const bool log = getenv("FK_TUNE_LOG") != nullptr;
+  if (log)
+    fprintf(stderr, "fk autotune %dx%d q=%d: window kernel rows %d (0: not eligible), band [%d, %d)\n",
+            p->grid.n[0], p->grid.n[1], p->q, p->win_max, p->win_row_lo, p->win_row_hi);
   float best = 1e30f;
-  int best_ty = p->tile[1], best_var = p->variant;
+  int best_ty = p->tile[1], best_var = p->variant, best_win = 0;
+  for (int wpass = 0; wpass < (p->win_max > 0 ? 2 : 1); ++wpass)
   for (const TileCand& c : kCands) {
     if (st != FK_OK) break;
-    if (!cand_fits(p, c, dev_smem)) continue;
+    const int win = wpass ? p->win_max : 0;
+    if (!cand_fits(p, c, dev_smem, win > 0)) continue;
     p->tile[1] = c.ty;
     p->variant = c.variant;
+    p->win = win;
     st = fk_enqueue_step(p, p->n_steps - 1, p->scratch, tmp, nullptr, s);  // warm-up
     if (st != FK_OK) break;
     cudaEventRecord(e0, s);
@@ -326,12 +371,13 @@ fk_status autotune(fk_plan* p) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     ms /= reps;
-    if (log) fprintf(stderr, "fk autotune %dx%d q=%d elem=%d: ty=%d variant=%d  %.2f us\n",
-                     p->grid.n[0], p->grid.n[1], p->q, p->elem, c.ty, c.variant, ms * 1e3f);
+    if (log) fprintf(stderr, "fk autotune %dx%d q=%d elem=%d: ty=%d variant=%d window=%d  %.2f us\n",
+                     p->grid.n[0], p->grid.n[1], p->q, p->elem, c.ty, c.variant, win, ms * 1e3f);
     if (ms < best) {
       best = ms;
       best_ty = c.ty;
       best_var = c.variant;
+      best_win = win;
     }
   }
   cudaEventDestroy(e0);
@@ -340,10 +386,12 @@ fk_status autotune(fk_plan* p) {
   cudaFree(tmp);
   p->tile[1] = best_ty;
   p->variant = best_var;
+  p->win = best_win;
   cudaMemset(p->d_err, 0, sizeof(unsigned));
   if (st == FK_OK) {
     key.ty = best_ty;
     key.variant = best_var;
+    key.win = best_win;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache.push_back(key);
   }
@@ -530,6 +578,7 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
     }
     p->halo[m] = (int)ceil(r) + 1;
   }
+  window_eligibility(p);
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) {
     delete p;
@@ -544,6 +593,12 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   if (st == FK_OK) st = (prec == FK_FP32) ? upload_tables<float>(p) : upload_tables<double>(p);
   if (st == FK_OK) st = cuda_status(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
   if (st == FK_OK) st = autotune(p);
+  if (st == FK_OK) {
+    // explicit choice of the 2D step kernel (tests exercise both paths)
+    const char* k = getenv("FK_STEP_KERNEL");
+    if (k && strcmp(k, "window") == 0) p->win = p->win_max;
+    if (k && strcmp(k, "direct") == 0) p->win = 0;
+  }
   if (st == FK_OK && path == FK_PATH_CSR) {
     st = fk_csr_assemble(p, p->cap_stream);
     if (st == FK_OK) st = cuda_status(cudaStreamSynchronize(p->cap_stream));

@@ -239,3 +239,38 @@ def test_1d_minimal_and_wide_reach(fk, oracle):
         got = _gpu_solve(fk, w)
         want = _oracle_march(oracle, w, 4, 0)
         assert np.abs(got - want).max() <= TOL64
+
+
+@pytest.fixture
+def window_kernel(monkeypatch):
+    """Plans created in the test use the window kernel where eligible."""
+    monkeypatch.setenv("FK_STEP_KERNEL", "window")
+
+
+@pytest.mark.parametrize("q,D", [(4, 0.02), (6, 0.02), (6, 0.005), (8, 0.01)])
+def test_window_kernel_fp32_vs_oracle(fk, oracle, window_kernel, q, D):
+    """FP32 window kernel (rows read once per x-point) against the oracle,
+    on meshes whose band split leaves both kernels work."""
+    w = fk_inputs.workload("cellular_1025x513", n=(161, 81), q=q, n_steps=100, precision="fp32",
+                           params=(1.0, 0.2, 2 * math.pi, D))
+    got = _gpu_solve(fk, w)
+    want = _oracle_march(oracle, w, w["n_steps"], 0)
+    assert np.abs(got - want).max() <= TOL32
+
+
+def test_window_kernel_equals_direct(fk, monkeypatch):
+    """The window and direct kernels agree to FP32 rounding on the
+    benchmark workload (200 steps, random terminal field)."""
+    import torch
+    w = fk_inputs.workload("cellular_1025x513", n_steps=200)
+    u0 = fk_inputs.random_field((513, 1025), seed=2)
+    res = {}
+    for kern in ("window", "direct"):
+        monkeypatch.setenv("FK_STEP_KERNEL", kern)
+        res[kern] = _gpu_solve(fk, w, u0)
+    assert np.abs(res["window"] - res["direct"]).max() <= 2e-6
+
+
+def test_window_kernel_full_march_vs_golden(fk, monkeypatch):
+    monkeypatch.setenv("FK_STEP_KERNEL", "window")
+    test_cellular_1025x513_fp32_full_march(fk)
