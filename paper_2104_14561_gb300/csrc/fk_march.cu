@@ -208,32 +208,14 @@ __device__ __forceinline__ void write_adjacent_boundary(const Step2D<T>& a, int 
 // The direct kernel.  mode 0: all interior rows.  mode 1: only the two row
 // bands next to the y faces, [1, row_lo) and [row_hi, ny-1), whose shifted
 // points may leave the box (the rows between go to the window kernel).
-template <typename T, int Q, int MINB>
-__global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// Phase 4 of the direct kernel: the Gauss-Hermite sum of every output node
+// of rows [k0, min(k0 + ty, k_end)) of this tile, one node per thread and
+// pass (column i0 + lane, row k0 + warp + 8 m).  Returns the range-check flag.
+template <typename T, int Q>
+__device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>* R,
+                                                 const V2<T>* S, int i0, int k0, int k_end,
+                                                 int gi0, int gk0, int warp, int lane) {
   const int lx = a.lx, ly = a.ly, lyr = a.lyr;
-  V4<T>* R = reinterpret_cast<V4<T>*>(smem);
-  V2<T>* S = reinterpret_cast<V2<T>*>(R + lx * lyr);
-  T* U = reinterpret_cast<T*>(S + lx * lyr);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  const int i0 = 1 + blockIdx.x * 32;  // first interior output node of the tile
-  int k0, k_end;
-  if (a.mode == 0) {
-    k0 = 1 + blockIdx.y * a.ty;
-    k_end = a.ny - 1;
-  } else if ((int)blockIdx.y < a.nb_lo) {
-    k0 = 1 + blockIdx.y * a.ty;
-    k_end = a.row_lo;
-  } else {
-    k0 = a.row_hi + (blockIdx.y - a.nb_lo) * a.ty;
-    k_end = a.ny - 1;
-  }
-  const int gi0 = i0 - a.hx - 1;  // global node of staged column 0
-  const int gk0 = k0 - a.hy - 1;
-  stage_tile(a, R, S, U, gi0, gk0, warp, lane);
-
-  // 4. one output node per thread and pass: column i0 + lane, row k0 + warp + 8 m
   const int i = i0 + lane;
   const int li = i - gi0;
   const bool colok = i <= a.nx - 2;
@@ -342,6 +324,35 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) 
     if (a.snap) a.snap[j] = un;
     write_adjacent_boundary(a, i, k);
   }
+  return bad;
+}
+
+template <typename T, int Q, int MINB>
+__global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lx = a.lx, ly = a.ly, lyr = a.lyr;
+  V4<T>* R = reinterpret_cast<V4<T>*>(smem);
+  V2<T>* S = reinterpret_cast<V2<T>*>(R + lx * lyr);
+  T* U = reinterpret_cast<T*>(S + lx * lyr);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  const int i0 = 1 + blockIdx.x * 32;  // first interior output node of the tile
+  int k0, k_end;
+  if (a.mode == 0) {
+    k0 = 1 + blockIdx.y * a.ty;
+    k_end = a.ny - 1;
+  } else if ((int)blockIdx.y < a.nb_lo) {
+    k0 = 1 + blockIdx.y * a.ty;
+    k_end = a.row_lo;
+  } else {
+    k0 = a.row_hi + (blockIdx.y - a.nb_lo) * a.ty;
+    k_end = a.ny - 1;
+  }
+  const int gi0 = i0 - a.hx - 1;  // global node of staged column 0
+  const int gk0 = k0 - a.hy - 1;
+  stage_tile(a, R, S, U, gi0, gk0, warp, lane);
+
+  const unsigned bad = direct_phase<T, Q>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
 
@@ -422,9 +433,28 @@ __global__ void __launch_bounds__(FK_THREADS, 4) k_step2dw(const Step2D<float> a
   T* U = reinterpret_cast<T*>(S + lx * lyr);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = 1 + blockIdx.x * 32;
-  const int k0 = a.row_lo + blockIdx.y * a.ty;
+  // tiles [0, nwin) cover the window rows; the rest cover the two bands
+  // next to the y faces with the direct path (one launch per step)
+  const int nwin = (a.row_hi - a.row_lo + a.ty - 1) / a.ty;
+  const bool window = (int)blockIdx.y < nwin;
+  int k0, k_end;
+  if (window) {
+    k0 = a.row_lo + blockIdx.y * a.ty;
+    k_end = a.row_hi;
+  } else if ((int)blockIdx.y - nwin < a.nb_lo) {
+    k0 = 1 + (blockIdx.y - nwin) * a.ty;
+    k_end = a.row_lo;
+  } else {
+    k0 = a.row_hi + (blockIdx.y - nwin - a.nb_lo) * a.ty;
+    k_end = a.ny - 1;
+  }
   const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;
   stage_tile(a, R, S, U, gi0, gk0, warp, lane);
+  if (!window) {
+    const unsigned b = direct_phase<T, Q>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
+    if (b) atomicOr(a.err, FK_DEVERR_RANGE);
+    return;
+  }
 
   const int i = i0 + lane;
   const int li = i - gi0;
@@ -636,7 +666,9 @@ template <int Q, int W>
 cudaError_t launchw(const Step2D<float>& a, cudaStream_t s) {
   const Step2D<float> w = window_args(a);
   const size_t smem = fk_step2d_smem(w.lx, w.ly, w.lyr, 4);
-  dim3 grid((w.nx - 2 + 31) / 32, (w.row_hi - w.row_lo + w.ty - 1) / w.ty);
+  const int nwin = (w.row_hi - w.row_lo + w.ty - 1) / w.ty;
+  const int nb_hi = (w.ny - 1 - w.row_hi + w.ty - 1) / w.ty;
+  dim3 grid((w.nx - 2 + 31) / 32, nwin + w.nb_lo + nb_hi);
   k_step2dw<Q, W><<<grid, FK_THREADS, smem, s>>>(w);
   return cudaGetLastError();
 }
@@ -718,11 +750,7 @@ bool fk_window_available(int q, int w) {
 template <typename T>
 cudaError_t fk_launch_step2d(const Step2D<T>& a, int q, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (a.win > 0) {
-      cudaError_t e = launch_window(a, q, s);
-      if (e != cudaSuccess) return e;
-      // the direct kernel takes the bands next to the y faces (mode 1)
-    }
+    if (a.win > 0) return launch_window(a, q, s);  // window rows and face bands
   }
   switch (q) {
     case 1: return launch2d_var<T, 1>(a, s);

@@ -317,6 +317,24 @@ std::vector<TuneEntry> g_tune_cache;
 
 fk_status autotune(fk_plan* p) {
   if (p->grid.dim != 2 || p->path != FK_PATH_MATRIX_FREE) return FK_OK;
+  // explicit choice (profiling runs, where timing is distorted):
+  // FK_STEP_TILE=ty[,variant[,window]] with window 1 = the row-window kernel
+  if (const char* t = getenv("FK_STEP_TILE")) {
+    int ty = 0, var = 0, w = 0;
+    if (sscanf(t, "%d,%d,%d", &ty, &var, &w) >= 1 && ty >= 8 && ty % 8 == 0 &&
+        (var == 0 || var == 1)) {
+      int dev_smem = 0;
+      cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+      const TileCand c = {ty, p->elem == 8 ? 0 : var};
+      const int win = (w && p->win_max > 0) ? p->win_max : 0;
+      if (cand_fits(p, c, dev_smem, win > 0)) {
+        p->tile[1] = c.ty;
+        p->variant = c.variant;
+        p->win = win;
+        return FK_OK;
+      }
+    }
+  }
   if (p->J_int < 16384) return FK_OK;  // small meshes: launch-bound, keep the default
   TuneEntry key = {p->device, p->grid.n[0], p->grid.n[1], p->q, p->elem, p->halo[0], p->halo[1],
                    p->coeffs.family, 0, 0, 0};
