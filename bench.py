@@ -42,7 +42,8 @@ UNIT = "node-quadrature updates/s"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FLOP_PER_UPDATE = 26                # see the design doc: 13 multiply-adds per query
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-PROFILE_JSON = os.path.join(ROOT, "profiles", "k_step2d_cellular_1025x513.json")
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (profiling recipe)
+PROFILE_DIR = os.path.join(ROOT, "profiles")
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -80,6 +81,8 @@ def parse():
                     help="override the workload's number of time steps")
     ap.add_argument("--grid", type=int, nargs=2, default=None, metavar=("NX", "NY"),
                     help="override the workload's mesh")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default=None,
+                    help="override the workload's precision")
     return ap.parse_args()
 
 
@@ -89,6 +92,8 @@ def workload_of(args):
         over["n_steps"] = args.time_steps
     if args.grid:
         over["n"] = tuple(args.grid)
+    if args.precision:
+        over["precision"] = args.precision
     return fk_inputs.workload(args.workload, **over)
 
 
@@ -222,11 +227,11 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
-def profile_traffic():
+def profile_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of the step kernel from the committed ncu
     summary, or None when the kernel source changed since the capture."""
     try:
-        prof = json.load(open(PROFILE_JSON))
+        prof = json.load(open(os.path.join(PROFILE_DIR, f"{kernel}_{workload}.json")))
         src = os.path.join(ROOT, "paper_2104_14561_gb300", "csrc", "fk_march.cu")
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         if prof.get("source_sha256") != h:
@@ -436,10 +441,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # end to end through the public API: pinned host in -> device -> march -> host out
     host_in = torch.zeros(plan.shape, dtype=plan.dtype).pin_memory()
-    host_in[0, :] = 1.0
-    host_in[-1, :] = 1.0
-    host_in[:, 0] = 1.0
-    host_in[:, -1] = 1.0
+    for ax in range(host_in.dim()):  # the terminal indicator: 1 on the boundary
+        host_in.narrow(ax, 0, 1).fill_(1.0)
+        host_in.narrow(ax, host_in.shape[ax] - 1, 1).fill_(1.0)
     host_out = torch.empty(plan.shape, dtype=plan.dtype).pin_memory()
     dev_in = plan.empty()
     e_ms = []
@@ -477,12 +481,16 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                     "csr_nnz": info["csr_nnz"]}
     else:
         flops_launch = FLOP_PER_UPDATE * units / w["n_steps"]
-        peak_flops = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6
+        peak_flops = (SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 if w["precision"] == "fp32"
+                      else FP64_PEAK_TFLOPS * 1e12)
         achieved = flops_launch / (launch_ms * 1e-3)
-        roofline = {"kernel": "k_step2d", "bound": "alu", "achieved": achieved / 1e12,
+        kname = ("k_step1d" if len(w["n"]) == 1 else
+                 "k_step2dw" if info.get("window_rows", 0) > 0 else "k_step2d")
+        roofline = {"kernel": kname, "bound": "alu", "achieved": achieved / 1e12,
                     "peak": peak_flops / 1e12, "unit": "TFLOP/s", "frac": achieved / peak_flops,
-                    "traffic": profile_traffic(), "flop_per_launch": flops_launch,
-                    "launch_ms": launch_ms}
+                    "traffic": profile_traffic(kname, args.workload),
+                    "flop_per_launch": flops_launch, "launch_ms": launch_ms,
+                    "window_rows": info.get("window_rows", 0)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,

@@ -105,6 +105,9 @@ typedef struct fk_plan_info {
   double reach_cells[3];    /* bound on |shift| in cells, per axis      */
   int64_t csr_nnz;          /* stored entries of Q Psi (FK_PATH_CSR)    */
   int64_t workspace_bytes;  /* device memory owned by the plan          */
+  int window_rows;          /* 2D FP32 step kernel: rows of its y-window
+                               (0 = the direct kernel, 2Q row reads per
+                               x-point)                                  */
 } fk_plan_info;
 
 /* ------------------------------------------------------------------------

@@ -467,7 +467,11 @@ fk_status run_batch(int n, fk_plan* const* plans, const void* const* u_terminal,
   // buffers, before the real inputs are staged; skipped when an input
   // aliases its output)
   int bps = max_bps;
-  {
+  // explicit CTAs per SM (profiling runs, where timing is distorted)
+  const char* fixed = getenv("FK_BATCH_CTAS_PER_SM");
+  if (fixed && atoi(fixed) >= 1 && atoi(fixed) <= max_bps) {
+    bps = atoi(fixed);
+  } else {
     std::lock_guard<std::mutex> lock(g_batch_mu);
     bool found = false;
     for (const BatchTune& t : g_batch_tune)

@@ -289,7 +289,11 @@ fk_status choose_tiles(fk_plan* p) {
   cudaError_t e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
   if (e != cudaSuccess) return FK_ERR_CUDA;
   if (p->grid.dim == 1) {
-    p->tile[0] = 1024;
+    // enough CTAs to spread a short line over the SMs (2 per SM), 32..1024 nodes each
+    const int interior = p->grid.n[0] - 2;
+    int t = (interior + 2 * 152 - 1) / (2 * 152);
+    t = (t + 31) / 32 * 32;
+    p->tile[0] = t < 32 ? 32 : (t > 1024 ? 1024 : t);
     const int lx = p->tile[0] + 2 * p->halo[0] + 2;
     if (fk_step1d_smem(lx, p->elem) > (size_t)dev_smem) return FK_ERR_UNSUPPORTED;
     return FK_OK;
@@ -670,6 +674,7 @@ fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
   }
   info->csr_nnz = p->csr_nnz;
   info->workspace_bytes = p->workspace_bytes;
+  info->window_rows = p->win;
   return FK_OK;
 }
 

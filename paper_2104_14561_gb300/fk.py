@@ -87,7 +87,8 @@ class Plan:
         return {"n_nodes": i.n_nodes, "n_interior": i.n_interior, "dim": i.dim,
                 "q_per_dim": i.q_per_dim, "n_steps": i.n_steps, "halo": list(i.halo),
                 "tile": list(i.tile), "reach_cells": list(i.reach_cells),
-                "csr_nnz": i.csr_nnz, "workspace_bytes": i.workspace_bytes}
+                "csr_nnz": i.csr_nnz, "workspace_bytes": i.workspace_bytes,
+                "window_rows": i.window_rows}
 
     def _check_field(self, t: torch.Tensor, name: str):
         if t.dtype != self.dtype or t.device.type != "cuda" or tuple(t.shape) != self.shape \
