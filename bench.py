@@ -493,12 +493,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                       else FP64_PEAK_TFLOPS * 1e12)
         achieved = flops_launch / (launch_ms * 1e-3)
         kname = ("k_step1d" if len(w["n"]) == 1 else
-                 "k_step2dw" if info.get("window_rows", 0) > 0 else "k_step2d")
+                 {"direct": "k_step2d", "window": "k_step2dw",
+                  "masked": "k_step2dm"}[info.get("step_kernel", "direct")])
         roofline = {"kernel": kname, "bound": "alu", "achieved": achieved / 1e12,
                     "peak": peak_flops / 1e12, "unit": "TFLOP/s", "frac": achieved / peak_flops,
                     "traffic": profile_traffic(kname, args.workload),
                     "flop_per_launch": flops_launch, "launch_ms": launch_ms,
-                    "window_rows": info.get("window_rows", 0)}
+                    "window_rows": info.get("window_rows", 0),
+                    "step_kernel": info.get("step_kernel")}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,

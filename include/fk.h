@@ -105,9 +105,13 @@ typedef struct fk_plan_info {
   double reach_cells[3];    /* bound on |shift| in cells, per axis      */
   int64_t csr_nnz;          /* stored entries of Q Psi (FK_PATH_CSR)    */
   int64_t workspace_bytes;  /* device memory owned by the plan          */
-  int window_rows;          /* 2D FP32 step kernel: rows of its y-window
-                               (0 = the direct kernel, 2Q row reads per
-                               x-point)                                  */
+  int window_rows;          /* 2D FP32 step kernel: width W of its node
+                               window (0 = the direct kernel)            */
+  int step_kernel;          /* 2D step kernel in use: 0 direct (per-point
+                               Hermite evaluation), 1 row window (y-rows
+                               read once per x-point, direct face bands),
+                               2 masked tensor window (W x W nodes per
+                               node, exits as zero weights)              */
 } fk_plan_info;
 
 /* ------------------------------------------------------------------------

@@ -392,6 +392,13 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
     fk_fill_step2d_f32(p, n, (Step2D<float>*)&g.s);
   else
     fk_fill_step2d_f64(p, n, (Step2D<double>*)&g.s);
+  // the adjoint kernels stage the direct kernel's column-major layout,
+  // whatever step kernel the forward march uses
+  g.s.mode = 0;
+  g.s.win = 0;
+  g.s.hx = p->halo[0];
+  g.s.hy = p->halo[1];
+  g.s.lx = g.s.tx + 2 * g.s.hx + 2;
   g.s.ty = ty;
   g.s.ly = ty + 2 * g.s.hy + 2;
   g.s.lyr = g.s.ly | 1;

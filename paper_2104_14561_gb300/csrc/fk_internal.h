@@ -38,10 +38,12 @@ struct Step2D {
   T* snap;         // optional second copy of u^n (snapshot), or nullptr
   int nx, ny;
   int tx, ty;      // output tile (interior nodes) per CTA: tx = 32, ty = 8 m
-  int variant;     // register-budget variant (FP32: 0 -> 4 CTAs/SM, 1 -> 3)
+  int variant;     // register-budget variant (FP32 direct and row window: 0 -> 4
+                   // CTAs/SM, 1 -> 3; masked window: 0 -> 3, 1 -> 2)
   int hx, hy;      // halo in cells
   int lx, ly;      // staged value tile: tx + 2 hx + 2, ty + 2 hy + 2
-  int lyr;         // column pitch (records) of the column-major record tiles, odd
+  int lyr;         // odd pitch of the record tiles: column pitch of the column-major
+                   // tiles (modes 0, 1), row pitch of the row-major tile (mode 2)
   int family;
   // drift in cells: cellular flow  dx = kx cos(pi y)(A sin(pi x) + e1 sin(2 pi x))
   //                                dy = ky sin(pi y)(A cos(pi x) + e2 cos(2 pi x))
@@ -54,8 +56,11 @@ struct Step2D {
   // row split between the direct and the window kernel (win > 0): the
   // window kernel takes rows [row_lo, row_hi), the direct kernel (mode 1)
   // the bands [1, row_lo) and [row_hi, ny-1), nb_lo tiles for the lower one
+  // (mode 2: the masked tensor-window kernel on every interior row; win is
+  // then its window width W on both axes and hx, hy its halo)
   int mode, win, row_lo, row_hi, nb_lo;
   int wm[FK_MAXQ_2D];  // floor(gy_q - gy_0): y-cell offset of point q in the window
+  T wmf[FK_MAXQ_2D];   // the same offsets as T (mode 2: equal on both axes)
 };
 
 template <typename T>
@@ -86,6 +91,13 @@ cudaError_t fk_launch_step1d(const Step1D<T>& a, int q, cudaStream_t s);
 cudaError_t fk_prepare_step_kernels(int dim, int q, int elem);
 // Whether a window kernel with W rows exists for rule size q (FP32 only).
 bool fk_window_available(int q, int w);
+// The masked tensor-window kernel (fk_window.cu, FP32): launcher, shared
+// memory of one CTA, availability for (q, W), and the large-shared-memory
+// opt-in (plan creation only).
+cudaError_t fk_launch_step2dm(const Step2D<float>& a, int q, cudaStream_t s);
+size_t fk_step2dm_smem(int ly, int lp);  // ly staged rows of pitch lp
+bool fk_masked_available(int q, int w);
+cudaError_t fk_prepare_masked_kernels(int q);
 cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s);
 cudaError_t fk_launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
 
@@ -109,6 +121,10 @@ struct fk_plan {
   int win_max;       // rows the window kernel needs (0: not eligible)
   int win_row_lo, win_row_hi;
   int wm[FK_MAXQ_2D];
+  int mwin;          // window width of the masked tensor-window kernel (0: not eligible)
+  int mwm[FK_MAXQ_2D];  // its cell offsets floor(g_q - g_0), equal on both axes
+  int mhalo[2];      // its halo per axis
+  int use_masked;    // the masked kernel is the step kernel
   double gh_a[FK_MAXQ], gh_w[FK_MAXQ];
   // device memory owned by the plan
   void* scratch;     // one field

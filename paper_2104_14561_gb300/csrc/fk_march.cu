@@ -26,17 +26,9 @@
 #include <stdint.h>
 
 #include "fk_internal.h"
+#include "fk_device.cuh"
 
 namespace {
-
-// Scaled PCHIP slope h*u'_j from the two neighbouring differences
-// (Eq. (e300)): 0 unless both have the same strict sign, else their
-// harmonic mean 2 dl dr / (dl + dr).
-template <typename T>
-__device__ __forceinline__ T pchip_scaled(T dl, T dr) {
-  const T p = dl * dr;
-  return p > T(0) ? (T(2) * p) / (dl + dr) : T(0);
-}
 
 // Scaled slope along a staged line at local position l of a node whose
 // global index on that axis is g (0..n-1); stride is the distance between
@@ -71,16 +63,6 @@ __device__ __forceinline__ bool locate(int k, T d, int n, int* cell, T* t) {
   return out;
 }
 
-// Slope of Eq. (e300) from two neighbouring differences, in the FP32 path
-// with a fast reciprocal (the slope feeds an O(h) correction term, so a
-// 2-ulp quotient is far inside the 1e-5 parity budget); FP64 divides exactly.
-template <typename T>
-__device__ __forceinline__ T pchip_fast(T dl, T dr) { return pchip_scaled(dl, dr); }
-template <>
-__device__ __forceinline__ float pchip_fast<float>(float dl, float dr) {
-  const float p = dl * dr;
-  return p > 0.f ? __fdividef(2.f * p, dl + dr) : 0.f;
-}
 template <typename T>
 __device__ __forceinline__ T slope_fast(const T* u, int l, int stride, int g, int n) {
   if (g < 0 || g >= n) return T(0);
@@ -179,30 +161,6 @@ __device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* 
     }
   }
   __syncthreads();
-}
-
-// Boundary nodes adjacent to interior node (i, k) hold 1 (Eq. (e3)).  On a
-// mesh with 3 nodes along an axis the single interior line is next to both
-// faces of that axis, so every flag is tested on its own.
-template <typename T>
-__device__ __forceinline__ void write_adjacent_boundary(const Step2D<T>& a, int i, int k) {
-  const int64_t nx = a.nx;
-  const bool L = (i == 1), Rt = (i == a.nx - 2), B = (k == 1), Tp = (k == a.ny - 2);
-  if (L | Rt | B | Tp) {
-    const int64_t top = (int64_t)(a.ny - 1) * nx, row = (int64_t)k * nx;
-    auto one = [&](int64_t j) {
-      a.u_out[j] = T(1);
-      if (a.snap) a.snap[j] = T(1);
-    };
-    if (L) one(row);
-    if (Rt) one(row + nx - 1);
-    if (B) one(i);
-    if (Tp) one(top + i);
-    if (L & B) one(0);
-    if (Rt & B) one(nx - 1);
-    if (L & Tp) one(top);
-    if (Rt & Tp) one(top + nx - 1);
-  }
 }
 
 // The direct kernel.  mode 0: all interior rows.  mode 1: only the two row
@@ -750,6 +708,7 @@ bool fk_window_available(int q, int w) {
 template <typename T>
 cudaError_t fk_launch_step2d(const Step2D<T>& a, int q, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
+    if (a.mode == 2) return fk_launch_step2dm(a, q, s);  // masked tensor window
     if (a.win > 0) return launch_window(a, q, s);  // window rows and face bands
   }
   switch (q) {
@@ -790,6 +749,8 @@ cudaError_t fk_launch_step1d(const Step1D<T>& a, int q, cudaStream_t s) {
 
 cudaError_t fk_prepare_step_kernels(int dim, int q, int elem) {
   if (dim == 2 && elem == 4) {
+    cudaError_t em = fk_prepare_masked_kernels(q);
+    if (em != cudaSuccess) return em;
 #define FK_W(QQ, WW)                     \
   if (q == QQ) {                         \
     cudaError_t e = attrw<QQ, WW>();     \

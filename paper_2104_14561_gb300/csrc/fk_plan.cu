@@ -8,6 +8,7 @@
 
 #include <stdio.h>
 
+#include <iterator>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -220,6 +221,19 @@ void fill2d(const fk_plan* p, int n, Step2D<T>* a) {
     a->nb_lo = (a->row_lo - 1 + a->ty - 1) / a->ty;
     for (int q = 0; q < p->q; ++q) a->wm[q] = p->wm[q];
   }
+  if (sizeof(T) == 4 && p->use_masked && p->mwin > 0) {
+    a->mode = 2;
+    a->win = p->mwin;
+    a->hx = p->mhalo[0];
+    a->hy = p->mhalo[1];
+    a->lx = a->tx + 2 * a->hx + 2;
+    a->ly = a->ty + 2 * a->hy + 2;
+    a->lyr = a->lx | 1;  // row pitch of the row-major records
+    for (int q = 0; q < p->q; ++q) {
+      a->wm[q] = p->mwm[q];
+      a->wmf[q] = (T)p->mwm[q];
+    }
+  }
 }
 
 template <typename T>
@@ -247,11 +261,33 @@ struct TileCand {
 const TileCand kCands[] = {{16, 0}, {8, 0}, {24, 0}, {32, 0}, {40, 0}, {48, 0}, {64, 0},
                            {16, 1}, {8, 1},  {24, 1}, {32, 1}, {48, 1}};
 
-bool cand_fits(const fk_plan* p, const TileCand& c, int dev_smem, bool window = false) {
+// Step kernels of a 2D plan: 0 direct, 1 row window (+ direct face bands),
+// 2 masked tensor window.
+enum { kDirect = 0, kRowWindow = 1, kMasked = 2 };
+
+bool kernel_eligible(const fk_plan* p, int kern) {
+  return kern == kDirect || (kern == kRowWindow && p->win_max > 0) ||
+         (kern == kMasked && p->mwin > 0);
+}
+
+bool cand_fits(const fk_plan* p, const TileCand& c, int dev_smem, int kern = kDirect) {
   if (p->elem == 8 && c.variant != 0) return false;
-  const int hy = p->halo[1] + (window ? 1 : 0);
+  if (kern == kMasked) {
+    const int lx = 32 + 2 * p->mhalo[0] + 2, ly = c.ty + 2 * p->mhalo[1] + 2;
+    return fk_step2dm_smem(ly, lx | 1) <= (size_t)dev_smem;
+  }
+  const int hy = p->halo[1] + (kern == kRowWindow ? 1 : 0);
   const int lx = 32 + 2 * p->halo[0] + 2, ly = c.ty + 2 * hy + 2;
   return fk_step2d_smem(lx, ly, ly | 1, p->elem) <= (size_t)dev_smem;
+}
+
+void set_kernel(fk_plan* p, int kern) {
+  p->win = kern == kRowWindow ? p->win_max : 0;
+  p->use_masked = kern == kMasked ? 1 : 0;
+}
+
+int current_kernel(const fk_plan* p) {
+  return p->use_masked ? kMasked : (p->win > 0 ? kRowWindow : kDirect);
 }
 
 // The window kernel (FP32, 2D, matrix-free) evaluates each cell row once per
@@ -283,6 +319,43 @@ void window_eligibility(fk_plan* p) {
   p->win_max = W;
 }
 
+// The masked tensor-window kernel (FP32, 2D, matrix-free) needs: the cell
+// offsets m_q = floor(g_q - g_0) the same on both axes (one uniform scatter
+// pattern for the x and the y weights) with the fractional part of
+// g_q - g_0 away from 0 and 1 by a margin that the FP32 rounding of the
+// shifted positions cannot cross (then the cell of point q is m_q or
+// m_q + 1 after the cell of point 0 for every drift); and a window width
+// W = m_{Q-1} + 3 it is built for.  Its halo H = floor(reach) + 2 keeps
+// the whole W x W window of every node of a tile inside the staged nodes.
+void masked_eligibility(fk_plan* p) {
+  const double kMargin = 1e-4;
+  p->mwin = 0;
+  if (p->grid.dim != 2 || p->prec != FK_FP32 || p->path != FK_PATH_MATRIX_FREE) return;
+  const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * p->dt);
+  float gx[FK_MAXQ_2D], gy[FK_MAXQ_2D];
+  for (int q = 0; q < p->q; ++q) {
+    gx[q] = (float)(sg * p->gh_a[q] / p->h[0]);
+    gy[q] = (float)(sg * p->gh_a[q] / p->h[1]);
+  }
+  p->mwm[0] = 0;
+  for (int q = 1; q < p->q; ++q) {
+    const double dx = (double)gx[q] - (double)gx[0], dy = (double)gy[q] - (double)gy[0];
+    const double fx = dx - floor(dx), fy = dy - floor(dy);
+    if (fx < kMargin || fx > 1.0 - kMargin || fy < kMargin || fy > 1.0 - kMargin) return;
+    if (floor(dx) != floor(dy)) return;
+    p->mwm[q] = (int)floor(dy);
+  }
+  const int W = p->mwm[p->q - 1] + 3;
+  if (!fk_masked_available(p->q, W)) return;
+  for (int m = 0; m < 2; ++m) {
+    // |error of an FP32 position difference| <= 2 ulp(reach + 1) << margin
+    if ((p->reach[m] + 1.0) * 4.8e-7 > 0.5 * kMargin) return;
+    const double r = p->reach[m] * (1.0 + 1e-6) + 1e-3;
+    p->mhalo[m] = (int)floor(r) + 2;
+  }
+  p->mwin = W;
+}
+
 // Choose the output tile and check the shared-memory budget.
 fk_status choose_tiles(fk_plan* p) {
   int dev_smem = 0;
@@ -309,37 +382,87 @@ fk_status choose_tiles(fk_plan* p) {
   return FK_ERR_UNSUPPORTED;
 }
 
-// Autotuner: time one step of every fitting candidate on this device (from
-// the terminal indicator) and keep the fastest.  Results are cached per
-// problem shape for the life of the process.
+// Autotuner: time one step of every fitting candidate (tile height x
+// register budget x step kernel) on this device, from the terminal
+// indicator, and keep the fastest.  Results are cached per problem shape
+// for the life of the process.
 struct TuneEntry {
   int dev, nx, ny, q, elem, hx, hy, family;
-  int ty, variant, win;
+  int ty, variant, kern;
 };
 std::mutex g_tune_mu;
 std::vector<TuneEntry> g_tune_cache;
 
+// The first fitting tile of the kernel in use (after an explicit kernel
+// choice that the tuned tile does not fit).
+void refit_tile(fk_plan* p) {
+  int dev_smem = 0;
+  cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+  const int kern = current_kernel(p);
+  if (cand_fits(p, TileCand{p->tile[1], p->variant}, dev_smem, kern)) return;
+  for (const TileCand& c : kCands) {
+    if (cand_fits(p, c, dev_smem, kern)) {
+      p->tile[1] = c.ty;
+      p->variant = c.variant;
+      return;
+    }
+  }
+  set_kernel(p, kDirect);
+}
+
+// Tile candidates of the masked kernel: the fixed list plus tile heights
+// that make the number of tiles just fit 1-4 waves of resident CTAs (3 per
+// SM for variant 0, 2 for variant 1), so that the last wave is not short.
+std::vector<TileCand> masked_cands(const fk_plan* p) {
+  std::vector<TileCand> v(std::begin(kCands), std::end(kCands));
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+    sms = 152;
+  const int nxt = (p->grid.n[0] - 2 + 31) / 32, rows = p->grid.n[1] - 2;
+  for (int var = 0; var < 2; ++var) {
+    const int per_sm = var == 0 ? 3 : 2;
+    for (int waves = 1; waves <= 4; ++waves) {
+      const int row_tiles = waves * sms * per_sm / nxt;
+      if (row_tiles < 1) continue;
+      const int ty = (rows + row_tiles - 1) / row_tiles;
+      if (ty < 4 || ty > 64) continue;
+      bool seen = false;
+      for (const TileCand& c : v) seen = seen || (c.ty == ty && c.variant == var);
+      if (!seen) v.push_back(TileCand{ty, var});
+    }
+  }
+  return v;
+}
+
 fk_status autotune(fk_plan* p) {
   if (p->grid.dim != 2 || p->path != FK_PATH_MATRIX_FREE) return FK_OK;
   // explicit choice (profiling runs, where timing is distorted):
-  // FK_STEP_TILE=ty[,variant[,window]] with window 1 = the row-window kernel
+  // FK_STEP_TILE=ty[,variant[,kernel]], kernel 0 direct, 1 row window, 2 masked window
   if (const char* t = getenv("FK_STEP_TILE")) {
-    int ty = 0, var = 0, w = 0;
-    if (sscanf(t, "%d,%d,%d", &ty, &var, &w) >= 1 && ty >= 8 && ty % 8 == 0 &&
-        (var == 0 || var == 1)) {
+    int ty = 0, var = 0, kern = 0;
+    if (sscanf(t, "%d,%d,%d", &ty, &var, &kern) >= 1 && ty >= 4 && ty <= 64 &&
+        (var == 0 || var == 1) && kern >= 0 && kern <= 2) {
+      if (kern != kMasked && ty % 8 != 0) ty = (ty + 7) / 8 * 8;
       int dev_smem = 0;
       cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
       const TileCand c = {ty, p->elem == 8 ? 0 : var};
-      const int win = (w && p->win_max > 0) ? p->win_max : 0;
-      if (cand_fits(p, c, dev_smem, win > 0)) {
+      if (!kernel_eligible(p, kern)) kern = kDirect;
+      if (cand_fits(p, c, dev_smem, kern)) {
         p->tile[1] = c.ty;
         p->variant = c.variant;
-        p->win = win;
+        set_kernel(p, kern);
         return FK_OK;
       }
     }
   }
-  if (p->J_int < 16384) return FK_OK;  // small meshes: launch-bound, keep the default
+  // small meshes are launch-bound: keep the default tile, prefer the masked kernel
+  if (p->J_int < 16384) {
+    if (p->mwin > 0) {
+      set_kernel(p, kMasked);
+      refit_tile(p);
+    }
+    return FK_OK;
+  }
   TuneEntry key = {p->device, p->grid.n[0], p->grid.n[1], p->q, p->elem, p->halo[0], p->halo[1],
                    p->coeffs.family, 0, 0, 0};
   {
@@ -349,7 +472,7 @@ fk_status autotune(fk_plan* p) {
           t.elem == key.elem && t.hx == key.hx && t.hy == key.hy && t.family == key.family) {
         p->tile[1] = t.ty;
         p->variant = t.variant;
-        p->win = t.win > 0 ? p->win_max : 0;
+        set_kernel(p, kernel_eligible(p, t.kern) ? t.kern : kDirect);
         return FK_OK;
       }
     }
@@ -370,36 +493,43 @@ fk_status autotune(fk_plan* p) {
   fk_status st = cuda_status(fk_launch_fill_chi(p->scratch, 2, p->grid.n[0], p->grid.n[1], p->elem, s));
   const bool log = getenv("FK_TUNE_LOG") != nullptr;
   if (log)
-    fprintf(stderr, "fk autotune %dx%d q=%d: window kernel rows %d (0: not eligible), band [%d, %d)\n",
-            p->grid.n[0], p->grid.n[1], p->q, p->win_max, p->win_row_lo, p->win_row_hi);
+    fprintf(stderr,
+            "fk autotune %dx%d q=%d: row window %d (0: not eligible), band [%d, %d); "
+            "masked window %d, halo %d %d\n",
+            p->grid.n[0], p->grid.n[1], p->q, p->win_max, p->win_row_lo, p->win_row_hi, p->mwin,
+            p->mhalo[0], p->mhalo[1]);
   float best = 1e30f;
-  int best_ty = p->tile[1], best_var = p->variant, best_win = 0;
-  for (int wpass = 0; wpass < (p->win_max > 0 ? 2 : 1); ++wpass)
-  for (const TileCand& c : kCands) {
-    if (st != FK_OK) break;
-    const int win = wpass ? p->win_max : 0;
-    if (!cand_fits(p, c, dev_smem, win > 0)) continue;
-    p->tile[1] = c.ty;
-    p->variant = c.variant;
-    p->win = win;
-    st = fk_enqueue_step(p, p->n_steps - 1, p->scratch, tmp, nullptr, s);  // warm-up
-    if (st != FK_OK) break;
-    cudaEventRecord(e0, s);
-    const int reps = 4;
-    for (int r = 0; r < reps && st == FK_OK; ++r)
-      st = fk_enqueue_step(p, p->n_steps - 1, p->scratch, tmp, nullptr, s);
-    cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) st = FK_ERR_CUDA;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    ms /= reps;
-    if (log) fprintf(stderr, "fk autotune %dx%d q=%d elem=%d: ty=%d variant=%d window=%d  %.2f us\n",
-                     p->grid.n[0], p->grid.n[1], p->q, p->elem, c.ty, c.variant, win, ms * 1e3f);
-    if (ms < best) {
-      best = ms;
-      best_ty = c.ty;
-      best_var = c.variant;
-      best_win = win;
+  int best_ty = p->tile[1], best_var = p->variant, best_kern = kDirect;
+  for (int kern = kDirect; kern <= kMasked; ++kern) {
+    if (!kernel_eligible(p, kern)) continue;
+    const std::vector<TileCand> cands =
+        kern == kMasked ? masked_cands(p) : std::vector<TileCand>(std::begin(kCands), std::end(kCands));
+    for (const TileCand& c : cands) {
+      if (st != FK_OK) break;
+      if (!cand_fits(p, c, dev_smem, kern)) continue;
+      p->tile[1] = c.ty;
+      p->variant = c.variant;
+      set_kernel(p, kern);
+      st = fk_enqueue_step(p, p->n_steps - 1, p->scratch, tmp, nullptr, s);  // warm-up
+      if (st != FK_OK) break;
+      cudaEventRecord(e0, s);
+      const int reps = 4;
+      for (int r = 0; r < reps && st == FK_OK; ++r)
+        st = fk_enqueue_step(p, p->n_steps - 1, p->scratch, tmp, nullptr, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = FK_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (log)
+        fprintf(stderr, "fk autotune %dx%d q=%d elem=%d: ty=%d variant=%d kernel=%d  %.2f us\n",
+                p->grid.n[0], p->grid.n[1], p->q, p->elem, c.ty, c.variant, kern, ms * 1e3f);
+      if (ms < best) {
+        best = ms;
+        best_ty = c.ty;
+        best_var = c.variant;
+        best_kern = kern;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -408,12 +538,12 @@ fk_status autotune(fk_plan* p) {
   cudaFree(tmp);
   p->tile[1] = best_ty;
   p->variant = best_var;
-  p->win = best_win;
+  set_kernel(p, best_kern);
   cudaMemset(p->d_err, 0, sizeof(unsigned));
   if (st == FK_OK) {
     key.ty = best_ty;
     key.variant = best_var;
-    key.win = best_win;
+    key.kern = best_kern;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache.push_back(key);
   }
@@ -601,6 +731,7 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
     p->halo[m] = (int)ceil(r) + 1;
   }
   window_eligibility(p);
+  masked_eligibility(p);
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) {
     delete p;
@@ -618,8 +749,14 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   if (st == FK_OK) {
     // explicit choice of the 2D step kernel (tests exercise both paths)
     const char* k = getenv("FK_STEP_KERNEL");
-    if (k && strcmp(k, "window") == 0) p->win = p->win_max;
-    if (k && strcmp(k, "direct") == 0) p->win = 0;
+    int kern = -1;
+    if (k && strcmp(k, "direct") == 0) kern = kDirect;
+    if (k && strcmp(k, "window") == 0) kern = kRowWindow;
+    if (k && strcmp(k, "masked") == 0) kern = kMasked;
+    if (kern >= 0 && kernel_eligible(p, kern) && p->grid.dim == 2) {
+      set_kernel(p, kern);
+      refit_tile(p);
+    }
   }
   if (st == FK_OK && path == FK_PATH_CSR) {
     st = fk_csr_assemble(p, p->cap_stream);
@@ -674,7 +811,8 @@ fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
   }
   info->csr_nnz = p->csr_nnz;
   info->workspace_bytes = p->workspace_bytes;
-  info->window_rows = p->win;
+  info->window_rows = p->use_masked ? p->mwin : p->win;
+  info->step_kernel = current_kernel(p);
   return FK_OK;
 }
 

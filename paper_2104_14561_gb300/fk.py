@@ -88,7 +88,8 @@ class Plan:
                 "q_per_dim": i.q_per_dim, "n_steps": i.n_steps, "halo": list(i.halo),
                 "tile": list(i.tile), "reach_cells": list(i.reach_cells),
                 "csr_nnz": i.csr_nnz, "workspace_bytes": i.workspace_bytes,
-                "window_rows": i.window_rows}
+                "window_rows": i.window_rows,
+                "step_kernel": ("direct", "window", "masked")[i.step_kernel]}
 
     def _check_field(self, t: torch.Tensor, name: str):
         if t.dtype != self.dtype or t.device.type != "cuda" or tuple(t.shape) != self.shape \

@@ -274,3 +274,90 @@ def test_window_kernel_equals_direct(fk, monkeypatch):
 def test_window_kernel_full_march_vs_golden(fk, monkeypatch):
     monkeypatch.setenv("FK_STEP_KERNEL", "window")
     test_cellular_1025x513_fp32_full_march(fk)
+
+
+# ---------------------------------------------------------------- masked window kernel
+@pytest.fixture
+def masked_kernel(monkeypatch):
+    """Plans created in the test use the masked tensor-window kernel where eligible."""
+    monkeypatch.setenv("FK_STEP_KERNEL", "masked")
+
+
+def _gpu_solve_info(fk, w, u_terminal=None):
+    import torch
+    plan = fk.Plan(_spec(fk, w))
+    info = plan.info()
+    ut = None if u_terminal is None else torch.tensor(u_terminal, dtype=plan.dtype, device="cuda")
+    out = plan.solve(ut)
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    res = out.double().cpu().numpy()
+    plan.close()
+    return res, info
+
+
+# isotropic meshes on [0,2]x[0,1] (equal cell offsets on both axes), window
+# widths 3..9, reach from under one cell to about three cells, so that
+# exits along x, along y and along both occur on many nodes
+MASKED_CASES = [
+    ((81, 41), 4, 0.02, 1e-3, 4),
+    ((161, 81), 6, 0.025, 1e-3, 6),
+    ((161, 81), 8, 0.03, 1e-3, 8),
+    ((161, 81), 8, 0.05, 1e-3, 9),
+    ((161, 81), 4, 0.05, 1e-3, 6),
+    ((41, 21), 6, 0.05, 1e-2, 7),
+    ((33, 17), 4, 0.02, 1e-2, 4),
+    ((9, 5), 4, 0.02, 1e-2, 3),
+    ((5, 3), 4, 0.01, 1e-2, 3),
+]
+
+
+@pytest.mark.parametrize("n,q,D,dt,W", MASKED_CASES)
+def test_masked_kernel_fp32_vs_oracle(fk, oracle, masked_kernel, n, q, D, dt, W):
+    """Masked tensor-window kernel (exits as zero weights, every node on one
+    path) against the FP64 oracle over 100 steps."""
+    w = fk_inputs.workload("cellular_1025x513", n=n, q=q, n_steps=100, precision="fp32",
+                           params=(1.0, 0.2, 2 * math.pi, D), dt=dt)
+    got, info = _gpu_solve_info(fk, w)
+    assert info["step_kernel"] == "masked" and info["window_rows"] == W
+    want = _oracle_march(oracle, w, w["n_steps"], 0)
+    assert np.abs(got - want).max() <= TOL32
+
+
+def test_masked_kernel_const_drift(fk, oracle, masked_kernel):
+    w = _small2d(4, "fp32", family="const_drift", n_steps=60, n=(81, 41))
+    w.update(params=(0.7, -0.4, 0.0, 0.3))
+    got, info = _gpu_solve_info(fk, w)
+    assert info["step_kernel"] == "masked"
+    want = _oracle_march(oracle, w, w["n_steps"], 0)
+    assert np.abs(got - want).max() <= TOL32
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_masked_kernel_random_field(fk, oracle, masked_kernel, seed):
+    """From a random terminal field (slopes of both signs at every face and
+    corner; the end rule and the masked weights meet there)."""
+    w = _small2d(6, "fp32", n=(101, 51), n_steps=5)
+    u0 = fk_inputs.random_field((51, 101), seed=seed)
+    got, info = _gpu_solve_info(fk, w, u0)
+    assert info["step_kernel"] == "masked"
+    want = _oracle_march(oracle, w, w["n_steps"], 0, u0)
+    assert np.abs(got - want).max() <= TOL32
+
+
+def test_masked_kernel_equals_direct(fk, monkeypatch):
+    """The masked and direct kernels agree to FP32 rounding on the benchmark
+    workload (200 steps, random terminal field)."""
+    w = fk_inputs.workload("cellular_1025x513", n_steps=200)
+    u0 = fk_inputs.random_field((513, 1025), seed=2)
+    res = {}
+    for kern in ("masked", "direct"):
+        monkeypatch.setenv("FK_STEP_KERNEL", kern)
+        res[kern], info = _gpu_solve_info(fk, w, u0)
+        assert info["step_kernel"] == kern
+    assert np.abs(res["masked"] - res["direct"]).max() <= 2e-6
+
+
+def test_masked_kernel_full_march_vs_golden(fk, monkeypatch):
+    monkeypatch.setenv("FK_STEP_KERNEL", "masked")
+    test_cellular_1025x513_fp32_full_march(fk)
