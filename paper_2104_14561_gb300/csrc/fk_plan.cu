@@ -353,6 +353,7 @@ void masked_eligibility(fk_plan* p) {
     const double r = p->reach[m] * (1.0 + 1e-6) + 1e-3;
     p->mhalo[m] = (int)floor(r) + 2;
   }
+  if (32 + 2 * p->mhalo[0] + 2 > 2 + FK_THREADS) return;  // one column per thread in the sweep
   p->mwin = W;
 }
 
