@@ -240,7 +240,7 @@ def profile_traffic(kernel: str, workload: str):
     summary, or None when the kernel source changed since the capture."""
     try:
         prof = json.load(open(os.path.join(PROFILE_DIR, f"{kernel}_{workload}.json")))
-        src = os.path.join(ROOT, "paper_2104_14561_gb300", "csrc", "fk_march.cu")
+        src = os.path.join(ROOT, prof["source"])
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         if prof.get("source_sha256") != h:
             return None
