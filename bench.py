@@ -251,9 +251,10 @@ def profile_traffic(kernel: str, workload: str):
 
 # ----------------------------------------------------------- batched -----
 def run_batched(args, rank: int, world: int, local_rank: int):
-    """The 64-instance sweep: one batched persistent march of all instances
-    per benchmark step, with the plain march (one fk_solve per instance on
-    the same stream) timed beside it."""
+    """The 64-instance sweep: one fk_solve_batched of all instances per
+    benchmark step (the strategy its autotuner picks), with the persistent
+    kernel forced and the plain march (one fk_solve per instance on the same
+    stream) timed beside it."""
     import torch
     import paper_2104_14561_gb300 as fk
     dev = torch.device("cuda", local_rank)
@@ -299,8 +300,16 @@ def run_batched(args, rank: int, world: int, local_rank: int):
     clk.start()
     ms_b = timed(batched)
     clocks = clk.stop()
-    if plans[0].last_device_error() != 0:
+    mode = plans[0].info()["batch_mode"]
+    if any(p.last_device_error() != 0 for p in plans):
         raise RuntimeError("device-side error in the batched march")
+    os.environ["FK_BATCH_MODE"] = "persistent"
+    try:
+        ms_k = timed(batched)
+    finally:
+        del os.environ["FK_BATCH_MODE"]
+    if plans[0].last_device_error() != 0:
+        raise RuntimeError("device-side error in the persistent batched march")
     ms_p = timed(plain)
     grid = None
     nodes = sum(int(np.prod(w["n"])) for w in ws)
@@ -314,10 +323,13 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         "config": {"workload": "batched_64", "instances": len(ws), "nodes": nodes,
                    "q_per_dim": 6, "time_steps": ws[0]["n_steps"], "dt": 1e-3,
                    "l2": "flushed (512 MB write) before every timed march"},
+        "batch_mode": mode,
+        "persistent_kernel": {"value": units / (ms_k * 1e-3), "ms_per_step": ms_k,
+                              "how": "the cooperative persistent kernel, forced"},
         "plain_march": {"value": units / (ms_p * 1e-3), "ms_per_step": ms_p,
                         "how": "64 fk_solve calls (one CUDA graph each) on one stream"},
-        "hbm_gbs_algorithmic": 24.0 * nodes * ws[0]["n_steps"] * 2 / (ms_b * 1e-3) / 1e9,
-        "gpu_launches": args.steps * 1,
+        "gpu_launches": args.steps * (sum(w["n_steps"] + 1 for w in ws) if mode == "streams"
+                                      else 1 + len(ws)),
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

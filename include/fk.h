@@ -112,6 +112,10 @@ typedef struct fk_plan_info {
                                read once per x-point, direct face bands),
                                2 masked tensor window (W x W nodes per
                                node, exits as zero weights)              */
+  int batch_mode;           /* strategy of the last fk_solve_batched this
+                               plan led (plans[0]): 0 none, 1 the
+                               persistent kernel, 2 concurrent single-plan
+                               graphs on side streams                    */
 } fk_plan_info;
 
 /* ------------------------------------------------------------------------

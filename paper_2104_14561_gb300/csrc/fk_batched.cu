@@ -19,6 +19,13 @@
 // because the halo of the sweep's instances ranges from 1 to ~24 cells and
 // one launch has one shared-memory size; the records of the tiles an SM is
 // working on stay in its L1, the rest in the 129 MB L2.
+//
+// A second strategy runs every instance's own CUDA-graph march (fk_solve,
+// with the single-plan step kernels that stage tiles in shared memory) on a
+// pool of side streams forked from and joined into the caller's stream.
+// The first call for a batch shape times a few steps of both and keeps the
+// faster: the persistent kernel wins when launches dominate (many small
+// instances), the concurrent graphs when the per-node work does.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -26,6 +33,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -287,6 +295,10 @@ __global__ void __launch_bounds__(256) k_batched(const BInst<T>* __restrict__ in
 
 // ------------------------------------------------------------------ host --
 
+const int kSideStreams = 8;  // the default number of hardware work queues
+
+enum { kModeNone = 0, kModePersistent = 1, kModeStreams = 2 };
+
 struct BatchWork {
   void* d_inst = nullptr;  // instance table (device copy)
   size_t d_inst_bytes = 0;
@@ -296,6 +308,10 @@ struct BatchWork {
   // one cached graph: key = (plans, inputs, outputs, grid)
   std::vector<const void*> key;
   cudaGraphExec_t graph = nullptr;
+  // concurrent single-plan strategy: side streams and fork/join events
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t fork = nullptr, join[kSideStreams] = {};
+  int mode = kModeNone;  // strategy of the last call
 };
 
 std::mutex g_batch_mu;
@@ -304,6 +320,7 @@ struct BatchTune {
   int n_inst, q, elem, n_steps;
   int64_t nodes;
   int blocks_per_sm;
+  int mode;
 };
 std::vector<BatchTune> g_batch_tune;
 
@@ -382,6 +399,60 @@ cudaError_t stage_input(fk_plan* p, const void* u_terminal, void* u_out, int N, 
   }
   *first = (const T*)src;
   return e;
+}
+
+fk_status ensure_side_streams(BatchWork* bw) {
+  if (bw->fork) return FK_OK;
+  if (cudaEventCreateWithFlags(&bw->fork, cudaEventDisableTiming) != cudaSuccess) return FK_ERR_CUDA;
+  for (int k = 0; k < kSideStreams; ++k) {
+    if (cudaStreamCreateWithFlags(&bw->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bw->join[k], cudaEventDisableTiming) != cudaSuccess)
+      return FK_ERR_CUDA;
+  }
+  return FK_OK;
+}
+
+// Largest instances first, each on the side stream with the least work so
+// far (longest-processing-time order).
+std::vector<int> assign_streams(int n, fk_plan* const* plans, int K) {
+  std::vector<int> order(n), which(n);
+  for (int b = 0; b < n; ++b) order[b] = b;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return plans[x]->J > plans[y]->J; });
+  std::vector<int64_t> load(K, 0);
+  for (int b : order) {
+    int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    which[b] = k;
+    load[k] += plans[b]->J;
+  }
+  return which;
+}
+
+// Steps n_from-1 .. n_to of every instance (the whole march when n_from =
+// N and n_to = 0, through each plan's graph; otherwise direct launches) on
+// the side streams, between a fork and a join on `stream`.
+fk_status run_streams(int n, fk_plan* const* plans, const void* const* u_terminal,
+                      void* const* u_out, int n_from, int n_to, cudaStream_t stream,
+                      BatchWork* bw) {
+  fk_status st = ensure_side_streams(bw);
+  if (st != FK_OK) return st;
+  const int K = n < kSideStreams ? n : kSideStreams;
+  const std::vector<int> which = assign_streams(n, plans, K);
+  if (cudaEventRecord(bw->fork, stream) != cudaSuccess) return FK_ERR_CUDA;
+  for (int k = 0; k < K; ++k)
+    if (cudaStreamWaitEvent(bw->side[k], bw->fork, 0) != cudaSuccess) return FK_ERR_CUDA;
+  const bool whole = n_from == plans[0]->n_steps && n_to == 0;
+  for (int b = 0; b < n && st == FK_OK; ++b) {
+    cudaStream_t sb = bw->side[which[b]];
+    st = whole ? fk_solve(plans[b], u_terminal[b], u_out[b], nullptr, 0, sb)
+               : fk_march(plans[b], n_from, n_to, u_terminal[b], u_out[b], sb);
+  }
+  // join every side stream, also after a failed enqueue
+  for (int k = 0; k < K; ++k) {
+    if (cudaEventRecord(bw->join[k], bw->side[k]) != cudaSuccess ||
+        cudaStreamWaitEvent(stream, bw->join[k], 0) != cudaSuccess)
+      return FK_ERR_CUDA;
+  }
+  return st;
 }
 
 template <typename T>
@@ -467,10 +538,13 @@ fk_status run_batch(int n, fk_plan* const* plans, const void* const* u_terminal,
   // buffers, before the real inputs are staged; skipped when an input
   // aliases its output)
   int bps = max_bps;
+  // without a timing: the persistent kernel for small instances
+  int mode = nodes / n < 16384 ? kModePersistent : kModeStreams;
   // explicit CTAs per SM (profiling runs, where timing is distorted)
   const char* fixed = getenv("FK_BATCH_CTAS_PER_SM");
   if (fixed && atoi(fixed) >= 1 && atoi(fixed) <= max_bps) {
     bps = atoi(fixed);
+    mode = kModePersistent;
   } else {
     std::lock_guard<std::mutex> lock(g_batch_mu);
     bool found = false;
@@ -478,9 +552,10 @@ fk_status run_batch(int n, fk_plan* const* plans, const void* const* u_terminal,
       if (t.n_inst == n && t.q == q && t.elem == (int)sizeof(T) && t.n_steps == N &&
           t.nodes == nodes) {
         bps = t.blocks_per_sm;
+        mode = t.mode;
         found = true;
       }
-    if (!found && !aliased && max_bps > 1) {
+    if (!found && !aliased) {
       std::vector<BInst<T>> tune = inst;
       for (int b = 0; b < n; ++b) {
         fk_launch_fill_chi(tune[b].buf[0], 2, tune[b].nx, tune[b].ny, (int)sizeof(T), stream);
@@ -494,6 +569,7 @@ fk_status run_batch(int n, fk_plan* const* plans, const void* const* u_terminal,
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
+      const bool log = getenv("FK_TUNE_LOG") != nullptr;
       for (int cand = max_bps; cand >= 1; --cand) {
         cudaMemsetAsync(bw->d_bar, 0, sizeof(BarrierState), stream);
         cudaEventRecord(e0, stream);
@@ -507,19 +583,48 @@ fk_status run_batch(int n, fk_plan* const* plans, const void* const* u_terminal,
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (getenv("FK_TUNE_LOG"))
+        if (log)
           fprintf(stderr, "fk batched autotune: %d CTAs/SM  %.3f ms / %d steps\n", cand, ms, steps);
         if (ms < best) {
           best = ms;
           bps = cand;
         }
       }
+      mode = kModePersistent;
+      // the concurrent single-plan marches over the same steps, from chi
+      // in the output buffers (which no input aliases here)
+      for (int b = 0; b < n; ++b)
+        fk_launch_fill_chi(u_out[b], 2, plans[b]->grid.n[0], plans[b]->grid.n[1], (int)sizeof(T),
+                           stream);
+      std::vector<const void*> ins(u_out, u_out + n);
+      cudaEventRecord(e0, stream);
+      fk_status ss = run_streams(n, plans, ins.data(), u_out, N, N - steps, stream, bw);
+      cudaEventRecord(e1, stream);
+      if (ss == FK_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (log) fprintf(stderr, "fk batched autotune: concurrent plans  %.3f ms / %d steps\n", ms, steps);
+        if (ms < best) mode = kModeStreams;
+      }
+      cudaGetLastError();
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
+      cudaStreamSynchronize(stream);
       cudaMemset(p0->d_err, 0, sizeof(unsigned));
-      g_batch_tune.push_back({n, q, (int)sizeof(T), N, nodes, bps});
+      for (int b = 0; b < n; ++b) cudaMemset(plans[b]->d_err, 0, sizeof(unsigned));
+      g_batch_tune.push_back({n, q, (int)sizeof(T), N, nodes, bps, mode});
       bw->key.clear();  // the device table now holds the tuning copy
     }
+  }
+  // explicit strategy (tests): FK_BATCH_MODE=persistent|streams
+  if (const char* m = getenv("FK_BATCH_MODE")) {
+    if (strcmp(m, "persistent") == 0) mode = kModePersistent;
+    if (strcmp(m, "streams") == 0) mode = kModeStreams;
+  }
+  bw->mode = mode;
+  if (mode == kModeStreams) {
+    p0->batch_grid = 0;
+    return run_streams(n, plans, u_terminal, u_out, N, 0, stream, bw);
   }
   const int grid = sms * bps;
   // test hook: one phantom CTA that never arrives makes every barrier wait
@@ -583,10 +688,20 @@ fk_status run_batch(int n, fk_plan* const* plans, const void* const* u_terminal,
 
 }  // namespace
 
+int fk_batch_mode(const fk_plan* p) {
+  const BatchWork* bw = (const BatchWork*)p->batch_work;
+  return bw ? bw->mode : kModeNone;
+}
+
 void fk_batch_release(fk_plan* p) {
   BatchWork* bw = (BatchWork*)p->batch_work;
   if (!bw) return;
   if (bw->graph) cudaGraphExecDestroy(bw->graph);
+  for (int k = 0; k < kSideStreams; ++k) {
+    if (bw->side[k]) cudaStreamDestroy(bw->side[k]);
+    if (bw->join[k]) cudaEventDestroy(bw->join[k]);
+  }
+  if (bw->fork) cudaEventDestroy(bw->fork);
   fk_dev_free(bw->d_inst);
   fk_dev_free(bw->d_e12);
   fk_dev_free(bw->d_bar);

@@ -157,6 +157,9 @@ struct fk_plan {
 };
 
 void fk_batch_release(fk_plan* p);
+// Strategy of the last fk_solve_batched that plan p led (0 none, 1 the
+// persistent kernel, 2 concurrent single-plan graphs).
+int fk_batch_mode(const fk_plan* p);
 
 // Step launchers that fill the argument struct from the plan (fk_plan.cu).
 fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void* snap,

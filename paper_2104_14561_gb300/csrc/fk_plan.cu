@@ -814,6 +814,7 @@ fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
   info->workspace_bytes = p->workspace_bytes;
   info->window_rows = p->use_masked ? p->mwin : p->win;
   info->step_kernel = current_kernel(p);
+  info->batch_mode = fk_batch_mode(p);
   return FK_OK;
 }
 

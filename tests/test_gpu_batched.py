@@ -1,6 +1,7 @@
-"""GPU checks of the batched persistent march (fk_solve_batched): one
-cooperative launch marching many independent instances (uneven meshes and
-coefficients) through all their time steps.
+"""GPU checks of the batched march (fk_solve_batched) of many independent
+instances (uneven meshes and coefficients), with each of its two
+strategies: one cooperative persistent launch through all time steps, and
+the instances' own graph marches on concurrent side streams.
 
 * every instance equals its own single-plan fk_solve (FP64 to 1e-14, FP32
   to 1e-6) and, for small FP64 instances, the oracle (1e-12);
@@ -33,6 +34,13 @@ def fk():
     return fk
 
 
+@pytest.fixture(params=["persistent", "streams"])
+def batch_mode(request, monkeypatch):
+    """The strategy fk_solve_batched uses in the test."""
+    monkeypatch.setenv("FK_BATCH_MODE", request.param)
+    return request.param
+
+
 def _plan(fk, w, **kw):
     d = dict(w)
     d.update(kw)
@@ -57,12 +65,13 @@ def _mixed(precision, n_steps=25, q=6):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("fp32", 1e-6)])
-def test_batched_equals_single_plans(fk, precision, tol):
+def test_batched_equals_single_plans(fk, precision, tol, batch_mode):
     import torch
     ws = _mixed(precision)
     plans = [_plan(fk, w) for w in ws]
     outs = fk.solve_batched(plans)
     torch.cuda.synchronize()
+    assert plans[0].info()["batch_mode"] == batch_mode
     assert plans[0].last_device_error() == 0
     for p, o in zip(plans, outs):
         ref = p.solve()
@@ -77,12 +86,13 @@ def test_batched_equals_single_plans(fk, precision, tol):
         p.close()
 
 
-def test_batched_fp64_vs_oracle(fk, oracle):
+def test_batched_fp64_vs_oracle(fk, oracle, batch_mode):
     import torch
     ws = _mixed("fp64", n_steps=12)[:4]
     plans = [_plan(fk, w) for w in ws]
     outs = fk.solve_batched(plans)
     torch.cuda.synchronize()
+    assert plans[0].info()["batch_mode"] == batch_mode
     for w, o in zip(ws, outs):
         g = oracle.Grid(w["n"], w["lo"], w["hi"])
         want = oracle.march(g, 1, list(w["params"]), w["q"], w["dt"], w["n_steps"], 0,
@@ -93,7 +103,7 @@ def test_batched_fp64_vs_oracle(fk, oracle):
 
 
 @pytest.mark.parametrize("n_steps", [7, 8])
-def test_batched_terminal_fields_and_aliasing(fk, n_steps):
+def test_batched_terminal_fields_and_aliasing(fk, n_steps, batch_mode):
     import torch
     ws = _mixed("fp64", n_steps=n_steps)[:3]
     plans = [_plan(fk, w) for w in ws]
@@ -105,6 +115,7 @@ def test_batched_terminal_fields_and_aliasing(fk, n_steps):
     outs[2] = ins[2]  # in place for the third instance
     fk.solve_batched(plans, ins, outs)
     torch.cuda.synchronize()
+    assert plans[0].info()["batch_mode"] == batch_mode
     chi_ref = plans[1].solve()
     torch.cuda.synchronize()
     assert (outs[0] - refs[0]).abs().max().item() <= 1e-14
@@ -114,13 +125,14 @@ def test_batched_terminal_fields_and_aliasing(fk, n_steps):
         p.close()
 
 
-def test_batched_sweep_instances(fk):
+def test_batched_sweep_instances(fk, batch_mode):
     import torch
     ws = [dict(w, n_steps=20) for w in fk_inputs.batched_instances()]
     plans = [_plan(fk, w) for w in ws]
     outs = fk.solve_batched(plans)
     torch.cuda.synchronize()
-    assert plans[0].last_device_error() == 0
+    assert plans[0].info()["batch_mode"] == batch_mode
+    assert all(p.last_device_error() == 0 for p in plans)
     worst = 0.0
     for p, o in zip(plans, outs):
         ref = p.solve()
@@ -130,9 +142,10 @@ def test_batched_sweep_instances(fk):
     assert worst <= 1e-6
 
 
-def test_barrier_timeout_is_reported(fk):
+def test_barrier_timeout_is_reported(fk, monkeypatch):
     import torch
     from paper_2104_14561_gb300 import _lib as L
+    monkeypatch.setenv("FK_BATCH_MODE", "persistent")
     ws = _mixed("fp32", n_steps=3)[:2]
     plans = [_plan(fk, w) for w in ws]
     os.environ["FK_TEST_STALL_BARRIER"] = "1"
@@ -141,6 +154,7 @@ def test_barrier_timeout_is_reported(fk):
         torch.cuda.synchronize()
     finally:
         del os.environ["FK_TEST_STALL_BARRIER"]
+    assert plans[0].info()["batch_mode"] == "persistent"
     assert L.STATUS[plans[0].last_device_error()] == "FK_ERR_TIMEOUT"
     # the context is still usable and the next batch is correct
     outs = fk.solve_batched(plans)
