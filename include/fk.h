@@ -116,6 +116,9 @@ typedef struct fk_plan_info {
                                plan led (plans[0]): 0 none, 1 the
                                persistent kernel, 2 concurrent single-plan
                                graphs on side streams                    */
+  int adjoint_kernel;       /* backward step of the last fk_adjoint: 0 none
+                               yet, 1 per-point transposed scatter, 2 masked
+                               tensor window                             */
 } fk_plan_info;
 
 /* ------------------------------------------------------------------------

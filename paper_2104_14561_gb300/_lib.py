@@ -52,7 +52,8 @@ class PlanInfo(ctypes.Structure):
                 ("halo", ctypes.c_int * 3), ("tile", ctypes.c_int * 3),
                 ("reach_cells", ctypes.c_double * 3), ("csr_nnz", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("window_rows", ctypes.c_int),
-                ("step_kernel", ctypes.c_int), ("batch_mode", ctypes.c_int)]
+                ("step_kernel", ctypes.c_int), ("batch_mode", ctypes.c_int),
+                ("adjoint_kernel", ctypes.c_int)]
 
 
 _lib = None

@@ -24,6 +24,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "fk_device.cuh"
 #include "fk_internal.h"
 
 namespace {
@@ -288,6 +289,262 @@ __global__ void __launch_bounds__(FK_THREADS) k_adj_scatter(const AdjArgs<T> g) 
   }
 }
 
+// ------------------------------------------- masked tensor-window adjoint
+// For an FP32 plan eligible for the masked step kernel the forward step is
+// u^n_j = u_j + sum_{c,r} [(u_{c,r} - u_j) phi_c Phi_r + X_{c,r} psi_c Phi_r
+//                          + Y_{c,r} phi_c Psi_r] + (1 - u_j) E
+// over the node's W x W window (X, Y the scaled slopes; phi, psi and Phi,
+// Psi the x and y Hermite weights of the node's points, exiting points
+// dropped; E the exit mass).  Its transpose is rank one per node:
+//   mu_u += lambda phi_c Phi_r,  mu_X += lambda psi_c Phi_r,  mu_Y += lambda phi_c Psi_r
+// (the explicit u_j terms cancel: the in-box weights and E sum to one).
+// The parameter derivatives need the weights' derivatives in the point
+// positions: phi^d = sum_p w_p V'(.), the same for psi, and phi^g with each
+// point scaled by its offset g_p (the sigma direction); Gx = sum (u - u_j)
+// phi^d Phi + X psi^d Phi + Y phi^d Psi, and Gy, Gxn, Gyn alike.  Two
+// passes over the window keep the weight arrays in registers: the first
+// with the x values (atomics, A_r = sum_c (u - u_j) phi_c + X psi_c and
+// B_r = sum_c Y phi_c, hence Gy and Gyn), the second with the x derivatives
+// (Gx, Gxn).
+
+// Weighted cubic Hermite node functions of one point at local position t
+// in its cell: values (v0, v1), slopes (s0, s1), and their t-derivatives.
+struct HermW {
+  float v0, v1, s0, s1, dv0, dv1, ds0, ds1;
+};
+__device__ __forceinline__ HermW herm_w(float w, float t) {
+  HermW h;
+  const float tt = t * t, omt = 1.f - t;
+  h.v1 = w * (tt * (3.f - 2.f * t));
+  h.v0 = w - h.v1;
+  h.s0 = w * (t * omt * omt);
+  h.s1 = -w * (tt * omt);
+  h.dv1 = w * (6.f * t * omt);
+  h.dv0 = -h.dv1;
+  h.ds0 = w * (omt * (1.f - 3.f * t));
+  h.ds1 = w * (t * (3.f * t - 2.f));
+  return h;
+}
+
+// A set of K weight arrays over W window slots, and the uniform scatter of
+// one point's (a, b) node pair into slots (m + beta, m + beta + 1).
+template <int W, int K>
+struct Slots {
+  float v[K][W];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int s = 0; s < W; ++s) v[k][s] = 0.f;
+  }
+};
+template <int W, int K, int M>
+struct SlotAdd {
+  __device__ __forceinline__ static void run(int m, bool beta, Slots<W, K>& S, const float (&a)[K],
+                                             const float (&b)[K]) {
+    if (m == M) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        S.v[k][M] += beta ? 0.f : a[k];
+        S.v[k][M + 1] += beta ? a[k] : b[k];
+        S.v[k][M + 2] += beta ? b[k] : 0.f;
+      }
+    } else {
+      SlotAdd<W, K, M + 1>::run(m, beta, S, a, b);
+    }
+  }
+};
+template <int W, int K>
+struct SlotAdd<W, K, W - 2> {
+  __device__ __forceinline__ static void run(int, bool, Slots<W, K>&, const float (&)[K],
+                                             const float (&)[K]) {}
+};
+
+// 1D weights of one axis over the window slots, point position z + g_q
+// after the window origin, exiting points (outside [lo, hi]) dropped.
+// K = 2: values and slopes; K = 4: their position derivatives, plain and
+// times the point's offset g_q.
+template <int Q, int W, int K>
+__device__ __forceinline__ void axis_weights(Slots<W, K>& S, const Step2D<float>& a, float z,
+                                             const float* gq_all, float lo, float hi) {
+  S.zero();
+#pragma unroll 1
+  for (int q = 0; q < Q; ++q) {
+    const float sq = z + gq_all[q], tp = sq - a.wmf[q];
+    const bool beta = tp >= 1.f;
+    const float w = (sq < lo || sq > hi) ? 0.f : a.w[q];
+    const HermW h = herm_w(w, beta ? tp - 1.f : tp);
+    if constexpr (K == 2) {
+      const float A[2] = {h.v0, h.s0}, B[2] = {h.v1, h.s1};
+      SlotAdd<W, 2, 0>::run(a.wm[q], beta, S, A, B);
+    } else {
+      const float gq = gq_all[q];
+      const float A[4] = {h.dv0, h.ds0, h.dv0 * gq, h.ds0 * gq};
+      const float B[4] = {h.dv1, h.ds1, h.dv1 * gq, h.ds1 * gq};
+      SlotAdd<W, 4, 0>::run(a.wm[q], beta, S, A, B);
+    }
+  }
+}
+
+template <int Q, int W>
+__global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<float> g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Step2D<float>& a = g.s;
+  const int lx = a.lx, ly = a.ly, lp = a.lyr;
+  float4* Rec = reinterpret_cast<float4*>(smem);
+  float* U = reinterpret_cast<float*>(Rec + ly * lp);
+  float* MU = U + ly * lp;  // 3 planes of ly x lp: mu_u, mu_X, mu_Y
+  __shared__ double red[4][FK_THREADS / 32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i0 = 1 + blockIdx.x * 32, k0 = 1 + blockIdx.y * a.ty;
+  const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;
+  for (int e = tid; e < 3 * ly * lp; e += FK_THREADS) MU[e] = 0.f;
+  masked_stage(a, Rec, U, gi0, gk0);  // ends with a barrier
+
+  double dth0 = 0.0, dth1 = 0.0, dth2 = 0.0, dth3 = 0.0;
+  unsigned bad = 0;
+  const int i = i0 + lane, li = i - gi0;
+  float* MX = MU + ly * lp;
+  float* MY = MX + ly * lp;
+#pragma unroll 1
+  for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
+    const int k = k0 + ty;
+    if (i > a.nx - 2 || k > a.ny - 2) break;
+    const float lam = g.lam[(int64_t)k * a.nx + i];
+    if (lam == 0.f) continue;
+    const int lk = k - gk0;
+    const float uj = U[lk * lp + li];
+    float dx, dy, ax[3], ay[3];
+    if (a.family == FK_CELLULAR_FLOW) {
+      const float* ct = a.col_tab + 4 * (int64_t)i;
+      const float* rt = a.row_tab + 2 * (int64_t)k;
+      dx = a.kx * rt[0] * (a.A * ct[0] + a.e1 * ct[1]);
+      dy = a.ky * rt[1] * (a.A * ct[2] + a.e2 * ct[3]);
+      const float cx = a.kx * rt[0], cy = a.ky * rt[1];
+      ax[0] = cx * ct[0];
+      ay[0] = cy * ct[2];
+      ax[1] = cx * g.st * ct[1];
+      ay[1] = cy * 2.f * g.st * ct[3];
+      ax[2] = cx * g.sw * ct[1];
+      ay[2] = cy * 2.f * g.sw * ct[3];
+    } else {
+      dx = a.cdx;
+      dy = a.cdy;
+      ax[0] = g.cbx; ay[0] = 0.f;
+      ax[1] = 0.f;   ay[1] = g.cby;
+      ax[2] = 0.f;   ay[2] = 0.f;
+    }
+    const float fx0 = floorf(dx + a.gx[0]), fy0 = floorf(dy + a.gy[0]);
+    int wx = li + (int)fx0, wy = lk + (int)fy0;
+    if (wx < 1 || wx + W - 1 > lx - 2 || wy < 1 || wy + W - 1 > ly - 2) {
+      bad = 1u;
+      wx = 1;
+      wy = 1;
+    }
+    const float zx = dx - fx0, zy = dy - fy0;
+    const float lox = -(float)i - fx0, hix = (float)(a.nx - 1 - i) - fx0;
+    const float loy = -(float)k - fy0, hiy = (float)(a.ny - 1 - k) - fy0;
+    Slots<W, 2> YV;  // Phi, Psi
+    axis_weights<Q>(YV, a, zy, a.gy, loy, hiy);
+    // pass 1: x values; the transposed scatter and the row sums
+    // A_r = sum_c (u - u_j) phi_c + X psi_c, B_r = sum_c Y phi_c
+    float AR[W], BR[W];
+    {
+      Slots<W, 2> XV;  // phi, psi
+      axis_weights<Q>(XV, a, zx, a.gx, lox, hix);
+#pragma unroll
+      for (int r = 0; r < W; ++r) {
+        const int o = (wy + r) * lp + wx;
+        const float4* row = Rec + o;
+        const float lP = lam * YV.v[0][r], lS = lam * YV.v[1][r];
+        float Ar = 0.f, Br = 0.f;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          const float4 v = row[c];
+          Ar = fmaf(XV.v[0][c], v.x - uj, fmaf(XV.v[1][c], v.y, Ar));
+          Br = fmaf(XV.v[0][c], v.z, Br);
+          atomicAdd(&MU[o + c], lP * XV.v[0][c]);
+          atomicAdd(&MX[o + c], lP * XV.v[1][c]);
+          atomicAdd(&MY[o + c], lS * XV.v[0][c]);
+        }
+        AR[r] = Ar;
+        BR[r] = Br;
+      }
+    }
+    // y-side derivatives from the row sums
+    float Gy = 0.f, Gyn = 0.f, Gx = 0.f, Gxn = 0.f;
+    {
+      Slots<W, 4> YD;
+      axis_weights<Q>(YD, a, zy, a.gy, loy, hiy);
+#pragma unroll
+      for (int r = 0; r < W; ++r) {
+        Gy = fmaf(YD.v[0][r], AR[r], fmaf(YD.v[1][r], BR[r], Gy));
+        Gyn = fmaf(YD.v[2][r], AR[r], fmaf(YD.v[3][r], BR[r], Gyn));
+      }
+    }
+    // pass 2: x derivatives (and x derivatives x g_p) against the y values
+    {
+      Slots<W, 4> XD;
+      axis_weights<Q>(XD, a, zx, a.gx, lox, hix);
+#pragma unroll
+      for (int r = 0; r < W; ++r) {
+        const float4* row = Rec + (wy + r) * lp + wx;
+        float Ad = 0.f, Bd = 0.f, Ag = 0.f, Bg = 0.f;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          const float4 v = row[c];
+          const float e = v.x - uj;
+          Ad = fmaf(XD.v[0][c], e, fmaf(XD.v[1][c], v.y, Ad));
+          Bd = fmaf(XD.v[0][c], v.z, Bd);
+          Ag = fmaf(XD.v[2][c], e, fmaf(XD.v[3][c], v.y, Ag));
+          Bg = fmaf(XD.v[2][c], v.z, Bg);
+        }
+        Gx = fmaf(YV.v[0][r], Ad, fmaf(YV.v[1][r], Bd, Gx));
+        Gxn = fmaf(YV.v[0][r], Ag, fmaf(YV.v[1][r], Bg, Gxn));
+      }
+    }
+    const double l = (double)lam;
+    dth0 += l * ((double)ax[0] * Gx + (double)ay[0] * Gy);
+    dth1 += l * ((double)ax[1] * Gx + (double)ay[1] * Gy);
+    dth2 += l * ((double)ax[2] * Gx + (double)ay[2] * Gy);
+    dth3 += l * (double)g.cn * ((double)Gxn + (double)Gyn);
+  }
+  if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
+  __syncthreads();
+  // flush the tile's accumulators (halo included) into the global mu
+  const int64_t J = (int64_t)a.nx * a.ny;
+  for (int r = warp; r < ly; r += FK_THREADS / 32) {
+    const int gk = gk0 + r;
+    if (gk < 0 || gk >= a.ny) continue;
+    for (int c = lane; c < lx; c += 32) {
+      const int gi = gi0 + c;
+      if (gi < 0 || gi >= a.nx) continue;
+      const int64_t j = (int64_t)gk * a.nx + gi;
+      const int o = r * lp + c;
+      const float m0 = MU[o], m1 = MX[o], m2 = MY[o];
+      if (m0 != 0.f) atomicAdd(&g.mu[j], m0);
+      if (m1 != 0.f) atomicAdd(&g.mu[J + j], m1);
+      if (m2 != 0.f) atomicAdd(&g.mu[2 * J + j], m2);
+    }
+  }
+  dth0 = warp_sum(dth0);
+  dth1 = warp_sum(dth1);
+  dth2 = warp_sum(dth2);
+  dth3 = warp_sum(dth3);
+  if (lane == 0) {
+    red[0][warp] = dth0;
+    red[1][warp] = dth1;
+    red[2][warp] = dth2;
+    red[3][warp] = dth3;
+  }
+  __syncthreads();
+  if (tid < 4) {
+    double sum = 0.0;
+    for (int w = 0; w < FK_THREADS / 32; ++w) sum += red[tid][w];
+    if (sum != 0.0) atomicAdd(&g.dth[tid], sum);
+  }
+}
+
 // d(scaled slope at m)/d u_i along one line, with the end rule
 template <typename T>
 __device__ __forceinline__ T dslope(const T* u, int64_t stride, int n, int m, int i) {
@@ -383,6 +640,54 @@ cudaError_t launch_adj(const AdjArgs<T>& g, int q, cudaStream_t s) {
   }
 }
 
+size_t adj_masked_smem(int ly, int lp) { return (size_t)ly * lp * (16 + 4 + 12); }
+
+template <int Q, int W>
+cudaError_t launch_adj_masked_qw(const AdjArgs<float>& g, cudaStream_t s) {
+  const size_t smem = adj_masked_smem(g.s.ly, g.s.lyr);
+  static bool set = false;
+  if (!set) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_adj_masked<Q, W>);
+    int dev = 0, optin = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_adj_masked<Q, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    set = true;
+  }
+  dim3 grid((g.s.nx - 2 + 31) / 32, (g.s.ny - 2 + g.s.ty - 1) / g.s.ty);
+  k_adj_masked<Q, W><<<grid, FK_THREADS, smem, s>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_masked(const AdjArgs<float>& g, int q, cudaStream_t s) {
+#define FK_M(QQ, WW) \
+  if (q == QQ && g.s.win == WW) return launch_adj_masked_qw<QQ, WW>(g, s);
+  FK_MASKED_LIST(FK_M)
+#undef FK_M
+  return cudaErrorInvalidValue;
+}
+
+// Whether the backward steps of plan p use the masked window form (FP32
+// plans eligible for the masked step kernel; FK_ADJ_KERNEL=scatter|masked
+// chooses explicitly where both apply), and its tile height.
+bool adj_use_masked(const fk_plan* p) {
+  if (p->prec != FK_FP32 || p->mwin <= 0) return false;
+  const char* k = getenv("FK_ADJ_KERNEL");
+  return !(k && strcmp(k, "scatter") == 0);
+}
+int adj_masked_ty(const fk_plan* p, int smem_max) {
+  const int lx = 32 + 2 * p->mhalo[0] + 2;
+  for (int ty = 16; ty >= 4; ty -= 4)
+    if (adj_masked_smem(ty + 2 * p->mhalo[1] + 2, lx | 1) + kAdjStatic <= (size_t)smem_max)
+      return ty;
+  return 0;
+}
+
 template <typename T>
 fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* lam_out,
                    double* dth, int ty, cudaStream_t s) {
@@ -417,7 +722,29 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
     g.cby = (T)(p->dt / p->h[1]);
     g.cn = (T)(p->coeffs.p[3] > 0.0 ? 1.0 / p->coeffs.p[3] : 0.0);  // sigma = s
   }
-  cudaError_t e = launch_adj<T>(g, p->q, s);
+  cudaError_t e;
+  if constexpr (sizeof(T) == 4) {
+    if (adj_use_masked(p)) {
+      // the masked window's layout: halo, row-major records, cell offsets
+      g.s.mode = 2;
+      g.s.win = p->mwin;
+      g.s.hx = p->mhalo[0];
+      g.s.hy = p->mhalo[1];
+      g.s.lx = g.s.tx + 2 * g.s.hx + 2;
+      g.s.ty = p->adj_ty;
+      g.s.ly = g.s.ty + 2 * g.s.hy + 2;
+      g.s.lyr = g.s.lx | 1;
+      for (int q = 0; q < p->q; ++q) {
+        g.s.wm[q] = p->mwm[q];
+        g.s.wmf[q] = (T)p->mwm[q];
+      }
+      e = launch_adj_masked((const AdjArgs<float>&)g, p->q, s);
+    } else {
+      e = launch_adj<T>(g, p->q, s);
+    }
+  } else {
+    e = launch_adj<T>(g, p->q, s);
+  }
   if (e != cudaSuccess) return FK_ERR_CUDA;
   const dim3 b(32, 8), gr((p->grid.n[0] + 31) / 32, (p->grid.n[1] + 7) / 8);
   k_adj_slopes_t<T><<<gr, b, 0, s>>>((const T*)u_in, (const T*)p->adj_mu, (T*)lam_out,
@@ -454,6 +781,9 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
     if (adj_smem(32 + 2 * p->halo[0] + 2, ly, ly | 1, p->elem) + kAdjStatic > (size_t)smem_max)
       return FK_ERR_UNSUPPORTED;
   }
+  p->adj_ty = adj_use_masked(p) ? adj_masked_ty(p, smem_max) : 0;
+  if (adj_use_masked(p) && p->adj_ty == 0) return FK_ERR_UNSUPPORTED;
+  p->adj_kernel = adj_use_masked(p) ? 2 : 1;
   // workspace: checkpoints (M+1), a segment (K), lambda x2, mu (3 fields), dtheta
   const int64_t need = (int64_t)(M + 1 + K + 2 + 3) * fb + 64;
   if (p->adj_bytes < need) {

@@ -52,4 +52,80 @@ __device__ __forceinline__ void write_adjacent_boundary(const Step2D<T>& a, int 
   }
 }
 
+
+// Staging of the masked tensor-window kernels (the step and its adjoint),
+// for a CTA of FK_THREADS threads whose staged node (0, 0) is global node
+// (gi0, gk0); a.lx x a.ly nodes, row pitch a.lyr (odd).  Ends with the
+// records visible to the whole CTA.
+__device__ __forceinline__ void masked_stage(const Step2D<float>& a, float4* Rec, float* U,
+                                             int gi0, int gk0) {
+  const int lx = a.lx, ly = a.ly, lp = a.lyr;
+  const int tid = threadIdx.x;
+  // 1. u^{n+1} over the tile and halo, row-major with pitch lp (zero
+  // outside the mesh): rows by warp, columns by lane, so global reads are
+  // coalesced and shared-memory writes consecutive
+  {
+    const uint32_t sU = (uint32_t)__cvta_generic_to_shared(U);
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int r = warp; r < ly; r += FK_THREADS / 32) {
+      const int gk = gk0 + r;
+      const bool rowin = (unsigned)gk < (unsigned)a.ny;
+      const float* src = a.u_in + (int64_t)(rowin ? gk : 0) * a.nx;
+      const uint32_t drow = sU + (uint32_t)(r * lp) * 4u;
+      for (int c = lane; c < lx; c += 32) {
+        const int gi = gi0 + c;
+        const bool in = rowin && (unsigned)gi < (unsigned)a.nx;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c),
+                     "l"(in ? src + gi : a.u_in), "r"(in ? 4 : 0));
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+  }
+
+  // 2. records {u, h u_x, h u_y, 0} of staged nodes 1..lx-2 x 1..ly-2, by
+  // vertical sweeps: thread t owns column 1 + t % hc and a segment of rows,
+  // carrying u of the rows above and below in registers.  The end rule
+  // stated after Eq. (e300) gives node 0 the slope of node 1 and node n-1
+  // that of node n-2 (the harmonic mean is symmetric): an end column takes
+  // its x-differences one column inwards, and the end rows copy the y-slope
+  // of their neighbour row afterwards.  Nodes outside the mesh get finite
+  // values from the zero fill; they only ever carry weight 0.
+  {
+    const int hc = lx - 2, hr = ly - 2;
+    const int nseg = FK_THREADS / hc;  // hc <= 256: lx <= 258
+    const int seg = tid / hc, c = 1 + (tid - seg * hc);
+    if (seg < nseg) {
+      const int len = (hr + nseg - 1) / nseg;
+      const int r0 = 1 + seg * len, r1 = min(r0 + len, hr + 1);
+      const int gi = gi0 + c;
+      const int ax = c + (gi == 0) - (gi == a.nx - 1);
+      const float* col = U + c;
+      const float* colx = U + ax;
+      float up = col[(r0 - 1) * lp], uc = col[r0 * lp];
+      for (int r = r0; r < r1; ++r) {
+        const float un = col[(r + 1) * lp];
+        const float* rx = colx + r * lp;
+        const float X = pchip_fast(rx[0] - rx[-1], rx[1] - rx[0]);
+        const float Y = pchip_fast(uc - up, un - uc);
+        Rec[r * lp + c] = make_float4(uc, X, Y, 0.f);
+        up = uc;
+        uc = un;
+      }
+    }
+    __syncthreads();
+    // y end rule: staged rows of mesh rows 0 and ny-1 take their neighbour's y-slope
+    const int rb = -gk0, rt = a.ny - 1 - gk0;
+    const bool fb = rb >= 1 && rb <= hr, ft = rt >= 1 && rt <= hr;
+    if (fb || ft) {
+      for (int e = tid; e < hc; e += FK_THREADS) {
+        if (fb) Rec[rb * lp + 1 + e].z = Rec[(rb + 1) * lp + 1 + e].z;
+        if (ft) Rec[rt * lp + 1 + e].z = Rec[(rt - 1) * lp + 1 + e].z;
+      }
+      __syncthreads();
+    }
+  }
+
+}
+
 }  // namespace

@@ -98,6 +98,13 @@ cudaError_t fk_launch_step2dm(const Step2D<float>& a, int q, cudaStream_t s);
 size_t fk_step2dm_smem(int ly, int lp);  // ly staged rows of pitch lp
 bool fk_masked_available(int q, int w);
 cudaError_t fk_prepare_masked_kernels(int q);
+// (Q, W) pairs built: the window form pays off while W^2 cells stay below
+// the direct form's 4 Q^2 corner reads and its weights fit in registers.
+#define FK_MASKED_LIST(X)                                                  \
+  X(4, 3) X(4, 4) X(4, 5) X(4, 6) X(4, 7)                                  \
+  X(6, 3) X(6, 4) X(6, 5) X(6, 6) X(6, 7) X(6, 8) X(6, 9)                  \
+  X(8, 3) X(8, 4) X(8, 5) X(8, 6) X(8, 7) X(8, 8) X(8, 9)
+
 cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s);
 cudaError_t fk_launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
 
@@ -154,6 +161,8 @@ struct fk_plan {
   void* adj_ws;
   int64_t adj_bytes;
   void* adj_mu;      // 3 J accumulators inside adj_ws
+  int adj_ty;        // tile height of the masked-window adjoint (0: per-point scatter)
+  int adj_kernel;    // backward form of the last fk_adjoint: 0 none, 1 scatter, 2 masked
 };
 
 void fk_batch_release(fk_plan* p);

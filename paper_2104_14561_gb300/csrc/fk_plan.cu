@@ -815,6 +815,7 @@ fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
   info->window_rows = p->use_masked ? p->mwin : p->win;
   info->step_kernel = current_kernel(p);
   info->batch_mode = fk_batch_mode(p);
+  info->adjoint_kernel = p->adj_kernel;
   return FK_OK;
 }
 

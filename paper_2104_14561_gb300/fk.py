@@ -90,7 +90,8 @@ class Plan:
                 "csr_nnz": i.csr_nnz, "workspace_bytes": i.workspace_bytes,
                 "window_rows": i.window_rows,
                 "step_kernel": ("direct", "window", "masked")[i.step_kernel],
-                "batch_mode": ("none", "persistent", "streams")[i.batch_mode]}
+                "batch_mode": ("none", "persistent", "streams")[i.batch_mode],
+                "adjoint_kernel": ("none", "scatter", "masked")[i.adjoint_kernel]}
 
     def _check_field(self, t: torch.Tensor, name: str):
         if t.dtype != self.dtype or t.device.type != "cuda" or tuple(t.shape) != self.shape \

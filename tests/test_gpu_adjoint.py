@@ -41,7 +41,7 @@ def _spec(fk, w, precision):
                        precision=precision)
 
 
-def _gpu_adjoint(fk, w, precision, cot, u0=None, K=50):
+def _gpu_adjoint(fk, w, precision, cot, u0=None, K=50, kernel=None):
     import torch
     plan = fk.Plan(_spec(fk, w, precision))
     ut = None if u0 is None else torch.tensor(u0, dtype=plan.dtype, device="cuda")
@@ -49,6 +49,8 @@ def _gpu_adjoint(fk, w, precision, cot, u0=None, K=50):
     dth, du = plan.adjoint(g, ut, checkpoint_every=K)
     torch.cuda.synchronize()
     assert plan.last_device_error() == 0
+    if kernel is not None:
+        assert plan.info()["adjoint_kernel"] == kernel
     r = dth.cpu().numpy(), du.double().cpu().numpy()
     plan.close()
     return r
@@ -83,6 +85,32 @@ def test_adjoint_fp32_vs_oracle(fk, oracle):
     print(f"FP32 adjoint vs FP64 oracle adjoint: relative errors {rel}")
     assert rel.max() <= 1e-3
     assert np.abs(du - odu).max() <= 1e-3 * np.abs(odu).max()
+
+
+# 41 x 21 mesh, 6 x 6 points, reach about three cells: a 7 x 7 window for
+# the masked form, and exits along x, y and both at most nodes
+EXITS = dict(n=(41, 21), lo=(0.0, 0.0), hi=(2.0, 1.0), family="cellular_flow",
+             params=(1.0, 0.2, 2 * math.pi, 0.05), q=6, dt=1e-2, n_steps=20)
+
+
+@pytest.mark.parametrize("kernel", ["masked", "scatter"])
+def test_adjoint_fp32_forms_vs_oracle(fk, oracle, monkeypatch, kernel):
+    """Both FP32 backward forms (masked tensor window, per-point transposed
+    scatter) against the FP64 oracle adjoint, from a random terminal field."""
+    monkeypatch.setenv("FK_ADJ_KERNEL", kernel)
+    w = EXITS
+    shape = (w["n"][1], w["n"][0])
+    cot = np.random.default_rng(6).standard_normal(shape)
+    u0 = fk_inputs.random_field(shape, seed=7)
+    dth, du = _gpu_adjoint(fk, w, "fp32", cot, u0, K=7, kernel=kernel)
+    g = oracle.Grid(w["n"], w["lo"], w["hi"])
+    odth, odu = oracle.adjoint(g, oracle.CELLULAR_FLOW, list(w["params"]), w["q"], w["dt"],
+                               w["n_steps"], cot, u0)
+    rel = np.abs(dth - odth) / np.abs(odth)
+    print(f"{kernel}: FP32 adjoint vs FP64 oracle, parameters rel {rel}, "
+          f"terminal field max-abs {np.abs(du - odu).max():.2e} (scale {np.abs(odu).max():.2e})")
+    assert rel.max() <= 1e-3
+    assert np.abs(du - odu).max() <= 1e-4 * np.abs(odu).max()
 
 
 def test_adjoint_checkpoint_interval(fk):
