@@ -111,7 +111,9 @@ typedef struct fk_plan_info {
                                Hermite evaluation), 1 row window (y-rows
                                read once per x-point, direct face bands),
                                2 masked tensor window (W x W nodes per
-                               node, exits as zero weights)              */
+                               node, exits as zero weights); 1D: 0 one
+                               launch per step, 3 the whole march in one
+                               CTA's shared memory                       */
   int batch_mode;           /* strategy of the last fk_solve_batched this
                                plan led (plans[0]): 0 none, 1 the
                                persistent kernel, 2 concurrent single-plan

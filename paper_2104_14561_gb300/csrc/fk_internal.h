@@ -105,6 +105,14 @@ cudaError_t fk_prepare_masked_kernels(int q);
   X(6, 3) X(6, 4) X(6, 5) X(6, 6) X(6, 7) X(6, 8) X(6, 9)                  \
   X(8, 3) X(8, 4) X(8, 5) X(8, 6) X(8, 7) X(8, 8) X(8, 9)
 
+// 1D march resident in one CTA (fk_march1d.cu): all `steps` steps of
+// Scheme 1 from u_in (NULL = chi) into u_out (may alias u_in), snapshots
+// every `stride` steps when snaps != NULL.
+size_t fk_march1d_smem(int nx, int elem);
+template <typename T>
+cudaError_t fk_launch_march1d(const Step1D<T>& a, int q, const T* u_in, T* u_out, T* snaps,
+                              int stride, int steps, cudaStream_t s);
+cudaError_t fk_prepare_march1d(int q, int elem);
 cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s);
 cudaError_t fk_launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
 
@@ -132,6 +140,7 @@ struct fk_plan {
   int mwm[FK_MAXQ_2D];  // its cell offsets floor(g_q - g_0), equal on both axes
   int mhalo[2];      // its halo per axis
   int use_masked;    // the masked kernel is the step kernel
+  int resident1d;    // 1D: the whole march in one CTA (fk_march1d.cu)
   double gh_a[FK_MAXQ], gh_w[FK_MAXQ];
   // device memory owned by the plan
   void* scratch;     // one field

@@ -630,6 +630,21 @@ fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void
     if (u_in != u_out) return cuda_status(fk_launch_copy(u_out, u_in, bytes, s));
     return FK_OK;
   }
+  if (p->grid.dim == 1 && p->resident1d) {
+    cudaError_t e;
+    if (p->prec == FK_FP32) {
+      Step1D<float> a;
+      fill1d<float>(p, &a);
+      e = fk_launch_march1d<float>(a, p->q, (const float*)u_in, (float*)u_out, (float*)snaps,
+                                   stride, steps, s);
+    } else {
+      Step1D<double> a;
+      fill1d<double>(p, &a);
+      e = fk_launch_march1d<double>(a, p->q, (const double*)u_in, (double*)u_out, (double*)snaps,
+                                    stride, steps, s);
+    }
+    return cuda_status(e);
+  }
   const bool first_to_out = ((steps - 1) % 2) == 0;  // does step 1 write u_out?
   const void* src = u_in;
   if (!src) {
@@ -741,6 +756,16 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   st = choose_tiles(p);
   if (st == FK_OK && path == FK_PATH_MATRIX_FREE)
     st = cuda_status(fk_prepare_step_kernels(grid->dim, q_per_dim, p->elem));
+  if (st == FK_OK && grid->dim == 1) {
+    // an FP32 1D mesh whose field, second buffer and slopes fit one CTA's
+    // shared memory marches in that CTA (FK_1D_KERNEL=step keeps one launch
+    // per step; FP64 always does: at GB300's FP64 rate one SM is slower
+    // than the per-step kernel spread over several)
+    const char* k = getenv("FK_1D_KERNEL");
+    const bool step = k && strcmp(k, "step") == 0;
+    p->resident1d = !step && prec == FK_FP32 && fk_march1d_smem(grid->n[0], p->elem) <= 200 * 1024;
+    if (p->resident1d) st = cuda_status(fk_prepare_march1d(q_per_dim, p->elem));
+  }
   if (st == FK_OK) st = fk_dev_alloc(p, (void**)&p->d_err, sizeof(unsigned));
   if (st == FK_OK) st = cuda_status(cudaMemset(p->d_err, 0, sizeof(unsigned)));
   if (st == FK_OK) st = fk_dev_alloc(p, &p->scratch, (size_t)(p->J * p->elem));
@@ -813,7 +838,7 @@ fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
   info->csr_nnz = p->csr_nnz;
   info->workspace_bytes = p->workspace_bytes;
   info->window_rows = p->use_masked ? p->mwin : p->win;
-  info->step_kernel = current_kernel(p);
+  info->step_kernel = p->grid.dim == 1 ? (p->resident1d ? 3 : 0) : current_kernel(p);
   info->batch_mode = fk_batch_mode(p);
   info->adjoint_kernel = p->adj_kernel;
   return FK_OK;

@@ -63,6 +63,19 @@ def _gpu_solve(fk, w, u_terminal=None):
     return res
 
 
+def _gpu_solve_info(fk, w, u_terminal=None):
+    import torch
+    plan = fk.Plan(_spec(fk, w))
+    info = plan.info()
+    ut = None if u_terminal is None else torch.tensor(u_terminal, dtype=plan.dtype, device="cuda")
+    out = plan.solve(ut)
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    res = out.double().cpu().numpy()
+    plan.close()
+    return res, info
+
+
 def _small2d(q, precision, family="cellular_flow", n_steps=20, n=(77, 41)):
     w = fk_inputs.workload("cellular_1025x513", n=n, q=q, n_steps=n_steps,
                            precision=precision, params=(1.0, 0.2, 2 * math.pi, 0.02))
@@ -77,6 +90,14 @@ def test_gauss_hermite_matches_oracle(fk, oracle):
         ao, wo = oracle.gauss_hermite(q)
         np.testing.assert_allclose(a, ao, atol=2e-14)
         np.testing.assert_allclose(w, wo, atol=2e-15)
+
+
+@pytest.fixture(params=["resident", "step"])
+def kernel1d(request, monkeypatch):
+    """1D path of the test's plans: the march in one CTA, or one launch per step."""
+    if request.param == "step":
+        monkeypatch.setenv("FK_1D_KERNEL", "step")
+    return request.param
 
 
 def test_bm1d_drift_fp64_full_march(fk, oracle):
@@ -283,19 +304,6 @@ def masked_kernel(monkeypatch):
     monkeypatch.setenv("FK_STEP_KERNEL", "masked")
 
 
-def _gpu_solve_info(fk, w, u_terminal=None):
-    import torch
-    plan = fk.Plan(_spec(fk, w))
-    info = plan.info()
-    ut = None if u_terminal is None else torch.tensor(u_terminal, dtype=plan.dtype, device="cuda")
-    out = plan.solve(ut)
-    torch.cuda.synchronize()
-    assert plan.last_device_error() == 0
-    res = out.double().cpu().numpy()
-    plan.close()
-    return res, info
-
-
 # isotropic meshes on [0,2]x[0,1] (equal cell offsets on both axes), window
 # widths 3..9, reach from under one cell to about three cells, so that
 # exits along x, along y and along both occur on many nodes
@@ -361,3 +369,52 @@ def test_masked_kernel_equals_direct(fk, monkeypatch):
 def test_masked_kernel_full_march_vs_golden(fk, monkeypatch):
     monkeypatch.setenv("FK_STEP_KERNEL", "masked")
     test_cellular_1025x513_fp32_full_march(fk)
+
+
+def test_1d_resident_snapshots_and_resume(fk):
+    """The one-CTA 1D march: snapshots every 3 steps equal the per-step
+    path's, FP32 and FP64, and a resumed march (fk_march from a snapshot,
+    in place) ends where the full march does."""
+    import torch
+    for precision in ("fp64", "fp32"):
+        w = fk_inputs.workload("bm1d_drift", n=(301,), n_steps=20, precision=precision)
+        res = {}
+        for kern in ("resident", "step"):
+            if kern == "step":
+                os.environ["FK_1D_KERNEL"] = "step"
+            try:
+                plan = fk.Plan(_spec(fk, w))
+            finally:
+                os.environ.pop("FK_1D_KERNEL", None)
+            u0 = torch.tensor(fk_inputs.random_field((301,), seed=5), dtype=plan.dtype,
+                              device="cuda")
+            snaps = torch.empty((6, 301), dtype=plan.dtype, device="cuda")
+            out = plan.solve(u0, snapshots=snaps, snapshot_stride=3)
+            resumed = snaps[3].clone()  # u after 12 steps, i.e. u^8
+            plan.march(8, 0, resumed, out=resumed)
+            torch.cuda.synchronize()
+            resident = kern == "resident" and precision == "fp32"  # FP64: per step always
+            assert plan.info()["step_kernel"] == ("resident" if resident else "direct")
+            assert torch.equal(resumed, out)
+            res[kern] = (out.double().cpu().numpy(), snaps.double().cpu().numpy())
+            plan.close()
+        tol = 1e-14 if precision == "fp64" else 1e-6
+        assert np.abs(res["resident"][0] - res["step"][0]).max() <= tol
+        assert np.abs(res["resident"][1] - res["step"][1]).max() <= tol
+
+
+@pytest.mark.parametrize("n,q,dt,n_steps", [
+    ((201,), 8, 1e-3, 1000),   # the 1D workload in FP32
+    ((1500,), 12, 1e-3, 7),
+    ((3,), 8, 1e-3, 4),        # one interior node
+    ((11,), 8, 0.5, 4),        # reach far beyond the mesh: most points exit
+])
+def test_1d_fp32_vs_oracle(fk, oracle, kernel1d, n, q, dt, n_steps):
+    """FP32 1D march, one CTA for the whole march or one launch per step,
+    against the FP64 oracle from a random terminal field."""
+    w = fk_inputs.workload("bm1d_drift", n=n, q=q, dt=dt, n_steps=n_steps, precision="fp32")
+    u0 = fk_inputs.random_field(n, seed=q)
+    got, info = _gpu_solve_info(fk, w, u0)
+    assert info["step_kernel"] == ("resident" if kernel1d == "resident" else "direct")
+    want = _oracle_march(oracle, w, w["n_steps"], 0, u0)
+    assert np.abs(got - want).max() <= TOL32
