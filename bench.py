@@ -504,7 +504,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         peak_flops = (SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 if w["precision"] == "fp32"
                       else FP64_PEAK_TFLOPS * 1e12)
         achieved = flops_launch / (launch_ms * 1e-3)
-        kname = (("k_march1d" if info.get("step_kernel") == "resident" else "k_step1d")
+        kname = ({"resident": "k_march1d", "cluster": "k_march1d_cluster"}.get(
+                     info.get("step_kernel"), "k_step1d")
                  if len(w["n"]) == 1 else
                  {"direct": "k_step2d", "window": "k_step2dw",
                   "masked": "k_step2dm"}[info.get("step_kernel", "direct")])
@@ -528,7 +529,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,
                 "d2h_bytes_per_step": field_bytes},
-        "gpu_launches": args.steps * (1 if info.get("step_kernel") == "resident" else
+        "gpu_launches": args.steps * (1 if info.get("step_kernel") in ("resident", "cluster") else
                                       (2 if w["path"] == "csr" else 1) * w["n_steps"] + 1),
         "clocks": clocks,
         "wall_s_timed_region": wall,

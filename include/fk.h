@@ -113,7 +113,8 @@ typedef struct fk_plan_info {
                                2 masked tensor window (W x W nodes per
                                node, exits as zero weights); 1D: 0 one
                                launch per step, 3 the whole march in one
-                               CTA's shared memory                       */
+                               CTA's shared memory, 4 in one thread-block
+                               cluster (distributed shared memory)       */
   int batch_mode;           /* strategy of the last fk_solve_batched this
                                plan led (plans[0]): 0 none, 1 the
                                persistent kernel, 2 concurrent single-plan

@@ -113,6 +113,11 @@ template <typename T>
 cudaError_t fk_launch_march1d(const Step1D<T>& a, int q, const T* u_in, T* u_out, T* snaps,
                               int stride, int steps, cudaStream_t s);
 cudaError_t fk_prepare_march1d(int q, int elem);
+// The same march over a cluster of `ctas` CTAs (distributed shared memory).
+template <typename T>
+cudaError_t fk_launch_march1d_cluster(const Step1D<T>& a, int q, int ctas, const T* u_in,
+                                      T* u_out, T* snaps, int stride, int steps, cudaStream_t s);
+int fk_prepare_march1d_cluster(int q, int elem);
 cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s);
 cudaError_t fk_launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
 
@@ -140,7 +145,9 @@ struct fk_plan {
   int mwm[FK_MAXQ_2D];  // its cell offsets floor(g_q - g_0), equal on both axes
   int mhalo[2];      // its halo per axis
   int use_masked;    // the masked kernel is the step kernel
-  int resident1d;    // 1D: the whole march in one CTA (fk_march1d.cu)
+  int resident1d;    // 1D: 0 one launch per step, 1 the whole march in one CTA,
+                     // 2 in one cluster of cluster1d CTAs (fk_march1d.cu)
+  int cluster1d;
   double gh_a[FK_MAXQ], gh_w[FK_MAXQ];
   // device memory owned by the plan
   void* scratch;     // one field

@@ -632,16 +632,21 @@ fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void
   }
   if (p->grid.dim == 1 && p->resident1d) {
     cudaError_t e;
+    const int c = p->resident1d == 2 ? p->cluster1d : 0;
     if (p->prec == FK_FP32) {
       Step1D<float> a;
       fill1d<float>(p, &a);
-      e = fk_launch_march1d<float>(a, p->q, (const float*)u_in, (float*)u_out, (float*)snaps,
-                                   stride, steps, s);
+      e = c ? fk_launch_march1d_cluster<float>(a, p->q, c, (const float*)u_in, (float*)u_out,
+                                               (float*)snaps, stride, steps, s)
+            : fk_launch_march1d<float>(a, p->q, (const float*)u_in, (float*)u_out,
+                                       (float*)snaps, stride, steps, s);
     } else {
       Step1D<double> a;
       fill1d<double>(p, &a);
-      e = fk_launch_march1d<double>(a, p->q, (const double*)u_in, (double*)u_out, (double*)snaps,
-                                    stride, steps, s);
+      e = c ? fk_launch_march1d_cluster<double>(a, p->q, c, (const double*)u_in, (double*)u_out,
+                                                (double*)snaps, stride, steps, s)
+            : fk_launch_march1d<double>(a, p->q, (const double*)u_in, (double*)u_out,
+                                        (double*)snaps, stride, steps, s);
     }
     return cuda_status(e);
   }
@@ -757,14 +762,30 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   if (st == FK_OK && path == FK_PATH_MATRIX_FREE)
     st = cuda_status(fk_prepare_step_kernels(grid->dim, q_per_dim, p->elem));
   if (st == FK_OK && grid->dim == 1) {
-    // an FP32 1D mesh whose field, second buffer and slopes fit one CTA's
-    // shared memory marches in that CTA (FK_1D_KERNEL=step keeps one launch
-    // per step; FP64 always does: at GB300's FP64 rate one SM is slower
-    // than the per-step kernel spread over several)
+    // The whole 1D march in one launch: FP32 in one CTA when the field, its
+    // second buffer and the slopes fit its shared memory; FP64 over a
+    // cluster of up to 16 CTAs (at GB300's FP64 rate one SM is slower than
+    // one launch per step spread over several SMs), about 16 nodes per CTA.
+    // FK_1D_KERNEL=step|resident|cluster chooses explicitly (tests).
     const char* k = getenv("FK_1D_KERNEL");
-    const bool step = k && strcmp(k, "step") == 0;
-    p->resident1d = !step && prec == FK_FP32 && fk_march1d_smem(grid->n[0], p->elem) <= 200 * 1024;
-    if (p->resident1d) st = cuda_status(fk_prepare_march1d(q_per_dim, p->elem));
+    const int nx = grid->n[0];
+    int want = prec == FK_FP32 ? 1 : 2;
+    if (k && strcmp(k, "step") == 0) want = 0;
+    if (k && strcmp(k, "resident") == 0) want = 1;
+    if (k && strcmp(k, "cluster") == 0) want = 2;
+    if (want == 1 && fk_march1d_smem(nx, p->elem) <= 200 * 1024) {
+      st = cuda_status(fk_prepare_march1d(q_per_dim, p->elem));
+      if (st == FK_OK) p->resident1d = 1;
+    } else if (want == 2) {
+      const int maxc = fk_prepare_march1d_cluster(q_per_dim, p->elem);
+      int c = (nx + 15) / 16;
+      if (c > maxc) c = maxc;
+      const int chunk = c > 0 ? (nx + c - 1) / c : 0, L = chunk + 2 * (p->halo[0] + 2);
+      if (c >= 1 && (size_t)(3 * L + chunk * q_per_dim) * p->elem <= 200 * 1024) {
+        p->resident1d = 2;
+        p->cluster1d = c;
+      }
+    }
   }
   if (st == FK_OK) st = fk_dev_alloc(p, (void**)&p->d_err, sizeof(unsigned));
   if (st == FK_OK) st = cuda_status(cudaMemset(p->d_err, 0, sizeof(unsigned)));
@@ -838,7 +859,8 @@ fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
   info->csr_nnz = p->csr_nnz;
   info->workspace_bytes = p->workspace_bytes;
   info->window_rows = p->use_masked ? p->mwin : p->win;
-  info->step_kernel = p->grid.dim == 1 ? (p->resident1d ? 3 : 0) : current_kernel(p);
+  info->step_kernel = p->grid.dim == 1 ? (p->resident1d ? 2 + p->resident1d : 0)
+                                        : current_kernel(p);
   info->batch_mode = fk_batch_mode(p);
   info->adjoint_kernel = p->adj_kernel;
   return FK_OK;

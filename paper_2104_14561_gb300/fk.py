@@ -89,7 +89,7 @@ class Plan:
                 "tile": list(i.tile), "reach_cells": list(i.reach_cells),
                 "csr_nnz": i.csr_nnz, "workspace_bytes": i.workspace_bytes,
                 "window_rows": i.window_rows,
-                "step_kernel": ("direct", "window", "masked", "resident")[i.step_kernel],
+                "step_kernel": ("direct", "window", "masked", "resident", "cluster")[i.step_kernel],
                 "batch_mode": ("none", "persistent", "streams")[i.batch_mode],
                 "adjoint_kernel": ("none", "scatter", "masked")[i.adjoint_kernel]}
 

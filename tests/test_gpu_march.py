@@ -92,17 +92,21 @@ def test_gauss_hermite_matches_oracle(fk, oracle):
         np.testing.assert_allclose(w, wo, atol=2e-15)
 
 
-@pytest.fixture(params=["resident", "step"])
+KERNEL1D = {"step": "direct", "resident": "resident", "cluster": "cluster"}
+
+
+@pytest.fixture(params=["step", "resident", "cluster"])
 def kernel1d(request, monkeypatch):
-    """1D path of the test's plans: the march in one CTA, or one launch per step."""
-    if request.param == "step":
-        monkeypatch.setenv("FK_1D_KERNEL", "step")
+    """1D path of the test's plans: one launch per step, the whole march in
+    one CTA, or in one thread-block cluster."""
+    monkeypatch.setenv("FK_1D_KERNEL", request.param)
     return request.param
 
 
-def test_bm1d_drift_fp64_full_march(fk, oracle):
+def test_bm1d_drift_fp64_full_march(fk, oracle, kernel1d):
     w = fk_inputs.workload("bm1d_drift")
-    got = _gpu_solve(fk, w)
+    got, info = _gpu_solve_info(fk, w)
+    assert info["step_kernel"] == KERNEL1D[kernel1d]
     want = _oracle_march(oracle, w, w["n_steps"], 0)
     assert np.abs(got - want).max() <= TOL64
 
@@ -132,7 +136,7 @@ def test_small2d_const_drift(fk, oracle, precision, tol):
 
 
 @pytest.mark.parametrize("q", [1, 3, 8, 12, 16])
-def test_1d_random_field_fp64(fk, oracle, q):
+def test_1d_random_field_fp64(fk, oracle, q, kernel1d):
     w = fk_inputs.workload("bm1d_drift", n=(1500,), q=q, n_steps=7)
     u0 = fk_inputs.random_field((1500,), seed=q)
     got = _gpu_solve(fk, w, u0)
@@ -254,7 +258,7 @@ def test_degenerate_meshes(fk, oracle, n, q, params):
     assert np.abs(got - want).max() <= TOL64
 
 
-def test_1d_minimal_and_wide_reach(fk, oracle):
+def test_1d_minimal_and_wide_reach(fk, oracle, kernel1d):
     for n, dt in ((3, 1e-3), (11, 0.5)):
         w = fk_inputs.workload("bm1d_drift", n=(n,), n_steps=4, dt=dt)
         got = _gpu_solve(fk, w)
@@ -372,16 +376,15 @@ def test_masked_kernel_full_march_vs_golden(fk, monkeypatch):
 
 
 def test_1d_resident_snapshots_and_resume(fk):
-    """The one-CTA 1D march: snapshots every 3 steps equal the per-step
-    path's, FP32 and FP64, and a resumed march (fk_march from a snapshot,
-    in place) ends where the full march does."""
+    """The one-CTA and the cluster 1D marches: snapshots every 3 steps equal
+    the per-step path's, FP32 and FP64, and a resumed march (fk_march from a
+    snapshot, in place) ends where the full march does."""
     import torch
     for precision in ("fp64", "fp32"):
         w = fk_inputs.workload("bm1d_drift", n=(301,), n_steps=20, precision=precision)
         res = {}
-        for kern in ("resident", "step"):
-            if kern == "step":
-                os.environ["FK_1D_KERNEL"] = "step"
+        for kern in ("resident", "cluster", "step"):
+            os.environ["FK_1D_KERNEL"] = kern
             try:
                 plan = fk.Plan(_spec(fk, w))
             finally:
@@ -393,14 +396,14 @@ def test_1d_resident_snapshots_and_resume(fk):
             resumed = snaps[3].clone()  # u after 12 steps, i.e. u^8
             plan.march(8, 0, resumed, out=resumed)
             torch.cuda.synchronize()
-            resident = kern == "resident" and precision == "fp32"  # FP64: per step always
-            assert plan.info()["step_kernel"] == ("resident" if resident else "direct")
+            assert plan.info()["step_kernel"] == KERNEL1D[kern]
             assert torch.equal(resumed, out)
             res[kern] = (out.double().cpu().numpy(), snaps.double().cpu().numpy())
             plan.close()
         tol = 1e-14 if precision == "fp64" else 1e-6
-        assert np.abs(res["resident"][0] - res["step"][0]).max() <= tol
-        assert np.abs(res["resident"][1] - res["step"][1]).max() <= tol
+        for kern in ("resident", "cluster"):
+            assert np.abs(res[kern][0] - res["step"][0]).max() <= tol
+            assert np.abs(res[kern][1] - res["step"][1]).max() <= tol
 
 
 @pytest.mark.parametrize("n,q,dt,n_steps", [
@@ -415,6 +418,15 @@ def test_1d_fp32_vs_oracle(fk, oracle, kernel1d, n, q, dt, n_steps):
     w = fk_inputs.workload("bm1d_drift", n=n, q=q, dt=dt, n_steps=n_steps, precision="fp32")
     u0 = fk_inputs.random_field(n, seed=q)
     got, info = _gpu_solve_info(fk, w, u0)
-    assert info["step_kernel"] == ("resident" if kernel1d == "resident" else "direct")
+    assert info["step_kernel"] == KERNEL1D[kernel1d]
     want = _oracle_march(oracle, w, w["n_steps"], 0, u0)
     assert np.abs(got - want).max() <= TOL32
+
+
+@pytest.mark.parametrize("precision,kernel", [("fp32", "resident"), ("fp64", "cluster")])
+def test_1d_default_kernel(fk, precision, kernel):
+    """Without an explicit choice the 1D march runs in one launch: FP32 in
+    one CTA, FP64 over a cluster."""
+    w = fk_inputs.workload("bm1d_drift", precision=precision)
+    _, info = _gpu_solve_info(fk, w)
+    assert info["step_kernel"] == kernel
