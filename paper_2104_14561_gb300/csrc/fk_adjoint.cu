@@ -24,6 +24,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "fk_device.cuh"
 #include "fk_internal.h"
 
@@ -41,6 +44,11 @@ struct AdjArgs {
   T st, sw;         // sin(omega t_n), eps t_n cos(omega t_n)
   T cbx, cby;       // constant drift: dt / h per axis
   T cn;             // d sigma / d theta_3 divided by sigma
+  // masked form, nodes whose points all stay inside: the 1D weights as
+  // piecewise cubics in the fractional cell position of point 0
+  const float4* tab;          // see adj_tables
+  float brk[2][FK_MAXQ_2D];   // piece boundaries per axis, unused ones 2
+  float last[2];              // g_{Q-1} - g_0 per axis
 };
 
 template <typename T>
@@ -386,12 +394,56 @@ __device__ __forceinline__ void axis_weights(Slots<W, K>& S, const Step2D<float>
   }
 }
 
+// Weight tables (adj_tables): float4 quadruples [axis][slot][quad][piece]
+// after kTabHead float4 of piece starts [axis][piece]; quad 0 {V3, S3, V2,
+// S2} and 1 {V1, S1, V0, S0}, the value/slope cubics in u = zeta - start;
+// quad 2 {G2v, G2s, G1v, G1s} and 3 {G0v, G0s, 0, 0}, the quadratics of
+// the position derivatives times the point offsets.
+constexpr int kTabHead = 2 * FK_MAXQ_2D / 4;
+__host__ __device__ constexpr int adj_tab_float4(int W) { return kTabHead + 2 * W * 4 * FK_MAXQ_2D; }
+
+__device__ __forceinline__ int adj_piece(const float* brk, int nb, float zeta) {
+  int k = 0;
+  for (int b = 0; b < nb; ++b) k += zeta >= brk[b] ? 1 : 0;
+  return k;
+}
+
+// values and slopes (K = 2), or position derivatives plain and times the
+// point offsets (K = 4), of one axis from its table
+template <int W, int K>
+__device__ __forceinline__ void tab_weights(Slots<W, K>& S, const float4* TB, int axis, int piece,
+                                            float u) {
+  const float2 U = f2(u, u);
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    const float4* e = TB + kTabHead + ((axis * W + c) * 4) * FK_MAXQ_2D + piece;
+    const float4 h = e[0], l = e[FK_MAXQ_2D];
+    if constexpr (K == 2) {
+      const float2 v = fma2(fma2(fma2(f2(h.x, h.y), U, f2(h.z, h.w)), U, f2(l.x, l.y)), U,
+                            f2(l.z, l.w));
+      S.v[0][c] = v.x;
+      S.v[1][c] = v.y;
+    } else {
+      // d/du of the cubic: (3 c3 u + 2 c2) u + c1
+      const float2 d = fma2(fma2(mul2(f2(3.f, 3.f), f2(h.x, h.y)), U, mul2(f2(2.f, 2.f), f2(h.z, h.w))),
+                            U, f2(l.x, l.y));
+      const float4 q2 = e[2 * FK_MAXQ_2D], q0 = e[3 * FK_MAXQ_2D];
+      const float2 gq = fma2(fma2(f2(q2.x, q2.y), U, f2(q2.z, q2.w)), U, f2(q0.x, q0.y));
+      S.v[0][c] = d.x;
+      S.v[1][c] = d.y;
+      S.v[2][c] = gq.x;
+      S.v[3][c] = gq.y;
+    }
+  }
+}
+
 template <int Q, int W>
 __global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<float> g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Step2D<float>& a = g.s;
   const int lx = a.lx, ly = a.ly, lp = a.lyr;
-  float4* Rec = reinterpret_cast<float4*>(smem);
+  float4* TB = reinterpret_cast<float4*>(smem);  // weight tables
+  float4* Rec = TB + adj_tab_float4(W);
   float* U = reinterpret_cast<float*>(Rec + ly * lp);
   float* MU = U + ly * lp;  // 3 planes of ly x lp: mu_u, mu_X, mu_Y
   __shared__ double red[4][FK_THREADS / 32];
@@ -399,6 +451,7 @@ __global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<floa
   const int i0 = 1 + blockIdx.x * 32, k0 = 1 + blockIdx.y * a.ty;
   const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;
   for (int e = tid; e < 3 * ly * lp; e += FK_THREADS) MU[e] = 0.f;
+  for (int e = tid; e < adj_tab_float4(W); e += FK_THREADS) TB[e] = g.tab[e];
   masked_stage(a, Rec, U, gi0, gk0);  // ends with a barrier
 
   double dth0 = 0.0, dth1 = 0.0, dth2 = 0.0, dth3 = 0.0;
@@ -444,14 +497,27 @@ __global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<floa
     const float zx = dx - fx0, zy = dy - fy0;
     const float lox = -(float)i - fx0, hix = (float)(a.nx - 1 - i) - fx0;
     const float loy = -(float)k - fy0, hiy = (float)(a.ny - 1 - k) - fy0;
+    // nodes whose points all stay inside take the tables: zeta is point 0's
+    // fractional cell position, u its offset in its piece
+    const float ex = (dx + a.gx[0]) - fx0, ey = (dy + a.gy[0]) - fy0;
+    const bool inside = ex >= lox && ex + g.last[0] <= hix && ey >= loy && ey + g.last[1] <= hiy;
+    const float* starts = reinterpret_cast<const float*>(TB);
+    const int px = adj_piece(g.brk[0], Q - 1, ex), py = adj_piece(g.brk[1], Q - 1, ey);
+    const float ux = ex - starts[px], uy = ey - starts[FK_MAXQ_2D + py];
     Slots<W, 2> YV;  // Phi, Psi
-    axis_weights<Q>(YV, a, zy, a.gy, loy, hiy);
+    if (inside)
+      tab_weights(YV, TB, 1, py, uy);
+    else
+      axis_weights<Q>(YV, a, zy, a.gy, loy, hiy);
     // pass 1: x values; the transposed scatter and the row sums
     // A_r = sum_c (u - u_j) phi_c + X psi_c, B_r = sum_c Y phi_c
     float AR[W], BR[W];
     {
       Slots<W, 2> XV;  // phi, psi
-      axis_weights<Q>(XV, a, zx, a.gx, lox, hix);
+      if (inside)
+        tab_weights(XV, TB, 0, px, ux);
+      else
+        axis_weights<Q>(XV, a, zx, a.gx, lox, hix);
 #pragma unroll
       for (int r = 0; r < W; ++r) {
         const int o = (wy + r) * lp + wx;
@@ -475,7 +541,10 @@ __global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<floa
     float Gy = 0.f, Gyn = 0.f, Gx = 0.f, Gxn = 0.f;
     {
       Slots<W, 4> YD;
-      axis_weights<Q>(YD, a, zy, a.gy, loy, hiy);
+      if (inside)
+        tab_weights(YD, TB, 1, py, uy);
+      else
+        axis_weights<Q>(YD, a, zy, a.gy, loy, hiy);
 #pragma unroll
       for (int r = 0; r < W; ++r) {
         Gy = fmaf(YD.v[0][r], AR[r], fmaf(YD.v[1][r], BR[r], Gy));
@@ -485,7 +554,10 @@ __global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<floa
     // pass 2: x derivatives (and x derivatives x g_p) against the y values
     {
       Slots<W, 4> XD;
-      axis_weights<Q>(XD, a, zx, a.gx, lox, hix);
+      if (inside)
+        tab_weights(XD, TB, 0, px, ux);
+      else
+        axis_weights<Q>(XD, a, zx, a.gx, lox, hix);
 #pragma unroll
       for (int r = 0; r < W; ++r) {
         const float4* row = Rec + (wy + r) * lp + wx;
@@ -640,11 +712,98 @@ cudaError_t launch_adj(const AdjArgs<T>& g, int q, cudaStream_t s) {
   }
 }
 
-size_t adj_masked_smem(int ly, int lp) { return (size_t)ly * lp * (16 + 4 + 12); }
+size_t adj_masked_smem(int ly, int lp, int w) {
+  return (size_t)adj_tab_float4(w) * 16 + (size_t)ly * lp * (16 + 4 + 12);
+}
+
+// The piecewise-cubic weight tables of the masked adjoint, per axis.  With
+// point 0 at fractional cell position zeta in [0, 1) after the window
+// origin, point q sits at zeta + D_q (D_q = g_q - g_0).  The value weight of
+// window slot s is phi_s(zeta) = sum_q w_q V(zeta + D_q - s), the slope
+// weight psi_s the same with S; V, S are the cubic Hermite node functions
+// (h00, h01, h10, h11 of Eq. (Lag11) in one piece each).  Both are cubic in
+// zeta between the positions where some point crosses a cell boundary,
+// zeta = 1 - frac(D_q): at most Q pieces.  d phi_s / d zeta is the weight
+// of the common position derivative (the drift direction); the sigma
+// direction needs sum_q w_q g_q V'(...), a quadratic per piece.  All are
+// expanded in u = zeta - (start of the piece, as float).  The weights are
+// continuous in zeta (the node functions are C^1), so a zeta that rounds
+// across a piece boundary takes either piece.
+bool adj_tables(fk_plan* p, std::vector<float>& tab) {
+  const int Q = p->q, W = p->mwin;
+  const size_t head = 4 * kTabHead;
+  tab.assign((size_t)4 * adj_tab_float4(W), 0.f);
+  const double sg = (p->coeffs.family == FK_CONST_DRIFT ? p->coeffs.p[3] : sqrt(2.0 * p->coeffs.p[3])) *
+                    sqrt(2.0 * p->dt);
+  for (int m = 0; m < 2; ++m) {
+    double gq[FK_MAXQ_2D];
+    for (int q = 0; q < Q; ++q) gq[q] = (double)(float)(sg * p->gh_a[q] / p->h[m]);
+    std::vector<double> br;
+    for (int q = 1; q < Q; ++q) {
+      const double d = gq[q] - gq[0], f = d - floor(d);
+      if (f > 0.0) br.push_back((double)(float)(1.0 - f));
+    }
+    std::sort(br.begin(), br.end());
+    br.erase(std::unique(br.begin(), br.end()), br.end());
+    const int P = (int)br.size() + 1;
+    if (P > FK_MAXQ_2D) return false;
+    for (int b = 0; b < FK_MAXQ_2D; ++b) p->adj_break[m][b] = b < P - 1 ? (float)br[b] : 2.0f;
+    p->adj_last[m] = (float)(gq[Q - 1] - gq[0]);
+    for (int k = 0; k < P; ++k) {
+      const double a0 = k == 0 ? 0.0 : br[k - 1], a1 = k == P - 1 ? 1.0 : br[k];
+      const double mid = 0.5 * (a0 + a1);
+      double V[FK_MAXQ_2D + 8][4] = {}, S[FK_MAXQ_2D + 8][4] = {};
+      double GV[FK_MAXQ_2D + 8][3] = {}, GS[FK_MAXQ_2D + 8][3] = {};
+      for (int q = 0; q < Q; ++q) {
+        const double D = gq[q] - gq[0];
+        const int o = (int)floor(mid + D);  // cell of point q over this piece
+        if (o < 0 || o + 1 > W - 1) return false;
+        const double t0 = a0 + D - o;      // its local coordinate at u = 0
+        // t = t0 + u: coefficients of t, t^2, t^3 in powers of u
+        const double c1[4] = {t0, 1.0, 0.0, 0.0};
+        const double c2[4] = {t0 * t0, 2.0 * t0, 1.0, 0.0};
+        const double c3[4] = {t0 * t0 * t0, 3.0 * t0 * t0, 3.0 * t0, 1.0};
+        const double w = p->gh_w[q], wg = w * gq[q];
+        for (int e = 0; e < 4; ++e) {
+          const double h01 = 3.0 * c2[e] - 2.0 * c3[e];
+          const double h00 = (e == 0 ? 1.0 : 0.0) - h01;
+          const double h10 = c1[e] - 2.0 * c2[e] + c3[e];
+          const double h11 = c3[e] - c2[e];
+          V[o][e] += w * h00;
+          V[o + 1][e] += w * h01;
+          S[o][e] += w * h10;
+          S[o + 1][e] += w * h11;
+        }
+        for (int e = 0; e < 3; ++e) {  // d/du of the same cubics, times g_q
+          const double d01 = (e + 1) * (3.0 * c2[e + 1] - 2.0 * c3[e + 1]);
+          const double d10 = (e + 1) * (c1[e + 1] - 2.0 * c2[e + 1] + c3[e + 1]);
+          const double d11 = (e + 1) * (c3[e + 1] - c2[e + 1]);
+          GV[o][e] -= wg * d01;
+          GV[o + 1][e] += wg * d01;
+          GS[o][e] += wg * d10;
+          GS[o + 1][e] += wg * d11;
+        }
+      }
+      tab[m * FK_MAXQ_2D + k] = (float)a0;
+      for (int c = 0; c < W; ++c) {
+        auto quad = [&](int j) { return &tab[head + 4 * ((size_t)((m * W + c) * 4 + j) * FK_MAXQ_2D + k)]; };
+        float* q0 = quad(0);
+        q0[0] = (float)V[c][3]; q0[1] = (float)S[c][3]; q0[2] = (float)V[c][2]; q0[3] = (float)S[c][2];
+        float* q1 = quad(1);
+        q1[0] = (float)V[c][1]; q1[1] = (float)S[c][1]; q1[2] = (float)V[c][0]; q1[3] = (float)S[c][0];
+        float* q2 = quad(2);
+        q2[0] = (float)GV[c][2]; q2[1] = (float)GS[c][2]; q2[2] = (float)GV[c][1]; q2[3] = (float)GS[c][1];
+        float* q3 = quad(3);
+        q3[0] = (float)GV[c][0]; q3[1] = (float)GS[c][0];
+      }
+    }
+  }
+  return true;
+}
 
 template <int Q, int W>
 cudaError_t launch_adj_masked_qw(const AdjArgs<float>& g, cudaStream_t s) {
-  const size_t smem = adj_masked_smem(g.s.ly, g.s.lyr);
+  const size_t smem = adj_masked_smem(g.s.ly, g.s.lyr, W);
   static bool set = false;
   if (!set) {
     cudaFuncAttributes fa;
@@ -683,7 +842,7 @@ bool adj_use_masked(const fk_plan* p) {
 int adj_masked_ty(const fk_plan* p, int smem_max) {
   const int lx = 32 + 2 * p->mhalo[0] + 2;
   for (int ty = 16; ty >= 4; ty -= 4)
-    if (adj_masked_smem(ty + 2 * p->mhalo[1] + 2, lx | 1) + kAdjStatic <= (size_t)smem_max)
+    if (adj_masked_smem(ty + 2 * p->mhalo[1] + 2, lx | 1, p->mwin) + kAdjStatic <= (size_t)smem_max)
       return ty;
   return 0;
 }
@@ -738,7 +897,13 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
         g.s.wm[q] = p->mwm[q];
         g.s.wmf[q] = (T)p->mwm[q];
       }
-      e = launch_adj_masked((const AdjArgs<float>&)g, p->q, s);
+      AdjArgs<float>& gf = (AdjArgs<float>&)g;
+      gf.tab = (const float4*)p->adj_tab;
+      for (int m = 0; m < 2; ++m) {
+        for (int b = 0; b < FK_MAXQ_2D; ++b) gf.brk[m][b] = p->adj_break[m][b];
+        gf.last[m] = p->adj_last[m];
+      }
+      e = launch_adj_masked(gf, p->q, s);
     } else {
       e = launch_adj<T>(g, p->q, s);
     }
@@ -784,6 +949,16 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
   p->adj_ty = adj_use_masked(p) ? adj_masked_ty(p, smem_max) : 0;
   if (adj_use_masked(p) && p->adj_ty == 0) return FK_ERR_UNSUPPORTED;
   p->adj_kernel = adj_use_masked(p) ? 2 : 1;
+  if (adj_use_masked(p) && !p->adj_tab) {
+    std::vector<float> tab;
+    if (!adj_tables(p, tab)) return FK_ERR_UNSUPPORTED;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FK_ERR_CUDA;
+    fk_status st = fk_dev_alloc(p, &p->adj_tab, tab.size() * sizeof(float));
+    if (st != FK_OK) return st;
+    if (cudaMemcpy(p->adj_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return FK_ERR_CUDA;
+  }
   // workspace: checkpoints (M+1), a segment (K), lambda x2, mu (3 fields), dtheta
   const int64_t need = (int64_t)(M + 1 + K + 2 + 3) * fb + 64;
   if (p->adj_bytes < need) {

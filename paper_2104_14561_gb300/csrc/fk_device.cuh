@@ -8,6 +8,12 @@
 
 namespace {
 
+// Packed FP32 pairs (two lanes of work per instruction on sm_100 and later).
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // Scaled PCHIP slope h*u'_j from the two neighbouring differences
 // (Eq. (e300)): 0 unless both have the same strict sign, else their
 // harmonic mean 2 dl dr / (dl + dr).

@@ -179,6 +179,9 @@ struct fk_plan {
   void* adj_mu;      // 3 J accumulators inside adj_ws
   int adj_ty;        // tile height of the masked-window adjoint (0: per-point scatter)
   int adj_kernel;    // backward form of the last fk_adjoint: 0 none, 1 scatter, 2 masked
+  void* adj_tab;     // piecewise-cubic weight tables of the masked adjoint (device, float4)
+  float adj_break[2][FK_MAXQ_2D];  // their piece boundaries per axis, unused ones 2
+  float adj_last[2];               // g_{Q-1} - g_0 per axis
 };
 
 void fk_batch_release(fk_plan* p);

@@ -836,6 +836,7 @@ fk_status fk_plan_destroy(fk_plan* p) {
   fk_dev_free(p->stack);
   fk_dev_free(p->batch_rec);
   fk_dev_free(p->adj_ws);
+  fk_dev_free(p->adj_tab);
   fk_batch_release(p);
   delete p;
   return FK_OK;

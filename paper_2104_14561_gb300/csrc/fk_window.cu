@@ -44,10 +44,6 @@
 
 namespace {
 
-__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // Adds the contributions (v0, v1, v2) of one point to slots m, m+1, m+2 of
 // the value weights PH and (s0, s1, s2) to the slope weights PS.  m is the
