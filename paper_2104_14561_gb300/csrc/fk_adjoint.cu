@@ -924,6 +924,7 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
 
 extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double* cotangent_u0,
                                 double* dtheta, void* du_terminal, int K, cudaStream_t s) {
+  FkRange range("fk_adjoint");
   if (!p || !cotangent_u0 || K < 1) return FK_ERR_INVALID_ARG;
   if (p->grid.dim != 2 || p->path != FK_PATH_MATRIX_FREE) return FK_ERR_UNSUPPORTED;
   const int N = p->n_steps;
@@ -979,18 +980,21 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
   auto slot = [&](int n) { return n == N ? M : n / K; };  // n == N or n % K == 0
 
   // forward pass with checkpoints
-  cudaError_t e;
-  if (u_terminal)
-    e = fk_launch_copy(ckpt(M), u_terminal, fb, s);
-  else
-    e = fk_launch_fill_chi(ckpt(M), 2, p->grid.n[0], p->grid.n[1], p->elem, s);
-  if (e != cudaSuccess) return FK_ERR_CUDA;
-  const void* src = ckpt(M);
-  for (int n = N - 1; n >= 1; --n) {  // u^0 itself is not needed
-    void* dst = (n % K == 0) ? ckpt(slot(n)) : lam[n & 1];
-    fk_status st = fk_enqueue_step(p, n, src, dst, nullptr, s);
-    if (st != FK_OK) return st;
-    src = dst;
+  {
+    FkRange fwd_range("fk_adjoint forward pass");
+    cudaError_t e;
+    if (u_terminal)
+      e = fk_launch_copy(ckpt(M), u_terminal, fb, s);
+    else
+      e = fk_launch_fill_chi(ckpt(M), 2, p->grid.n[0], p->grid.n[1], p->elem, s);
+    if (e != cudaSuccess) return FK_ERR_CUDA;
+    const void* src = ckpt(M);
+    for (int n = N - 1; n >= 1; --n) {  // u^0 itself is not needed
+      void* dst = (n % K == 0) ? ckpt(slot(n)) : lam[n & 1];
+      fk_status st = fk_enqueue_step(p, n, src, dst, nullptr, s);
+      if (st != FK_OK) return st;
+      src = dst;
+    }
   }
   if (cudaMemsetAsync(p->adj_mu, 0, (size_t)3 * fb, s) != cudaSuccess ||
       cudaMemsetAsync(dth, 0, 4 * sizeof(double), s) != cudaSuccess)
@@ -1007,6 +1011,7 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
   }
   // backward over segments [mK, top)
   for (int m = 0; m < M; ++m) {
+    FkRange seg_range("fk_adjoint segment");
     const int lo = m * K, top = (m + 1) * K < N ? (m + 1) * K : N;
     // recompute u^{top-1} .. u^{lo+1} into the segment buffer
     const void* s2 = ckpt(slot(top));

@@ -711,6 +711,7 @@ void fk_batch_release(fk_plan* p) {
 
 extern "C" fk_status fk_solve_batched(int n, fk_plan* const* plans, const void* const* u_terminal,
                                       void* const* u_out, cudaStream_t stream) {
+  FkRange range("fk_solve_batched");
   if (n < 1 || n > kMaxInst || !plans || !u_terminal || !u_out) return FK_ERR_INVALID_ARG;
   for (int b = 0; b < n; ++b) {
     if (!plans[b] || !u_out[b]) return FK_ERR_INVALID_ARG;

@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(256) k_csr_spmv(const int64_t* __restrict__ ro
 }  // namespace
 
 fk_status fk_csr_assemble(fk_plan* p, cudaStream_t s) {
+  FkRange range("fk_csr_assemble");
   CsrAsm a;
   memset(&a, 0, sizeof(a));
   a.nx = p->grid.n[0];

@@ -17,6 +17,16 @@
 #define FK_DEVERR_RANGE 1u    // a shifted point fell outside its tile halo
 #define FK_DEVERR_TIMEOUT 2u  // a bounded grid-barrier wait gave up
 
+// Named NVTX range over a host scope (profiler timelines; free when no
+// profiler is attached: NVTX v3 is header-only and loads a tool on demand).
+#include <nvtx3/nvToolsExt.h>
+struct FkRange {
+  explicit FkRange(const char* name) { nvtxRangePushA(name); }
+  ~FkRange() { nvtxRangePop(); }
+  FkRange(const FkRange&) = delete;
+  FkRange& operator=(const FkRange&) = delete;
+};
+
 // Two- and four-component records aligned for single vector shared-memory
 // accesses (16 B for float4-like, 32 B for double4-like).
 template <typename T>
@@ -195,7 +205,9 @@ fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void
 void fk_fill_step2d_f32(const fk_plan* p, int n, Step2D<float>* a);
 void fk_fill_step2d_f64(const fk_plan* p, int n, Step2D<double>* a);
 
-// Device allocation through the plan's accounting.
+// Device allocation through the plan's accounting.  Fault injection for
+// tests: with FK_TEST_FAIL_ALLOC=n set, the n-th allocation after the value
+// was set fails with FK_ERR_OOM (the count restarts when the value changes).
 fk_status fk_dev_alloc(fk_plan* p, void** ptr, size_t bytes);
 void fk_dev_free(void* ptr);
 

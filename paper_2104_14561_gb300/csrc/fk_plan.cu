@@ -555,9 +555,24 @@ fk_status autotune(fk_plan* p) {
 
 // ------------------------------------------------------------ internal --
 
+namespace {
+std::mutex g_alloc_mu;
+long g_alloc_fail_at = 0, g_alloc_count = 0;  // FK_TEST_FAIL_ALLOC state
+}  // namespace
+
 fk_status fk_dev_alloc(fk_plan* p, void** ptr, size_t bytes) {
   *ptr = nullptr;
   if (bytes == 0) return FK_OK;
+  {
+    const char* f = getenv("FK_TEST_FAIL_ALLOC");
+    const long n = f ? atol(f) : 0;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    if (n != g_alloc_fail_at) {  // set, changed or cleared: count afresh
+      g_alloc_fail_at = n;
+      g_alloc_count = 0;
+    }
+    if (n > 0 && ++g_alloc_count == n) return FK_ERR_OOM;
+  }
   cudaError_t e = cudaMalloc(ptr, bytes);
   if (e != cudaSuccess) {
     *ptr = nullptr;
@@ -703,6 +718,7 @@ fk_status fk_gauss_hermite(int q, double* a, double* w) {
 fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* region,
                          const fk_coeffs* coeffs, int q_per_dim, double dt, int n_steps,
                          fk_precision prec, fk_path path) {
+  FkRange range("fk_plan_create");
   if (!out) return FK_ERR_INVALID_ARG;
   *out = nullptr;
   fk_status st = validate(grid, region, coeffs, q_per_dim, dt, n_steps, prec, path);
@@ -869,6 +885,7 @@ fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
 
 fk_status fk_march(fk_plan* p, int n_from, int n_to, const void* u_in, void* u_out,
                    cudaStream_t stream) {
+  FkRange range("fk_march");
   if (!p || !u_in || !u_out) return FK_ERR_INVALID_ARG;
   if (n_to < 0 || n_from < n_to || n_from > p->n_steps) return FK_ERR_INVALID_ARG;
   return enqueue_march(p, n_from, n_to, u_in, u_out, nullptr, 0, stream);
@@ -876,6 +893,7 @@ fk_status fk_march(fk_plan* p, int n_from, int n_to, const void* u_in, void* u_o
 
 fk_status fk_solve(fk_plan* p, const void* u_terminal, void* u_out, void* snapshots,
                    int snapshot_stride, cudaStream_t stream) {
+  FkRange range("fk_solve");
   if (!p || !u_out) return FK_ERR_INVALID_ARG;
   if (snapshots && snapshot_stride < 1) return FK_ERR_INVALID_ARG;
   if (!snapshots) snapshot_stride = 0;
