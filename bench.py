@@ -228,7 +228,8 @@ def run_reference(args, rank: int):
             "config": {"workload": args.workload, "grid": list(w["n"]), "q_per_dim": w["q"],
                        "dt": w["dt"], "step": "one time step of the march per benchmark step"},
             "cpu_baseline": {"kind": "oracle", "cores": cores if O.has_openmp() else 1,
-                             "sample": f"{args.steps} time steps of {w['n'][0]}x{w['n'][1]}, FP64",
+                             "sample": f"{args.steps} time steps of "
+                                       f"{'x'.join(str(v) for v in w['n'])}, FP64",
                              "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -404,6 +405,24 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
     plan.close()
 
 
+# ------------------------------------------------------------ ranks -----
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest per-rank figure over all ranks (the value itself when the
+    job has one rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Throughput of the whole job when every rank marches its own instance
+    (weak scaling): all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
 # --------------------------------------------------------------- ours ----
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
@@ -453,11 +472,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     ms_step = sum(ms) / len(ms)
     if plan.last_device_error() != 0:
         raise RuntimeError("device-side range check fired during the benchmark")
-    t_max = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_step_max = float(t_max.item())
-    value = units * world / (ms_step_max * 1e-3)
+    ms_step_max = max_over_ranks(ms_step, dist, dev)
+    value = whole_job_rate(units, world, ms_step_max)
 
     # end to end through the public API: pinned host in -> device -> march -> host out
     host_in = torch.zeros(plan.shape, dtype=plan.dtype).pin_memory()
@@ -480,10 +496,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             b.synchronize()
             if i >= max(args.warmup, 1):
                 e_ms.append(a.elapsed_time(b))
-    e2e_t = torch.tensor([sum(e_ms) / len(e_ms)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = units * world / (float(e2e_t.item()) * 1e-3)
+    e2e_value = whole_job_rate(units, world, max_over_ranks(sum(e_ms) / len(e_ms), dist, dev))
     field_bytes = int(host_in.numel() * host_in.element_size())
 
     if rank != 0:
