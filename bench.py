@@ -202,21 +202,26 @@ def oracle_rate(w, max_seconds: float = 20.0):
 def run_reference(args, rank: int):
     if rank != 0:
         return
-    w = fk_inputs.workload(args.workload)
     from oracle import fk_oracle as O
     O.build()
-    fam = {"const_drift": O.CONST_DRIFT, "cellular_flow": O.CELLULAR_FLOW}[w["family"]]
-    g = O.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]))
-    cores = os.cpu_count() or 1
-    per_step = units_per_solve(w) / w["n_steps"]
+    fams = {"const_drift": O.CONST_DRIFT, "cellular_flow": O.CELLULAR_FLOW}
     # one benchmark step of the reference arm = one time step of the march
-    # (a bounded sample of the workload), so that K + W steps take seconds
-    u = None
+    # (of every instance, for the batched sweep): a bounded sample of the
+    # workload, so that K + W steps take seconds to a minute
+    ws = (fk_inputs.batched_instances() if args.workload == "batched_64"
+          else [fk_inputs.workload(args.workload)])
+    w = ws[0]
+    cores = os.cpu_count() or 1
+    per_step = sum(units_per_solve(x) / x["n_steps"] for x in ws)
+    us = [None] * len(ws)
     times = []
     for s in range(args.warmup + args.steps):
-        n = w["n_steps"] - s
         t = time.perf_counter()
-        u = O.march(g, fam, list(w["params"]), w["q"], w["dt"], n, n - 1, u, nthreads=cores)
+        for b, x in enumerate(ws):
+            n = x["n_steps"] - s
+            g = O.Grid(tuple(x["n"]), tuple(x["lo"]), tuple(x["hi"]))
+            us[b] = O.march(g, fams[x["family"]], list(x["params"]), x["q"], x["dt"], n, n - 1,
+                            us[b], nthreads=cores)
         if s >= args.warmup:
             times.append(time.perf_counter() - t)
     sec = sum(times) / len(times)
@@ -229,7 +234,8 @@ def run_reference(args, rank: int):
                        "dt": w["dt"], "step": "one time step of the march per benchmark step"},
             "cpu_baseline": {"kind": "oracle", "cores": cores if O.has_openmp() else 1,
                              "sample": f"{args.steps} time steps of "
-                                       f"{'x'.join(str(v) for v in w['n'])}, FP64",
+                                       + (f"each of the {len(ws)} instances" if len(ws) > 1 else
+                                          'x'.join(str(v) for v in w['n'])) + ", FP64",
                              "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
