@@ -160,3 +160,13 @@ def test_csr_snapshots_monotone_in_time_to_go(fk):
     assert worst <= 1e-6
     assert s.min() >= -1e-6 and s.max() <= 1.0 + 1e-6
     p.close()
+
+
+def test_csr_reach_wider_than_any_tile(fk, oracle):
+    """A reach of about 190 cells, far wider than the mesh and than any
+    step-kernel tile: the CSR path needs no tile and matches the oracle."""
+    w = _small(8, n=(65, 33), n_steps=3)
+    w.update(params=(1.0, 0.0, 2 * math.pi, 20.0), dt=0.05)
+    got, _ = _solve(fk, w)
+    want = _oracle(oracle, w, 3, 0)
+    assert np.abs(got - want).max() <= 1e-12
