@@ -13,6 +13,9 @@
 * first-order convergence in dt on the Fig. 2 setup (L = 10, T = 3, Q = 3,
   sigma = 1, b = 0, Sec. 4.1) with grids that satisfy Remark 2, so that
   Delta x ~ sqrt(dt) and the error also falls as Delta x^2 (Eq. (e_err));
+* second-order convergence in Delta x at fixed dt (the error estimate after
+  Scheme 1 in Sec. 3.1, and Fig. 4 of Sec. 4.2) with smooth terminal data
+  that meets the exit value;
 * 0 <= u <= 1 and monotonicity in time-to-go for the autonomous 1D problem.
 """
 import math
@@ -74,6 +77,36 @@ def test_first_order_in_dt(oracle):
     orders = [math.log(errs[i] / errs[i + 1], 2) for i in range(len(errs) - 1)]
     assert all(0.85 < o < 1.4 for o in orders), orders
     assert errs[-1] < 2e-4
+
+
+def test_second_order_in_dx(oracle):
+    """Fixed dt = 0.02, T = 0.2 (10 steps), drift 0.3, sigma 0.2 on (-1, 1),
+    terminal data 1 - (1 - x^2)^2 (smooth, equal to the exit value 1 at the
+    ends).  The reference is the same march on 1281 nodes, so the time error
+    cancels and what is left is the spatial error of the PCHIP interpolant at
+    the shifted points.  Semi-Lagrangian errors wobble from level to level
+    (the shifted points' fractional cell positions change with h), so the
+    pin is the least-squares slope of log error against log h, plus a floor
+    on each single-level ratio.  The ladder stops at 321 nodes: below ~1e-6
+    the difference to the reference runs into the limiter's switching noise."""
+    def run(n):
+        g = oracle.Grid((n,), (-1.0,), (1.0,))
+        x = g.axis(0)
+        return g, oracle.march(g, oracle.CONST_DRIFT, [0.3, 0, 0, 0.2], 8, 0.02, 10, 0,
+                               1 - (1 - x * x) ** 2, nthreads=4)
+    _, ref = run(1281)
+    hs, errs = [], []
+    for n in (41, 81, 161, 321):
+        g, u = run(n)
+        x = g.axis(0)
+        inner = np.abs(x) <= 0.6
+        errs.append(np.abs(u - ref[::1280 // (n - 1)])[inner].max())
+        hs.append(2.0 / (n - 1))
+    slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    assert slope > 2.0, (slope, errs)
+    orders = [math.log(errs[i] / errs[i + 1], 2) for i in range(len(errs) - 1)]
+    assert all(o > 1.8 for o in orders), orders
+    assert errs[-1] < 1e-5, errs
 
 
 def test_bounds_and_monotone_in_time_to_go(oracle):
