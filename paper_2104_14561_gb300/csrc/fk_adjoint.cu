@@ -309,11 +309,11 @@ __global__ void __launch_bounds__(FK_THREADS) k_adj_scatter(const AdjArgs<T> g) 
 // The parameter derivatives need the weights' derivatives in the point
 // positions: phi^d = sum_p w_p V'(.), the same for psi, and phi^g with each
 // point scaled by its offset g_p (the sigma direction); Gx = sum (u - u_j)
-// phi^d Phi + X psi^d Phi + Y phi^d Psi, and Gy, Gxn, Gyn alike.  Two
-// passes over the window keep the weight arrays in registers: the first
-// with the x values (atomics, A_r = sum_c (u - u_j) phi_c + X psi_c and
-// B_r = sum_c Y phi_c, hence Gy and Gyn), the second with the x derivatives
-// (Gx, Gxn).
+// phi^d Phi + X psi^d Phi + Y phi^d Psi, and Gy, Gxn, Gyn alike.  Each
+// of these is a double sum of one rank-one weight against the window, so
+// one pass suffices: it scatters mu and forms the row sums (contracted
+// with the y derivatives: Gy, Gyn) and the column sums (contracted with
+// the x derivatives: Gx, Gxn).
 
 // Weighted cubic Hermite node functions of one point at local position t
 // in its cell: values (v0, v1), slopes (s0, s1), and their t-derivatives.
@@ -437,8 +437,38 @@ __device__ __forceinline__ void tab_weights(Slots<W, K>& S, const float4* TB, in
   }
 }
 
+// Position of a node's points along one axis, in cells after the window
+// origin (the cell of point 0): z = offset of point 0, [lo, hi] the box;
+// whether all points stay inside, and then point 0's table piece and its
+// offset u in it.
+struct AxisPos {
+  float z, lo, hi, u;
+  int piece;
+  bool inside;
+};
+template <int Q>
+__device__ __forceinline__ AxisPos axis_pos(float d, float g0, int node, int n, const float* brk,
+                                            float last, const float4* TB, int axis) {
+  AxisPos P;
+  const float f0 = floorf(d + g0);
+  P.z = d - f0;
+  P.lo = -(float)node - f0;
+  P.hi = (float)(n - 1 - node) - f0;
+  const float e = (d + g0) - f0;
+  P.inside = e >= P.lo && e + last <= P.hi;
+  P.piece = adj_piece(brk, Q - 1, e);
+  P.u = e - reinterpret_cast<const float*>(TB)[axis * FK_MAXQ_2D + P.piece];
+  return P;
+}
+
+// Register budget for kAdjMinBlocks CTAs per SM (80 registers): the window
+// pass keeps only the 1D weights and the column sums in registers.
+#ifndef FK_ADJ_MINB
+#define FK_ADJ_MINB 3
+#endif
+constexpr int kAdjMinBlocks = FK_ADJ_MINB;
 template <int Q, int W>
-__global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<float> g) {
+__global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const AdjArgs<float> g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Step2D<float>& a = g.s;
   const int lx = a.lx, ly = a.ly, lp = a.lyr;
@@ -446,6 +476,7 @@ __global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<floa
   float4* Rec = TB + adj_tab_float4(W);
   float* U = reinterpret_cast<float*>(Rec + ly * lp);
   float* MU = U + ly * lp;  // 3 planes of ly x lp: mu_u, mu_X, mu_Y
+  float* RS = MU + 3 * ly * lp;  // per-thread row sums A_r, B_r
   __shared__ double red[4][FK_THREADS / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = 1 + blockIdx.x * 32, k0 = 1 + blockIdx.y * a.ty;
@@ -454,7 +485,11 @@ __global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<floa
   for (int e = tid; e < adj_tab_float4(W); e += FK_THREADS) TB[e] = g.tab[e];
   masked_stage(a, Rec, U, gi0, gk0);  // ends with a barrier
 
-  double dth0 = 0.0, dth1 = 0.0, dth2 = 0.0, dth3 = 0.0;
+  // per-thread FP64 sums of the parameter derivatives (in shared memory:
+  // registers go to the window pass)
+  double* DA = reinterpret_cast<double*>(RS + 2 * W * FK_THREADS) + tid;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) DA[m * FK_THREADS] = 0.0;
   unsigned bad = 0;
   const int i = i0 + lane, li = i - gi0;
   float* MX = MU + ly * lp;
@@ -467,25 +502,15 @@ __global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<floa
     if (lam == 0.f) continue;
     const int lk = k - gk0;
     const float uj = U[lk * lp + li];
-    float dx, dy, ax[3], ay[3];
+    float dx, dy;
     if (a.family == FK_CELLULAR_FLOW) {
       const float* ct = a.col_tab + 4 * (int64_t)i;
       const float* rt = a.row_tab + 2 * (int64_t)k;
       dx = a.kx * rt[0] * (a.A * ct[0] + a.e1 * ct[1]);
       dy = a.ky * rt[1] * (a.A * ct[2] + a.e2 * ct[3]);
-      const float cx = a.kx * rt[0], cy = a.ky * rt[1];
-      ax[0] = cx * ct[0];
-      ay[0] = cy * ct[2];
-      ax[1] = cx * g.st * ct[1];
-      ay[1] = cy * 2.f * g.st * ct[3];
-      ax[2] = cx * g.sw * ct[1];
-      ay[2] = cy * 2.f * g.sw * ct[3];
     } else {
       dx = a.cdx;
       dy = a.cdy;
-      ax[0] = g.cbx; ay[0] = 0.f;
-      ax[1] = 0.f;   ay[1] = g.cby;
-      ax[2] = 0.f;   ay[2] = 0.f;
     }
     const float fx0 = floorf(dx + a.gx[0]), fy0 = floorf(dy + a.gy[0]);
     int wx = li + (int)fx0, wy = lk + (int)fy0;
@@ -494,92 +519,111 @@ __global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<floa
       wx = 1;
       wy = 1;
     }
-    const float zx = dx - fx0, zy = dy - fy0;
-    const float lox = -(float)i - fx0, hix = (float)(a.nx - 1 - i) - fx0;
-    const float loy = -(float)k - fy0, hiy = (float)(a.ny - 1 - k) - fy0;
-    // nodes whose points all stay inside take the tables: zeta is point 0's
-    // fractional cell position, u its offset in its piece
-    const float ex = (dx + a.gx[0]) - fx0, ey = (dy + a.gy[0]) - fy0;
-    const bool inside = ex >= lox && ex + g.last[0] <= hix && ey >= loy && ey + g.last[1] <= hiy;
-    const float* starts = reinterpret_cast<const float*>(TB);
-    const int px = adj_piece(g.brk[0], Q - 1, ex), py = adj_piece(g.brk[1], Q - 1, ey);
-    const float ux = ex - starts[px], uy = ey - starts[FK_MAXQ_2D + py];
-    Slots<W, 2> YV;  // Phi, Psi
-    if (inside)
-      tab_weights(YV, TB, 1, py, uy);
-    else
-      axis_weights<Q>(YV, a, zy, a.gy, loy, hiy);
-    // pass 1: x values; the transposed scatter and the row sums
-    // A_r = sum_c (u - u_j) phi_c + X psi_c, B_r = sum_c Y phi_c
-    float AR[W], BR[W];
+    Slots<W, 2> YV, XV;  // (Phi, Psi) and (phi, psi)
     {
-      Slots<W, 2> XV;  // phi, psi
-      if (inside)
-        tab_weights(XV, TB, 0, px, ux);
-      else
-        axis_weights<Q>(XV, a, zx, a.gx, lox, hix);
-#pragma unroll
-      for (int r = 0; r < W; ++r) {
-        const int o = (wy + r) * lp + wx;
-        const float4* row = Rec + o;
-        const float lP = lam * YV.v[0][r], lS = lam * YV.v[1][r];
-        float Ar = 0.f, Br = 0.f;
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-          const float4 v = row[c];
-          Ar = fmaf(XV.v[0][c], v.x - uj, fmaf(XV.v[1][c], v.y, Ar));
-          Br = fmaf(XV.v[0][c], v.z, Br);
-          atomicAdd(&MU[o + c], lP * XV.v[0][c]);
-          atomicAdd(&MX[o + c], lP * XV.v[1][c]);
-          atomicAdd(&MY[o + c], lS * XV.v[0][c]);
-        }
-        AR[r] = Ar;
-        BR[r] = Br;
+      const AxisPos X = axis_pos<Q>(dx, a.gx[0], i, a.nx, g.brk[0], g.last[0], TB, 0);
+      const AxisPos Y = axis_pos<Q>(dy, a.gy[0], k, a.ny, g.brk[1], g.last[1], TB, 1);
+      if (X.inside && Y.inside) {
+        tab_weights(YV, TB, 1, Y.piece, Y.u);
+        tab_weights(XV, TB, 0, X.piece, X.u);
+      } else {
+        axis_weights<Q>(YV, a, Y.z, a.gy, Y.lo, Y.hi);
+        axis_weights<Q>(XV, a, X.z, a.gx, X.lo, X.hi);
       }
     }
-    // y-side derivatives from the row sums
+    // one pass over the window: the transposed scatter, the row sums
+    //   A_r = sum_c (u - u_j) phi_c + X psi_c,  B_r = sum_c Y phi_c
+    // and the column sums
+    //   C_c = sum_r (u - u_j) Phi_r + Y Psi_r,  D_c = sum_r X Phi_r
+    // (the y and x position derivatives then contract with the row and
+    // the column sums respectively)
+    // (A_r, B_r kept in shared memory, thread-minor: registers go to the
+    // window pass)
+    float* AR = RS + tid;
+    float* BR = RS + W * FK_THREADS + tid;
+    float2 CD[W];  // (C_c, D_c)
+#pragma unroll
+    for (int c = 0; c < W; ++c) CD[c] = f2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      const int o = (wy + r) * lp + wx;
+      const float4* row = Rec + o;
+      const float Pr = YV.v[0][r], Sr = YV.v[1][r];
+      const float lP = lam * Pr, lS = lam * Sr;
+      const float2 PP = f2(Pr, Pr), LP = f2(lP, lP);
+      float2 AE = f2(0.f, 0.f);
+      float Br = 0.f;
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const float4 v = row[c];
+        const float2 ex = f2(v.x - uj, v.y);
+        const float2 ph = f2(XV.v[0][c], XV.v[1][c]);
+        AE = fma2(ph, ex, AE);
+        Br = fmaf(ph.x, v.z, Br);
+        CD[c] = fma2(PP, ex, CD[c]);
+        CD[c].x = fmaf(Sr, v.z, CD[c].x);
+        const float2 m = mul2(LP, ph);
+        atomicAdd(&MU[o + c], m.x);
+        atomicAdd(&MX[o + c], m.y);
+        atomicAdd(&MY[o + c], lS * ph.x);
+      }
+      AR[r * FK_THREADS] = AE.x + AE.y;
+      BR[r * FK_THREADS] = Br;
+    }
+    // the positions again, recomputed from the drift rather than held
+    // through the window pass
+    const AxisPos X = axis_pos<Q>(opaque(dx), a.gx[0], i, a.nx, g.brk[0], g.last[0], TB, 0);
+    const AxisPos Y = axis_pos<Q>(opaque(dy), a.gy[0], k, a.ny, g.brk[1], g.last[1], TB, 1);
+    const bool inside = X.inside && Y.inside;
     float Gy = 0.f, Gyn = 0.f, Gx = 0.f, Gxn = 0.f;
     {
-      Slots<W, 4> YD;
+      Slots<W, 4> YD;  // y position derivatives, plain and times g_q
       if (inside)
-        tab_weights(YD, TB, 1, py, uy);
+        tab_weights(YD, TB, 1, Y.piece, Y.u);
       else
-        axis_weights<Q>(YD, a, zy, a.gy, loy, hiy);
+        axis_weights<Q>(YD, a, Y.z, a.gy, Y.lo, Y.hi);
 #pragma unroll
       for (int r = 0; r < W; ++r) {
-        Gy = fmaf(YD.v[0][r], AR[r], fmaf(YD.v[1][r], BR[r], Gy));
-        Gyn = fmaf(YD.v[2][r], AR[r], fmaf(YD.v[3][r], BR[r], Gyn));
+        const float Ar = AR[r * FK_THREADS], Br = BR[r * FK_THREADS];
+        Gy = fmaf(YD.v[0][r], Ar, fmaf(YD.v[1][r], Br, Gy));
+        Gyn = fmaf(YD.v[2][r], Ar, fmaf(YD.v[3][r], Br, Gyn));
       }
     }
-    // pass 2: x derivatives (and x derivatives x g_p) against the y values
     {
-      Slots<W, 4> XD;
+      Slots<W, 4> XD;  // x position derivatives, plain and times g_p
       if (inside)
-        tab_weights(XD, TB, 0, px, ux);
+        tab_weights(XD, TB, 0, X.piece, X.u);
       else
-        axis_weights<Q>(XD, a, zx, a.gx, lox, hix);
+        axis_weights<Q>(XD, a, X.z, a.gx, X.lo, X.hi);
 #pragma unroll
-      for (int r = 0; r < W; ++r) {
-        const float4* row = Rec + (wy + r) * lp + wx;
-        float Ad = 0.f, Bd = 0.f, Ag = 0.f, Bg = 0.f;
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-          const float4 v = row[c];
-          const float e = v.x - uj;
-          Ad = fmaf(XD.v[0][c], e, fmaf(XD.v[1][c], v.y, Ad));
-          Bd = fmaf(XD.v[0][c], v.z, Bd);
-          Ag = fmaf(XD.v[2][c], e, fmaf(XD.v[3][c], v.y, Ag));
-          Bg = fmaf(XD.v[2][c], v.z, Bg);
-        }
-        Gx = fmaf(YV.v[0][r], Ad, fmaf(YV.v[1][r], Bd, Gx));
-        Gxn = fmaf(YV.v[0][r], Ag, fmaf(YV.v[1][r], Bg, Gxn));
+      for (int c = 0; c < W; ++c) {
+        Gx = fmaf(XD.v[0][c], CD[c].x, fmaf(XD.v[1][c], CD[c].y, Gx));
+        Gxn = fmaf(XD.v[2][c], CD[c].x, fmaf(XD.v[3][c], CD[c].y, Gxn));
       }
+    }
+    // d(shift in cells)/d theta per axis (the derivative of the drift in
+    // A, eps, omega; or in b_1, b_2)
+    float ax[3], ay[3];
+    if (a.family == FK_CELLULAR_FLOW) {
+      const float* ct = a.col_tab + 4 * (int64_t)i;
+      const float* rt = a.row_tab + 2 * (int64_t)k;
+      const float cx = a.kx * rt[0], cy = a.ky * rt[1];
+      ax[0] = cx * ct[0];
+      ay[0] = cy * ct[2];
+      ax[1] = cx * g.st * ct[1];
+      ay[1] = cy * 2.f * g.st * ct[3];
+      ax[2] = cx * g.sw * ct[1];
+      ay[2] = cy * 2.f * g.sw * ct[3];
+    } else {
+      ax[0] = g.cbx; ay[0] = 0.f;
+      ax[1] = 0.f;   ay[1] = g.cby;
+      ax[2] = 0.f;   ay[2] = 0.f;
     }
     const double l = (double)lam;
-    dth0 += l * ((double)ax[0] * Gx + (double)ay[0] * Gy);
-    dth1 += l * ((double)ax[1] * Gx + (double)ay[1] * Gy);
-    dth2 += l * ((double)ax[2] * Gx + (double)ay[2] * Gy);
-    dth3 += l * (double)g.cn * ((double)Gxn + (double)Gyn);
+    DA[0] += l * ((double)ax[0] * Gx + (double)ay[0] * Gy);
+    DA[FK_THREADS] += l * ((double)ax[1] * Gx + (double)ay[1] * Gy);
+    DA[2 * FK_THREADS] += l * ((double)ax[2] * Gx + (double)ay[2] * Gy);
+    DA[3 * FK_THREADS] += l * (double)g.cn * ((double)Gxn + (double)Gyn);
   }
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
   __syncthreads();
@@ -599,6 +643,7 @@ __global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<floa
       if (m2 != 0.f) atomicAdd(&g.mu[2 * J + j], m2);
     }
   }
+  double dth0 = DA[0], dth1 = DA[FK_THREADS], dth2 = DA[2 * FK_THREADS], dth3 = DA[3 * FK_THREADS];
   dth0 = warp_sum(dth0);
   dth1 = warp_sum(dth1);
   dth2 = warp_sum(dth2);
@@ -617,23 +662,57 @@ __global__ void __launch_bounds__(FK_THREADS, 2) k_adj_masked(const AdjArgs<floa
   }
 }
 
-// d(scaled slope at m)/d u_i along one line, with the end rule
+// Gradient of the slope rule H(dl, dr) = 2 dl dr / (dl + dr) (dl dr > 0,
+// else 0) of Eq. (e300): dH/d dl = 2 (dr / (dl + dr))^2 and
+// dH/d dr = 2 (dl / (dl + dr))^2, 0 on the zero branch.  Formed from the
+// ratios, which lie in [0, 1]: differences near the bottom of the exponent
+// range (a march from the indicator leaves such values far from the
+// boundary) would overflow 1 / (dl + dr)^2.
 template <typename T>
-__device__ __forceinline__ T dslope(const T* u, int64_t stride, int n, int m, int i) {
-  int l1, l0, r1, r0;
-  if (m == 0) {
-    l1 = 1; l0 = 0; r1 = 2; r0 = 1;
-  } else if (m == n - 1) {
-    l1 = n - 1; l0 = n - 2; r1 = n - 2; r0 = n - 3;
+__device__ __forceinline__ void harm_grad(T dl, T dr, T& gl, T& gr) {
+  if (dl * dr > T(0)) {
+    const T sum = dl + dr;
+    const T ql = dl / sum, qr = dr / sum;
+    gl = T(2) * qr * qr;
+    gr = T(2) * ql * ql;
   } else {
-    l1 = m; l0 = m - 1; r1 = m + 1; r0 = m;
+    gl = T(0);
+    gr = T(0);
   }
-  const T dl = u[l1 * stride] - u[l0 * stride];
-  const T dr = u[r1 * stride] - u[r0 * stride];
-  if (!(dl * dr > T(0))) return T(0);
-  const T s = dl + dr;
-  const T gl = T(2) * dr * dr / (s * s), gr = T(2) * dl * dl / (s * s);
-  return gl * (T(i == l1) - T(i == l0)) + gr * (T(i == r1) - T(i == r0));
+}
+
+// Transposed slope map along one grid line, at node i of n (u and mu point
+// at node i, s is the stride between neighbours): the sum over the slopes
+// m = i-1, i, i+1 that read u_i of mu_m dH_m/du_i, where slope m reads
+// dl = u_m - u_{m-1} and dr = u_{m+1} - u_m.  The end rule stated after
+// Eq. (e300) makes the slope of node 0 the same function of u as that of
+// node 1 (the harmonic mean is symmetric), and node n-1 that of node n-2,
+// so mu of the end nodes is added to their neighbours' and only interior
+// three-point slopes remain.
+template <typename T>
+__device__ __forceinline__ T slope_line_t(const T* u, const T* mu, int64_t s, int n, int i) {
+  auto mu_f = [&](int d) {  // mu at node i + d, end nodes folded in
+    const int m = i + d;
+    if (m < 1 || m > n - 2) return T(0);
+    T v = mu[d * s];
+    if (m == 1) v += mu[(d - 1) * s];
+    if (m == n - 2) v += mu[(d + 1) * s];
+    return v;
+  };
+  T acc = T(0), gl, gr;
+  if (i >= 2) {  // slope i-1: u_i is its right node
+    harm_grad(u[-s] - u[-2 * s], u[0] - u[-s], gl, gr);
+    acc += mu_f(-1) * gr;
+  }
+  if (i >= 1 && i <= n - 2) {  // slope i
+    harm_grad(u[0] - u[-s], u[s] - u[0], gl, gr);
+    acc += mu_f(0) * (gl - gr);
+  }
+  if (i <= n - 3) {  // slope i+1: u_i is its left node
+    harm_grad(u[s] - u[0], u[2 * s] - u[s], gl, gr);
+    acc -= mu_f(1) * gl;
+  }
+  return acc;
 }
 
 // lambda^{n+1}_i = mu_u[i] + sum_m mu_x[m] dD^x_m/du_i + sum_m mu_y[m] dD^y_m/du_i
@@ -644,25 +723,8 @@ __global__ void k_adj_slopes_t(const T* __restrict__ u, const T* __restrict__ mu
   const int k = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || k >= ny) return;
   const int64_t J = (int64_t)nx * ny, j = (int64_t)k * nx + i;
-  T acc = mu[j];
-  const T* urow = u + (int64_t)k * nx;
-  const T* mx = mu + J + (int64_t)k * nx;
-  // slopes that read u_i: nodes i-1, i, i+1, and the end nodes within reach
-  for (int m = i - 2; m <= i + 2; ++m) {
-    if (m < 0 || m >= nx) continue;
-    const bool reach = (m >= i - 1 && m <= i + 1) || m == 0 || m == nx - 1;
-    if (!reach || mx[m] == T(0)) continue;
-    acc += mx[m] * dslope(urow, 1, nx, m, i);
-  }
-  const T* ucol = u + i;
-  const T* my = mu + 2 * J + i;
-  for (int m = k - 2; m <= k + 2; ++m) {
-    if (m < 0 || m >= ny) continue;
-    const bool reach = (m >= k - 1 && m <= k + 1) || m == 0 || m == ny - 1;
-    if (!reach || my[(int64_t)m * nx] == T(0)) continue;
-    acc += my[(int64_t)m * nx] * dslope(ucol, nx, ny, m, k);
-  }
-  lam_out[j] = acc;
+  lam_out[j] = mu[j] + slope_line_t(u + j, mu + J + j, (int64_t)1, nx, i) +
+               slope_line_t(u + j, mu + 2 * J + j, (int64_t)nx, ny, k);
 }
 
 template <typename T>
@@ -713,7 +775,8 @@ cudaError_t launch_adj(const AdjArgs<T>& g, int q, cudaStream_t s) {
 }
 
 size_t adj_masked_smem(int ly, int lp, int w) {
-  return (size_t)adj_tab_float4(w) * 16 + (size_t)ly * lp * (16 + 4 + 12);
+  return (size_t)adj_tab_float4(w) * 16 + (size_t)ly * lp * (16 + 4 + 12) +
+         (size_t)2 * w * FK_THREADS * 4 + (size_t)4 * FK_THREADS * 8;
 }
 
 // The piecewise-cubic weight tables of the masked adjoint, per axis.  With
@@ -841,9 +904,22 @@ bool adj_use_masked(const fk_plan* p) {
 }
 int adj_masked_ty(const fk_plan* p, int smem_max) {
   const int lx = 32 + 2 * p->mhalo[0] + 2;
+  auto bytes = [&](int ty) {
+    return adj_masked_smem(ty + 2 * p->mhalo[1] + 2, lx | 1, p->mwin) + kAdjStatic;
+  };
+  // FK_ADJ_TILE=ty: an explicit tile height (profiling)
+  if (const char* t = getenv("FK_ADJ_TILE")) {
+    const int ty = atoi(t);
+    if (ty >= 4 && ty <= 32 && bytes(ty) <= (size_t)smem_max) return ty;
+  }
+  // the tallest tile (<= 16 rows) with which kAdjMinBlocks CTAs share an
+  // SM, else the tallest that fits at all
+  int sm_smem = 0;
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
   for (int ty = 16; ty >= 4; ty -= 4)
-    if (adj_masked_smem(ty + 2 * p->mhalo[1] + 2, lx | 1, p->mwin) + kAdjStatic <= (size_t)smem_max)
-      return ty;
+    if (kAdjMinBlocks * (bytes(ty) + 1024) <= (size_t)sm_smem) return ty;
+  for (int ty = 16; ty >= 4; ty -= 4)
+    if (bytes(ty) <= (size_t)smem_max) return ty;
   return 0;
 }
 

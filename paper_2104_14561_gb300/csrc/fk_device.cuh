@@ -14,6 +14,21 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// Values the compiler cannot see through.  An offset by opaque_zero()
+// keeps per-point constants in shared memory from being hoisted out of a
+// loop into registers held across it; opaque(x) makes a later use of x
+// recompute what it derives from x instead of keeping those results live.
+__device__ __forceinline__ int opaque_zero() {
+  int z;
+  asm volatile("mov.u32 %0, 0;" : "=r"(z));
+  return z;
+}
+__device__ __forceinline__ float opaque(float x) {
+  float y;
+  asm volatile("mov.b32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Scaled PCHIP slope h*u'_j from the two neighbouring differences
 // (Eq. (e300)): 0 unless both have the same strict sign, else their
 // harmonic mean 2 dl dr / (dl + dr).

@@ -71,15 +71,6 @@ struct Scatter<W, W - 2> {
                                              float2, float2) {}
 };
 
-// A zero the compiler cannot see through: offsets by it keep per-point
-// constants in shared memory from being hoisted out of the node loop into
-// registers held across it.
-__device__ __forceinline__ int opaque_zero() {
-  int z;
-  asm volatile("mov.u32 %0, 0;" : "=r"(z));
-  return z;
-}
-
 // MINB: CTAs of 256 threads per SM the register budget is sized for
 // (3 -> 80 registers, 2 -> 128; variant 0 and 1 of the plan).
 template <int Q, int W, int MINB>

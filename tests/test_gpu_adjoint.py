@@ -73,6 +73,23 @@ def test_adjoint_fp64_vs_oracle(fk, oracle, family):
     assert np.abs(du - odu).max() <= 1e-12
 
 
+@pytest.mark.parametrize("n", [(3, 3), (5, 3), (3, 6), (4, 4)])
+def test_adjoint_fp64_tiny_meshes_vs_oracle(fk, oracle, n):
+    """Meshes with 3 or 4 nodes on an axis, where the end rule of the slopes
+    (node 0 takes node 1's slope, node n-1 that of node n-2) puts both ends'
+    slopes on the same interior stencil."""
+    w = dict(SMALL, n=n, n_steps=6)
+    shape = (n[1], n[0])
+    cot = np.random.default_rng(5).standard_normal(shape)
+    u0 = fk_inputs.random_field(shape, seed=7)
+    dth, du = _gpu_adjoint(fk, w, "fp64", cot, u0, K=2)
+    g = oracle.Grid(w["n"], w["lo"], w["hi"])
+    odth, odu = oracle.adjoint(g, oracle.CELLULAR_FLOW, list(w["params"]), w["q"], w["dt"],
+                               w["n_steps"], cot, u0)
+    np.testing.assert_allclose(dth, odth, rtol=1e-10, atol=1e-12)
+    assert np.abs(du - odu).max() <= 1e-12
+
+
 def test_adjoint_fp32_vs_oracle(fk, oracle):
     w = dict(SMALL, n_steps=60)
     shape = (w["n"][1], w["n"][0])
