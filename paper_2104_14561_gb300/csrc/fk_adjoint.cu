@@ -20,6 +20,7 @@
 // Memory: u is checkpointed every K steps on a forward pass; each segment
 // of K steps is recomputed from its checkpoint before its backward steps.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -437,6 +438,21 @@ __device__ __forceinline__ void tab_weights(Slots<W, K>& S, const float4* TB, in
   }
 }
 
+// Drift of node (i, k) over one step in cells (dt b / h), the same
+// expression as the forward step's.
+__device__ __forceinline__ void node_drift(const Step2D<float>& a, int i, int k, float& dx,
+                                           float& dy) {
+  if (a.family == FK_CELLULAR_FLOW) {
+    const float* ct = a.col_tab + 4 * (int64_t)i;
+    const float* rt = a.row_tab + 2 * (int64_t)k;
+    dx = a.kx * rt[0] * (a.A * ct[0] + a.e1 * ct[1]);
+    dy = a.ky * rt[1] * (a.A * ct[2] + a.e2 * ct[3]);
+  } else {
+    dx = a.cdx;
+    dy = a.cdy;
+  }
+}
+
 // Position of a node's points along one axis, in cells after the window
 // origin (the cell of point 0): z = offset of point 0, [lo, hi] the box;
 // whether all points stay inside, and then point 0's table piece and its
@@ -475,43 +491,102 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
   float4* TB = reinterpret_cast<float4*>(smem);  // weight tables
   float4* Rec = TB + adj_tab_float4(W);
   float* U = reinterpret_cast<float*>(Rec + ly * lp);
-  float* MU = U + ly * lp;  // 3 planes of ly x lp: mu_u, mu_X, mu_Y
-  float* RS = MU + 3 * ly * lp;  // per-thread row sums A_r, B_r
+  // the tile's mu accumulators: 3 planes of ly x lp (mu_u, mu_X, mu_Y) in
+  // fixed point, because 32-bit integer adds are the shared-memory atomics
+  // the hardware has (a float add is a compare-and-swap loop)
+  int* MU = reinterpret_cast<int*>(U + ly * lp);
+  float* RS = reinterpret_cast<float*>(MU + 3 * ly * lp);  // per-thread row sums A_r, B_r
   __shared__ double red[4][FK_THREADS / 32];
+  __shared__ float lred[FK_THREADS / 32];
+  __shared__ int fred[4][FK_THREADS / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = 1 + blockIdx.x * 32, k0 = 1 + blockIdx.y * a.ty;
   const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;
-  for (int e = tid; e < 3 * ly * lp; e += FK_THREADS) MU[e] = 0.f;
-  for (int e = tid; e < adj_tab_float4(W); e += FK_THREADS) TB[e] = g.tab[e];
-  masked_stage(a, Rec, U, gi0, gk0);  // ends with a barrier
-
-  // per-thread FP64 sums of the parameter derivatives (in shared memory:
-  // registers go to the window pass)
-  double* DA = reinterpret_cast<double*>(RS + 2 * W * FK_THREADS) + tid;
-#pragma unroll
-  for (int m = 0; m < 4; ++m) DA[m * FK_THREADS] = 0.0;
-  unsigned bad = 0;
   const int i = i0 + lane, li = i - gi0;
-  float* MX = MU + ly * lp;
-  float* MY = MX + ly * lp;
+  for (int e = tid; e < 3 * ly * lp; e += FK_THREADS) MU[e] = 0;
+  for (int e = tid; e < adj_tab_float4(W); e += FK_THREADS) TB[e] = g.tab[e];
+  {
+    // Fixed-point scale S (a power of two).  A node's 1D value weights are
+    // non-negative and sum to at most 1, its slope weights are at most 4/27
+    // in absolute value, so each of its contributions to a cell is at most
+    // |lambda_j|.  A cell is in the window of node j only if the window
+    // origin i_j + floor(dx_j + g_0) lies in the W columns up to the cell,
+    // so at most W + (spread of those floors over the tile) node columns,
+    // and as many rows, reach it: every accumulator stays below
+    // max|lambda| (W + spread_x)(W + spread_y), which S puts below 2^30.
+    float lmax = 0.f;
+    int fxl = INT_MAX, fxh = INT_MIN, fyl = INT_MAX, fyh = INT_MIN;
+    for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
+      const int k = k0 + ty;
+      if (i > a.nx - 2 || k > a.ny - 2) break;
+      const float lam = g.lam[(int64_t)k * a.nx + i];
+      if (lam == 0.f) continue;
+      float dx, dy;
+      node_drift(a, i, k, dx, dy);
+      const int fx = (int)floorf(dx + a.gx[0]), fy = (int)floorf(dy + a.gy[0]);
+      lmax = fmaxf(lmax, fabsf(lam));
+      fxl = min(fxl, fx);
+      fxh = max(fxh, fx);
+      fyl = min(fyl, fy);
+      fyh = max(fyh, fy);
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+      lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, m));
+      fxl = min(fxl, __shfl_xor_sync(0xffffffffu, fxl, m));
+      fxh = max(fxh, __shfl_xor_sync(0xffffffffu, fxh, m));
+      fyl = min(fyl, __shfl_xor_sync(0xffffffffu, fyl, m));
+      fyh = max(fyh, __shfl_xor_sync(0xffffffffu, fyh, m));
+    }
+    if (lane == 0) {
+      lred[warp] = lmax;
+      fred[0][warp] = fxl;
+      fred[1][warp] = fxh;
+      fred[2][warp] = fyl;
+      fred[3][warp] = fyh;
+    }
+  }
+  masked_stage(a, Rec, U, gi0, gk0);  // ends with a barrier
+  int s_exp = 0;  // S = 2^s_exp
+  {
+    float lmax = 0.f;
+    int fxl = INT_MAX, fxh = INT_MIN, fyl = INT_MAX, fyh = INT_MIN;
+#pragma unroll
+    for (int w = 0; w < FK_THREADS / 32; ++w) {
+      lmax = fmaxf(lmax, lred[w]);
+      fxl = min(fxl, fred[0][w]);
+      fxh = max(fxh, fred[1][w]);
+      fyl = min(fyl, fred[2][w]);
+      fyh = max(fyh, fred[3][w]);
+    }
+    if (lmax > 0.f) {
+      const float ncov = (float)(W + fxh - fxl) * (float)(W + fyh - fyl);
+      int b_exp = 0;
+      frexpf(lmax * ncov, &b_exp);  // bound < 2^b_exp
+      s_exp = min(30 - b_exp, 126);
+    }
+  }
+
+  // per-thread sums of the parameter derivatives over the thread's few
+  // nodes (in shared memory: registers go to the window pass); the sums
+  // over the tile and the grid are FP64
+  float* DA = RS + 2 * W * FK_THREADS + tid;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) DA[m * FK_THREADS] = 0.f;
+  unsigned bad = 0;
+  int* MX = MU + ly * lp;
+  int* MY = MX + ly * lp;
 #pragma unroll 1
   for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
     const int k = k0 + ty;
     if (i > a.nx - 2 || k > a.ny - 2) break;
-    const float lam = g.lam[(int64_t)k * a.nx + i];
-    if (lam == 0.f) continue;
+    const float* lam_at = g.lam + (int64_t)k * a.nx + i;
+    const float lamS = ldexpf(*lam_at, s_exp);  // scaled to the accumulators' fixed point
+    if (lamS == 0.f) continue;
     const int lk = k - gk0;
     const float uj = U[lk * lp + li];
     float dx, dy;
-    if (a.family == FK_CELLULAR_FLOW) {
-      const float* ct = a.col_tab + 4 * (int64_t)i;
-      const float* rt = a.row_tab + 2 * (int64_t)k;
-      dx = a.kx * rt[0] * (a.A * ct[0] + a.e1 * ct[1]);
-      dy = a.ky * rt[1] * (a.A * ct[2] + a.e2 * ct[3]);
-    } else {
-      dx = a.cdx;
-      dy = a.cdy;
-    }
+    node_drift(a, i, k, dx, dy);
     const float fx0 = floorf(dx + a.gx[0]), fy0 = floorf(dy + a.gy[0]);
     int wx = li + (int)fx0, wy = lk + (int)fy0;
     if (wx < 1 || wx + W - 1 > lx - 2 || wy < 1 || wy + W - 1 > ly - 2) {
@@ -549,7 +624,7 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
       const int o = (wy + r) * lp + wx;
       const float4* row = Rec + o;
       const float Pr = YV.v[0][r], Sr = YV.v[1][r];
-      const float lP = lam * Pr, lS = lam * Sr;
+      const float lP = lamS * Pr, lS = lamS * Sr;
       const float2 PP = f2(Pr, Pr), LP = f2(lP, lP);
       float2 AE = f2(0.f, 0.f);
       float Br = 0.f;
@@ -563,9 +638,9 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
         CD[c] = fma2(PP, ex, CD[c]);
         CD[c].x = fmaf(Sr, v.z, CD[c].x);
         const float2 m = mul2(LP, ph);
-        atomicAdd(&MU[o + c], m.x);
-        atomicAdd(&MX[o + c], m.y);
-        atomicAdd(&MY[o + c], lS * ph.x);
+        atomicAdd(&MU[o + c], __float2int_rn(m.x));
+        atomicAdd(&MX[o + c], __float2int_rn(m.y));
+        atomicAdd(&MY[o + c], __float2int_rn(lS * ph.x));
       }
       AR[r * FK_THREADS] = AE.x + AE.y;
       BR[r * FK_THREADS] = Br;
@@ -619,16 +694,17 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
       ax[1] = 0.f;   ay[1] = g.cby;
       ax[2] = 0.f;   ay[2] = 0.f;
     }
-    const double l = (double)lam;
-    DA[0] += l * ((double)ax[0] * Gx + (double)ay[0] * Gy);
-    DA[FK_THREADS] += l * ((double)ax[1] * Gx + (double)ay[1] * Gy);
-    DA[2 * FK_THREADS] += l * ((double)ax[2] * Gx + (double)ay[2] * Gy);
-    DA[3 * FK_THREADS] += l * (double)g.cn * ((double)Gxn + (double)Gyn);
+    const float lam = *lam_at;
+    DA[0] += lam * (ax[0] * Gx + ay[0] * Gy);
+    DA[FK_THREADS] += lam * (ax[1] * Gx + ay[1] * Gy);
+    DA[2 * FK_THREADS] += lam * (ax[2] * Gx + ay[2] * Gy);
+    DA[3 * FK_THREADS] += lam * g.cn * (Gxn + Gyn);
   }
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
   __syncthreads();
   // flush the tile's accumulators (halo included) into the global mu
   const int64_t J = (int64_t)a.nx * a.ny;
+  const float fix_inv = ldexpf(1.f, -s_exp);
   for (int r = warp; r < ly; r += FK_THREADS / 32) {
     const int gk = gk0 + r;
     if (gk < 0 || gk >= a.ny) continue;
@@ -637,13 +713,15 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
       if (gi < 0 || gi >= a.nx) continue;
       const int64_t j = (int64_t)gk * a.nx + gi;
       const int o = r * lp + c;
-      const float m0 = MU[o], m1 = MX[o], m2 = MY[o];
+      const float m0 = (float)MU[o] * fix_inv, m1 = (float)MX[o] * fix_inv,
+                  m2 = (float)MY[o] * fix_inv;
       if (m0 != 0.f) atomicAdd(&g.mu[j], m0);
       if (m1 != 0.f) atomicAdd(&g.mu[J + j], m1);
       if (m2 != 0.f) atomicAdd(&g.mu[2 * J + j], m2);
     }
   }
-  double dth0 = DA[0], dth1 = DA[FK_THREADS], dth2 = DA[2 * FK_THREADS], dth3 = DA[3 * FK_THREADS];
+  double dth0 = DA[0], dth1 = DA[FK_THREADS], dth2 = DA[2 * FK_THREADS],
+         dth3 = DA[3 * FK_THREADS];
   dth0 = warp_sum(dth0);
   dth1 = warp_sum(dth1);
   dth2 = warp_sum(dth2);
@@ -671,8 +749,7 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
 template <typename T>
 __device__ __forceinline__ void harm_grad(T dl, T dr, T& gl, T& gr) {
   if (dl * dr > T(0)) {
-    const T sum = dl + dr;
-    const T ql = dl / sum, qr = dr / sum;
+    const T ql = dl / (dl + dr), qr = T(1) - ql;  // dr / (dl + dr)
     gl = T(2) * qr * qr;
     gr = T(2) * ql * ql;
   } else {
@@ -715,16 +792,22 @@ __device__ __forceinline__ T slope_line_t(const T* u, const T* mu, int64_t s, in
   return acc;
 }
 
-// lambda^{n+1}_i = mu_u[i] + sum_m mu_x[m] dD^x_m/du_i + sum_m mu_y[m] dD^y_m/du_i
+// lambda^{n+1}_i = mu_u[i] + sum_m mu_x[m] dD^x_m/du_i + sum_m mu_y[m] dD^y_m/du_i;
+// also clears node i of the other mu buffer, which the next backward step
+// accumulates into
 template <typename T>
 __global__ void k_adj_slopes_t(const T* __restrict__ u, const T* __restrict__ mu,
-                               T* __restrict__ lam_out, int nx, int ny) {
+                               T* __restrict__ lam_out, T* __restrict__ mu_next, int nx,
+                               int ny) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || k >= ny) return;
   const int64_t J = (int64_t)nx * ny, j = (int64_t)k * nx + i;
   lam_out[j] = mu[j] + slope_line_t(u + j, mu + J + j, (int64_t)1, nx, i) +
                slope_line_t(u + j, mu + 2 * J + j, (int64_t)nx, ny, k);
+  mu_next[j] = T(0);
+  mu_next[J + j] = T(0);
+  mu_next[2 * J + j] = T(0);
 }
 
 template <typename T>
@@ -776,7 +859,7 @@ cudaError_t launch_adj(const AdjArgs<T>& g, int q, cudaStream_t s) {
 
 size_t adj_masked_smem(int ly, int lp, int w) {
   return (size_t)adj_tab_float4(w) * 16 + (size_t)ly * lp * (16 + 4 + 12) +
-         (size_t)2 * w * FK_THREADS * 4 + (size_t)4 * FK_THREADS * 8;
+         (size_t)2 * w * FK_THREADS * 4 + (size_t)4 * FK_THREADS * 4;
 }
 
 // The piecewise-cubic weight tables of the masked adjoint, per axis.  With
@@ -944,7 +1027,10 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
   g.s.lyr = g.s.ly | 1;
   g.s.u_in = (const T*)u_in;
   g.lam = (const T*)lam;
-  g.mu = (T*)p->adj_mu;
+  // two mu buffers of 3 J values: step n accumulates into buffer n % 2
+  // while its slope transpose clears the other one for step n + 1
+  g.mu = (T*)p->adj_mu + (n & 1) * 3 * p->J;
+  T* mu_next = (T*)p->adj_mu + ((n + 1) & 1) * 3 * p->J;
   g.dth = dth;
   const double tn = n * p->dt;
   if (p->coeffs.family == FK_CELLULAR_FLOW) {
@@ -988,11 +1074,9 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
   }
   if (e != cudaSuccess) return FK_ERR_CUDA;
   const dim3 b(32, 8), gr((p->grid.n[0] + 31) / 32, (p->grid.n[1] + 7) / 8);
-  k_adj_slopes_t<T><<<gr, b, 0, s>>>((const T*)u_in, (const T*)p->adj_mu, (T*)lam_out,
+  k_adj_slopes_t<T><<<gr, b, 0, s>>>((const T*)u_in, (const T*)g.mu, (T*)lam_out, mu_next,
                                      p->grid.n[0], p->grid.n[1]);
   e = cudaGetLastError();
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(p->adj_mu, 0, (size_t)3 * p->J * sizeof(T), s);
   return e == cudaSuccess ? FK_OK : FK_ERR_CUDA;
 }
 
@@ -1036,8 +1120,8 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
         cudaSuccess)
       return FK_ERR_CUDA;
   }
-  // workspace: checkpoints (M+1), a segment (K), lambda x2, mu (3 fields), dtheta
-  const int64_t need = (int64_t)(M + 1 + K + 2 + 3) * fb + 64;
+  // workspace: checkpoints (M+1), a segment (K), lambda x2, mu (2 x 3 fields), dtheta
+  const int64_t need = (int64_t)(M + 1 + K + 2 + 6) * fb + 64;
   if (p->adj_bytes < need) {
     if (cudaStreamSynchronize(s) != cudaSuccess) return FK_ERR_CUDA;
     fk_dev_free(p->adj_ws);
@@ -1052,7 +1136,7 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
   char* seg = base + (int64_t)(M + 1) * fb;
   void* lam[2] = {seg + (int64_t)K * fb, seg + (int64_t)(K + 1) * fb};
   p->adj_mu = seg + (int64_t)(K + 2) * fb;
-  double* dth = dtheta ? dtheta : (double*)(seg + (int64_t)(K + 5) * fb);
+  double* dth = dtheta ? dtheta : (double*)(seg + (int64_t)(K + 8) * fb);
   auto slot = [&](int n) { return n == N ? M : n / K; };  // n == N or n % K == 0
 
   // forward pass with checkpoints
@@ -1072,7 +1156,7 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
       src = dst;
     }
   }
-  if (cudaMemsetAsync(p->adj_mu, 0, (size_t)3 * fb, s) != cudaSuccess ||
+  if (cudaMemsetAsync(p->adj_mu, 0, (size_t)6 * fb, s) != cudaSuccess ||
       cudaMemsetAsync(dth, 0, 4 * sizeof(double), s) != cudaSuccess)
     return FK_ERR_CUDA;
   // lambda^0 = g

@@ -186,7 +186,7 @@ struct fk_plan {
   // adjoint (fk_adjoint.cu): checkpoints, segment, lambda, mu, dtheta
   void* adj_ws;
   int64_t adj_bytes;
-  void* adj_mu;      // 3 J accumulators inside adj_ws
+  void* adj_mu;      // two buffers of 3 J accumulators inside adj_ws
   int adj_ty;        // tile height of the masked-window adjoint (0: per-point scatter)
   int adj_kernel;    // backward form of the last fk_adjoint: 0 none, 1 scatter, 2 masked
   void* adj_tab;     // piecewise-cubic weight tables of the masked adjoint (device, float4)
