@@ -496,7 +496,6 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
   // the hardware has (a float add is a compare-and-swap loop)
   int* MU = reinterpret_cast<int*>(U + ly * lp);
   float* RS = reinterpret_cast<float*>(MU + 3 * ly * lp);  // per-thread row sums A_r, B_r
-  __shared__ double red[4][FK_THREADS / 32];
   __shared__ float lred[FK_THREADS / 32];
   __shared__ int fred[4][FK_THREADS / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -720,23 +719,17 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
       if (m2 != 0.f) atomicAdd(&g.mu[2 * J + j], m2);
     }
   }
-  double dth0 = DA[0], dth1 = DA[FK_THREADS], dth2 = DA[2 * FK_THREADS],
-         dth3 = DA[3 * FK_THREADS];
-  dth0 = warp_sum(dth0);
-  dth1 = warp_sum(dth1);
-  dth2 = warp_sum(dth2);
-  dth3 = warp_sum(dth3);
-  if (lane == 0) {
-    red[0][warp] = dth0;
-    red[1][warp] = dth1;
-    red[2][warp] = dth2;
-    red[3][warp] = dth3;
-  }
-  __syncthreads();
-  if (tid < 4) {
-    double sum = 0.0;
-    for (int w = 0; w < FK_THREADS / 32; ++w) sum += red[tid][w];
-    if (sum != 0.0) atomicAdd(&g.dth[tid], sum);
+  // tile sums of the parameter derivatives (the per-thread sums are visible
+  // since the barrier above): warp q < 4 adds up quantity q, 8 per-thread
+  // sums per lane in FP32, then the lanes in FP64 (the FP64 pipe is slow:
+  // one reduction per quantity, not one per warp)
+  if (warp < 4) {
+    const float* dq = RS + 2 * W * FK_THREADS + warp * FK_THREADS;
+    float part = 0.f;
+#pragma unroll
+    for (int m = 0; m < FK_THREADS / 32; ++m) part += dq[lane + 32 * m];
+    const double sum = warp_sum((double)part);
+    if (lane == 0 && sum != 0.0) atomicAdd(&g.dth[warp], sum);
   }
 }
 
@@ -795,19 +788,27 @@ __device__ __forceinline__ T slope_line_t(const T* u, const T* mu, int64_t s, in
 // lambda^{n+1}_i = mu_u[i] + sum_m mu_x[m] dD^x_m/du_i + sum_m mu_y[m] dD^y_m/du_i;
 // also clears node i of the other mu buffer, which the next backward step
 // accumulates into
+// (kSlopesRows rows per thread, blockDim.y apart, so that each thread has
+// several independent gathers in flight)
+constexpr int kSlopesRows = 2;
 template <typename T>
 __global__ void k_adj_slopes_t(const T* __restrict__ u, const T* __restrict__ mu,
                                T* __restrict__ lam_out, T* __restrict__ mu_next, int nx,
                                int ny) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= nx || k >= ny) return;
-  const int64_t J = (int64_t)nx * ny, j = (int64_t)k * nx + i;
-  lam_out[j] = mu[j] + slope_line_t(u + j, mu + J + j, (int64_t)1, nx, i) +
-               slope_line_t(u + j, mu + 2 * J + j, (int64_t)nx, ny, k);
-  mu_next[j] = T(0);
-  mu_next[J + j] = T(0);
-  mu_next[2 * J + j] = T(0);
+  if (i >= nx) return;
+  const int64_t J = (int64_t)nx * ny;
+#pragma unroll
+  for (int r = 0; r < kSlopesRows; ++r) {
+    const int k = (blockIdx.y * kSlopesRows + r) * blockDim.y + threadIdx.y;
+    if (k >= ny) break;
+    const int64_t j = (int64_t)k * nx + i;
+    lam_out[j] = mu[j] + slope_line_t(u + j, mu + J + j, (int64_t)1, nx, i) +
+                 slope_line_t(u + j, mu + 2 * J + j, (int64_t)nx, ny, k);
+    mu_next[j] = T(0);
+    mu_next[J + j] = T(0);
+    mu_next[2 * J + j] = T(0);
+  }
 }
 
 template <typename T>
@@ -1073,7 +1074,8 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
     e = launch_adj<T>(g, p->q, s);
   }
   if (e != cudaSuccess) return FK_ERR_CUDA;
-  const dim3 b(32, 8), gr((p->grid.n[0] + 31) / 32, (p->grid.n[1] + 7) / 8);
+  const dim3 b(32, 8),
+      gr((p->grid.n[0] + 31) / 32, (p->grid.n[1] + 8 * kSlopesRows - 1) / (8 * kSlopesRows));
   k_adj_slopes_t<T><<<gr, b, 0, s>>>((const T*)u_in, (const T*)g.mu, (T*)lam_out, mu_next,
                                      p->grid.n[0], p->grid.n[1]);
   e = cudaGetLastError();
