@@ -788,27 +788,19 @@ __device__ __forceinline__ T slope_line_t(const T* u, const T* mu, int64_t s, in
 // lambda^{n+1}_i = mu_u[i] + sum_m mu_x[m] dD^x_m/du_i + sum_m mu_y[m] dD^y_m/du_i;
 // also clears node i of the other mu buffer, which the next backward step
 // accumulates into
-// (kSlopesRows rows per thread, blockDim.y apart, so that each thread has
-// several independent gathers in flight)
-constexpr int kSlopesRows = 2;
 template <typename T>
 __global__ void k_adj_slopes_t(const T* __restrict__ u, const T* __restrict__ mu,
                                T* __restrict__ lam_out, T* __restrict__ mu_next, int nx,
                                int ny) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nx) return;
-  const int64_t J = (int64_t)nx * ny;
-#pragma unroll
-  for (int r = 0; r < kSlopesRows; ++r) {
-    const int k = (blockIdx.y * kSlopesRows + r) * blockDim.y + threadIdx.y;
-    if (k >= ny) break;
-    const int64_t j = (int64_t)k * nx + i;
-    lam_out[j] = mu[j] + slope_line_t(u + j, mu + J + j, (int64_t)1, nx, i) +
-                 slope_line_t(u + j, mu + 2 * J + j, (int64_t)nx, ny, k);
-    mu_next[j] = T(0);
-    mu_next[J + j] = T(0);
-    mu_next[2 * J + j] = T(0);
-  }
+  const int k = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || k >= ny) return;
+  const int64_t J = (int64_t)nx * ny, j = (int64_t)k * nx + i;
+  lam_out[j] = mu[j] + slope_line_t(u + j, mu + J + j, (int64_t)1, nx, i) +
+               slope_line_t(u + j, mu + 2 * J + j, (int64_t)nx, ny, k);
+  mu_next[j] = T(0);
+  mu_next[J + j] = T(0);
+  mu_next[2 * J + j] = T(0);
 }
 
 template <typename T>
@@ -1074,8 +1066,7 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
     e = launch_adj<T>(g, p->q, s);
   }
   if (e != cudaSuccess) return FK_ERR_CUDA;
-  const dim3 b(32, 8),
-      gr((p->grid.n[0] + 31) / 32, (p->grid.n[1] + 8 * kSlopesRows - 1) / (8 * kSlopesRows));
+  const dim3 b(32, 8), gr((p->grid.n[0] + 31) / 32, (p->grid.n[1] + 7) / 8);
   k_adj_slopes_t<T><<<gr, b, 0, s>>>((const T*)u_in, (const T*)g.mu, (T*)lam_out, mu_next,
                                      p->grid.n[0], p->grid.n[1]);
   e = cudaGetLastError();
