@@ -40,7 +40,7 @@ import fk_inputs  # noqa: E402
 METRIC = "node-quadrature updates/s & HBM GB/s (2D, 36-pt GH, FP32/FP64); adjoint/forward"
 UNIT = "node-quadrature updates/s"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
-FLOP_PER_UPDATE = 26                # see the design doc: 13 multiply-adds per query
+FLOP_PER_UPDATE = 26                # 13 multiply-adds per query: 12 Hermite terms + the weighted sum
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (profiling recipe)
 PROFILE_DIR = os.path.join(ROOT, "profiles")
@@ -411,6 +411,86 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
     plan.close()
 
 
+# ---------------------------------------------------------- horizons -----
+def run_horizons(args, rank: int, world: int, local_rank: int):
+    """Algorithm 1 workload: P(t_k, .) for every horizon k = 1..200 of the
+    time-dependent flow on 1025 x 513 (FP32), one fk_solve_horizons call per
+    step: N (N + 1) / 2 = 20100 field-steps, with all horizons still active
+    at a step advanced by one launch.  The single march of N steps (the last
+    horizon alone) is timed beside it."""
+    import torch
+    import paper_2104_14561_gb300 as fk
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = workload_of(args)
+    plan = fk.Plan(fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
+                               params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
+                               precision=w["precision"]))
+    N = w["n_steps"]
+    out_all = torch.empty((N,) + plan.shape, dtype=plan.dtype, device=dev)
+    out = plan.empty()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    field_steps = N * (N + 1) // 2
+    units = units_per_solve(w) / N * field_steps
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+        stream.synchronize()
+        ms = []
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        return sum(ms) / len(ms)
+
+    clk = ClockSampler(local_rank)
+    clk.start()
+    ms_h = timed(lambda: plan.solve_horizons(None, out_all, stream=stream))
+    clocks = clk.stop()
+    ms_single = timed(lambda: plan.solve(None, out, stream=stream))
+    torch.cuda.synchronize()
+    if plan.last_device_error() != 0:
+        raise RuntimeError("device-side error in the horizon march")
+    info = plan.info()
+    ms_max = max_over_ranks(ms_h)
+    if rank != 0:
+        plan.close()
+        return
+    flop = FLOP_PER_UPDATE * units
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flop / (ms_h * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": whole_job_rate(units, world, ms_max), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "grid": list(w["n"]), "q_per_dim": w["q"],
+                   "horizons": N, "field_steps": field_steps, "dt": w["dt"],
+                   "step_kernel": info["step_kernel"],
+                   "l2": "flushed (512 MB write) before every timed call; the "
+                         f"{2 * N * math.prod(w['n']) * 4 / 1e9:.1f} GB of fields exceed the L2"},
+        "roofline": {"kernel": "k_step2dm (all horizons of a step per launch)", "bound": "alu",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None},
+        "single_march_ms": ms_single,
+        "field_step_us": ms_h * 1e3 / field_steps,
+        "single_step_us": ms_single * 1e3 / N,
+        "gpu_launches": N + 1,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 # ------------------------------------------------------------ ranks -----
 def max_over_ranks(value: float, dist=None, device=None) -> float:
     """The largest per-rank figure over all ranks (the value itself when the
@@ -580,6 +660,8 @@ def main():
             run_batched(args, rank, world, local_rank)
         elif args.workload == "adjoint_1025x513":
             run_adjoint(args, rank, world, local_rank)
+        elif args.workload == "horizons_1025x513":
+            run_horizons(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

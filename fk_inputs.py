@@ -58,6 +58,10 @@ WORKLOADS = {
     "adjoint_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
                              family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
                              q=6, dt=1e-3, n_steps=2000, precision="fp32"),
+    # every horizon t_k = k dt, k = 1..200, of the time-dependent flow (Algorithm 1)
+    "horizons_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
+                              family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
+                              q=6, dt=1e-3, n_steps=200, precision="fp32"),
 }
 
 BATCH_SEED = 20240214

@@ -186,6 +186,28 @@ fk_status fk_march(fk_plan *plan, int n_from, int n_to, const void *u_in,
                    void *u_out, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * fk_solve_horizons -- Algorithm 1 of Sec. 3.2: P(t_k, x_j) for every
+ * horizon t_k = k dt, k = 1..N, in one backward pass.  Horizon k is the
+ * march of Scheme 1 over k steps with the coefficients of times
+ * t_{k-1}, ..., t_0 (start at time 0, exit by t_k), so for coefficients
+ * that depend on t each horizon is a separate march; the pass updates all
+ * horizons that are still active at step n with one launch.  Work is
+ * N (N + 1) / 2 single-field steps.  (For coefficients that do not depend
+ * on t, fk_solve's snapshots give the same history from one march.)
+ *   u_terminal  device pointer to the terminal field (J values) shared by
+ *               all horizons, or NULL for the indicator chi.  Read only; it
+ *               must not overlap p_out.
+ *   p_out       device buffer of N fields of J values (the plan's precision);
+ *               field k - 1 receives P(t_k, .).
+ *   stream      CUDA stream; N launches are enqueued.
+ * The plan allocates a second buffer of N fields on first use (grown on
+ * demand, freed with the plan).  Errors: FK_ERR_INVALID_ARG,
+ * FK_ERR_UNSUPPORTED (FK_PATH_CSR plans), FK_ERR_OOM, FK_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+fk_status fk_solve_horizons(fk_plan *plan, const void *u_terminal, void *p_out,
+                            cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * fk_solve_batched -- fk_solve for n independent plans (same precision,
  * dim = 2, FK_PATH_MATRIX_FREE, same q_per_dim and n_steps) in ONE
  * persistent kernel: the tiles of every instance share one work list and

@@ -22,8 +22,8 @@ FK_ALL_FACES_ABSORBING = 0x3F
 
 # every symbol include/fk.h declares
 EXPORTS = ("fk_plan_create", "fk_plan_destroy", "fk_plan_get_info", "fk_gauss_hermite",
-           "fk_solve", "fk_march", "fk_solve_batched", "fk_adjoint", "fk_status_string",
-           "fk_last_device_error", "fk_solve_static")
+           "fk_solve", "fk_march", "fk_solve_horizons", "fk_solve_batched", "fk_adjoint",
+           "fk_status_string", "fk_last_device_error", "fk_solve_static")
 
 
 class FkError(RuntimeError):
@@ -89,6 +89,8 @@ def load(build_if_missing: bool = False):
     lib.fk_solve.restype = st
     lib.fk_march.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     lib.fk_march.restype = st
+    lib.fk_solve_horizons.argtypes = [vp, vp, vp, vp]
+    lib.fk_solve_horizons.restype = st
     lib.fk_solve_batched.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(vp), vp]
     lib.fk_solve_batched.restype = st

@@ -14,6 +14,20 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// The fields of a step launch: with MF (several fields, Algorithm 1) the
+// field of blockIdx.z, else u_in / u_out as passed (no offset arithmetic
+// in the single-field kernels).
+template <bool MF, typename T>
+__device__ __forceinline__ const T* field_in(const Step2D<T>& a) {
+  if constexpr (MF) return a.in();
+  else return a.u_in;
+}
+template <bool MF, typename T>
+__device__ __forceinline__ T* field_out(const Step2D<T>& a) {
+  if constexpr (MF) return a.out();
+  else return a.u_out;
+}
+
 // Values the compiler cannot see through.  An offset by opaque_zero()
 // keeps per-point constants in shared memory from being hoisted out of a
 // loop into registers held across it; opaque(x) makes a later use of x
@@ -52,14 +66,14 @@ __device__ __forceinline__ float pchip_fast<float>(float dl, float dr) {
 // Boundary nodes adjacent to interior node (i, k) hold 1 (Eq. (e3)).  On a
 // mesh with 3 nodes along an axis the single interior line is next to both
 // faces of that axis, so every flag is tested on its own.
-template <typename T>
+template <bool MF, typename T>
 __device__ __forceinline__ void write_adjacent_boundary(const Step2D<T>& a, int i, int k) {
   const int64_t nx = a.nx;
   const bool L = (i == 1), Rt = (i == a.nx - 2), B = (k == 1), Tp = (k == a.ny - 2);
   if (L | Rt | B | Tp) {
     const int64_t top = (int64_t)(a.ny - 1) * nx, row = (int64_t)k * nx;
     auto one = [&](int64_t j) {
-      a.u_out[j] = T(1);
+      field_out<MF>(a)[j] = T(1);
       if (a.snap) a.snap[j] = T(1);
     };
     if (L) one(row);
@@ -78,6 +92,7 @@ __device__ __forceinline__ void write_adjacent_boundary(const Step2D<T>& a, int 
 // for a CTA of FK_THREADS threads whose staged node (0, 0) is global node
 // (gi0, gk0); a.lx x a.ly nodes, row pitch a.lyr (odd).  Ends with the
 // records visible to the whole CTA.
+template <bool MF = false>
 __device__ __forceinline__ void masked_stage(const Step2D<float>& a, float4* Rec, float* U,
                                              int gi0, int gk0) {
   const int lx = a.lx, ly = a.ly, lp = a.lyr;
@@ -91,13 +106,13 @@ __device__ __forceinline__ void masked_stage(const Step2D<float>& a, float4* Rec
     for (int r = warp; r < ly; r += FK_THREADS / 32) {
       const int gk = gk0 + r;
       const bool rowin = (unsigned)gk < (unsigned)a.ny;
-      const float* src = a.u_in + (int64_t)(rowin ? gk : 0) * a.nx;
+      const float* src = field_in<MF>(a) + (int64_t)(rowin ? gk : 0) * a.nx;
       const uint32_t drow = sU + (uint32_t)(r * lp) * 4u;
       for (int c = lane; c < lx; c += 32) {
         const int gi = gi0 + c;
         const bool in = rowin && (unsigned)gi < (unsigned)a.nx;
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c),
-                     "l"(in ? src + gi : a.u_in), "r"(in ? 4 : 0));
+                     "l"(in ? src + gi : field_in<MF>(a)), "r"(in ? 4 : 0));
       }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");

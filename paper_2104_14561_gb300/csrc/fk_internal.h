@@ -71,6 +71,14 @@ struct Step2D {
   int mode, win, row_lo, row_hi, nb_lo;
   int wm[FK_MAXQ_2D];  // floor(gy_q - gy_0): y-cell offset of point q in the window
   T wmf[FK_MAXQ_2D];   // the same offsets as T (mode 2: equal on both axes)
+  // Several independent fields marched by one launch (the horizons of
+  // Algorithm 1, Sec. 3.2): blockIdx.z selects the field at offset
+  // z * zstride of u_in and u_out, ncols fields (1 and zstride 0 for one
+  // field; snapshots are not taken then).
+  int64_t zstride;
+  int ncols;
+  __device__ __forceinline__ const T* in() const { return u_in + (int64_t)blockIdx.z * zstride; }
+  __device__ __forceinline__ T* out() const { return u_out + (int64_t)blockIdx.z * zstride; }
 };
 
 template <typename T>
@@ -85,6 +93,10 @@ struct Step1D {
   T cdx;    // b dt / h
   T g[FK_MAXQ], w[FK_MAXQ];
   unsigned* err;
+  int64_t zstride;  // fields marched by one launch, as in Step2D
+  int ncols;
+  __device__ __forceinline__ const T* in() const { return u_in + (int64_t)blockIdx.z * zstride; }
+  __device__ __forceinline__ T* out() const { return u_out + (int64_t)blockIdx.z * zstride; }
 };
 
 // Shared memory bytes of one 2D step CTA.
@@ -129,6 +141,11 @@ cudaError_t fk_launch_march1d_cluster(const Step1D<T>& a, int q, int ctas, const
                                       T* u_out, T* snaps, int stride, int steps, cudaStream_t s);
 int fk_prepare_march1d_cluster(int q, int elem);
 cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s);
+// Starting fields of the horizon march: field c = 1..nfields (at offset
+// (c - 1) J) of buffer `odd` for odd c and of buffer `even` for even c gets
+// src (J values) or, with src NULL, the terminal indicator.
+cudaError_t fk_launch_fill_fields(void* even, void* odd, const void* src, int dim, int nx, int ny,
+                                  int elem, int nfields, cudaStream_t s);
 cudaError_t fk_launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
 
 struct fk_plan {
@@ -183,6 +200,9 @@ struct fk_plan {
   void* batch_rec;   // 6 J values: slope records of this instance
   void* batch_work;  // BatchWork of a batch whose first plan is this one
   int batch_grid;    // CTAs of the last batched launch
+  // fk_solve_horizons: the second buffer of the N horizon fields
+  void* hz_ws;
+  int64_t hz_bytes;
   // adjoint (fk_adjoint.cu): checkpoints, segment, lambda, mu, dtheta
   void* adj_ws;
   int64_t adj_bytes;
@@ -202,6 +222,10 @@ int fk_batch_mode(const fk_plan* p);
 // Step launchers that fill the argument struct from the plan (fk_plan.cu).
 fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void* snap,
                           cudaStream_t s);
+// The same step for nfields fields at J-value spacing (u_in and u_out point
+// at the first), one launch (matrix-free path only).
+fk_status fk_enqueue_step_fields(fk_plan* p, int n, const void* u_in, void* u_out, int nfields,
+                                 cudaStream_t s);
 void fk_fill_step2d_f32(const fk_plan* p, int n, Step2D<float>* a);
 void fk_fill_step2d_f64(const fk_plan* p, int n, Step2D<double>* a);
 

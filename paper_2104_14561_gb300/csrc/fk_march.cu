@@ -113,7 +113,7 @@ __device__ __forceinline__ void lds_s_next(uint32_t a, double& x, double& y) {
 // Phases 1-3 of a step CTA: stage u^{n+1} over the tile plus halo, compute
 // the scaled PCHIP slopes, pack the cell records.  gi0/gk0 are the global
 // node indices of staged column / row 0.
-template <typename T>
+template <bool MF, typename T>
 __device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* S, T* U, int gi0,
                                            int gk0, int warp, int lane) {
   const int lx = a.lx, ly = a.ly, lyr = a.lyr;
@@ -125,11 +125,11 @@ __device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* 
   for (int lk = warp; lk < ly; lk += FK_THREADS / 32) {
     const int gk = gk0 + lk;
     const bool rowin = gk >= 0 && gk < a.ny;
-    const T* src = a.u_in + (int64_t)(rowin ? gk : 0) * a.nx;
+    const T* src = field_in<MF>(a) + (int64_t)(rowin ? gk : 0) * a.nx;
     for (int li = lane; li < lx; li += 32) {
       const int gi = gi0 + li;
       const bool in = rowin && gi >= 0 && gi < a.nx;
-      const T* g = in ? src + gi : a.u_in;
+      const T* g = in ? src + gi : field_in<MF>(a);
       const uint32_t d = sU + (uint32_t)(lk * lx + li) * (uint32_t)sizeof(T);
       asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(g),
                    "n"(sizeof(T)), "r"(in ? (int)sizeof(T) : 0));
@@ -169,7 +169,7 @@ __device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* 
 // Phase 4 of the direct kernel: the Gauss-Hermite sum of every output node
 // of rows [k0, min(k0 + ty, k_end)) of this tile, one node per thread and
 // pass (column i0 + lane, row k0 + warp + 8 m).  Returns the range-check flag.
-template <typename T, int Q>
+template <typename T, int Q, bool MF>
 __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>* R,
                                                  const V2<T>* S, int i0, int k0, int k_end,
                                                  int gi0, int gk0, int warp, int lane) {
@@ -278,14 +278,15 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
     }
     const T un = uj + acc;
     const int64_t j = (int64_t)k * a.nx + i;
-    a.u_out[j] = un;
+    field_out<MF>(a)[j] = un;
     if (a.snap) a.snap[j] = un;
-    write_adjacent_boundary(a, i, k);
+    write_adjacent_boundary<MF>(a, i, k);
   }
   return bad;
 }
 
-template <typename T, int Q, int MINB>
+// MF: several fields per launch (blockIdx.z), for Algorithm 1.
+template <typename T, int Q, int MINB, bool MF>
 __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lx = a.lx, ly = a.ly, lyr = a.lyr;
@@ -308,9 +309,9 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) 
   }
   const int gi0 = i0 - a.hx - 1;  // global node of staged column 0
   const int gk0 = k0 - a.hy - 1;
-  stage_tile(a, R, S, U, gi0, gk0, warp, lane);
+  stage_tile<MF>(a, R, S, U, gi0, gk0, warp, lane);
 
-  const unsigned bad = direct_phase<T, Q>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
+  const unsigned bad = direct_phase<T, Q, MF>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
 
@@ -407,9 +408,9 @@ __global__ void __launch_bounds__(FK_THREADS, 4) k_step2dw(const Step2D<float> a
     k_end = a.ny - 1;
   }
   const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;
-  stage_tile(a, R, S, U, gi0, gk0, warp, lane);
+  stage_tile<false>(a, R, S, U, gi0, gk0, warp, lane);
   if (!window) {
-    const unsigned b = direct_phase<T, Q>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
+    const unsigned b = direct_phase<T, Q, false>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
     if (b) atomicOr(a.err, FK_DEVERR_RANGE);
     return;
   }
@@ -503,7 +504,7 @@ __global__ void __launch_bounds__(FK_THREADS, 4) k_step2dw(const Step2D<float> a
     const int64_t j = (int64_t)k * a.nx + i;
     a.u_out[j] = un;
     if (a.snap) a.snap[j] = un;
-    write_adjacent_boundary(a, i, k);
+    write_adjacent_boundary<false>(a, i, k);
   }
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
@@ -518,9 +519,11 @@ __global__ void __launch_bounds__(FK_THREADS) k_step1d(const Step1D<T> a) {
   T* U = reinterpret_cast<T*>(R + lx);
   const int i0 = 1 + blockIdx.x * a.tx;
   const int gi0 = i0 - a.hx - 1;
+  const T* const uin = a.in();
+  T* const uo = a.out();
   for (int e = threadIdx.x; e < lx; e += blockDim.x) {
     const int gi = gi0 + e;
-    U[e] = (gi >= 0 && gi < a.nx) ? a.u_in[gi] : T(0);
+    U[e] = (gi >= 0 && gi < a.nx) ? uin[gi] : T(0);
   }
   __syncthreads();
   for (int lc = 1 + threadIdx.x; lc <= lx - 3; lc += blockDim.x) {
@@ -562,14 +565,14 @@ __global__ void __launch_bounds__(FK_THREADS) k_step1d(const Step1D<T> a) {
     }
     if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
     const T un = uj + acc;
-    a.u_out[i] = un;
+    uo[i] = un;
     if (a.snap) a.snap[i] = un;
     if (i == 1) {
-      a.u_out[0] = T(1);
+      uo[0] = T(1);
       if (a.snap) a.snap[0] = T(1);
     }
     if (i == a.nx - 2) {
-      a.u_out[a.nx - 1] = T(1);
+      uo[a.nx - 1] = T(1);
       if (a.snap) a.snap[a.nx - 1] = T(1);
     }
   }
@@ -590,11 +593,37 @@ __global__ void k_fill_chi(T* u, int dim, int nx, int ny) {
   }
 }
 
+template <typename T>
+__global__ void k_fill_fields(T* even, T* odd, const T* src, int dim, int nx, int ny, int nf) {
+  const int64_t J = (int64_t)nx * (dim == 2 ? ny : 1), total = J * nf;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / J, j = e - c * J;  // field c + 1
+    T v;
+    if (src) {
+      v = src[j];
+    } else {
+      const int i = (int)(j % nx);
+      bool b = (i == 0 || i == nx - 1);
+      if (dim == 2) {
+        const int k = (int)(j / nx);
+        b = b || k == 0 || k == ny - 1;
+      }
+      v = b ? T(1) : T(0);
+    }
+    (((c + 1) & 1) ? odd : even)[e] = v;
+  }
+}
+
 __global__ void k_copy16(uint4* dst, const uint4* src, int64_t n16) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n16;
        j += (int64_t)gridDim.x * blockDim.x)
     dst[j] = src[j];
 }
+
+// Register budget of the several-field launches: FP32 4 CTAs/SM, FP64 2.
+template <typename T>
+constexpr int kMinbFields = sizeof(T) == 8 ? 2 : 4;
 
 template <typename T, int Q, int MINB>
 cudaError_t launch2d_q(const Step2D<T>& a, cudaStream_t s) {
@@ -605,8 +634,12 @@ cudaError_t launch2d_q(const Step2D<T>& a, cudaStream_t s) {
   else
     gy = a.nb_lo + (a.ny - 1 - a.row_hi + a.ty - 1) / a.ty;
   if (gy <= 0) return cudaSuccess;
-  dim3 grid((a.nx - 2 + 31) / 32, gy);
-  k_step2d<T, Q, MINB><<<grid, FK_THREADS, smem, s>>>(a);
+  const int nf = a.ncols > 1 ? a.ncols : 1;
+  dim3 grid((a.nx - 2 + 31) / 32, gy, nf);
+  if (nf > 1)
+    k_step2d<T, Q, kMinbFields<T>, true><<<grid, FK_THREADS, smem, s>>>(a);
+  else
+    k_step2d<T, Q, MINB, false><<<grid, FK_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -653,8 +686,12 @@ cudaError_t launch_window(const Step2D<float>& a, int q, cudaStream_t s) {
 
 template <typename T, int Q, int MINB>
 cudaError_t attr2d_q() {
-  return cudaFuncSetAttribute(k_step2d<T, Q, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess && MINB == kMinbFields<T>)
+    e = cudaFuncSetAttribute(k_step2d<T, Q, kMinbFields<T>, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return e;
 }
 
 // Register-budget variants per precision: FP32 {4, 3} CTAs/SM, FP64 {2}.
@@ -679,7 +716,7 @@ cudaError_t attr2d_var() {
 template <typename T, int Q>
 cudaError_t launch1d_q(const Step1D<T>& a, cudaStream_t s) {
   const size_t smem = fk_step1d_smem(a.lx, (int)sizeof(T));
-  dim3 grid((a.nx - 2 + a.tx - 1) / a.tx);
+  dim3 grid((a.nx - 2 + a.tx - 1) / a.tx, 1, a.ncols > 1 ? a.ncols : 1);
   k_step1d<T, Q><<<grid, FK_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -709,7 +746,14 @@ template <typename T>
 cudaError_t fk_launch_step2d(const Step2D<T>& a, int q, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
     if (a.mode == 2) return fk_launch_step2dm(a, q, s);  // masked tensor window
-    if (a.win > 0) return launch_window(a, q, s);  // window rows and face bands
+    if (a.win > 0) {
+      if (a.ncols <= 1) return launch_window(a, q, s);  // window rows and face bands
+      // several fields: the direct kernel on every row (same tile and halo)
+      Step2D<float> d = a;
+      d.win = 0;
+      d.mode = 0;
+      return fk_launch_step2d<float>(d, q, s);
+    }
   }
   switch (q) {
     case 1: return launch2d_var<T, 1>(a, s);
@@ -791,6 +835,20 @@ cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaS
     k_fill_chi<float><<<blocks, 256, 0, s>>>((float*)u, dim, nx, ny);
   else
     k_fill_chi<double><<<blocks, 256, 0, s>>>((double*)u, dim, nx, ny);
+  return cudaGetLastError();
+}
+
+cudaError_t fk_launch_fill_fields(void* even, void* odd, const void* src, int dim, int nx, int ny,
+                                  int elem, int nfields, cudaStream_t s) {
+  const int64_t total = (int64_t)nx * (dim == 2 ? ny : 1) * nfields;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (elem == 4)
+    k_fill_fields<float><<<blocks, 256, 0, s>>>((float*)even, (float*)odd, (const float*)src, dim,
+                                                nx, ny, nfields);
+  else
+    k_fill_fields<double><<<blocks, 256, 0, s>>>((double*)even, (double*)odd,
+                                                 (const double*)src, dim, nx, ny, nfields);
   return cudaGetLastError();
 }
 

@@ -180,6 +180,7 @@ fk_status upload_tables(fk_plan* p) {
 template <typename T>
 void fill2d(const fk_plan* p, int n, Step2D<T>* a) {
   memset(a, 0, sizeof(*a));
+  a->ncols = 1;
   a->nx = p->grid.n[0];
   a->ny = p->grid.n[1];
   a->tx = p->tile[0];
@@ -239,6 +240,7 @@ void fill2d(const fk_plan* p, int n, Step2D<T>* a) {
 template <typename T>
 void fill1d(const fk_plan* p, Step1D<T>* a) {
   memset(a, 0, sizeof(*a));
+  a->ncols = 1;
   a->nx = p->grid.n[0];
   a->tx = p->tile[0];
   a->hx = p->halo[0];
@@ -590,9 +592,9 @@ void fk_dev_free(void* ptr) {
 void fk_fill_step2d_f32(const fk_plan* p, int n, Step2D<float>* a) { fill2d<float>(p, n, a); }
 void fk_fill_step2d_f64(const fk_plan* p, int n, Step2D<double>* a) { fill2d<double>(p, n, a); }
 
-fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void* snap,
-                          cudaStream_t s) {
-  if (p->path == FK_PATH_CSR) return fk_csr_step(p, u_in, u_out, snap, s);
+namespace {
+fk_status enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void* snap,
+                       int nfields, cudaStream_t s) {
   cudaError_t e;
   if (p->grid.dim == 2) {
     if (p->prec == FK_FP32) {
@@ -601,6 +603,8 @@ fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void
       a.u_in = (const float*)u_in;
       a.u_out = (float*)u_out;
       a.snap = (float*)snap;
+      a.ncols = nfields;
+      a.zstride = nfields > 1 ? p->J : 0;
       e = fk_launch_step2d<float>(a, p->q, s);
     } else {
       Step2D<double> a;
@@ -608,6 +612,8 @@ fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void
       a.u_in = (const double*)u_in;
       a.u_out = (double*)u_out;
       a.snap = (double*)snap;
+      a.ncols = nfields;
+      a.zstride = nfields > 1 ? p->J : 0;
       e = fk_launch_step2d<double>(a, p->q, s);
     }
   } else {
@@ -617,6 +623,8 @@ fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void
       a.u_in = (const float*)u_in;
       a.u_out = (float*)u_out;
       a.snap = (float*)snap;
+      a.ncols = nfields;
+      a.zstride = nfields > 1 ? p->J : 0;
       e = fk_launch_step1d<float>(a, p->q, s);
     } else {
       Step1D<double> a;
@@ -624,10 +632,25 @@ fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void
       a.u_in = (const double*)u_in;
       a.u_out = (double*)u_out;
       a.snap = (double*)snap;
+      a.ncols = nfields;
+      a.zstride = nfields > 1 ? p->J : 0;
       e = fk_launch_step1d<double>(a, p->q, s);
     }
   }
   return cuda_status(e);
+}
+}  // namespace
+
+fk_status fk_enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void* snap,
+                          cudaStream_t s) {
+  if (p->path == FK_PATH_CSR) return fk_csr_step(p, u_in, u_out, snap, s);
+  return enqueue_step(p, n, u_in, u_out, snap, 1, s);
+}
+
+fk_status fk_enqueue_step_fields(fk_plan* p, int n, const void* u_in, void* u_out, int nfields,
+                                 cudaStream_t s) {
+  if (p->path == FK_PATH_CSR || nfields < 1) return FK_ERR_UNSUPPORTED;
+  return enqueue_step(p, n, u_in, u_out, nullptr, nfields, s);
 }
 
 namespace {
@@ -854,6 +877,7 @@ fk_status fk_plan_destroy(fk_plan* p) {
   fk_dev_free(p->csr_c);
   fk_dev_free(p->stack);
   fk_dev_free(p->batch_rec);
+  fk_dev_free(p->hz_ws);
   fk_dev_free(p->adj_ws);
   fk_dev_free(p->adj_tab);
   fk_batch_release(p);
@@ -929,6 +953,48 @@ fk_status fk_solve(fk_plan* p, const void* u_terminal, void* u_out, void* snapsh
     p->g_stride = snapshot_stride;
   }
   return cuda_status(cudaGraphLaunch(p->graph, stream));
+}
+
+// Algorithm 1 (Sec. 3.2).  Field c (1-based) starts in buffer c mod 2 (odd:
+// the plan's second buffer, even: p_out) and takes one step at each loop
+// index n = c, c-1, ..., 1, so at index n every active field has taken
+// c - n steps and sits in buffer (c + c - n) mod 2 = n mod 2: all active
+// fields read the same buffer and write the other, and after index 1 every
+// field is in p_out.  Index n applies the step with the coefficients of
+// t_{n-1}.
+fk_status fk_solve_horizons(fk_plan* p, const void* u_terminal, void* p_out,
+                            cudaStream_t stream) {
+  FkRange range("fk_solve_horizons");
+  if (!p || !p_out) return FK_ERR_INVALID_ARG;
+  if (p->path != FK_PATH_MATRIX_FREE) return FK_ERR_UNSUPPORTED;
+  const int N = p->n_steps;
+  const int64_t fb = p->J * p->elem;
+  const char* t0 = (const char*)u_terminal;
+  const char* o0 = (const char*)p_out;
+  if (t0 && t0 + fb > o0 && t0 < o0 + (int64_t)N * fb) return FK_ERR_INVALID_ARG;
+  if (p->hz_bytes < (int64_t)N * fb) {
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return FK_ERR_CUDA;
+    fk_dev_free(p->hz_ws);
+    p->hz_ws = nullptr;
+    p->hz_bytes = 0;
+    fk_status st = fk_dev_alloc(p, &p->hz_ws, (size_t)N * fb);
+    if (st != FK_OK) return st;
+    p->hz_bytes = (int64_t)N * fb;
+  }
+  char* buf[2] = {(char*)p_out, (char*)p->hz_ws};
+  fk_status st = cuda_status(fk_launch_fill_fields(buf[0], buf[1], u_terminal, p->grid.dim,
+                                                   p->grid.n[0], p->grid.n[1], p->elem, N,
+                                                   stream));
+  const int kMaxFields = 65535;  // grid z limit
+  for (int n = N; n >= 1 && st == FK_OK; --n) {
+    const int par = n & 1;
+    for (int c0 = n; c0 <= N && st == FK_OK; c0 += kMaxFields) {
+      const int nf = N - c0 + 1 < kMaxFields ? N - c0 + 1 : kMaxFields;
+      const int64_t off = (int64_t)(c0 - 1) * fb;
+      st = fk_enqueue_step_fields(p, n - 1, buf[par] + off, buf[par ^ 1] + off, nf, stream);
+    }
+  }
+  return st;
 }
 
 fk_status fk_last_device_error(fk_plan* p) {

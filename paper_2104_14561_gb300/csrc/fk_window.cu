@@ -73,7 +73,8 @@ struct Scatter<W, W - 2> {
 
 // MINB: CTAs of 256 threads per SM the register budget is sized for
 // (3 -> 80 registers, 2 -> 128; variant 0 and 1 of the plan).
-template <int Q, int W, int MINB>
+// MF: several fields per launch (blockIdx.z), for Algorithm 1.
+template <int Q, int W, int MINB, bool MF>
 __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lx = a.lx, ly = a.ly, lp = a.lyr;  // staged extent; lp: odd row pitch
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float
   const int i0 = 1 + blockIdx.x * 32, k0 = 1 + blockIdx.y * a.ty;
   const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;  // global node of staged (0, 0)
 
-  masked_stage(a, Rec, U, gi0, gk0);
+  masked_stage<MF>(a, Rec, U, gi0, gk0);
 
   // 3. one output node per thread and pass: column i0 + lane, row k0 + warp + 8 m
   const int lane = tid & 31, warp = tid >> 5;
@@ -207,28 +208,38 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float
     const float ext = (1.f - uj) * (E.x + E.y - E.x * E.y);
     const float un = uj + (acc + ext);
     const int64_t j = (int64_t)k * a.nx + i;
-    a.u_out[j] = un;
+    field_out<MF>(a)[j] = un;
     if (a.snap) a.snap[j] = un;
-    write_adjacent_boundary(a, i, k);
+    write_adjacent_boundary<MF>(a, i, k);
   }
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
 
+// Several fields run the 3-CTA/SM register budget whatever the variant.
 template <int Q, int W, int MINB>
 cudaError_t launch_m(const Step2D<float>& a, cudaStream_t s) {
   const size_t smem = fk_step2dm_smem(a.ly, a.lyr);
-  dim3 grid((a.nx - 2 + 31) / 32, (a.ny - 2 + a.ty - 1) / a.ty);
-  k_step2dm<Q, W, MINB><<<grid, FK_THREADS, smem, s>>>(a);
+  const int nf = a.ncols > 1 ? a.ncols : 1;
+  dim3 grid((a.nx - 2 + 31) / 32, (a.ny - 2 + a.ty - 1) / a.ty, nf);
+  if (nf > 1)
+    k_step2dm<Q, W, 3, true><<<grid, FK_THREADS, smem, s>>>(a);
+  else
+    k_step2dm<Q, W, MINB, false><<<grid, FK_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int Q, int W>
 cudaError_t attr_m() {
-  cudaError_t e = cudaFuncSetAttribute(k_step2dm<Q, W, 3>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_step2dm<Q, W, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              227 * 1024);
+  const int big = 227 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_step2dm<Q, W, 3, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step2dm<Q, W, 2, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step2dm<Q, W, 3, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  return e;
 }
 
 }  // namespace

@@ -133,6 +133,22 @@ class Plan:
                                                _ptr(out), _stream(stream)))
         return out
 
+    def solve_horizons(self, u_terminal: torch.Tensor | None = None,
+                       out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Algorithm 1 (Sec. 3.2): out[k-1] = P(t_k, x) for every horizon
+        t_k = k dt, k = 1..N (each a march of k steps from time t_k to 0)."""
+        if u_terminal is not None:
+            self._check_field(u_terminal, "u_terminal")
+        shape = (self.spec.n_steps,) + self.shape
+        if out is None:
+            out = torch.empty(shape, dtype=self.dtype, device=self.device)
+        if out.dtype != self.dtype or tuple(out.shape) != shape or not out.is_contiguous() \
+                or out.device.type != "cuda":
+            raise ValueError(f"out: expected a contiguous {self.dtype} CUDA tensor of shape {shape}")
+        L.check("fk_solve_horizons", self._lib.fk_solve_horizons(self._h, _ptr(u_terminal),
+                                                                 _ptr(out), _stream(stream)))
+        return out
+
     def adjoint(self, cotangent_u0: torch.Tensor, u_terminal: torch.Tensor | None = None,
                 checkpoint_every: int = 50, want_dtheta: bool = True,
                 want_du_terminal: bool = True, stream=None):
