@@ -23,6 +23,11 @@
  *   Step 3: u^n_j = sum_q w_q u^{n+1,J}(z_{jq}), Eq. (e304);
  *   boundary nodes take u^n = 1 (Eq. (e3), Dirichlet value 1 on the boundary).
  *
+ * An axis may instead be periodic (the x_1 direction of the paper's own 2D
+ * example, Sec. 4.2): its two end nodes are the same point, the period is
+ * the n - 1 distinct nodes, slopes and shifted points wrap around, and no
+ * point exits through that axis.
+ *
  * Readings where the paper is silent or garbled are documented next to the
  * code that takes them.  Coefficient time is the left end t_n = n dt
  * (Eq. (ref-X)).  Every floating-point value is IEEE binary64; the library
@@ -40,6 +45,7 @@
 #define FKO_MAXDIM 3
 #define FKO_CONST_DRIFT 0
 #define FKO_CELLULAR_FLOW 1
+#define FKO_PAPER_CELLULAR 2
 
 static const double FKO_PI = 3.14159265358979323846264338327950288;
 
@@ -48,7 +54,10 @@ typedef struct fko_grid {
   int n[FKO_MAXDIM];
   double lo[FKO_MAXDIM];
   double hi[FKO_MAXDIM];
+  int periodic; /* bit m: axis m is periodic (node n-1 is node 0) */
 } fko_grid;
+
+static int axis_periodic(const fko_grid *g, int m) { return (g->periodic >> m) & 1; }
 
 /* ---------------------------------------------------------------- grid -- */
 
@@ -81,9 +90,17 @@ static void grid_unflatten(const fko_grid *g, int64_t j, int *idx) {
   }
 }
 
+/* The node an update is computed at: the last node of a periodic axis is
+ * node 0 (the same point), so it takes node 0's value. */
+static void grid_canonical(const fko_grid *g, int *idx) {
+  for (int m = 0; m < g->dim; ++m)
+    if (axis_periodic(g, m) && idx[m] == g->n[m] - 1) idx[m] = 0;
+}
+
+/* Nodes on a face of a non-periodic axis are boundary nodes. */
 static int grid_is_boundary(const fko_grid *g, const int *idx) {
   for (int m = 0; m < g->dim; ++m)
-    if (idx[m] == 0 || idx[m] == g->n[m] - 1) return 1;
+    if (!axis_periodic(g, m) && (idx[m] == 0 || idx[m] == g->n[m] - 1)) return 1;
   return 0;
 }
 
@@ -93,6 +110,8 @@ static int grid_check(const fko_grid *g) {
     if (g->n[m] < 3) return 1;
     if (!(g->hi[m] > g->lo[m])) return 1;
   }
+  if (g->periodic & ~((1 << g->dim) - 1)) return 1;
+  if (g->periodic == (1 << g->dim) - 1) return 1; /* some face must absorb */
   return 0;
 }
 
@@ -110,6 +129,11 @@ static int grid_check(const fko_grid *g) {
  *   velocity b = (-d psi/dy, d psi/dx) (the orientation of the paper's
  *   cellular-flow velocity), and sigma = sqrt(2 D) I, so that the generator
  *   is b.grad + D Laplacian.
+ * FKO_PAPER_CELLULAR (d = 2), p = (Pe, n, eps, omega): the paper's own
+ *   example of Sec. 4.2, dx = Pe v dt + dW with
+ *     v_1 = -pi cos(pi x_2) [sin(n x_1) + eps f(t) cos(n x_1)],
+ *     v_2 =  n sin(pi x_2) [cos(n x_1) - eps f(t) sin(n x_1)],
+ *   f(t) = cos(omega t), and sigma = I (unit Brownian motions).
  */
 void fko_coefficients(int family, const double *p, int dim, double t,
                       const double *x, double *b, double *sig) {
@@ -119,6 +143,16 @@ void fko_coefficients(int family, const double *p, int dim, double t,
       b[m] = p[m];
       sig[m * dim + m] = p[3];
     }
+    return;
+  }
+  if (family == FKO_PAPER_CELLULAR) {
+    double Pe = p[0], nn = p[1], eps = p[2], omega = p[3];
+    double f = cos(omega * t);
+    double X = x[0], Y = x[1];
+    b[0] = Pe * (-FKO_PI * cos(FKO_PI * Y) * (sin(nn * X) + eps * f * cos(nn * X)));
+    b[1] = Pe * (nn * sin(FKO_PI * Y) * (cos(nn * X) - eps * f * sin(nn * X)));
+    sig[0] = 1.0;
+    sig[3] = 1.0;
     return;
   }
   /* FKO_CELLULAR_FLOW */
@@ -140,6 +174,7 @@ void fko_coefficients(int family, const double *p, int dim, double t,
 static int family_check(int family, int dim, const double *p) {
   if (family == FKO_CONST_DRIFT) return !(p[3] >= 0.0);
   if (family == FKO_CELLULAR_FLOW) return dim != 2 || !(p[3] >= 0.0);
+  if (family == FKO_PAPER_CELLULAR) return dim != 2;
   return 1;
 }
 
@@ -163,7 +198,8 @@ static double pchip_rule(double d_left, double d_right) {
  * (delta_{i-1}, delta_i); the first node uses (delta_1, delta_2) and the
  * last node (delta_{J-1}, delta_{J-2}) in the paper's 1-based numbering of
  * the divided differences, i.e. (delta_0, delta_1) and (delta_{n-2},
- * delta_{n-3}) in 0-based numbering.
+ * delta_{n-3}) in 0-based numbering.  On a periodic axis every node is
+ * interior: its neighbours are taken modulo the period n - 1.
  */
 static void slopes_axis(const fko_grid *g, int m, const double *u, double *du) {
   int64_t J = grid_size(g);
@@ -178,7 +214,11 @@ static void slopes_axis(const fko_grid *g, int m, const double *u, double *du) {
 #define U_(k) u[base + (int64_t)(k) * st]
 #define DELTA(k) ((U_((k) + 1) - U_(k)) / h)
     double d;
-    if (i == 0)
+    if (axis_periodic(g, m)) {
+      int P = nm - 1, ic = i % P;
+      int il = (ic + P - 1) % P, ir = (ic + 1) % P;
+      d = pchip_rule((U_(ic) - U_(il)) / h, (U_(ir) - U_(ic)) / h);
+    } else if (i == 0)
       d = pchip_rule(DELTA(0), DELTA(1));
     else if (i == nm - 1)
       d = pchip_rule(DELTA(nm - 2), DELTA(nm - 3));
@@ -289,7 +329,15 @@ static double node_update(const fko_grid *g, int family, const double *p,
       double noise = 0.0;
       for (int k = 0; k < d; ++k) noise += sig[m * d + k] * a[q[k]];
       z[m] = x[m] + b[m] * dt + noise * sq;
-      if (z[m] < g->lo[m] || z[m] > g->hi[m]) outside = 1;
+      if (axis_periodic(g, m)) {
+        /* wrap into [lo, hi): the axis has no exit */
+        double L = g->hi[m] - g->lo[m];
+        double r = fmod(z[m] - g->lo[m], L);
+        if (r < 0.0) r += L;
+        z[m] = g->lo[m] + r;
+      } else if (z[m] < g->lo[m] || z[m] > g->hi[m]) {
+        outside = 1;
+      }
     }
     double val = outside ? 1.0 : interpolate(g, u, du, z);
     sum += wq * val;
@@ -329,6 +377,7 @@ int fko_march(const fko_grid *g, int family, const double *p, int nq,
     for (int64_t j = 0; j < J; ++j) {
       int idx[FKO_MAXDIM];
       grid_unflatten(g, j, idx);
+      grid_canonical(g, idx);
       if (boundary_rule && grid_is_boundary(g, idx))
         nxt[j] = 1.0;
       else
@@ -362,6 +411,7 @@ int fko_step_nodes(const fko_grid *g, int family, const double *p, int nq,
   for (int64_t k = 0; k < count; ++k) {
     int idx[FKO_MAXDIM];
     grid_unflatten(g, nodes[k], idx);
+    grid_canonical(g, idx);
     if (boundary_rule && grid_is_boundary(g, idx))
       out[k] = 1.0;
     else
@@ -504,6 +554,7 @@ int fko_adjoint(const fko_grid *g, int family, const double *p, int nq,
                 double *dtheta, double *du_terminal) {
   if (grid_check(g) || family_check(family, g->dim, p)) return 1;
   if (nq < 1 || !(dt > 0.0) || n_steps < 1) return 1;
+  if (g->periodic || family == FKO_PAPER_CELLULAR) return 3; /* not differentiated */
   int d = g->dim;
   int64_t J = grid_size(g);
   double *us = (double *)malloc(sizeof(double) * J * (size_t)(n_steps + 1));

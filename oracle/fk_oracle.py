@@ -43,6 +43,7 @@ _LIB = os.path.join(_HERE, "libfk_oracle.so")
 
 CONST_DRIFT = 0
 CELLULAR_FLOW = 1
+PAPER_CELLULAR = 2   # the paper's own example of Sec. 4.2: p = (Pe, n, eps, omega), sigma = I
 
 
 def build(force: bool = False) -> str:
@@ -62,7 +63,8 @@ def build(force: bool = False) -> str:
 
 class _Grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
-                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("periodic", ctypes.c_int)]
 
 
 _lib = None
@@ -106,10 +108,13 @@ def _dp(a: np.ndarray):
 @dataclass(frozen=True)
 class Grid:
     """Uniform Cartesian mesh S of Sec. 3.1.2: ``n[m]`` nodes on
-    ``[lo[m], hi[m]]`` per axis; fields are stored x fastest."""
+    ``[lo[m], hi[m]]`` per axis; fields are stored x fastest.  Bit m of
+    ``periodic`` makes axis m periodic: its last node is its first (the
+    period is n[m] - 1 nodes) and nothing exits through it."""
     n: tuple
     lo: tuple
     hi: tuple
+    periodic: int = 0
 
     @property
     def dim(self) -> int:
@@ -137,6 +142,7 @@ class Grid:
             g.n[m] = int(self.n[m])
             g.lo[m] = float(self.lo[m])
             g.hi[m] = float(self.hi[m])
+        g.periodic = int(self.periodic)
         return g
 
 
@@ -168,9 +174,12 @@ def gauss_hermite(q: int):
 # ------------------------------------------------------------- fields ----
 
 def terminal_indicator(grid: Grid) -> np.ndarray:
-    """chi of Sec. 3.2: 0 at interior nodes, 1 at boundary nodes."""
+    """chi of Sec. 3.2: 0 at interior nodes, 1 at boundary nodes (the faces
+    of the non-periodic axes)."""
     chi = np.zeros(grid.shape, dtype=np.float64)
     for ax in range(chi.ndim):
+        if (grid.periodic >> (chi.ndim - 1 - ax)) & 1:
+            continue
         sl = [slice(None)] * chi.ndim
         sl[ax] = 0
         chi[tuple(sl)] = 1.0
@@ -337,6 +346,13 @@ def _drift_numpy(family: int, params, t: float, x: np.ndarray) -> tuple:
     if family == CONST_DRIFT:
         d = x.shape[1]
         return np.broadcast_to(np.asarray(params[:d], dtype=np.float64), x.shape), float(params[3])
+    if family == PAPER_CELLULAR:
+        Pe, nn, eps, omega = params[:4]
+        f = math.cos(omega * t)
+        X, Y = x[:, 0], x[:, 1]
+        bx = -Pe * math.pi * np.cos(math.pi * Y) * (np.sin(nn * X) + eps * f * np.cos(nn * X))
+        by = Pe * nn * np.sin(math.pi * Y) * (np.cos(nn * X) - eps * f * np.sin(nn * X))
+        return np.stack([bx, by], axis=1), 1.0
     A, eps, omega, D = params[:4]
     f = math.sin(omega * t)
     X, Y = x[:, 0], x[:, 1]
@@ -347,7 +363,7 @@ def _drift_numpy(family: int, params, t: float, x: np.ndarray) -> tuple:
 
 def mc_exit_prob(family: int, params, lo, hi, x0, dt: float, n_steps: int,
                  paths: int, seed: int, chunk: int = 250_000,
-                 bridge: bool = False) -> float:
+                 bridge: bool = False, periodic: int = 0) -> float:
     """Euler-Maruyama (Eq. (ref-X)) from t_0 = 0 over n_steps steps; returns
     the fraction of paths that left the open box by t_N.
 
@@ -357,11 +373,13 @@ def mc_exit_prob(family: int, params, lo, hi, x0, dt: float, n_steps: int,
     a path that is inside at both ends of a step is also killed with the
     probability that the Brownian bridge between them crossed a face,
     exp(-2 d_n d_{n+1} / (sigma^2 dt)) per face (d = distance to that
-    face), taken as independent across faces."""
+    face), taken as independent across faces.  Bit m of periodic wraps
+    axis m onto [lo, hi) instead (no exit through it)."""
     rng = np.random.default_rng(seed)
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     d = lo.size
+    per = np.array([(periodic >> k) & 1 == 1 for k in range(d)])
     exited = 0
     done = 0
     while done < paths:
@@ -371,11 +389,15 @@ def mc_exit_prob(family: int, params, lo, hi, x0, dt: float, n_steps: int,
         for n in range(n_steps):
             b, s = _drift_numpy(family, params, n * dt, x)
             xn = x + b * dt + s * math.sqrt(dt) * rng.standard_normal((m, d))
-            out = np.any((xn <= lo) | (xn >= hi), axis=1)
+            if per.any():
+                xn[:, per] = lo[per] + np.mod(xn[:, per] - lo[per], (hi - lo)[per])
+            out = np.any(((xn <= lo) | (xn >= hi)) & ~per, axis=1)
             if bridge and s > 0:
                 var = s * s * dt
                 stay = np.ones(m)
                 for k in range(d):
+                    if per[k]:
+                        continue
                     dl0, dl1 = x[:, k] - lo[k], xn[:, k] - lo[k]
                     du0, du1 = hi[k] - x[:, k], hi[k] - xn[:, k]
                     stay *= 1.0 - np.exp(-2.0 * np.clip(dl0 * dl1, 0, None) / var)
