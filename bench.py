@@ -98,9 +98,12 @@ def workload_of(args):
 
 
 def units_per_solve(w) -> float:
+    """Node-quadrature updates of one march: the updated nodes (interior
+    ones; a periodic x axis has n - 1 distinct columns, all updated) times
+    the points per node times the steps."""
     interior = 1
-    for n in w["n"]:
-        interior *= n - 2
+    for m, n in enumerate(w["n"]):
+        interior *= (n - 1) if (m == 0 and w.get("periodic_x")) else (n - 2)
     return float(interior) * (w["q"] ** len(w["n"])) * w["n_steps"]
 
 
@@ -180,8 +183,9 @@ def oracle_rate(w, max_seconds: float = 20.0):
     """FP64 CPU oracle on the host cores over a bounded sample of the
     workload's march (consecutive time steps from the terminal field)."""
     from oracle import fk_oracle as O
-    fam = {"const_drift": O.CONST_DRIFT, "cellular_flow": O.CELLULAR_FLOW}[w["family"]]
-    g = O.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]))
+    fam = {"const_drift": O.CONST_DRIFT, "cellular_flow": O.CELLULAR_FLOW,
+           "paper_cellular": O.PAPER_CELLULAR}[w["family"]]
+    g = O.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]), int(w.get("periodic_x", False)))
     cores = os.cpu_count() or 1
     per_step = units_per_solve(w) / w["n_steps"]
     t = time.perf_counter()
@@ -204,7 +208,8 @@ def run_reference(args, rank: int):
         return
     from oracle import fk_oracle as O
     O.build()
-    fams = {"const_drift": O.CONST_DRIFT, "cellular_flow": O.CELLULAR_FLOW}
+    fams = {"const_drift": O.CONST_DRIFT, "cellular_flow": O.CELLULAR_FLOW,
+            "paper_cellular": O.PAPER_CELLULAR}
     # one benchmark step of the reference arm = one time step of the march
     # (of every instance, for the batched sweep): a bounded sample of the
     # workload, so that K + W steps take seconds to a minute
@@ -219,7 +224,8 @@ def run_reference(args, rank: int):
         t = time.perf_counter()
         for b, x in enumerate(ws):
             n = x["n_steps"] - s
-            g = O.Grid(tuple(x["n"]), tuple(x["lo"]), tuple(x["hi"]))
+            g = O.Grid(tuple(x["n"]), tuple(x["lo"]), tuple(x["hi"]),
+                       int(x.get("periodic_x", False)))
             us[b] = O.march(g, fams[x["family"]], list(x["params"]), x["q"], x["dt"], n, n - 1,
                             us[b], nthreads=cores)
         if s >= args.warmup:
@@ -521,7 +527,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     w = workload_of(args)
     spec = fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
                        params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
-                       precision=w["precision"], path=w["path"])
+                       precision=w["precision"], path=w["path"],
+                       periodic_x=w.get("periodic_x", False))
     plan = fk.Plan(spec)
     stream = torch.cuda.Stream(device=dev)
     out = plan.empty()

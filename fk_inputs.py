@@ -58,6 +58,11 @@ WORKLOADS = {
     "adjoint_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
                              family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
                              q=6, dt=1e-3, n_steps=2000, precision="fp32"),
+    # the paper's own example (Sec. 4.2): Pe = 10, n = 2, eps = 0.15,
+    # omega = 2 pi / 10, T = 0.05 on [-pi, pi] x [0, 1], periodic in x
+    "paper_2d_1025x257": dict(n=(1025, 257), lo=(-math.pi, 0.0), hi=(math.pi, 1.0),
+                              family="paper_cellular", params=(10.0, 2.0, 0.15, TWO_PI / 10),
+                              q=6, dt=5e-5, n_steps=1000, precision="fp32", periodic_x=True),
     # every horizon t_k = k dt, k = 1..200, of the time-dependent flow (Algorithm 1)
     "horizons_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
                               family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),

@@ -68,8 +68,15 @@ typedef enum fk_path { FK_PATH_MATRIX_FREE = 0, FK_PATH_CSR = 1 } fk_path;
  *                     cellular flow of Sec. 4.2 written with the stream
  *                     function psi = A sin(pi x) sin(pi y)
  *                       + eps sin(omega t) sin(2 pi x) sin(pi y),
- *                     b = (-d psi/dy, d psi/dx), sigma = sqrt(2 D) I. */
-enum { FK_CONST_DRIFT = 0, FK_CELLULAR_FLOW = 1 };
+ *                     b = (-d psi/dy, d psi/dx), sigma = sqrt(2 D) I.
+ *  FK_PAPER_CELLULAR  p = {Pe, n, eps, omega}, d = 2: the paper's own
+ *                     example of Sec. 4.2, dx = Pe v dt + dW, with
+ *                       v_1 = -pi cos(pi x_2)[sin(n x_1) + eps f cos(n x_1)],
+ *                       v_2 =  n sin(pi x_2)[cos(n x_1) - eps f sin(n x_1)],
+ *                     f = cos(omega t), sigma = I.  Usually with the region
+ *                     FK_PERIODIC_X on [-pi, pi] x [0, 1].  Matrix-free
+ *                     path only; fk_adjoint returns FK_ERR_UNSUPPORTED. */
+enum { FK_CONST_DRIFT = 0, FK_CELLULAR_FLOW = 1, FK_PAPER_CELLULAR = 2 };
 
 /* Uniform Cartesian mesh S (Sec. 3.1.2): n[m] >= 3 nodes on [lo[m], hi[m]]
  * for m < dim; entries for m >= dim are ignored. */
@@ -81,12 +88,22 @@ typedef struct fk_grid {
 } fk_grid;
 
 /* Which faces of the box absorb (exit value 1).  Bit 2m is the lower face
- * of axis m, bit 2m+1 the upper face.  Only "all faces absorbing" is
- * implemented; any other mask gives FK_ERR_UNSUPPORTED. */
+ * of axis m, bit 2m+1 the upper face.  Two masks are implemented:
+ *  FK_ALL_FACES_ABSORBING  every face absorbs;
+ *  FK_PERIODIC_X           (d = 2, matrix-free path) the two x faces are
+ *                          identified instead: node n[0]-1 is node 0, the
+ *                          period is n[0] - 1 nodes, slopes and shifted
+ *                          points wrap around in x and nothing exits
+ *                          through x; the y faces absorb (Sec. 4.2's
+ *                          example).  The terminal indicator is then 1 on
+ *                          the y faces only, and fields must hold equal
+ *                          values in columns 0 and n[0]-1.
+ * Any other mask gives FK_ERR_UNSUPPORTED. */
 typedef struct fk_region {
   unsigned absorbing_faces;
 } fk_region;
 #define FK_ALL_FACES_ABSORBING 0x3Fu
+#define FK_PERIODIC_X 0x3Cu
 
 typedef struct fk_coeffs {
   int family;

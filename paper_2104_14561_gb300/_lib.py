@@ -17,8 +17,9 @@ STATUS = {0: "FK_OK", 1: "FK_ERR_INVALID_ARG", 2: "FK_ERR_UNSUPPORTED", 3: "FK_E
 
 FK_FP32, FK_FP64 = 0, 1
 FK_PATH_MATRIX_FREE, FK_PATH_CSR = 0, 1
-FK_CONST_DRIFT, FK_CELLULAR_FLOW = 0, 1
+FK_CONST_DRIFT, FK_CELLULAR_FLOW, FK_PAPER_CELLULAR = 0, 1, 2
 FK_ALL_FACES_ABSORBING = 0x3F
+FK_PERIODIC_X = 0x3C
 
 # every symbol include/fk.h declares
 EXPORTS = ("fk_plan_create", "fk_plan_destroy", "fk_plan_get_info", "fk_gauss_hermite",

@@ -520,6 +520,15 @@ fk_status run_batch(int n, fk_plan* const* plans, const void* const* u_terminal,
     bw = new BatchWork();
     p0->batch_work = bw;
   }
+  // the persistent kernel knows boxes whose faces all absorb and the two
+  // families of its own step; other batches run the plans' own graphs
+  for (int b = 0; b < n; ++b) {
+    if (plans[b]->periodic_x || plans[b]->coeffs.family == FK_PAPER_CELLULAR) {
+      bw->mode = kModeStreams;
+      p0->batch_grid = 0;
+      return run_streams(n, plans, u_terminal, u_out, N, 0, stream, bw);
+    }
+  }
   fk_status st = grow(p0, &bw->d_inst, &bw->d_inst_bytes, sizeof(BInst<T>) * n);
   if (st == FK_OK) st = grow(p0, &bw->d_e12, &bw->d_e12_bytes, sizeof(T) * e12.size());
   if (st == FK_OK && !bw->d_bar) st = fk_dev_alloc(p0, (void**)&bw->d_bar, sizeof(BarrierState));

@@ -88,6 +88,27 @@ __device__ __forceinline__ void write_adjacent_boundary(const Step2D<T>& a, int 
 }
 
 
+// Periodic x: node (nx-1, k) is node (0, k), so it gets the same value;
+// the y-face nodes of the column (and of column 0 with it) hold 1.
+template <bool MF, typename T>
+__device__ __forceinline__ void write_periodic_x(const Step2D<T>& a, int i, int k, T un) {
+  const int64_t nx = a.nx, top = (int64_t)(a.ny - 1) * nx;
+  const bool last = (i == a.nx - 1);
+  auto put = [&](int64_t j, T v) {
+    field_out<MF>(a)[j] = v;
+    if (a.snap) a.snap[j] = v;
+  };
+  if (last) put((int64_t)k * nx, un);
+  if (k == 1) {
+    put(i, T(1));
+    if (last) put(0, T(1));
+  }
+  if (k == a.ny - 2) {
+    put(top + i, T(1));
+    if (last) put(top, T(1));
+  }
+}
+
 // Staging of the masked tensor-window kernels (the step and its adjoint),
 // for a CTA of FK_THREADS threads whose staged node (0, 0) is global node
 // (gi0, gk0); a.lx x a.ly nodes, row pitch a.lyr (odd).  Ends with the

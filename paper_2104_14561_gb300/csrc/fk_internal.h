@@ -79,6 +79,10 @@ struct Step2D {
   int ncols;
   __device__ __forceinline__ const T* in() const { return u_in + (int64_t)blockIdx.z * zstride; }
   __device__ __forceinline__ T* out() const { return u_out + (int64_t)blockIdx.z * zstride; }
+  // Periodic x (Sec. 4.2's example): node nx-1 is node 0, the period is
+  // nx - 1 nodes, staging and slopes wrap, no point exits through x, and
+  // only the y faces are boundary nodes (direct kernel only).
+  int px;
 };
 
 template <typename T>
@@ -140,12 +144,15 @@ template <typename T>
 cudaError_t fk_launch_march1d_cluster(const Step1D<T>& a, int q, int ctas, const T* u_in,
                                       T* u_out, T* snaps, int stride, int steps, cudaStream_t s);
 int fk_prepare_march1d_cluster(int q, int elem);
-cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s);
+// The terminal indicator chi: 1 on the boundary nodes (with px, the x faces
+// are identified and only the y faces are boundary), 0 elsewhere.
+cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s,
+                               int px = 0);
 // Starting fields of the horizon march: field c = 1..nfields (at offset
 // (c - 1) J) of buffer `odd` for odd c and of buffer `even` for even c gets
 // src (J values) or, with src NULL, the terminal indicator.
 cudaError_t fk_launch_fill_fields(void* even, void* odd, const void* src, int dim, int nx, int ny,
-                                  int elem, int nfields, cudaStream_t s);
+                                  int elem, int nfields, cudaStream_t s, int px = 0);
 cudaError_t fk_launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
 
 struct fk_plan {
@@ -200,6 +207,7 @@ struct fk_plan {
   void* batch_rec;   // 6 J values: slope records of this instance
   void* batch_work;  // BatchWork of a batch whose first plan is this one
   int batch_grid;    // CTAs of the last batched launch
+  int periodic_x;    // the x faces are identified (region FK_PERIODIC_X)
   // fk_solve_horizons: the second buffer of the N horizon fields
   void* hz_ws;
   int64_t hz_bytes;

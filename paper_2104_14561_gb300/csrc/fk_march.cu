@@ -113,7 +113,9 @@ __device__ __forceinline__ void lds_s_next(uint32_t a, double& x, double& y) {
 // Phases 1-3 of a step CTA: stage u^{n+1} over the tile plus halo, compute
 // the scaled PCHIP slopes, pack the cell records.  gi0/gk0 are the global
 // node indices of staged column / row 0.
-template <bool MF, typename T>
+// PX: periodic x (staged columns wrap modulo nx - 1; every x slope is an
+// interior one).
+template <bool MF, bool PX, typename T>
 __device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* S, T* U, int gi0,
                                            int gk0, int warp, int lane) {
   const int lx = a.lx, ly = a.ly, lyr = a.lyr;
@@ -127,7 +129,8 @@ __device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* 
     const bool rowin = gk >= 0 && gk < a.ny;
     const T* src = field_in<MF>(a) + (int64_t)(rowin ? gk : 0) * a.nx;
     for (int li = lane; li < lx; li += 32) {
-      const int gi = gi0 + li;
+      int gi = gi0 + li;
+      if constexpr (PX) gi += gi < 0 ? a.nx - 1 : (gi >= a.nx - 1 ? 1 - a.nx : 0);
       const bool in = rowin && gi >= 0 && gi < a.nx;
       const T* g = in ? src + gi : field_in<MF>(a);
       const uint32_t d = sU + (uint32_t)(lk * lx + li) * (uint32_t)sizeof(T);
@@ -142,7 +145,10 @@ __device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* 
     const int gk = gk0 + lk;
     const T* row = U + lk * lx;
     for (int li = 1 + lane; li <= lx - 2; li += 32) {
-      DX[lk * lx + li] = slope_fast(row, li, 1, gi0 + li, a.nx);
+      if constexpr (PX)
+        DX[lk * lx + li] = pchip_fast(row[li] - row[li - 1], row[li + 1] - row[li]);
+      else
+        DX[lk * lx + li] = slope_fast(row, li, 1, gi0 + li, a.nx);
       DY[lk * lx + li] = slope_fast(U + li, lk, lx, gk, a.ny);
     }
   }
@@ -169,14 +175,15 @@ __device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* 
 // Phase 4 of the direct kernel: the Gauss-Hermite sum of every output node
 // of rows [k0, min(k0 + ty, k_end)) of this tile, one node per thread and
 // pass (column i0 + lane, row k0 + warp + 8 m).  Returns the range-check flag.
-template <typename T, int Q, bool MF>
+template <typename T, int Q, bool MF, bool PX>
 __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>* R,
                                                  const V2<T>* S, int i0, int k0, int k_end,
                                                  int gi0, int gk0, int warp, int lane) {
   const int lx = a.lx, ly = a.ly, lyr = a.lyr;
   const int i = i0 + lane;
   const int li = i - gi0;
-  const bool colok = i <= a.nx - 2;
+  // periodic x: nodes 1 .. nx-1 (node 0 is node nx-1)
+  const bool colok = i <= a.nx - (PX ? 1 : 2);
   T cx0 = T(0), cx1 = T(0), cx2 = T(0), cx3 = T(0);
   if (a.family == FK_CELLULAR_FLOW && colok) {
     const T* ct = a.col_tab + 4 * (int64_t)i;
@@ -235,14 +242,14 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
 #pragma unroll 1
     for (int p = 0; p < Q; ++p) {
       const T d = dx + a.gx[p];
-      if ((d < nlo_x) || (d > nhi_x)) {
+      if (!PX && ((d < nlo_x) || (d > nhi_x))) {
         acc += a.w[p] * om;
         continue;
       }
       const T fl = floor(d);
       int c = i + (int)fl;
       T t = d - fl;
-      if (c > a.nx - 2) {
+      if (!PX && c > a.nx - 2) {
         c = a.nx - 2;
         t = T(1);
       }
@@ -280,13 +287,18 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
     const int64_t j = (int64_t)k * a.nx + i;
     field_out<MF>(a)[j] = un;
     if (a.snap) a.snap[j] = un;
-    write_adjacent_boundary<MF>(a, i, k);
+    if constexpr (PX) {
+      write_periodic_x<MF>(a, i, k, un);
+    } else {
+      write_adjacent_boundary<MF>(a, i, k);
+    }
   }
   return bad;
 }
 
-// MF: several fields per launch (blockIdx.z), for Algorithm 1.
-template <typename T, int Q, int MINB, bool MF>
+// MF: several fields per launch (blockIdx.z), for Algorithm 1.  PX:
+// periodic x.
+template <typename T, int Q, int MINB, bool MF, bool PX>
 __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lx = a.lx, ly = a.ly, lyr = a.lyr;
@@ -309,9 +321,9 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) 
   }
   const int gi0 = i0 - a.hx - 1;  // global node of staged column 0
   const int gk0 = k0 - a.hy - 1;
-  stage_tile<MF>(a, R, S, U, gi0, gk0, warp, lane);
+  stage_tile<MF, PX>(a, R, S, U, gi0, gk0, warp, lane);
 
-  const unsigned bad = direct_phase<T, Q, MF>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
+  const unsigned bad = direct_phase<T, Q, MF, PX>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
 
@@ -408,9 +420,9 @@ __global__ void __launch_bounds__(FK_THREADS, 4) k_step2dw(const Step2D<float> a
     k_end = a.ny - 1;
   }
   const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;
-  stage_tile<false>(a, R, S, U, gi0, gk0, warp, lane);
+  stage_tile<false, false>(a, R, S, U, gi0, gk0, warp, lane);
   if (!window) {
-    const unsigned b = direct_phase<T, Q, false>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
+    const unsigned b = direct_phase<T, Q, false, false>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
     if (b) atomicOr(a.err, FK_DEVERR_RANGE);
     return;
   }
@@ -579,12 +591,12 @@ __global__ void __launch_bounds__(FK_THREADS) k_step1d(const Step1D<T> a) {
 }
 
 template <typename T>
-__global__ void k_fill_chi(T* u, int dim, int nx, int ny) {
+__global__ void k_fill_chi(T* u, int dim, int nx, int ny, int px) {
   const int64_t J = (int64_t)nx * (dim == 2 ? ny : 1);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
        j += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(j % nx);
-    bool b = (i == 0 || i == nx - 1);
+    bool b = !px && (i == 0 || i == nx - 1);
     if (dim == 2) {
       const int k = (int)(j / nx);
       b = b || k == 0 || k == ny - 1;
@@ -594,7 +606,8 @@ __global__ void k_fill_chi(T* u, int dim, int nx, int ny) {
 }
 
 template <typename T>
-__global__ void k_fill_fields(T* even, T* odd, const T* src, int dim, int nx, int ny, int nf) {
+__global__ void k_fill_fields(T* even, T* odd, const T* src, int dim, int nx, int ny, int nf,
+                              int px) {
   const int64_t J = (int64_t)nx * (dim == 2 ? ny : 1), total = J * nf;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -604,7 +617,7 @@ __global__ void k_fill_fields(T* even, T* odd, const T* src, int dim, int nx, in
       v = src[j];
     } else {
       const int i = (int)(j % nx);
-      bool b = (i == 0 || i == nx - 1);
+      bool b = !px && (i == 0 || i == nx - 1);
       if (dim == 2) {
         const int k = (int)(j / nx);
         b = b || k == 0 || k == ny - 1;
@@ -635,11 +648,20 @@ cudaError_t launch2d_q(const Step2D<T>& a, cudaStream_t s) {
     gy = a.nb_lo + (a.ny - 1 - a.row_hi + a.ty - 1) / a.ty;
   if (gy <= 0) return cudaSuccess;
   const int nf = a.ncols > 1 ? a.ncols : 1;
+  constexpr int D = kMinbFields<T>;
+  if (a.px) {  // periodic x: nodes 1 .. nx-1, the default register budget
+    dim3 grid((a.nx - 1 + 31) / 32, gy, nf);
+    if (nf > 1)
+      k_step2d<T, Q, D, true, true><<<grid, FK_THREADS, smem, s>>>(a);
+    else
+      k_step2d<T, Q, D, false, true><<<grid, FK_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+  }
   dim3 grid((a.nx - 2 + 31) / 32, gy, nf);
   if (nf > 1)
-    k_step2d<T, Q, kMinbFields<T>, true><<<grid, FK_THREADS, smem, s>>>(a);
+    k_step2d<T, Q, D, true, false><<<grid, FK_THREADS, smem, s>>>(a);
   else
-    k_step2d<T, Q, MINB, false><<<grid, FK_THREADS, smem, s>>>(a);
+    k_step2d<T, Q, MINB, false, false><<<grid, FK_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -686,11 +708,20 @@ cudaError_t launch_window(const Step2D<float>& a, int q, cudaStream_t s) {
 
 template <typename T, int Q, int MINB>
 cudaError_t attr2d_q() {
-  cudaError_t e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  if (e == cudaSuccess && MINB == kMinbFields<T>)
-    e = cudaFuncSetAttribute(k_step2d<T, Q, kMinbFields<T>, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  const int big = 227 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, false, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if constexpr (MINB == kMinbFields<T>) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, true, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, false, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, true, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  }
   return e;
 }
 
@@ -827,28 +858,29 @@ template cudaError_t fk_launch_step2d<double>(const Step2D<double>&, int, cudaSt
 template cudaError_t fk_launch_step1d<float>(const Step1D<float>&, int, cudaStream_t);
 template cudaError_t fk_launch_step1d<double>(const Step1D<double>&, int, cudaStream_t);
 
-cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s) {
+cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s,
+                               int px) {
   const int64_t J = (int64_t)nx * (dim == 2 ? ny : 1);
   int blocks = (int)((J + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (elem == 4)
-    k_fill_chi<float><<<blocks, 256, 0, s>>>((float*)u, dim, nx, ny);
+    k_fill_chi<float><<<blocks, 256, 0, s>>>((float*)u, dim, nx, ny, px);
   else
-    k_fill_chi<double><<<blocks, 256, 0, s>>>((double*)u, dim, nx, ny);
+    k_fill_chi<double><<<blocks, 256, 0, s>>>((double*)u, dim, nx, ny, px);
   return cudaGetLastError();
 }
 
 cudaError_t fk_launch_fill_fields(void* even, void* odd, const void* src, int dim, int nx, int ny,
-                                  int elem, int nfields, cudaStream_t s) {
+                                  int elem, int nfields, cudaStream_t s, int px) {
   const int64_t total = (int64_t)nx * (dim == 2 ? ny : 1) * nfields;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (elem == 4)
     k_fill_fields<float><<<blocks, 256, 0, s>>>((float*)even, (float*)odd, (const float*)src, dim,
-                                                nx, ny, nfields);
+                                                nx, ny, nfields, px);
   else
     k_fill_fields<double><<<blocks, 256, 0, s>>>((double*)even, (double*)odd,
-                                                 (const double*)src, dim, nx, ny, nfields);
+                                                 (const double*)src, dim, nx, ny, nfields, px);
   return cudaGetLastError();
 }
 

@@ -99,6 +99,10 @@ void drift_bound(const fk_coeffs* c, int dim, double* bmax) {
   for (int m = 0; m < 3; ++m) bmax[m] = 0.0;
   if (c->family == FK_CONST_DRIFT) {
     for (int m = 0; m < dim; ++m) bmax[m] = fabs(c->p[m]);
+  } else if (c->family == FK_PAPER_CELLULAR) {
+    const double Pe = fabs(c->p[0]), n = fabs(c->p[1]), e = fabs(c->p[2]);
+    bmax[0] = Pe * kPi * (1.0 + e);
+    bmax[1] = Pe * n * (1.0 + e);
   } else {
     const double A = fabs(c->p[0]), e = fabs(c->p[1]);
     bmax[0] = kPi * (A + e);
@@ -107,6 +111,7 @@ void drift_bound(const fk_coeffs* c, int dim, double* bmax) {
 }
 
 double sigma_of(const fk_coeffs* c) {
+  if (c->family == FK_PAPER_CELLULAR) return 1.0;  // unit Brownian motions
   return c->family == FK_CONST_DRIFT ? c->p[3] : sqrt(2.0 * c->p[3]);
 }
 
@@ -121,17 +126,23 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
   if (!(dt > 0.0) || !finite(dt) || n_steps < 1) return FK_ERR_INVALID_ARG;
   if (prec != FK_FP32 && prec != FK_FP64) return FK_ERR_INVALID_ARG;
   if (path != FK_PATH_MATRIX_FREE && path != FK_PATH_CSR) return FK_ERR_INVALID_ARG;
-  if (c->family != FK_CONST_DRIFT && c->family != FK_CELLULAR_FLOW) return FK_ERR_INVALID_ARG;
+  if (c->family != FK_CONST_DRIFT && c->family != FK_CELLULAR_FLOW &&
+      c->family != FK_PAPER_CELLULAR)
+    return FK_ERR_INVALID_ARG;
   for (int k = 0; k < 8; ++k)
     if (!finite(c->p[k])) return FK_ERR_INVALID_ARG;
   if (c->family == FK_CONST_DRIFT && !(c->p[3] >= 0.0)) return FK_ERR_INVALID_ARG;
   if (c->family == FK_CELLULAR_FLOW && !(c->p[3] >= 0.0)) return FK_ERR_INVALID_ARG;
   if (g->dim == 3) return FK_ERR_UNSUPPORTED;
-  if (c->family == FK_CELLULAR_FLOW && g->dim != 2) return FK_ERR_INVALID_ARG;
+  if ((c->family == FK_CELLULAR_FLOW || c->family == FK_PAPER_CELLULAR) && g->dim != 2)
+    return FK_ERR_INVALID_ARG;
   if (q < 1 || q > (g->dim == 1 ? FK_MAXQ : FK_MAXQ_2D)) return FK_ERR_UNSUPPORTED;
-  if (r && r->absorbing_faces != FK_ALL_FACES_ABSORBING) return FK_ERR_UNSUPPORTED;
+  if (r && r->absorbing_faces != FK_ALL_FACES_ABSORBING) {
+    if (r->absorbing_faces != FK_PERIODIC_X || g->dim != 2 || path != FK_PATH_MATRIX_FREE)
+      return FK_ERR_UNSUPPORTED;
+  }
   if (path == FK_PATH_CSR) {
-    if (g->dim != 2) return FK_ERR_UNSUPPORTED;
+    if (g->dim != 2 || c->family == FK_PAPER_CELLULAR) return FK_ERR_UNSUPPORTED;
     if (c->family == FK_CELLULAR_FLOW && c->p[1] != 0.0) return FK_ERR_UNSUPPORTED;
   }
   int64_t J = 1;
@@ -156,12 +167,23 @@ fk_status upload_tables(fk_plan* p) {
     free(rt);
     return FK_ERR_OOM;
   }
+  // periodic x: column nx-1 is column 0 (its entries are node 0's)
+  const int per = p->periodic_x ? nx - 1 : nx;
+  const double nk = p->coeffs.p[1];
   for (int i = 0; i < nx; ++i) {
-    const double x = p->grid.lo[0] + i * p->h[0];
-    ct[4 * i + 0] = (T)sin(kPi * x);
-    ct[4 * i + 1] = (T)sin(2.0 * kPi * x);
-    ct[4 * i + 2] = (T)cos(kPi * x);
-    ct[4 * i + 3] = (T)cos(2.0 * kPi * x);
+    const double x = p->grid.lo[0] + (i % per) * p->h[0];
+    if (p->coeffs.family == FK_PAPER_CELLULAR) {
+      // v_1 ~ sin(n x) + eps f cos(n x), v_2 ~ cos(n x) + eps f (-sin(n x))
+      ct[4 * i + 0] = (T)sin(nk * x);
+      ct[4 * i + 1] = (T)cos(nk * x);
+      ct[4 * i + 2] = (T)cos(nk * x);
+      ct[4 * i + 3] = (T)(-sin(nk * x));
+    } else {
+      ct[4 * i + 0] = (T)sin(kPi * x);
+      ct[4 * i + 1] = (T)sin(2.0 * kPi * x);
+      ct[4 * i + 2] = (T)cos(kPi * x);
+      ct[4 * i + 3] = (T)cos(2.0 * kPi * x);
+    }
   }
   for (int k = 0; k < ny; ++k) {
     const double y = p->grid.dim == 2 ? p->grid.lo[1] + k * p->h[1] : 0.0;
@@ -191,9 +213,22 @@ void fill2d(const fk_plan* p, int n, Step2D<T>* a) {
   a->lx = a->tx + 2 * a->hx + 2;
   a->ly = a->ty + 2 * a->hy + 2;
   a->lyr = a->ly | 1;
-  a->family = p->coeffs.family;
+  // drift form in the kernels: FK_CONST_DRIFT constants, else the
+  // row x column tables (both cellular families)
+  a->family = p->coeffs.family == FK_CONST_DRIFT ? FK_CONST_DRIFT : FK_CELLULAR_FLOW;
+  a->px = p->periodic_x;
   const double dt = p->dt, tn = n * dt;
-  if (p->coeffs.family == FK_CELLULAR_FLOW) {
+  if (p->coeffs.family == FK_PAPER_CELLULAR) {
+    // dx = Pe dt/h (-pi cos(pi y)) (sin(n x) + eps f cos(n x)),
+    // dy = Pe dt/h (n sin(pi y)) (cos(n x) - eps f sin(n x)), f = cos(omega t)
+    const double Pe = p->coeffs.p[0], nk = p->coeffs.p[1], eps = p->coeffs.p[2];
+    const double f = cos(p->coeffs.p[3] * tn);
+    a->kx = (T)(-Pe * kPi * dt / p->h[0]);
+    a->ky = (T)(Pe * nk * dt / p->h[1]);
+    a->A = (T)1.0;
+    a->e1 = (T)(eps * f);
+    a->e2 = (T)(eps * f);
+  } else if (p->coeffs.family == FK_CELLULAR_FLOW) {
     const double A = p->coeffs.p[0], eps = p->coeffs.p[1], om = p->coeffs.p[2];
     const double st = sin(om * tn);
     a->kx = (T)(-kPi * dt / p->h[0]);
@@ -302,6 +337,7 @@ int current_kernel(const fk_plan* p) {
 void window_eligibility(fk_plan* p) {
   p->win_max = 0;
   if (p->grid.dim != 2 || p->prec != FK_FP32 || p->path != FK_PATH_MATRIX_FREE) return;
+  if (p->periodic_x) return;  // periodic x: the direct kernel only
   const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * p->dt);
   float gy[FK_MAXQ_2D];
   for (int q = 0; q < p->q; ++q) gy[q] = (float)(sg * p->gh_a[q] / p->h[1]);
@@ -333,6 +369,7 @@ void masked_eligibility(fk_plan* p) {
   const double kMargin = 1e-4;
   p->mwin = 0;
   if (p->grid.dim != 2 || p->prec != FK_FP32 || p->path != FK_PATH_MATRIX_FREE) return;
+  if (p->periodic_x) return;  // periodic x: the direct kernel only
   const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * p->dt);
   float gx[FK_MAXQ_2D], gy[FK_MAXQ_2D];
   for (int q = 0; q < p->q; ++q) {
@@ -493,7 +530,8 @@ fk_status autotune(fk_plan* p) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  fk_status st = cuda_status(fk_launch_fill_chi(p->scratch, 2, p->grid.n[0], p->grid.n[1], p->elem, s));
+  fk_status st = cuda_status(
+      fk_launch_fill_chi(p->scratch, 2, p->grid.n[0], p->grid.n[1], p->elem, s, p->periodic_x));
   const bool log = getenv("FK_TUNE_LOG") != nullptr;
   if (log)
     fprintf(stderr,
@@ -664,7 +702,7 @@ fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void
   const int steps = n_from - n_to;
   if (steps == 0) {
     if (!u_in) return cuda_status(fk_launch_fill_chi(u_out, p->grid.dim, p->grid.n[0],
-                                                      p->grid.n[1], p->elem, s));
+                                                      p->grid.n[1], p->elem, s, p->periodic_x));
     if (u_in != u_out) return cuda_status(fk_launch_copy(u_out, u_in, bytes, s));
     return FK_OK;
   }
@@ -693,7 +731,7 @@ fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void
   if (!src) {
     void* buf = first_to_out ? p->scratch : u_out;
     fk_status st = cuda_status(fk_launch_fill_chi(buf, p->grid.dim, p->grid.n[0], p->grid.n[1],
-                                                  p->elem, s));
+                                                  p->elem, s, p->periodic_x));
     if (st != FK_OK) return st;
     src = buf;
   } else if (src == u_out && first_to_out) {
@@ -755,7 +793,8 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
     p->grid.lo[m] = 0.0;
     p->grid.hi[m] = 0.0;
   }
-  p->region.absorbing_faces = FK_ALL_FACES_ABSORBING;
+  p->region.absorbing_faces = region ? region->absorbing_faces : FK_ALL_FACES_ABSORBING;
+  p->periodic_x = p->region.absorbing_faces == FK_PERIODIC_X ? 1 : 0;
   p->coeffs = *coeffs;
   p->q = q_per_dim;
   p->dt = dt;
@@ -789,6 +828,11 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
       return FK_ERR_UNSUPPORTED;
     }
     p->halo[m] = (int)ceil(r) + 1;
+  }
+  // periodic x: a staged column wraps by at most one period
+  if (p->periodic_x && p->halo[0] + 2 >= grid->n[0] - 1) {
+    delete p;
+    return FK_ERR_UNSUPPORTED;
   }
   window_eligibility(p);
   masked_eligibility(p);
@@ -984,7 +1028,7 @@ fk_status fk_solve_horizons(fk_plan* p, const void* u_terminal, void* p_out,
   char* buf[2] = {(char*)p_out, (char*)p->hz_ws};
   fk_status st = cuda_status(fk_launch_fill_fields(buf[0], buf[1], u_terminal, p->grid.dim,
                                                    p->grid.n[0], p->grid.n[1], p->elem, N,
-                                                   stream));
+                                                   stream, p->periodic_x));
   const int kMaxFields = 65535;  // grid z limit
   for (int n = N; n >= 1 && st == FK_OK; --n) {
     const int par = n & 1;

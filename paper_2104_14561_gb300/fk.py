@@ -17,7 +17,8 @@ from . import _lib as L
 _DTYPE = {"fp32": torch.float32, "fp64": torch.float64}
 _PREC = {"fp32": L.FK_FP32, "fp64": L.FK_FP64}
 _PATH = {"matrix_free": L.FK_PATH_MATRIX_FREE, "csr": L.FK_PATH_CSR}
-_FAMILY = {"const_drift": L.FK_CONST_DRIFT, "cellular_flow": L.FK_CELLULAR_FLOW}
+_FAMILY = {"const_drift": L.FK_CONST_DRIFT, "cellular_flow": L.FK_CELLULAR_FLOW,
+           "paper_cellular": L.FK_PAPER_CELLULAR}
 
 
 def _ptr(t: torch.Tensor | None):
@@ -50,6 +51,7 @@ class PlanSpec:
     n_steps: int
     precision: str = "fp32"
     path: str = "matrix_free"
+    periodic_x: bool = False  # x faces identified (node n[0]-1 is node 0), y faces absorb
 
 
 class Plan:
@@ -64,7 +66,7 @@ class Plan:
             g.n[m] = int(spec.n[m])
             g.lo[m] = float(spec.lo[m])
             g.hi[m] = float(spec.hi[m])
-        r = L.Region(L.FK_ALL_FACES_ABSORBING)
+        r = L.Region(L.FK_PERIODIC_X if spec.periodic_x else L.FK_ALL_FACES_ABSORBING)
         c = L.Coeffs()
         c.family = _FAMILY[spec.family]
         for k, v in enumerate(spec.params):

@@ -70,6 +70,11 @@ CASES = [
     (dict(path=1), 2),             # CSR with a time-dependent drift
     (dict(dim=3, n=(5, 5, 5)), 2),
     (dict(dim=1, n=(33,)), 1),     # the cellular flow is two-dimensional
+    (dict(family=2, dim=1, n=(33,), p=(10.0, 2.0, 0.15, 0.6)), 1),  # so is the paper's
+    (dict(faces=0x3C, dim=1, n=(33,), family=0, p=(0.1, 0, 0, 1.0)), 2),  # periodic x in 1D
+    (dict(faces=0x3C, path=1, p=(1.0, 0.0, 1.0, 1e-3)), 2),  # periodic x on the CSR path
+    (dict(faces=0x33), 2),         # periodic y is not offered
+    (dict(family=2, path=1, p=(10.0, 2.0, 0.0, 0.6)), 2),  # the paper's flow: matrix-free only
 ]
 
 
