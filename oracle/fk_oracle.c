@@ -55,6 +55,9 @@ typedef struct fko_grid {
   double lo[FKO_MAXDIM];
   double hi[FKO_MAXDIM];
   int periodic; /* bit m: axis m is periodic (node n-1 is node 0) */
+  /* axis[m]: NULL for the uniform mesh, else the n[m] increasing node
+   * coordinates of axis m (axis[m][0] = lo[m], axis[m][n-1] = hi[m]) */
+  const double *axis[FKO_MAXDIM];
 } fko_grid;
 
 static int axis_periodic(const fko_grid *g, int m) { return (g->periodic >> m) & 1; }
@@ -71,8 +74,11 @@ static double grid_h(const fko_grid *g, int m) {
   return (g->hi[m] - g->lo[m]) / (double)(g->n[m] - 1);
 }
 
-/* Mesh S of Sec. 3.1.2: uniform per axis, x_i = lo + i h. */
+/* Mesh S of Sec. 3.1.2: per axis either uniform, x_i = lo + i h, or the
+ * given increasing coordinates (the partition along each direction need
+ * not be uniform). */
 static double grid_x(const fko_grid *g, int m, int i) {
+  if (g->axis[m]) return g->axis[m][i];
   return g->lo[m] + (double)i * grid_h(g, m);
 }
 
@@ -111,6 +117,13 @@ static int grid_check(const fko_grid *g) {
     if (!(g->hi[m] > g->lo[m])) return 1;
   }
   if (g->periodic & ~((1 << g->dim) - 1)) return 1;
+  for (int m = 0; m < g->dim; ++m) {
+    if (!g->axis[m]) continue;
+    if (axis_periodic(g, m)) return 1; /* periodic axes are uniform */
+    if (g->axis[m][0] != g->lo[m] || g->axis[m][g->n[m] - 1] != g->hi[m]) return 1;
+    for (int i = 0; i + 1 < g->n[m]; ++i)
+      if (!(g->axis[m][i + 1] > g->axis[m][i])) return 1;
+  }
   if (g->periodic == (1 << g->dim) - 1) return 1; /* some face must absorb */
   return 0;
 }
@@ -205,18 +218,18 @@ static void slopes_axis(const fko_grid *g, int m, const double *u, double *du) {
   int64_t J = grid_size(g);
   int64_t st = grid_stride(g, m);
   int nm = g->n[m];
-  double h = grid_h(g, m);
   int idx[FKO_MAXDIM];
   for (int64_t j = 0; j < J; ++j) {
     grid_unflatten(g, j, idx);
     int i = idx[m];
     int64_t base = j - (int64_t)i * st; /* node 0 of this grid line */
 #define U_(k) u[base + (int64_t)(k) * st]
-#define DELTA(k) ((U_((k) + 1) - U_(k)) / h)
+#define DELTA(k) ((U_((k) + 1) - U_(k)) / (grid_x(g, m, (k) + 1) - grid_x(g, m, (k))))
     double d;
     if (axis_periodic(g, m)) {
       int P = nm - 1, ic = i % P;
       int il = (ic + P - 1) % P, ir = (ic + 1) % P;
+      double h = grid_h(g, m); /* periodic axes are uniform */
       d = pchip_rule((U_(ic) - U_(il)) / h, (U_(ir) - U_(ic)) / h);
     } else if (i == 0)
       d = pchip_rule(DELTA(0), DELTA(1));
@@ -262,11 +275,22 @@ static double interpolate(const fko_grid *g, const double *u, const double *du,
   int c[FKO_MAXDIM];
   double phi[FKO_MAXDIM][2], psi[FKO_MAXDIM][2];
   for (int m = 0; m < g->dim; ++m) {
-    double h = grid_h(g, m);
-    int cm = (int)floor((z[m] - g->lo[m]) / h);
+    int cm;
+    if (g->axis[m]) {
+      /* the last node at or left of z (bisection), clamped to a cell */
+      int a = 0, b = g->n[m] - 1;
+      while (b - a > 1) {
+        int mid = (a + b) / 2;
+        if (g->axis[m][mid] <= z[m]) a = mid; else b = mid;
+      }
+      cm = a;
+    } else {
+      cm = (int)floor((z[m] - g->lo[m]) / grid_h(g, m));
+    }
     if (cm < 0) cm = 0;
     if (cm > g->n[m] - 2) cm = g->n[m] - 2;
     c[m] = cm;
+    double h = grid_x(g, m, cm + 1) - grid_x(g, m, cm);
     double s = z[m] - grid_x(g, m, cm);
     hermite_basis(s, h, &phi[m][0], &phi[m][1], &psi[m][0], &psi[m][1]);
   }
@@ -555,6 +579,8 @@ int fko_adjoint(const fko_grid *g, int family, const double *p, int nq,
   if (grid_check(g) || family_check(family, g->dim, p)) return 1;
   if (nq < 1 || !(dt > 0.0) || n_steps < 1) return 1;
   if (g->periodic || family == FKO_PAPER_CELLULAR) return 3; /* not differentiated */
+  for (int m = 0; m < g->dim; ++m)
+    if (g->axis[m]) return 3; /* uniform meshes only */
   int d = g->dim;
   int64_t J = grid_size(g);
   double *us = (double *)malloc(sizeof(double) * J * (size_t)(n_steps + 1));

@@ -64,7 +64,7 @@ def build(force: bool = False) -> str:
 class _Grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
                 ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
-                ("periodic", ctypes.c_int)]
+                ("periodic", ctypes.c_int), ("axis", ctypes.POINTER(ctypes.c_double) * 3)]
 
 
 _lib = None
@@ -110,11 +110,14 @@ class Grid:
     """Uniform Cartesian mesh S of Sec. 3.1.2: ``n[m]`` nodes on
     ``[lo[m], hi[m]]`` per axis; fields are stored x fastest.  Bit m of
     ``periodic`` makes axis m periodic: its last node is its first (the
-    period is n[m] - 1 nodes) and nothing exits through it."""
+    period is n[m] - 1 nodes) and nothing exits through it.  ``axes[m]``,
+    if given, holds the increasing node coordinates of axis m (a
+    non-uniform mesh; first = lo[m], last = hi[m])."""
     n: tuple
     lo: tuple
     hi: tuple
     periodic: int = 0
+    axes: tuple | None = None
 
     @property
     def dim(self) -> int:
@@ -133,16 +136,26 @@ class Grid:
         return (self.hi[m] - self.lo[m]) / (self.n[m] - 1)
 
     def axis(self, m: int) -> np.ndarray:
+        if self.axes is not None and self.axes[m] is not None:
+            return np.asarray(self.axes[m], dtype=np.float64)
         return self.lo[m] + np.arange(self.n[m]) * self.h(m)
 
     def _c(self) -> _Grid:
+        keep = []
         g = _Grid()
         g.dim = self.dim
         for m in range(self.dim):
             g.n[m] = int(self.n[m])
             g.lo[m] = float(self.lo[m])
             g.hi[m] = float(self.hi[m])
+            if self.axes is not None and self.axes[m] is not None:
+                a = np.ascontiguousarray(self.axes[m], dtype=np.float64)
+                if a.size != self.n[m]:
+                    raise ValueError("axes[m] must hold n[m] coordinates")
+                keep.append(a)
+                g.axis[m] = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         g.periodic = int(self.periodic)
+        g._keep = keep  # the coordinate arrays live as long as the struct
         return g
 
 
