@@ -78,13 +78,20 @@ typedef enum fk_path { FK_PATH_MATRIX_FREE = 0, FK_PATH_CSR = 1 } fk_path;
  *                     path only; fk_adjoint returns FK_ERR_UNSUPPORTED. */
 enum { FK_CONST_DRIFT = 0, FK_CELLULAR_FLOW = 1, FK_PAPER_CELLULAR = 2 };
 
-/* Uniform Cartesian mesh S (Sec. 3.1.2): n[m] >= 3 nodes on [lo[m], hi[m]]
- * for m < dim; entries for m >= dim are ignored. */
+/* Cartesian mesh S (Sec. 3.1.2): n[m] >= 3 nodes on [lo[m], hi[m]] for
+ * m < dim; entries for m >= dim are ignored.  axis[m] = NULL gives the
+ * uniform mesh; otherwise it points to n[m] strictly increasing host
+ * coordinates with axis[m][0] = lo[m] and axis[m][n[m]-1] = hi[m] (the
+ * partition along a direction need not be uniform), read during plan
+ * creation only.  Non-uniform axes: d = 2, FK_PATH_MATRIX_FREE, every face
+ * absorbing; Eq. (e300) then takes divided differences over the actual
+ * spacings and the Hermite cell formula each cell's own width. */
 typedef struct fk_grid {
   int dim;
   int n[3];
   double lo[3];
   double hi[3];
+  const double *axis[3];
 } fk_grid;
 
 /* Which faces of the box absorb (exit value 1).  Bit 2m is the lower face

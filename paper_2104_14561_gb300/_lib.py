@@ -35,7 +35,8 @@ class FkError(RuntimeError):
 
 class Grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
-                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("axis", ctypes.POINTER(ctypes.c_double) * 3)]
 
 
 class Region(ctypes.Structure):

@@ -1081,8 +1081,8 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
   if (!p || !cotangent_u0 || K < 1) return FK_ERR_INVALID_ARG;
   if (p->grid.dim != 2 || p->path != FK_PATH_MATRIX_FREE) return FK_ERR_UNSUPPORTED;
   // the parameter derivatives are those of the cellular flow or the constant
-  // drift, in a box whose faces all absorb
-  if (p->periodic_x || p->coeffs.family == FK_PAPER_CELLULAR) return FK_ERR_UNSUPPORTED;
+  // drift, on a uniform mesh of a box whose faces all absorb
+  if (p->periodic_x || p->nu || p->coeffs.family == FK_PAPER_CELLULAR) return FK_ERR_UNSUPPORTED;
   const int N = p->n_steps;
   if (K > N) K = N;
   const int M = (N + K - 1) / K;  // checkpoints at n = 0, K, ..., and N

@@ -520,10 +520,11 @@ fk_status run_batch(int n, fk_plan* const* plans, const void* const* u_terminal,
     bw = new BatchWork();
     p0->batch_work = bw;
   }
-  // the persistent kernel knows boxes whose faces all absorb and the two
-  // families of its own step; other batches run the plans' own graphs
+  // the persistent kernel knows uniform meshes of boxes whose faces all
+  // absorb and the two families of its own step; other batches run the
+  // plans' own graphs
   for (int b = 0; b < n; ++b) {
-    if (plans[b]->periodic_x || plans[b]->coeffs.family == FK_PAPER_CELLULAR) {
+    if (plans[b]->periodic_x || plans[b]->nu || plans[b]->coeffs.family == FK_PAPER_CELLULAR) {
       bw->mode = kModeStreams;
       p0->batch_grid = 0;
       return run_streams(n, plans, u_terminal, u_out, N, 0, stream, bw);

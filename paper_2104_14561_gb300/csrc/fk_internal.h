@@ -83,6 +83,13 @@ struct Step2D {
   // nx - 1 nodes, staging and slopes wrap, no point exits through x, and
   // only the y faces are boundary nodes (direct kernel only).
   int px;
+  // Non-uniform axes (direct kernel only): node coordinates xc[nx], yc[ny];
+  // drift and point offsets (kx, ky, cdx, cdy, gx, gy) are then physical
+  // lengths, not cells, and [blo, bhi] is the box.
+  int nu;
+  const T* xc;
+  const T* yc;
+  T blo[2], bhi[2];
 };
 
 template <typename T>
@@ -103,8 +110,9 @@ struct Step1D {
   __device__ __forceinline__ T* out() const { return u_out + (int64_t)blockIdx.z * zstride; }
 };
 
-// Shared memory bytes of one 2D step CTA.
-size_t fk_step2d_smem(int lx, int ly, int lyr, int elem);
+// Shared memory bytes of one 2D step CTA (nu: plus the staged node
+// coordinates of a non-uniform mesh).
+size_t fk_step2d_smem(int lx, int ly, int lyr, int elem, int nu = 0);
 size_t fk_step1d_smem(int lx, int elem);
 
 // Launchers (fk_march.cu).  Return cudaGetLastError().
@@ -208,6 +216,9 @@ struct fk_plan {
   void* batch_work;  // BatchWork of a batch whose first plan is this one
   int batch_grid;    // CTAs of the last batched launch
   int periodic_x;    // the x faces are identified (region FK_PERIODIC_X)
+  int nu;            // non-uniform axes: node coordinates per axis
+  double* hcoord[2]; // host copies (malloc) and device copies in the plan's precision
+  void* dcoord[2];
   // fk_solve_horizons: the second buffer of the N horizon fields
   void* hz_ws;
   int64_t hz_bytes;

@@ -72,6 +72,28 @@ __device__ __forceinline__ T slope_fast(const T* u, int l, int stride, int g, in
   return pchip_fast(c[0] - c[-stride], c[stride] - c[0]);
 }
 
+// The same slope on a non-uniform mesh (raw derivative, not scaled): Eq.
+// (e300) with the divided differences over the actual spacings x.
+template <typename T>
+__device__ __forceinline__ T slope_nu(const T* u, const T* x, int l, int stride, int g, int n) {
+  if (g < 0 || g >= n) return T(0);
+  auto del = [&](int m) { return (u[(m + 1) * stride] - u[m * stride]) / (x[m + 1] - x[m]); };
+  if (g == 0) return pchip_fast(del(l), del(l + 1));
+  if (g == n - 1) return pchip_fast(del(l - 1), del(l - 2));
+  return pchip_fast(del(l - 1), del(l));
+}
+
+// Largest local index c in [1, hi] with x[c] <= z (bisection; x increasing).
+template <typename T>
+__device__ __forceinline__ int cell_of(const T* x, int hi, T z) {
+  int lo = 1, up = hi + 1;
+  while (up - lo > 1) {
+    const int m = (lo + up) >> 1;
+    if (x[m] <= z) lo = m; else up = m;
+  }
+  return lo;
+}
+
 // Record loads with explicit 32-bit shared-memory byte addresses: one add per
 // query for the R and one for the S record, the second row at an immediate
 // offset.  The compute phase only reads shared memory (it is written before
@@ -114,13 +136,29 @@ __device__ __forceinline__ void lds_s_next(uint32_t a, double& x, double& y) {
 // the scaled PCHIP slopes, pack the cell records.  gi0/gk0 are the global
 // node indices of staged column / row 0.
 // PX: periodic x (staged columns wrap modulo nx - 1; every x slope is an
-// interior one).
-template <bool MF, bool PX, typename T>
+// interior one).  NU: non-uniform mesh (the staged node coordinates go to
+// SX, SY; the records hold raw derivatives, scaled per cell at the query).
+template <bool MF, bool PX, bool NU, typename T>
 __device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* S, T* U, int gi0,
                                            int gk0, int warp, int lane) {
   const int lx = a.lx, ly = a.ly, lyr = a.lyr;
   T* DX = U + lx * ly;
   T* DY = DX + lx * ly;
+  T* SX = DY + lx * ly;
+  T* SY = SX + lx;
+  if constexpr (NU) {
+    // coordinates of the staged nodes; outside the mesh far-away sentinels
+    // (no point of an interior node lies there)
+    for (int e = threadIdx.x; e < lx + ly; e += FK_THREADS) {
+      if (e < lx) {
+        const int gi = gi0 + e;
+        SX[e] = gi < 0 ? T(-1e30) : (gi >= a.nx ? T(1e30) : a.xc[gi]);
+      } else {
+        const int gk = gk0 + e - lx;
+        SY[e - lx] = gk < 0 ? T(-1e30) : (gk >= a.ny ? T(1e30) : a.yc[gk]);
+      }
+    }
+  }
   // 1. stage u^{n+1} with asynchronous copies, all in flight at once (zero
   // fill outside the mesh; those entries are never read)
   const uint32_t sU = (uint32_t)__cvta_generic_to_shared(U);
@@ -145,6 +183,11 @@ __device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* 
     const int gk = gk0 + lk;
     const T* row = U + lk * lx;
     for (int li = 1 + lane; li <= lx - 2; li += 32) {
+      if constexpr (NU) {
+        DX[lk * lx + li] = slope_nu(row, SX, li, 1, gi0 + li, a.nx);
+        DY[lk * lx + li] = slope_nu(U + li, SY, lk, lx, gk, a.ny);
+        continue;
+      }
       if constexpr (PX)
         DX[lk * lx + li] = pchip_fast(row[li] - row[li - 1], row[li + 1] - row[li]);
       else
@@ -175,10 +218,11 @@ __device__ __forceinline__ void stage_tile(const Step2D<T>& a, V4<T>* R, V2<T>* 
 // Phase 4 of the direct kernel: the Gauss-Hermite sum of every output node
 // of rows [k0, min(k0 + ty, k_end)) of this tile, one node per thread and
 // pass (column i0 + lane, row k0 + warp + 8 m).  Returns the range-check flag.
-template <typename T, int Q, bool MF, bool PX>
+template <typename T, int Q, bool MF, bool PX, bool NU>
 __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>* R,
-                                                 const V2<T>* S, int i0, int k0, int k_end,
-                                                 int gi0, int gk0, int warp, int lane) {
+                                                 const V2<T>* S, const T* SX, const T* SY,
+                                                 int i0, int k0, int k_end, int gi0, int gk0,
+                                                 int warp, int lane) {
   const int lx = a.lx, ly = a.ly, lyr = a.lyr;
   const int i = i0 + lane;
   const int li = i - gi0;
@@ -189,7 +233,13 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
     const T* ct = a.col_tab + 4 * (int64_t)i;
     cx0 = ct[0]; cx1 = ct[1]; cx2 = ct[2]; cx3 = ct[3];
   }
-  const T nlo_x = T(-i), nhi_x = T(a.nx - 1 - i);
+  // the box relative to the node: in cells, or (NU) in physical lengths
+  T nlo_x = T(-i), nhi_x = T(a.nx - 1 - i), xi = T(0);
+  if constexpr (NU) {
+    xi = SX[li];
+    nlo_x = a.blo[0] - xi;
+    nhi_x = a.bhi[0] - xi;
+  }
   const uint32_t sR = (uint32_t)__cvta_generic_to_shared(R);
   const uint32_t sS = (uint32_t)__cvta_generic_to_shared(S);
   unsigned bad = 0;
@@ -208,7 +258,12 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
       dy = a.cdy;
     }
     // y factors of every query row, weights folded in
-    const T nlo_y = T(-k), nhi_y = T(a.ny - 1 - k);
+    T nlo_y = T(-k), nhi_y = T(a.ny - 1 - k), yk = T(0);
+    if constexpr (NU) {
+      yk = SY[lk];
+      nlo_y = a.blo[1] - yk;
+      nhi_y = a.bhi[1] - yk;
+    }
     uint32_t rq[Q];  // byte offset of the query's lower row within a column of records
     T w0[Q], w1[Q], w2[Q], w3[Q];
     T exit_y = T(0);
@@ -216,14 +271,32 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
     for (int q = 0; q < Q; ++q) {
       const T d = dy + a.gy[q];
       const bool out = (d < nlo_y) || (d > nhi_y);
-      const T fl = floor(d);
-      int c = k + (int)fl;
-      T t = d - fl;
-      if (c > a.ny - 2) {
-        c = a.ny - 2;
-        t = T(1);
+      int lc;
+      T t, hr = T(1);  // hr: the cell's height (NU), the slope basis scale
+      if constexpr (NU) {
+        const T z = yk + d;
+        lc = cell_of(SY, ly - 3, z);
+        if (lc + gk0 > a.ny - 2) {
+          lc = a.ny - 2 - gk0;
+          t = T(1);
+        } else {
+          t = (z - SY[lc]) / (SY[lc + 1] - SY[lc]);
+        }
+        hr = SY[lc + 1] - SY[lc];
+        if (!(t >= T(0) && t <= T(1))) {
+          bad |= out ? 0u : 1u;
+          t = T(0);
+        }
+      } else {
+        const T fl = floor(d);
+        int c = k + (int)fl;
+        t = d - fl;
+        if (c > a.ny - 2) {
+          c = a.ny - 2;
+          t = T(1);
+        }
+        lc = c - gk0;
       }
-      int lc = c - gk0;
       if ((unsigned)(lc - 1) > (unsigned)(ly - 4)) {
         bad |= out ? 0u : 1u;
         lc = lk;
@@ -236,6 +309,10 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
       w1[q] = wq * (t2 * (T(3) - T(2) * t));  // h01
       w2[q] = wq * (t * omt * omt);            // h10
       w3[q] = -wq * (t2 * omt);                // h11
+      if constexpr (NU) {
+        w2[q] *= hr;
+        w3[q] *= hr;
+      }
     }
     const T om = T(1) - uj;
     T acc = T(0);
@@ -246,20 +323,39 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
         acc += a.w[p] * om;
         continue;
       }
-      const T fl = floor(d);
-      int c = i + (int)fl;
-      T t = d - fl;
-      if (!PX && c > a.nx - 2) {
-        c = a.nx - 2;
-        t = T(1);
+      int lc;
+      T t, hc = T(1);  // hc: the cell's width (NU), the slope basis scale
+      if constexpr (NU) {
+        const T z = xi + d;
+        lc = cell_of(SX, lx - 3, z);
+        if (lc + gi0 > a.nx - 2) {
+          lc = a.nx - 2 - gi0;
+          t = T(1);
+        } else {
+          t = (z - SX[lc]) / (SX[lc + 1] - SX[lc]);
+        }
+        hc = SX[lc + 1] - SX[lc];
+        if (!(t >= T(0) && t <= T(1))) {
+          bad |= 1u;
+          t = T(0);
+        }
+      } else {
+        const T fl = floor(d);
+        int c = i + (int)fl;
+        t = d - fl;
+        if (!PX && c > a.nx - 2) {
+          c = a.nx - 2;
+          t = T(1);
+        }
+        lc = c - gi0;
       }
-      int lc = c - gi0;
       if ((unsigned)(lc - 1) > (unsigned)(lx - 4)) {
         bad |= 1u;
         lc = li;
       }
       const T t2 = t * t, omt = T(1) - t;
-      const T h01 = t2 * (T(3) - T(2) * t), h10 = t * omt * omt, h11 = -(t2 * omt);
+      const T h01 = t2 * (T(3) - T(2) * t);
+      const T h10 = t * omt * omt * hc, h11 = -(t2 * omt) * hc;
       const uint32_t baseS = sS + (uint32_t)(lc * lyr) * (uint32_t)sizeof(V2<T>);
       const uint32_t baseR = sR + (uint32_t)(lc * lyr) * (uint32_t)sizeof(V4<T>);
       T accp = exit_y * om;
@@ -297,8 +393,8 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
 }
 
 // MF: several fields per launch (blockIdx.z), for Algorithm 1.  PX:
-// periodic x.
-template <typename T, int Q, int MINB, bool MF, bool PX>
+// periodic x.  NU: non-uniform mesh.
+template <typename T, int Q, int MINB, bool MF, bool PX, bool NU>
 __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lx = a.lx, ly = a.ly, lyr = a.lyr;
@@ -321,9 +417,11 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2d(const Step2D<T> a) 
   }
   const int gi0 = i0 - a.hx - 1;  // global node of staged column 0
   const int gk0 = k0 - a.hy - 1;
-  stage_tile<MF, PX>(a, R, S, U, gi0, gk0, warp, lane);
-
-  const unsigned bad = direct_phase<T, Q, MF, PX>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
+  stage_tile<MF, PX, NU>(a, R, S, U, gi0, gk0, warp, lane);
+  const T* SX = U + 3 * lx * ly;  // staged coordinates (NU)
+  const T* SY = SX + lx;
+  const unsigned bad =
+      direct_phase<T, Q, MF, PX, NU>(a, R, S, SX, SY, i0, k0, k_end, gi0, gk0, warp, lane);
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
 
@@ -420,9 +518,10 @@ __global__ void __launch_bounds__(FK_THREADS, 4) k_step2dw(const Step2D<float> a
     k_end = a.ny - 1;
   }
   const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;
-  stage_tile<false, false>(a, R, S, U, gi0, gk0, warp, lane);
+  stage_tile<false, false, false>(a, R, S, U, gi0, gk0, warp, lane);
   if (!window) {
-    const unsigned b = direct_phase<T, Q, false, false>(a, R, S, i0, k0, k_end, gi0, gk0, warp, lane);
+    const unsigned b = direct_phase<T, Q, false, false, false>(a, R, S, nullptr, nullptr, i0, k0,
+                                                               k_end, gi0, gk0, warp, lane);
     if (b) atomicOr(a.err, FK_DEVERR_RANGE);
     return;
   }
@@ -640,7 +739,7 @@ constexpr int kMinbFields = sizeof(T) == 8 ? 2 : 4;
 
 template <typename T, int Q, int MINB>
 cudaError_t launch2d_q(const Step2D<T>& a, cudaStream_t s) {
-  const size_t smem = fk_step2d_smem(a.lx, a.ly, a.lyr, (int)sizeof(T));
+  const size_t smem = fk_step2d_smem(a.lx, a.ly, a.lyr, (int)sizeof(T), a.nu);
   int gy;
   if (a.mode == 0)
     gy = (a.ny - 2 + a.ty - 1) / a.ty;
@@ -652,16 +751,23 @@ cudaError_t launch2d_q(const Step2D<T>& a, cudaStream_t s) {
   if (a.px) {  // periodic x: nodes 1 .. nx-1, the default register budget
     dim3 grid((a.nx - 1 + 31) / 32, gy, nf);
     if (nf > 1)
-      k_step2d<T, Q, D, true, true><<<grid, FK_THREADS, smem, s>>>(a);
+      k_step2d<T, Q, D, true, true, false><<<grid, FK_THREADS, smem, s>>>(a);
     else
-      k_step2d<T, Q, D, false, true><<<grid, FK_THREADS, smem, s>>>(a);
+      k_step2d<T, Q, D, false, true, false><<<grid, FK_THREADS, smem, s>>>(a);
     return cudaGetLastError();
   }
   dim3 grid((a.nx - 2 + 31) / 32, gy, nf);
+  if (a.nu) {  // non-uniform mesh, the default register budget
+    if (nf > 1)
+      k_step2d<T, Q, D, true, false, true><<<grid, FK_THREADS, smem, s>>>(a);
+    else
+      k_step2d<T, Q, D, false, false, true><<<grid, FK_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+  }
   if (nf > 1)
-    k_step2d<T, Q, D, true, false><<<grid, FK_THREADS, smem, s>>>(a);
+    k_step2d<T, Q, D, true, false, false><<<grid, FK_THREADS, smem, s>>>(a);
   else
-    k_step2d<T, Q, MINB, false, false><<<grid, FK_THREADS, smem, s>>>(a);
+    k_step2d<T, Q, MINB, false, false, false><<<grid, FK_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -709,17 +815,23 @@ cudaError_t launch_window(const Step2D<float>& a, int q, cudaStream_t s) {
 template <typename T, int Q, int MINB>
 cudaError_t attr2d_q() {
   const int big = 227 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, false, false>,
+  cudaError_t e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, false, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if constexpr (MINB == kMinbFields<T>) {
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, true, false>,
+      e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, true, false, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, false, true>,
+      e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, false, true, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, true, true>,
+      e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, true, true, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, false, false, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_step2d<T, Q, MINB, true, false, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   }
   return e;
@@ -759,8 +871,9 @@ cudaError_t attr1d_q() {
 
 }  // namespace
 
-size_t fk_step2d_smem(int lx, int ly, int lyr, int elem) {
-  return (size_t)lx * lyr * (6 * elem) + (size_t)3 * lx * ly * elem;
+size_t fk_step2d_smem(int lx, int ly, int lyr, int elem, int nu) {
+  return (size_t)lx * lyr * (6 * elem) + (size_t)3 * lx * ly * elem +
+         (nu ? (size_t)(lx + ly) * elem : 0);
 }
 
 size_t fk_step1d_smem(int lx, int elem) { return (size_t)lx * (4 * elem) + (size_t)lx * elem; }

@@ -8,6 +8,7 @@
 
 #include <stdio.h>
 
+#include <algorithm>
 #include <iterator>
 #include <mutex>
 #include <new>
@@ -141,6 +142,18 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
     if (r->absorbing_faces != FK_PERIODIC_X || g->dim != 2 || path != FK_PATH_MATRIX_FREE)
       return FK_ERR_UNSUPPORTED;
   }
+  bool nu = false;
+  for (int m = 0; m < g->dim; ++m) {
+    const double* ax = g->axis[m];
+    if (!ax) continue;
+    nu = true;
+    if (ax[0] != g->lo[m] || ax[g->n[m] - 1] != g->hi[m]) return FK_ERR_INVALID_ARG;
+    for (int i = 0; i + 1 < g->n[m]; ++i)
+      if (!finite(ax[i + 1]) || !(ax[i + 1] > ax[i])) return FK_ERR_INVALID_ARG;
+  }
+  if (nu && (g->dim != 2 || path != FK_PATH_MATRIX_FREE ||
+             (r && r->absorbing_faces != FK_ALL_FACES_ABSORBING)))
+    return FK_ERR_UNSUPPORTED;
   if (path == FK_PATH_CSR) {
     if (g->dim != 2 || c->family == FK_PAPER_CELLULAR) return FK_ERR_UNSUPPORTED;
     if (c->family == FK_CELLULAR_FLOW && c->p[1] != 0.0) return FK_ERR_UNSUPPORTED;
@@ -151,10 +164,32 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
   return FK_OK;
 }
 
+void free_coords(fk_plan* p) {
+  for (int m = 0; m < 2; ++m) {
+    free(p->hcoord[m]);
+    p->hcoord[m] = nullptr;
+  }
+}
+
 fk_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return FK_OK;
   if (e == cudaErrorMemoryAllocation) return FK_ERR_OOM;
   return FK_ERR_CUDA;
+}
+
+// Node coordinates of a non-uniform plan, in the plan's precision.
+template <typename T>
+fk_status upload_coords(fk_plan* p) {
+  for (int m = 0; m < 2; ++m) {
+    const int nm = p->grid.n[m];
+    std::vector<T> c(nm);
+    for (int i = 0; i < nm; ++i) c[i] = (T)p->hcoord[m][i];
+    fk_status st = fk_dev_alloc(p, &p->dcoord[m], sizeof(T) * nm);
+    if (st == FK_OK)
+      st = cuda_status(cudaMemcpy(p->dcoord[m], c.data(), sizeof(T) * nm, cudaMemcpyHostToDevice));
+    if (st != FK_OK) return st;
+  }
+  return FK_OK;
 }
 
 template <typename T>
@@ -171,7 +206,7 @@ fk_status upload_tables(fk_plan* p) {
   const int per = p->periodic_x ? nx - 1 : nx;
   const double nk = p->coeffs.p[1];
   for (int i = 0; i < nx; ++i) {
-    const double x = p->grid.lo[0] + (i % per) * p->h[0];
+    const double x = p->nu ? p->hcoord[0][i] : p->grid.lo[0] + (i % per) * p->h[0];
     if (p->coeffs.family == FK_PAPER_CELLULAR) {
       // v_1 ~ sin(n x) + eps f cos(n x), v_2 ~ cos(n x) + eps f (-sin(n x))
       ct[4 * i + 0] = (T)sin(nk * x);
@@ -186,7 +221,8 @@ fk_status upload_tables(fk_plan* p) {
     }
   }
   for (int k = 0; k < ny; ++k) {
-    const double y = p->grid.dim == 2 ? p->grid.lo[1] + k * p->h[1] : 0.0;
+    const double y = p->grid.dim == 2 ? (p->nu ? p->hcoord[1][k] : p->grid.lo[1] + k * p->h[1])
+                                      : 0.0;
     rt[2 * k + 0] = (T)cos(kPi * y);
     rt[2 * k + 1] = (T)sin(kPi * y);
   }
@@ -218,37 +254,48 @@ void fill2d(const fk_plan* p, int n, Step2D<T>* a) {
   a->family = p->coeffs.family == FK_CONST_DRIFT ? FK_CONST_DRIFT : FK_CELLULAR_FLOW;
   a->px = p->periodic_x;
   const double dt = p->dt, tn = n * dt;
+  // lengths in cells on a uniform mesh; physical lengths on a non-uniform one
+  const double hx = p->nu ? 1.0 : p->h[0], hy = p->nu ? 1.0 : p->h[1];
   if (p->coeffs.family == FK_PAPER_CELLULAR) {
     // dx = Pe dt/h (-pi cos(pi y)) (sin(n x) + eps f cos(n x)),
     // dy = Pe dt/h (n sin(pi y)) (cos(n x) - eps f sin(n x)), f = cos(omega t)
     const double Pe = p->coeffs.p[0], nk = p->coeffs.p[1], eps = p->coeffs.p[2];
     const double f = cos(p->coeffs.p[3] * tn);
-    a->kx = (T)(-Pe * kPi * dt / p->h[0]);
-    a->ky = (T)(Pe * nk * dt / p->h[1]);
+    a->kx = (T)(-Pe * kPi * dt / hx);
+    a->ky = (T)(Pe * nk * dt / hy);
     a->A = (T)1.0;
     a->e1 = (T)(eps * f);
     a->e2 = (T)(eps * f);
   } else if (p->coeffs.family == FK_CELLULAR_FLOW) {
     const double A = p->coeffs.p[0], eps = p->coeffs.p[1], om = p->coeffs.p[2];
     const double st = sin(om * tn);
-    a->kx = (T)(-kPi * dt / p->h[0]);
-    a->ky = (T)(kPi * dt / p->h[1]);
+    a->kx = (T)(-kPi * dt / hx);
+    a->ky = (T)(kPi * dt / hy);
     a->A = (T)A;
     a->e1 = (T)(eps * st);
     a->e2 = (T)(2.0 * eps * st);
   } else {
-    a->cdx = (T)(p->coeffs.p[0] * dt / p->h[0]);
-    a->cdy = (T)(p->coeffs.p[1] * dt / p->h[1]);
+    a->cdx = (T)(p->coeffs.p[0] * dt / hx);
+    a->cdy = (T)(p->coeffs.p[1] * dt / hy);
   }
   a->col_tab = (const T*)p->col_tab;
   a->row_tab = (const T*)p->row_tab;
   const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * dt);
   for (int q = 0; q < p->q; ++q) {
-    a->gx[q] = (T)(sg * p->gh_a[q] / p->h[0]);
-    a->gy[q] = (T)(sg * p->gh_a[q] / p->h[1]);
+    a->gx[q] = (T)(sg * p->gh_a[q] / hx);
+    a->gy[q] = (T)(sg * p->gh_a[q] / hy);
     a->w[q] = (T)p->gh_w[q];
   }
   a->err = p->d_err;
+  if (p->nu) {
+    a->nu = 1;
+    a->xc = (const T*)p->dcoord[0];
+    a->yc = (const T*)p->dcoord[1];
+    for (int m = 0; m < 2; ++m) {
+      a->blo[m] = (T)p->grid.lo[m];
+      a->bhi[m] = (T)p->grid.hi[m];
+    }
+  }
   a->win = (sizeof(T) == 4) ? p->win : 0;
   a->mode = a->win > 0 ? 1 : 0;
   if (a->win > 0) {
@@ -315,7 +362,7 @@ bool cand_fits(const fk_plan* p, const TileCand& c, int dev_smem, int kern = kDi
   }
   const int hy = p->halo[1] + (kern == kRowWindow ? 1 : 0);
   const int lx = 32 + 2 * p->halo[0] + 2, ly = c.ty + 2 * hy + 2;
-  return fk_step2d_smem(lx, ly, ly | 1, p->elem) <= (size_t)dev_smem;
+  return fk_step2d_smem(lx, ly, ly | 1, p->elem, p->nu) <= (size_t)dev_smem;
 }
 
 void set_kernel(fk_plan* p, int kern) {
@@ -337,7 +384,7 @@ int current_kernel(const fk_plan* p) {
 void window_eligibility(fk_plan* p) {
   p->win_max = 0;
   if (p->grid.dim != 2 || p->prec != FK_FP32 || p->path != FK_PATH_MATRIX_FREE) return;
-  if (p->periodic_x) return;  // periodic x: the direct kernel only
+  if (p->periodic_x || p->nu) return;  // periodic x, non-uniform: the direct kernel only
   const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * p->dt);
   float gy[FK_MAXQ_2D];
   for (int q = 0; q < p->q; ++q) gy[q] = (float)(sg * p->gh_a[q] / p->h[1]);
@@ -369,7 +416,7 @@ void masked_eligibility(fk_plan* p) {
   const double kMargin = 1e-4;
   p->mwin = 0;
   if (p->grid.dim != 2 || p->prec != FK_FP32 || p->path != FK_PATH_MATRIX_FREE) return;
-  if (p->periodic_x) return;  // periodic x: the direct kernel only
+  if (p->periodic_x || p->nu) return;  // periodic x, non-uniform: the direct kernel only
   const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * p->dt);
   float gx[FK_MAXQ_2D], gy[FK_MAXQ_2D];
   for (int q = 0; q < p->q; ++q) {
@@ -793,6 +840,24 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
     p->grid.lo[m] = 0.0;
     p->grid.hi[m] = 0.0;
   }
+  // non-uniform axes: the plan keeps its own copy of every axis (the
+  // uniform ones written out) and drops the caller's pointers
+  for (int m = 0; m < 3; ++m) p->grid.axis[m] = nullptr;
+  for (int m = 0; m < grid->dim; ++m) p->nu |= grid->axis[m] ? 1 : 0;
+  if (p->nu) {
+    for (int m = 0; m < grid->dim; ++m) {
+      const int nm = grid->n[m];
+      p->hcoord[m] = (double*)malloc(sizeof(double) * nm);
+      if (!p->hcoord[m]) {
+        free_coords(p);
+        delete p;
+        return FK_ERR_OOM;
+      }
+      for (int i = 0; i < nm; ++i)
+        p->hcoord[m][i] = grid->axis[m] ? grid->axis[m][i]
+                                        : grid->lo[m] + i * (grid->hi[m] - grid->lo[m]) / (nm - 1);
+    }
+  }
   p->region.absorbing_faces = region ? region->absorbing_faces : FK_ALL_FACES_ABSORBING;
   p->periodic_x = p->region.absorbing_faces == FK_PERIODIC_X ? 1 : 0;
   p->coeffs = *coeffs;
@@ -803,6 +868,7 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   p->path = path;
   p->elem = prec == FK_FP32 ? 4 : 8;
   if (!gauss_hermite(q_per_dim, p->gh_a, p->gh_w)) {
+    free_coords(p);
     delete p;
     return FK_ERR_INVALID_ARG;
   }
@@ -824,13 +890,42 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
     p->reach[m] = (bmax[m] * dt + sg * amax) / p->h[m];
     const double r = p->reach[m] * (1.0 + 1e-6) + 1e-3;
     if (r > 4096.0) {
+      free_coords(p);
       delete p;
       return FK_ERR_UNSUPPORTED;
     }
     p->halo[m] = (int)ceil(r) + 1;
+    if (p->nu) {
+      // every shifted point of node i lies within R of x_i: its cell c must
+      // satisfy i - halo <= c <= i + halo - 1 (the cells staged around i)
+      const double* x = p->hcoord[m];
+      const int nm = grid->n[m];
+      const double R = (bmax[m] * dt + sg * amax) * (1.0 + 1e-6) + 1e-12;
+      auto cell = [&](double z) {
+        int lo = 0, up = nm - 1;
+        while (up - lo > 1) {
+          const int mid = (lo + up) / 2;
+          if (x[mid] <= z) lo = mid; else up = mid;
+        }
+        return lo;  // in [0, nm-2]
+      };
+      int h = 1;
+      for (int i = 0; i < nm; ++i) {
+        const int cl = cell(x[i] - R), cr = cell(x[i] + R);
+        h = std::max(h, std::max(i - cl, cr + 1 - i));
+      }
+      p->halo[m] = h + 1;  // one more for FP32 rounding of the positions
+      p->reach[m] = h;
+      if (p->halo[m] > 4096) {
+        free_coords(p);
+        delete p;
+        return FK_ERR_UNSUPPORTED;
+      }
+    }
   }
   // periodic x: a staged column wraps by at most one period
   if (p->periodic_x && p->halo[0] + 2 >= grid->n[0] - 1) {
+    free_coords(p);
     delete p;
     return FK_ERR_UNSUPPORTED;
   }
@@ -838,6 +933,7 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   masked_eligibility(p);
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) {
+    free_coords(p);
     delete p;
     return FK_ERR_CUDA;
   }
@@ -877,6 +973,8 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   if (st == FK_OK) st = cuda_status(cudaMemset(p->d_err, 0, sizeof(unsigned)));
   if (st == FK_OK) st = fk_dev_alloc(p, &p->scratch, (size_t)(p->J * p->elem));
   if (st == FK_OK) st = (prec == FK_FP32) ? upload_tables<float>(p) : upload_tables<double>(p);
+  if (st == FK_OK && p->nu)
+    st = (prec == FK_FP32) ? upload_coords<float>(p) : upload_coords<double>(p);
   if (st == FK_OK) st = cuda_status(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
   if (st == FK_OK) st = autotune(p);
   if (st == FK_OK) {
@@ -922,6 +1020,9 @@ fk_status fk_plan_destroy(fk_plan* p) {
   fk_dev_free(p->stack);
   fk_dev_free(p->batch_rec);
   fk_dev_free(p->hz_ws);
+  fk_dev_free(p->dcoord[0]);
+  fk_dev_free(p->dcoord[1]);
+  free_coords(p);
   fk_dev_free(p->adj_ws);
   fk_dev_free(p->adj_tab);
   fk_batch_release(p);

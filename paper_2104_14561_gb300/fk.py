@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -52,6 +53,7 @@ class PlanSpec:
     precision: str = "fp32"
     path: str = "matrix_free"
     periodic_x: bool = False  # x faces identified (node n[0]-1 is node 0), y faces absorb
+    axes: tuple | None = None  # per axis None (uniform) or the increasing node coordinates
 
 
 class Plan:
@@ -62,10 +64,15 @@ class Plan:
         self._lib = L.load()
         g = L.Grid()
         g.dim = len(spec.n)
+        keep = []
         for m in range(g.dim):
             g.n[m] = int(spec.n[m])
             g.lo[m] = float(spec.lo[m])
             g.hi[m] = float(spec.hi[m])
+            if spec.axes is not None and spec.axes[m] is not None:
+                a = np.ascontiguousarray(spec.axes[m], dtype=np.float64)
+                keep.append(a)
+                g.axis[m] = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         r = L.Region(L.FK_PERIODIC_X if spec.periodic_x else L.FK_ALL_FACES_ABSORBING)
         c = L.Coeffs()
         c.family = _FAMILY[spec.family]

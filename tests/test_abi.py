@@ -35,6 +35,9 @@ def test_exports_every_declared_symbol(L):
         assert hasattr(lib, n), n
 
 
+_KEEP = []
+
+
 def _args(L, **kw):
     g = L.Grid()
     g.dim = kw.get("dim", 2)
@@ -43,6 +46,11 @@ def _args(L, **kw):
         g.n[m] = n[m]
         g.lo[m] = 0.0
         g.hi[m] = (2.0, 1.0, 1.0)[m]
+    for m, ax in enumerate(kw.get("axes", ())):
+        if ax is not None:
+            arr = (ctypes.c_double * len(ax))(*ax)
+            _KEEP.append(arr)
+            g.axis[m] = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
     r = L.Region(kw.get("faces", L.FK_ALL_FACES_ABSORBING))
     c = L.Coeffs()
     c.family = kw.get("family", L.FK_CELLULAR_FLOW)
@@ -75,6 +83,13 @@ CASES = [
     (dict(faces=0x3C, path=1, p=(1.0, 0.0, 1.0, 1e-3)), 2),  # periodic x on the CSR path
     (dict(faces=0x33), 2),         # periodic y is not offered
     (dict(family=2, path=1, p=(10.0, 2.0, 0.0, 0.6)), 2),  # the paper's flow: matrix-free only
+    # non-uniform axes
+    (dict(n=(5, 3), axes=([0.0, 0.5, 1.0, 1.5, 2.1], None)), 1),  # last coordinate != hi
+    (dict(n=(5, 3), axes=([0.0, 0.5, 0.5, 1.5, 2.0], None)), 1),  # not increasing
+    (dict(n=(5, 3), axes=([0.0, 0.2, 1.0, 1.5, 2.0], None), faces=0x3C), 2),  # with periodic x
+    (dict(n=(5, 3), axes=([0.0, 0.2, 1.0, 1.5, 2.0], None), path=1,
+          p=(1.0, 0.0, 1.0, 1e-3)), 2),  # on the CSR path
+    (dict(dim=1, n=(5,), axes=([0.0, 0.2, 1.0, 1.5, 2.0],), family=0, p=(0.1, 0, 0, 1.0)), 2),
 ]
 
 
