@@ -185,7 +185,8 @@ def oracle_rate(w, max_seconds: float = 20.0):
     from oracle import fk_oracle as O
     fam = {"const_drift": O.CONST_DRIFT, "cellular_flow": O.CELLULAR_FLOW,
            "paper_cellular": O.PAPER_CELLULAR}[w["family"]]
-    g = O.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]), int(w.get("periodic_x", False)))
+    g = O.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]), int(w.get("periodic_x", False)),
+               fk_inputs.axes_of(w))
     cores = os.cpu_count() or 1
     per_step = units_per_solve(w) / w["n_steps"]
     t = time.perf_counter()
@@ -225,7 +226,7 @@ def run_reference(args, rank: int):
         for b, x in enumerate(ws):
             n = x["n_steps"] - s
             g = O.Grid(tuple(x["n"]), tuple(x["lo"]), tuple(x["hi"]),
-                       int(x.get("periodic_x", False)))
+                       int(x.get("periodic_x", False)), fk_inputs.axes_of(x))
             us[b] = O.march(g, fams[x["family"]], list(x["params"]), x["q"], x["dt"], n, n - 1,
                             us[b], nthreads=cores)
         if s >= args.warmup:
@@ -528,7 +529,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     spec = fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
                        params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
                        precision=w["precision"], path=w["path"],
-                       periodic_x=w.get("periodic_x", False))
+                       periodic_x=w.get("periodic_x", False), axes=fk_inputs.axes_of(w))
     plan = fk.Plan(spec)
     stream = torch.cuda.Stream(device=dev)
     out = plan.empty()

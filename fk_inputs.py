@@ -63,6 +63,11 @@ WORKLOADS = {
     "paper_2d_1025x257": dict(n=(1025, 257), lo=(-math.pi, 0.0), hi=(math.pi, 1.0),
                               family="paper_cellular", params=(10.0, 2.0, 0.15, TWO_PI / 10),
                               q=6, dt=5e-5, n_steps=1000, precision="fp32", periodic_x=True),
+    # the benchmark flow on a mesh graded towards every face (non-uniform
+    # axes: spacing 2x finer at the faces than in the middle)
+    "graded_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
+                            family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
+                            q=6, dt=1e-3, n_steps=2000, precision="fp32", graded=(0.4, 0.4)),
     # every horizon t_k = k dt, k = 1..200, of the time-dependent flow (Algorithm 1)
     "horizons_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
                               family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
@@ -70,6 +75,24 @@ WORKLOADS = {
 }
 
 BATCH_SEED = 20240214
+
+
+def graded_axis(lo: float, hi: float, n: int, strength: float) -> np.ndarray:
+    """n increasing coordinates on [lo, hi] clustered towards both ends: a
+    uniform grid xi in [-1, 1] mapped by (1 - s) xi + s sin(pi xi / 2)."""
+    xi = np.linspace(-1.0, 1.0, n)
+    t = (1.0 - strength) * xi + strength * np.sin(0.5 * math.pi * xi)
+    x = 0.5 * (lo + hi) + 0.5 * (hi - lo) * t
+    x[0], x[-1] = lo, hi
+    return x
+
+
+def axes_of(w: dict):
+    """The node coordinates of a workload with graded axes, else None."""
+    if not w.get("graded"):
+        return None
+    return tuple(graded_axis(w["lo"][m], w["hi"][m], w["n"][m], w["graded"][m])
+                 for m in range(len(w["n"])))
 
 
 def workload(name: str, **override) -> dict:

@@ -33,12 +33,7 @@ def fk():
     return fk
 
 
-def graded(lo, hi, n, strength):
-    xi = np.linspace(-1.0, 1.0, n)
-    s = np.sin(0.5 * math.pi * xi) * strength + xi * (1.0 - strength)
-    x = 0.5 * (lo + hi) + 0.5 * (hi - lo) * s
-    x[0], x[-1] = lo, hi
-    return x
+graded = fk_inputs.graded_axis
 
 
 def two_spacing(lo, mid, hi, coarse, fine):
@@ -141,3 +136,27 @@ def test_graded_batched_equals_single(fk):
         assert np.array_equal(o.double().cpu().numpy(), s)
     for p in plans:
         p.close()
+
+
+def test_graded_workload_sampled_step(fk, oracle):
+    """The graded benchmark workload (1025 x 513, 6 x 6 points, FP32): one
+    step from a random field at sampled nodes against the oracle's step."""
+    import torch
+    w = fk_inputs.workload("graded_1025x513")
+    axes = fk_inputs.axes_of(w)
+    ny, nx = w["n"][1], w["n"][0]
+    plan = fk.Plan(fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
+                               params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
+                               precision="fp32", axes=axes))
+    u1 = fk_inputs.random_field((ny, nx), seed=53)
+    n = 1234
+    got = plan.march(n + 1, n, torch.tensor(u1, dtype=torch.float32, device="cuda"))
+    got = got.double().cpu().numpy().reshape(-1)
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    plan.close()
+    nodes = fk_inputs.sample_nodes((ny, nx), 2000, seed=7)
+    g = oracle.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]), axes=axes)
+    want = oracle.step_nodes(g, oracle.CELLULAR_FLOW, list(w["params"]), w["q"], w["dt"], n, u1,
+                             nodes, nthreads=NCPU)
+    assert np.abs(got[nodes] - want).max() <= 1e-5

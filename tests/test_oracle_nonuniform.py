@@ -23,13 +23,7 @@ import fk_inputs
 PATHS = 1_000_000
 
 
-def _graded(lo, hi, n, strength):
-    """Nodes clustered towards both ends: a sine map of a uniform grid."""
-    xi = np.linspace(-1.0, 1.0, n)
-    s = np.sin(0.5 * math.pi * xi) * strength + xi * (1.0 - strength)
-    x = 0.5 * (lo + hi) + 0.5 * (hi - lo) * s
-    x[0], x[-1] = lo, hi
-    return x
+_graded = fk_inputs.graded_axis
 
 
 def test_explicit_uniform_axes_reproduce_uniform(oracle):
