@@ -267,6 +267,9 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
     uint32_t rq[Q];  // byte offset of the query's lower row within a column of records
     T w0[Q], w1[Q], w2[Q], w3[Q];
     T exit_y = T(0);
+    // NU: the points are sorted (ascending abscissae), so their cells are
+    // too: bisect for the first, walk forward for the others
+    int lcy = 0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const T d = dy + a.gy[q];
@@ -275,7 +278,12 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
       T t, hr = T(1);  // hr: the cell's height (NU), the slope basis scale
       if constexpr (NU) {
         const T z = yk + d;
-        lc = cell_of(SY, ly - 3, z);
+        if (q == 0) {
+          lcy = cell_of(SY, ly - 3, z);
+        } else {
+          while (lcy < ly - 3 && SY[lcy + 1] <= z) ++lcy;
+        }
+        lc = lcy;
         if (lc + gk0 > a.ny - 2) {
           lc = a.ny - 2 - gk0;
           t = T(1);
@@ -316,6 +324,7 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
     }
     const T om = T(1) - uj;
     T acc = T(0);
+    int lcx = 0;  // NU: the cell of the previous x-point (0: none yet)
 #pragma unroll 1
     for (int p = 0; p < Q; ++p) {
       const T d = dx + a.gx[p];
@@ -327,7 +336,12 @@ __device__ __forceinline__ unsigned direct_phase(const Step2D<T>& a, const V4<T>
       T t, hc = T(1);  // hc: the cell's width (NU), the slope basis scale
       if constexpr (NU) {
         const T z = xi + d;
-        lc = cell_of(SX, lx - 3, z);
+        if (lcx == 0) {
+          lcx = cell_of(SX, lx - 3, z);
+        } else {
+          while (lcx < lx - 3 && SX[lcx + 1] <= z) ++lcx;
+        }
+        lc = lcx;
         if (lc + gi0 > a.nx - 2) {
           lc = a.nx - 2 - gi0;
           t = T(1);
