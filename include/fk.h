@@ -146,6 +146,8 @@ typedef struct fk_plan_info {
   int adjoint_kernel;       /* backward step of the last fk_adjoint: 0 none
                                yet, 1 per-point transposed scatter, 2 masked
                                tensor window                             */
+  int periodic_x;           /* 1: region FK_PERIODIC_X                   */
+  int nonuniform;           /* 1: some axis has explicit coordinates     */
 } fk_plan_info;
 
 /* ------------------------------------------------------------------------

@@ -55,7 +55,8 @@ class PlanInfo(ctypes.Structure):
                 ("reach_cells", ctypes.c_double * 3), ("csr_nnz", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("window_rows", ctypes.c_int),
                 ("step_kernel", ctypes.c_int), ("batch_mode", ctypes.c_int),
-                ("adjoint_kernel", ctypes.c_int)]
+                ("adjoint_kernel", ctypes.c_int), ("periodic_x", ctypes.c_int),
+                ("nonuniform", ctypes.c_int)]
 
 
 _lib = None

@@ -1048,6 +1048,8 @@ fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
   info->csr_nnz = p->csr_nnz;
   info->workspace_bytes = p->workspace_bytes;
   info->window_rows = p->use_masked ? p->mwin : p->win;
+  info->periodic_x = p->periodic_x;
+  info->nonuniform = p->nu;
   info->step_kernel = p->grid.dim == 1 ? (p->resident1d ? 2 + p->resident1d : 0)
                                         : current_kernel(p);
   info->batch_mode = fk_batch_mode(p);

@@ -100,7 +100,8 @@ class Plan:
                 "window_rows": i.window_rows,
                 "step_kernel": ("direct", "window", "masked", "resident", "cluster")[i.step_kernel],
                 "batch_mode": ("none", "persistent", "streams")[i.batch_mode],
-                "adjoint_kernel": ("none", "scatter", "masked")[i.adjoint_kernel]}
+                "adjoint_kernel": ("none", "scatter", "masked")[i.adjoint_kernel],
+                "periodic_x": bool(i.periodic_x), "nonuniform": bool(i.nonuniform)}
 
     def _check_field(self, t: torch.Tensor, name: str):
         if t.dtype != self.dtype or t.device.type != "cuda" or tuple(t.shape) != self.shape \

@@ -46,11 +46,6 @@ def _oracle_grid(oracle, w):
     return oracle.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]), periodic=1)
 
 
-def _fam(oracle, w):
-    return {"paper_cellular": oracle.PAPER_CELLULAR, "const_drift": oracle.CONST_DRIFT,
-            "cellular_flow": oracle.CELLULAR_FLOW}[w["family"]]
-
-
 def _periodic_field(shape, seed):
     u = fk_inputs.random_field(shape, seed=seed, boundary_one=False)
     u[0, :] = 1.0
@@ -76,7 +71,7 @@ def _solve(fk, w, u0=None):
 def test_paper_fp64_vs_oracle(fk, oracle, n):
     w = _w(n)
     got, info = _solve(fk, w)
-    assert info["step_kernel"] == "direct"
+    assert info["step_kernel"] == "direct" and info["periodic_x"] and not info["nonuniform"]
     want = oracle.march(_oracle_grid(oracle, w), oracle.PAPER_CELLULAR, list(PAPER), w["q"],
                         w["dt"], w["n_steps"], 0, nthreads=NCPU)
     assert np.abs(got - want).max() <= 1e-12
