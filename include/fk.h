@@ -295,7 +295,9 @@ fk_status fk_last_device_error(fk_plan *plan);
  * 16 MiB, which every GPU that loads this library holds until the process
  * exits.
  *   grid, coeffs, q_per_dim, dt, n_steps, prec  as for fk_plan_create, with
- *               grid->dim = 2 (else FK_ERR_UNSUPPORTED).
+ *               grid->dim = 2, a uniform mesh (axis[] NULL) and the box's
+ *               faces all absorbing (else FK_ERR_UNSUPPORTED); families
+ *               FK_CONST_DRIFT and FK_CELLULAR_FLOW.
  *   u_terminal  device pointer to u^N, or NULL for chi; may equal u_out.
  *   u_out       device pointer, receives u^0.
  * Size limit: 256 + 4 n[0] e + 2 n[1] e + n[0] n[1] e bytes (e = 4 for FP32,

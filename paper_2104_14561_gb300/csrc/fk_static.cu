@@ -91,6 +91,7 @@ extern "C" fk_status fk_solve_static(const fk_grid* grid, const fk_coeffs* coeff
   // ---- arguments (no CUDA call before they are checked)
   if (!grid || !coeffs || !u_out) return FK_ERR_INVALID_ARG;
   if (grid->dim != 2) return FK_ERR_UNSUPPORTED;
+  if (grid->axis[0] || grid->axis[1]) return FK_ERR_UNSUPPORTED;  // uniform meshes only
   for (int m = 0; m < 2; ++m) {
     if (grid->n[m] < 3 || !finite_d(grid->lo[m]) || !finite_d(grid->hi[m]) ||
         !(grid->hi[m] > grid->lo[m]))

@@ -129,3 +129,17 @@ def test_status_strings(L):
     for code, name in L.STATUS.items():
         assert lib.fk_status_string(code).decode().startswith(name)
     assert b"unknown" in lib.fk_status_string(99)
+
+
+def test_static_entry_rejects_axes(L):
+    """fk_solve_static marches uniform meshes only; coordinates are refused
+    on the host, before any CUDA call."""
+    lib = L.load()
+    lib.fk_solve_static.argtypes = [ctypes.POINTER(L.Grid), ctypes.POINTER(L.Coeffs), ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]
+    lib.fk_solve_static.restype = ctypes.c_int
+    g, _, c = _args(L, n=(5, 3), axes=([0.0, 0.2, 1.0, 1.5, 2.0], None))
+    st = lib.fk_solve_static(ctypes.byref(g), ctypes.byref(c), 4, 1e-3, 5, 0, None,
+                             ctypes.c_void_p(256), None)
+    assert st == 2
