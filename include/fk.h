@@ -83,8 +83,8 @@ enum { FK_CONST_DRIFT = 0, FK_CELLULAR_FLOW = 1, FK_PAPER_CELLULAR = 2 };
  * uniform mesh; otherwise it points to n[m] strictly increasing host
  * coordinates with axis[m][0] = lo[m] and axis[m][n[m]-1] = hi[m] (the
  * partition along a direction need not be uniform), read during plan
- * creation only.  Non-uniform axes: d = 2, FK_PATH_MATRIX_FREE, every face
- * absorbing; Eq. (e300) then takes divided differences over the actual
+ * creation only.  Non-uniform axes: d = 1 or 2, FK_PATH_MATRIX_FREE, every
+ * face absorbing; Eq. (e300) then takes divided differences over the actual
  * spacings and the Hermite cell formula each cell's own width. */
 typedef struct fk_grid {
   int dim;

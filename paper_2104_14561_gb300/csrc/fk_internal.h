@@ -106,6 +106,9 @@ struct Step1D {
   unsigned* err;
   int64_t zstride;  // fields marched by one launch, as in Step2D
   int ncols;
+  int nu;           // non-uniform mesh (per-step kernel only): coordinates xc,
+  const T* xc;      // physical cdx and g, the box [blo, bhi]
+  T blo, bhi;
   __device__ __forceinline__ const T* in() const { return u_in + (int64_t)blockIdx.z * zstride; }
   __device__ __forceinline__ T* out() const { return u_out + (int64_t)blockIdx.z * zstride; }
 };
@@ -113,7 +116,7 @@ struct Step1D {
 // Shared memory bytes of one 2D step CTA (nu: plus the staged node
 // coordinates of a non-uniform mesh).
 size_t fk_step2d_smem(int lx, int ly, int lyr, int elem, int nu = 0);
-size_t fk_step1d_smem(int lx, int elem);
+size_t fk_step1d_smem(int lx, int elem, int nu = 0);
 
 // Launchers (fk_march.cu).  Return cudaGetLastError().
 template <typename T>

@@ -635,13 +635,15 @@ __global__ void __launch_bounds__(FK_THREADS, 4) k_step2dw(const Step2D<float> a
 }
 
 // 1D step: same structure with a record {u_c, u_{c+1}-u_c, h u'_c, h u'_{c+1}}
-// per staged cell.
-template <typename T, int Q>
+// per staged cell.  NU: non-uniform mesh (staged coordinates SX, raw
+// derivatives in the records, cell search, per-cell widths), as in 2D.
+template <typename T, int Q, bool NU>
 __global__ void __launch_bounds__(FK_THREADS) k_step1d(const Step1D<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lx = a.lx;
   V4<T>* R = reinterpret_cast<V4<T>*>(smem);
   T* U = reinterpret_cast<T*>(R + lx);
+  T* SX = U + lx;  // NU only
   const int i0 = 1 + blockIdx.x * a.tx;
   const int gi0 = i0 - a.hx - 1;
   const T* const uin = a.in();
@@ -649,6 +651,7 @@ __global__ void __launch_bounds__(FK_THREADS) k_step1d(const Step1D<T> a) {
   for (int e = threadIdx.x; e < lx; e += blockDim.x) {
     const int gi = gi0 + e;
     U[e] = (gi >= 0 && gi < a.nx) ? uin[gi] : T(0);
+    if constexpr (NU) SX[e] = gi < 0 ? T(-1e30) : (gi >= a.nx ? T(1e30) : a.xc[gi]);
   }
   __syncthreads();
   for (int lc = 1 + threadIdx.x; lc <= lx - 3; lc += blockDim.x) {
@@ -656,8 +659,13 @@ __global__ void __launch_bounds__(FK_THREADS) k_step1d(const Step1D<T> a) {
     V4<T> r;
     r.x = U[lc];
     r.y = U[lc + 1] - U[lc];
-    r.z = slope_line(U, lc, 1, gi, a.nx);
-    r.w = slope_line(U, lc + 1, 1, gi + 1, a.nx);
+    if constexpr (NU) {
+      r.z = slope_nu(U, SX, lc, 1, gi, a.nx);
+      r.w = slope_nu(U, SX, lc + 1, 1, gi + 1, a.nx);
+    } else {
+      r.z = slope_line(U, lc, 1, gi, a.nx);
+      r.w = slope_line(U, lc + 1, 1, gi + 1, a.nx);
+    }
     R[lc] = r;
   }
   __syncthreads();
@@ -669,23 +677,51 @@ __global__ void __launch_bounds__(FK_THREADS) k_step1d(const Step1D<T> a) {
     const T om = T(1) - uj;
     T acc = T(0);
     unsigned bad = 0;
+    int lcw = 0;  // NU: the cell of the previous point (the points are sorted)
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      int c;
-      T t;
-      const bool out = locate(i, a.cdx + a.g[q], a.nx, &c, &t);
-      if (out) {
-        acc += a.w[q] * om;
-        continue;
+      int lc;
+      T t, hc = T(1);  // hc: the cell's width (NU), the slope basis scale
+      if constexpr (NU) {
+        const T z = SX[li] + (a.cdx + a.g[q]);
+        if (z < a.blo || z > a.bhi) {
+          acc += a.w[q] * om;
+          continue;
+        }
+        if (lcw == 0) {
+          lcw = cell_of(SX, lx - 3, z);
+        } else {
+          while (lcw < lx - 3 && SX[lcw + 1] <= z) ++lcw;
+        }
+        lc = lcw;
+        if (lc + gi0 > a.nx - 2) {
+          lc = a.nx - 2 - gi0;
+          t = T(1);
+        } else {
+          t = (z - SX[lc]) / (SX[lc + 1] - SX[lc]);
+        }
+        hc = SX[lc + 1] - SX[lc];
+        if (!(t >= T(0) && t <= T(1))) {
+          bad |= 1u;
+          t = T(0);
+        }
+      } else {
+        int c;
+        const bool out = locate(i, a.cdx + a.g[q], a.nx, &c, &t);
+        if (out) {
+          acc += a.w[q] * om;
+          continue;
+        }
+        lc = c - gi0;
       }
-      int lc = c - gi0;
       if (lc < 1 || lc > lx - 3) {
         bad |= 1u;
         lc = li;
       }
       const T t2 = t * t, omt = T(1) - t;
       const V4<T> r = R[lc];
-      const T v = (r.x - uj) + (t2 * (T(3) - T(2) * t)) * r.y + (t * omt * omt) * r.z - (t2 * omt) * r.w;
+      const T v = (r.x - uj) + (t2 * (T(3) - T(2) * t)) * r.y + (t * omt * omt * hc) * r.z -
+                  (t2 * omt * hc) * r.w;
       acc += a.w[q] * v;
     }
     if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
@@ -872,15 +908,23 @@ cudaError_t attr2d_var() {
 
 template <typename T, int Q>
 cudaError_t launch1d_q(const Step1D<T>& a, cudaStream_t s) {
-  const size_t smem = fk_step1d_smem(a.lx, (int)sizeof(T));
+  const size_t smem = fk_step1d_smem(a.lx, (int)sizeof(T), a.nu);
   dim3 grid((a.nx - 2 + a.tx - 1) / a.tx, 1, a.ncols > 1 ? a.ncols : 1);
-  k_step1d<T, Q><<<grid, FK_THREADS, smem, s>>>(a);
+  if (a.nu)
+    k_step1d<T, Q, true><<<grid, FK_THREADS, smem, s>>>(a);
+  else
+    k_step1d<T, Q, false><<<grid, FK_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T, int Q>
 cudaError_t attr1d_q() {
-  return cudaFuncSetAttribute(k_step1d<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_step1d<T, Q, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step1d<T, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+  return e;
 }
 
 }  // namespace
@@ -890,7 +934,9 @@ size_t fk_step2d_smem(int lx, int ly, int lyr, int elem, int nu) {
          (nu ? (size_t)(lx + ly) * elem : 0);
 }
 
-size_t fk_step1d_smem(int lx, int elem) { return (size_t)lx * (4 * elem) + (size_t)lx * elem; }
+size_t fk_step1d_smem(int lx, int elem, int nu) {
+  return (size_t)lx * (4 * elem) + (size_t)lx * elem + (nu ? (size_t)lx * elem : 0);
+}
 
 bool fk_window_available(int q, int w) {
 #define FK_W(QQ, WW) \

@@ -151,7 +151,7 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
     for (int i = 0; i + 1 < g->n[m]; ++i)
       if (!finite(ax[i + 1]) || !(ax[i + 1] > ax[i])) return FK_ERR_INVALID_ARG;
   }
-  if (nu && (g->dim != 2 || path != FK_PATH_MATRIX_FREE ||
+  if (nu && (path != FK_PATH_MATRIX_FREE ||
              (r && r->absorbing_faces != FK_ALL_FACES_ABSORBING)))
     return FK_ERR_UNSUPPORTED;
   if (path == FK_PATH_CSR) {
@@ -180,7 +180,7 @@ fk_status cuda_status(cudaError_t e) {
 // Node coordinates of a non-uniform plan, in the plan's precision.
 template <typename T>
 fk_status upload_coords(fk_plan* p) {
-  for (int m = 0; m < 2; ++m) {
+  for (int m = 0; m < p->grid.dim; ++m) {
     const int nm = p->grid.n[m];
     std::vector<T> c(nm);
     for (int i = 0; i < nm; ++i) c[i] = (T)p->hcoord[m][i];
@@ -327,13 +327,21 @@ void fill1d(const fk_plan* p, Step1D<T>* a) {
   a->tx = p->tile[0];
   a->hx = p->halo[0];
   a->lx = a->tx + 2 * a->hx + 2;
-  a->cdx = (T)(p->coeffs.p[0] * p->dt / p->h[0]);
+  // lengths in cells on a uniform mesh; physical lengths on a non-uniform one
+  const double hx = p->nu ? 1.0 : p->h[0];
+  a->cdx = (T)(p->coeffs.p[0] * p->dt / hx);
   const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * p->dt);
   for (int q = 0; q < p->q; ++q) {
-    a->g[q] = (T)(sg * p->gh_a[q] / p->h[0]);
+    a->g[q] = (T)(sg * p->gh_a[q] / hx);
     a->w[q] = (T)p->gh_w[q];
   }
   a->err = p->d_err;
+  if (p->nu) {
+    a->nu = 1;
+    a->xc = (const T*)p->dcoord[0];
+    a->blo = (T)p->grid.lo[0];
+    a->bhi = (T)p->grid.hi[0];
+  }
 }
 
 // Candidate tiles of the 2D step kernel: 32 columns x ty rows, ty = 8 m,
@@ -455,7 +463,7 @@ fk_status choose_tiles(fk_plan* p) {
     t = (t + 31) / 32 * 32;
     p->tile[0] = t < 32 ? 32 : (t > 1024 ? 1024 : t);
     const int lx = p->tile[0] + 2 * p->halo[0] + 2;
-    if (fk_step1d_smem(lx, p->elem) > (size_t)dev_smem) return FK_ERR_UNSUPPORTED;
+    if (fk_step1d_smem(lx, p->elem, p->nu) > (size_t)dev_smem) return FK_ERR_UNSUPPORTED;
     return FK_OK;
   }
   for (const TileCand& c : kCands) {
@@ -955,6 +963,7 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
     if (k && strcmp(k, "step") == 0) want = 0;
     if (k && strcmp(k, "resident") == 0) want = 1;
     if (k && strcmp(k, "cluster") == 0) want = 2;
+    if (p->nu) want = 0;  // non-uniform: the per-step kernel only
     if (want == 1 && fk_march1d_smem(nx, p->elem) <= 200 * 1024) {
       st = cuda_status(fk_prepare_march1d(q_per_dim, p->elem));
       if (st == FK_OK) p->resident1d = 1;

@@ -89,7 +89,7 @@ CASES = [
     (dict(n=(5, 3), axes=([0.0, 0.2, 1.0, 1.5, 2.0], None), faces=0x3C), 2),  # with periodic x
     (dict(n=(5, 3), axes=([0.0, 0.2, 1.0, 1.5, 2.0], None), path=1,
           p=(1.0, 0.0, 1.0, 1e-3)), 2),  # on the CSR path
-    (dict(dim=1, n=(5,), axes=([0.0, 0.2, 1.0, 1.5, 2.0],), family=0, p=(0.1, 0, 0, 1.0)), 2),
+    (dict(dim=1, n=(5,), axes=([0.0, 0.2, 1.0, 1.5, 2.1],), family=0, p=(0.1, 0, 0, 1.0)), 1),
 ]
 
 

@@ -160,3 +160,29 @@ def test_graded_workload_sampled_step(fk, oracle):
     want = oracle.step_nodes(g, oracle.CELLULAR_FLOW, list(w["params"]), w["q"], w["dt"], n, u1,
                              nodes, nthreads=NCPU)
     assert np.abs(got[nodes] - want).max() <= 1e-5
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_graded_1d(fk, oracle, precision, tol):
+    """1D drifted Brownian motion (b = 0.5, sigma = 1 on (-1, 1)) on a mesh
+    graded towards both faces: the per-step 1D kernel against the oracle,
+    every horizon included."""
+    import torch
+    ax = graded(-1.0, 1.0, 121, 0.6)
+    spec = fk.PlanSpec(n=(121,), lo=(-1.0,), hi=(1.0,), family="const_drift",
+                       params=(0.5, 0.0, 0.0, 1.0), q=8, dt=1e-3, n_steps=60,
+                       precision=precision, axes=(ax,))
+    plan = fk.Plan(spec)
+    assert plan.info()["nonuniform"] and plan.info()["step_kernel"] == "direct"
+    got = plan.solve().double().cpu().numpy()
+    hz = plan.solve_horizons().double().cpu().numpy()
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    plan.close()
+    g = oracle.Grid((121,), (-1.0,), (1.0,), axes=(ax,))
+    want = oracle.march(g, oracle.CONST_DRIFT, [0.5, 0.0, 0.0, 1.0], 8, 1e-3, 60, 0)
+    assert np.abs(got - want).max() <= tol
+    for k in (1, 30):
+        wk = oracle.march(g, oracle.CONST_DRIFT, [0.5, 0.0, 0.0, 1.0], 8, 1e-3, k, 0)
+        assert np.abs(hz[k - 1] - wk).max() <= tol, k
+    assert np.abs(hz[-1] - got).max() <= tol
