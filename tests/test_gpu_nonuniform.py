@@ -186,3 +186,25 @@ def test_graded_1d(fk, oracle, precision, tol):
         wk = oracle.march(g, oracle.CONST_DRIFT, [0.5, 0.0, 0.0, 1.0], 8, 1e-3, k, 0)
         assert np.abs(hz[k - 1] - wk).max() <= tol, k
     assert np.abs(hz[-1] - got).max() <= tol
+
+
+def test_graded_workload_full_march_vs_golden(fk):
+    """The graded benchmark workload: all 2000 FP32 steps against the FP64
+    oracle's u^0 at 20k+ sampled nodes (every node next to the boundary
+    included), written by tests/golden/make_oracle_golden.py."""
+    import torch
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden",
+                                "graded_1025x513_oracle_u0.npz"))
+    w = fk_inputs.workload("graded_1025x513")
+    assert tuple(gold["n"]) == tuple(w["n"]) and int(gold["n_steps"]) == w["n_steps"]
+    plan = fk.Plan(fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
+                               params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
+                               precision="fp32", axes=fk_inputs.axes_of(w)))
+    out = plan.solve()
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    got = out.double().reshape(-1).cpu().numpy()[gold["nodes"]]
+    plan.close()
+    err = np.abs(got - gold["u0"]).max()
+    print(f"graded_1025x513 fp32 vs fp64 oracle, 2000 steps: max-abs {err:.3e}")
+    assert err <= 1e-5

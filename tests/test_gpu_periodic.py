@@ -162,3 +162,24 @@ def test_paper_workload_sampled_step(fk, oracle):
     assert np.array_equal(full[:, 0], full[:, -1])
     assert full[1:-1, 1:-1].max() > 0.05
     plan.close()
+
+
+def test_paper_workload_full_march_vs_golden(fk):
+    """The paper's example at the benchmark's size: all 1000 FP32 steps
+    against the FP64 oracle's u^0 at 22k sampled nodes (the rows next to the
+    y faces and the seam columns included), written by
+    tests/golden/make_oracle_golden.py."""
+    import torch
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden",
+                                "paper_2d_1025x257_oracle_u0.npz"))
+    w = fk_inputs.workload("paper_2d_1025x257")
+    assert tuple(gold["n"]) == tuple(w["n"]) and int(gold["n_steps"]) == w["n_steps"]
+    plan = fk.Plan(_spec(fk, w))
+    out = plan.solve()
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    got = out.double().reshape(-1).cpu().numpy()[gold["nodes"]]
+    plan.close()
+    err = np.abs(got - gold["u0"]).max()
+    print(f"paper_2d_1025x257 fp32 vs fp64 oracle, 1000 steps: max-abs {err:.3e}")
+    assert err <= 1e-5
