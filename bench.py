@@ -41,6 +41,7 @@ METRIC = "node-quadrature updates/s & HBM GB/s (2D, 36-pt GH, FP32/FP64); adjoin
 UNIT = "node-quadrature updates/s"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FLOP_PER_UPDATE = 26                # 13 multiply-adds per query: 12 Hermite terms + the weighted sum
+FLOP_PER_UPDATE_3D = 66             # 33 multiply-adds: 8 corners x (value + 3 partials) + the sum
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (profiling recipe)
 PROFILE_DIR = os.path.join(ROOT, "profiles")
@@ -79,7 +80,7 @@ def parse():
     # profiling aids: a smaller case of the same workload (not a benchmark line)
     ap.add_argument("--time-steps", type=int, default=None,
                     help="override the workload's number of time steps")
-    ap.add_argument("--grid", type=int, nargs=2, default=None, metavar=("NX", "NY"),
+    ap.add_argument("--grid", type=int, nargs="+", default=None, metavar="N",
                     help="override the workload's mesh")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default=None,
                     help="override the workload's precision")
@@ -200,7 +201,7 @@ def oracle_rate(w, max_seconds: float = 20.0):
     dt = time.perf_counter() - t
     return {"value": per_step * k / dt, "unit": UNIT, "cores": cores if O.has_openmp() else 1,
             "kind": "oracle",
-            "sample": f"{k} of {w['n_steps']} time steps of {w['n'][0]}x{w['n'][1] if len(w['n']) > 1 else 1}"
+            "sample": f"{k} of {w['n_steps']} time steps of {'x'.join(str(v) for v in w['n'])}"
                       f", FP64, OpenMP over nodes ({dt:.1f} s)"}
 
 
@@ -606,6 +607,20 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                     "bytes_per_launch": bytes_step, "launch_ms": launch_ms,
                     "csr_nnz": info["csr_nnz"]}
+    elif len(w["n"]) == 3:
+        # two launches per time step (records, then the window sums); the
+        # time of both is charged to the step, so the fraction is a floor
+        flops_launch = FLOP_PER_UPDATE_3D * units / w["n_steps"]
+        peak_flops = (SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 if w["precision"] == "fp32"
+                      else FP64_PEAK_TFLOPS * 1e12)
+        achieved = flops_launch / (launch_ms * 1e-3)
+        roofline = {"kernel": "k_step3d (with k_rec3d: one time step)", "bound": "alu",
+                    "achieved": achieved / 1e12, "peak": peak_flops / 1e12, "unit": "TFLOP/s",
+                    "frac": achieved / peak_flops,
+                    "traffic": profile_traffic("k_step3d", args.workload),
+                    "flop_per_launch": flops_launch, "launch_ms": launch_ms,
+                    "window_rows": info.get("window_rows", 0),
+                    "step_kernel": info.get("step_kernel")}
     else:
         flops_launch = FLOP_PER_UPDATE * units / w["n_steps"]
         peak_flops = (SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 if w["precision"] == "fp32"
@@ -637,7 +652,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,
                 "d2h_bytes_per_step": field_bytes},
         "gpu_launches": args.steps * (1 if info.get("step_kernel") in ("resident", "cluster") else
-                                      (2 if w["path"] == "csr" else 1) * w["n_steps"] + 1),
+                                      (2 if w["path"] == "csr" or len(w["n"]) == 3 else 1)
+                                      * w["n_steps"] + 1),
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }

@@ -28,6 +28,18 @@ Workloads (the paper has no datasets; every input is defined by formulas):
                               dt = 1e-3, 1000 steps, FP32, fixed seed.
 * ``adjoint_1025x513``     -- the 1025 x 513 workload differentiated with
                               respect to A, eps, D and the terminal field.
+* ``paper_2d_1025x257``    -- the paper's own 2D example (Sec. 4.2): Pe = 10,
+                              n = 2, eps = 0.15, omega = 2 pi / 10 on
+                              [-pi, pi] x [0, 1], periodic in x, 6 x 6
+                              points, dt = 5e-5, 1000 steps (T = 0.05), FP32.
+* ``graded_1025x513``      -- the cellular_1025x513 problem on a mesh graded
+                              towards every face (non-uniform axes).
+* ``horizons_1025x513``    -- every horizon t_k = k dt, k = 1..200, of the
+                              cellular flow (Algorithm 1).
+* ``drift3d_129``          -- d = 3: Brownian motion with drift
+                              b = (0.3, -0.2, 0.1), sigma = 0.5 in (-1, 1)^3,
+                              129^3 nodes, 4 x 4 x 4 points, dt = 1e-3,
+                              500 steps (T = 0.5), FP32.
 
 Values in every workload are probabilities in [0, 1] that start from the 0/1
 indicator chi with a sharp ramp at the boundary; ``random_field`` draws
@@ -68,6 +80,11 @@ WORKLOADS = {
     "graded_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
                             family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
                             q=6, dt=1e-3, n_steps=2000, precision="fp32", graded=(0.4, 0.4)),
+    # d = 3: Brownian motion with constant drift in the cube (-1, 1)^3
+    # (independent components, so the survival is a product of 1D ones)
+    "drift3d_129": dict(n=(129, 129, 129), lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0),
+                        family="const_drift", params=(0.3, -0.2, 0.1, 0.5), q=4, dt=1e-3,
+                        n_steps=500, precision="fp32"),
     # every horizon t_k = k dt, k = 1..200, of the time-dependent flow (Algorithm 1)
     "horizons_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
                               family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
@@ -156,4 +173,10 @@ def sample_nodes(shape, count: int, seed: int) -> np.ndarray:
         for k in (0, 1, ny // 2, ny - 2, ny - 1):
             for i in (0, 1, nx // 2, nx - 2, nx - 1):
                 pick.add(k * nx + i)
+    if len(shape) == 3:
+        nz, ny, nx = shape
+        for l in (0, 1, nz // 2, nz - 2, nz - 1):
+            for k in (0, 1, ny // 2, ny - 2, ny - 1):
+                for i in (0, 1, nx // 2, nx - 2, nx - 1):
+                    pick.add((l * ny + k) * nx + i)
     return np.array(sorted(pick), dtype=np.int64)

@@ -63,7 +63,8 @@ typedef enum fk_path { FK_PATH_MATRIX_FREE = 0, FK_PATH_CSR = 1 } fk_path;
 
 /* Coefficient families (b, sigma of Eq. (e1)):
  *  FK_CONST_DRIFT     p = {b_1, b_2, b_3, s}: b constant, sigma = s I
- *                     (Sec. 4.1 is d = 1, b = 0, s = 1).  d = 1 or 2.
+ *                     (Sec. 4.1 is d = 1, b = 0, s = 1).  d = 1, 2 or 3
+ *                     (the only family with d = 3).
  *  FK_CELLULAR_FLOW   p = {A, eps, omega, D}, d = 2: the time-periodic
  *                     cellular flow of Sec. 4.2 written with the stream
  *                     function psi = A sin(pi x) sin(pi y)
@@ -138,7 +139,9 @@ typedef struct fk_plan_info {
                                node, exits as zero weights); 1D: 0 one
                                launch per step, 3 the whole march in one
                                CTA's shared memory, 4 in one thread-block
-                               cluster (distributed shared memory)       */
+                               cluster (distributed shared memory); 3D:
+                               5, the node-window kernel (W^3 records
+                               per node, exits as zero weights)          */
   int batch_mode;           /* strategy of the last fk_solve_batched this
                                plan led (plans[0]): 0 none, 1 the
                                persistent kernel, 2 concurrent single-plan
@@ -157,11 +160,18 @@ typedef struct fk_plan_info {
  * q_per_dim^dim shifted points per node), Sec. 3.1.1 (uniform time step dt,
  * N = n_steps steps, T = N dt, coefficients evaluated at t_n = n dt).
  *   out        receives the new plan (set to NULL on failure).
- *   q_per_dim  1..8 for dim = 2, 1..16 for dim = 1.
+ *   q_per_dim  1..8 for dim = 2 or 3, 1..16 for dim = 1.
  *   dt > 0, n_steps >= 1.
  *   path       FK_PATH_CSR needs a family whose coefficients do not depend
  *              on t (FK_CONST_DRIFT, or FK_CELLULAR_FLOW with eps = 0),
  *              else FK_ERR_UNSUPPORTED.
+ *   dim = 3    FK_CONST_DRIFT on a uniform mesh (axis[] NULL), every face
+ *              absorbing, FK_PATH_MATRIX_FREE, n[m] <= 65535; the points
+ *              of one axis must span fewer than 6 cells (sigma sqrt(2 dt)
+ *              (a_{q-1} - a_0) / h_m < 6) and n[m] must be at least the
+ *              window width floor(span) + 3; else FK_ERR_UNSUPPORTED.
+ *              fk_solve_batched, fk_adjoint and fk_solve_static take
+ *              dim = 2 plans only (FK_ERR_UNSUPPORTED).
  * The plan allocates its own device workspace on the current CUDA device
  * (coefficient tables, one scratch field, for FK_PATH_CSR the assembled
  * matrix, which is built here).  Errors: FK_ERR_INVALID_ARG,

@@ -113,6 +113,25 @@ struct Step1D {
   __device__ __forceinline__ T* out() const { return u_out + (int64_t)blockIdx.z * zstride; }
 };
 
+// One 3D step (fk_march3d.cu): uniform mesh, lengths in cells as in Step2D.
+template <typename T>
+struct Step3D {
+  const T* u_in;
+  T* u_out;
+  T* snap;
+  V4<T>* rec;        // J records {u, hx u_x, hy u_y, hz u_z} (plan workspace)
+  int nx, ny, nz;
+  int q;             // Gauss-Hermite points per axis
+  int w3;            // window width W (3..8) on every axis
+  T cd[3];           // b dt / h per axis (constant drift)
+  T gs[3];           // sigma sqrt(2 dt) / h per axis
+  T ga[FK_MAXQ_2D], gw[FK_MAXQ_2D];  // abscissae (ascending) and weights
+  unsigned* err;
+};
+template <typename T>
+cudaError_t fk_launch_step3d(const Step3D<T>& a, cudaStream_t s);
+#define FK_MAXW_3D 8
+
 // Shared memory bytes of one 2D step CTA (nu: plus the staged node
 // coordinates of a non-uniform mesh).
 size_t fk_step2d_smem(int lx, int ly, int lyr, int elem, int nu = 0);
@@ -156,14 +175,15 @@ cudaError_t fk_launch_march1d_cluster(const Step1D<T>& a, int q, int ctas, const
                                       T* u_out, T* snaps, int stride, int steps, cudaStream_t s);
 int fk_prepare_march1d_cluster(int q, int elem);
 // The terminal indicator chi: 1 on the boundary nodes (with px, the x faces
-// are identified and only the y faces are boundary), 0 elsewhere.
+// are identified and only the y faces are boundary), 0 elsewhere; nz is the
+// third extent of a 3D mesh.
 cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s,
-                               int px = 0);
+                               int px = 0, int nz = 1);
 // Starting fields of the horizon march: field c = 1..nfields (at offset
 // (c - 1) J) of buffer `odd` for odd c and of buffer `even` for even c gets
 // src (J values) or, with src NULL, the terminal indicator.
 cudaError_t fk_launch_fill_fields(void* even, void* odd, const void* src, int dim, int nx, int ny,
-                                  int elem, int nfields, cudaStream_t s, int px = 0);
+                                  int elem, int nfields, cudaStream_t s, int px = 0, int nz = 1);
 cudaError_t fk_launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
 
 struct fk_plan {
@@ -222,6 +242,9 @@ struct fk_plan {
   int nu;            // non-uniform axes: node coordinates per axis
   double* hcoord[2]; // host copies (malloc) and device copies in the plan's precision
   void* dcoord[2];
+  // d = 3: the node records of the step and the window width
+  void* rec3d;
+  int w3;
   // fk_solve_horizons: the second buffer of the N horizon fields
   void* hz_ws;
   int64_t hz_bytes;

@@ -739,25 +739,35 @@ __global__ void __launch_bounds__(FK_THREADS) k_step1d(const Step1D<T> a) {
   }
 }
 
+// Whether flat node j lies on an absorbing face (Eq. (e3)); with px the x
+// faces are identified and only the other faces count.
+__device__ __forceinline__ bool on_boundary(int64_t j, int dim, int nx, int ny, int nz, int px) {
+  const int i = (int)(j % nx);
+  bool b = !px && (i == 0 || i == nx - 1);
+  if (dim >= 2) {
+    const int k = (int)((j / nx) % ny);
+    b = b || k == 0 || k == ny - 1;
+  }
+  if (dim == 3) {
+    const int l = (int)(j / ((int64_t)nx * ny));
+    b = b || l == 0 || l == nz - 1;
+  }
+  return b;
+}
+
 template <typename T>
-__global__ void k_fill_chi(T* u, int dim, int nx, int ny, int px) {
-  const int64_t J = (int64_t)nx * (dim == 2 ? ny : 1);
+__global__ void k_fill_chi(T* u, int dim, int nx, int ny, int px, int nz) {
+  const int64_t J = (int64_t)nx * (dim >= 2 ? ny : 1) * (dim == 3 ? nz : 1);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
        j += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(j % nx);
-    bool b = !px && (i == 0 || i == nx - 1);
-    if (dim == 2) {
-      const int k = (int)(j / nx);
-      b = b || k == 0 || k == ny - 1;
-    }
-    u[j] = b ? T(1) : T(0);
+    u[j] = on_boundary(j, dim, nx, ny, nz, px) ? T(1) : T(0);
   }
 }
 
 template <typename T>
 __global__ void k_fill_fields(T* even, T* odd, const T* src, int dim, int nx, int ny, int nf,
-                              int px) {
-  const int64_t J = (int64_t)nx * (dim == 2 ? ny : 1), total = J * nf;
+                              int px, int nz) {
+  const int64_t J = (int64_t)nx * (dim >= 2 ? ny : 1) * (dim == 3 ? nz : 1), total = J * nf;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = e / J, j = e - c * J;  // field c + 1
@@ -765,13 +775,7 @@ __global__ void k_fill_fields(T* even, T* odd, const T* src, int dim, int nx, in
     if (src) {
       v = src[j];
     } else {
-      const int i = (int)(j % nx);
-      bool b = !px && (i == 0 || i == nx - 1);
-      if (dim == 2) {
-        const int k = (int)(j / nx);
-        b = b || k == 0 || k == ny - 1;
-      }
-      v = b ? T(1) : T(0);
+      v = on_boundary(j, dim, nx, ny, nz, px) ? T(1) : T(0);
     }
     (((c + 1) & 1) ? odd : even)[e] = v;
   }
@@ -1032,28 +1036,28 @@ template cudaError_t fk_launch_step1d<float>(const Step1D<float>&, int, cudaStre
 template cudaError_t fk_launch_step1d<double>(const Step1D<double>&, int, cudaStream_t);
 
 cudaError_t fk_launch_fill_chi(void* u, int dim, int nx, int ny, int elem, cudaStream_t s,
-                               int px) {
-  const int64_t J = (int64_t)nx * (dim == 2 ? ny : 1);
+                               int px, int nz) {
+  const int64_t J = (int64_t)nx * (dim >= 2 ? ny : 1) * (dim == 3 ? nz : 1);
   int blocks = (int)((J + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (elem == 4)
-    k_fill_chi<float><<<blocks, 256, 0, s>>>((float*)u, dim, nx, ny, px);
+    k_fill_chi<float><<<blocks, 256, 0, s>>>((float*)u, dim, nx, ny, px, nz);
   else
-    k_fill_chi<double><<<blocks, 256, 0, s>>>((double*)u, dim, nx, ny, px);
+    k_fill_chi<double><<<blocks, 256, 0, s>>>((double*)u, dim, nx, ny, px, nz);
   return cudaGetLastError();
 }
 
 cudaError_t fk_launch_fill_fields(void* even, void* odd, const void* src, int dim, int nx, int ny,
-                                  int elem, int nfields, cudaStream_t s, int px) {
-  const int64_t total = (int64_t)nx * (dim == 2 ? ny : 1) * nfields;
+                                  int elem, int nfields, cudaStream_t s, int px, int nz) {
+  const int64_t total = (int64_t)nx * (dim >= 2 ? ny : 1) * (dim == 3 ? nz : 1) * nfields;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (elem == 4)
     k_fill_fields<float><<<blocks, 256, 0, s>>>((float*)even, (float*)odd, (const float*)src, dim,
-                                                nx, ny, nfields, px);
+                                                nx, ny, nfields, px, nz);
   else
     k_fill_fields<double><<<blocks, 256, 0, s>>>((double*)even, (double*)odd,
-                                                 (const double*)src, dim, nx, ny, nfields, px);
+                                                 (const double*)src, dim, nx, ny, nfields, px, nz);
   return cudaGetLastError();
 }
 

@@ -134,9 +134,16 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
     if (!finite(c->p[k])) return FK_ERR_INVALID_ARG;
   if (c->family == FK_CONST_DRIFT && !(c->p[3] >= 0.0)) return FK_ERR_INVALID_ARG;
   if (c->family == FK_CELLULAR_FLOW && !(c->p[3] >= 0.0)) return FK_ERR_INVALID_ARG;
-  if (g->dim == 3) return FK_ERR_UNSUPPORTED;
   if ((c->family == FK_CELLULAR_FLOW || c->family == FK_PAPER_CELLULAR) && g->dim != 2)
     return FK_ERR_INVALID_ARG;
+  if (g->dim == 3) {
+    // d = 3: constant drift on a uniform mesh with every face absorbing,
+    // matrix-free (the window kernel of fk_march3d.cu)
+    if (c->family != FK_CONST_DRIFT || path != FK_PATH_MATRIX_FREE) return FK_ERR_UNSUPPORTED;
+    if (r && r->absorbing_faces != FK_ALL_FACES_ABSORBING) return FK_ERR_UNSUPPORTED;
+    for (int m = 0; m < 3; ++m)
+      if (g->axis[m] || g->n[m] > 65535) return FK_ERR_UNSUPPORTED;
+  }
   if (q < 1 || q > (g->dim == 1 ? FK_MAXQ : FK_MAXQ_2D)) return FK_ERR_UNSUPPORTED;
   if (r && r->absorbing_faces != FK_ALL_FACES_ABSORBING) {
     if (r->absorbing_faces != FK_PERIODIC_X || g->dim != 2 || path != FK_PATH_MATRIX_FREE)
@@ -456,6 +463,7 @@ fk_status choose_tiles(fk_plan* p) {
   int dev_smem = 0;
   cudaError_t e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
   if (e != cudaSuccess) return FK_ERR_CUDA;
+  if (p->grid.dim == 3) return FK_OK;  // no tiles: records are read through L1/L2
   if (p->grid.dim == 1) {
     // enough CTAs to spread a short line over the SMs (2 per SM), 32..1024 nodes each
     const int interior = p->grid.n[0] - 2;
@@ -686,9 +694,52 @@ void fk_fill_step2d_f32(const fk_plan* p, int n, Step2D<float>* a) { fill2d<floa
 void fk_fill_step2d_f64(const fk_plan* p, int n, Step2D<double>* a) { fill2d<double>(p, n, a); }
 
 namespace {
+template <typename T>
+void fill3d(const fk_plan* p, Step3D<T>* a) {
+  memset(a, 0, sizeof(*a));
+  a->rec = (V4<T>*)p->rec3d;
+  a->nx = p->grid.n[0];
+  a->ny = p->grid.n[1];
+  a->nz = p->grid.n[2];
+  a->q = p->q;
+  a->w3 = p->w3;
+  const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * p->dt);
+  for (int m = 0; m < 3; ++m) {
+    a->cd[m] = (T)(p->coeffs.p[m] * p->dt / p->h[m]);
+    a->gs[m] = (T)(sg / p->h[m]);
+  }
+  for (int q = 0; q < p->q; ++q) {
+    a->ga[q] = (T)p->gh_a[q];
+    a->gw[q] = (T)p->gh_w[q];
+  }
+  a->err = p->d_err;
+}
+
+// One step of each of nfields fields (J values apart): the record pass and
+// the window pass per field (the records are one field's workspace).
+template <typename T>
+cudaError_t step3d(const fk_plan* p, const void* u_in, void* u_out, void* snap, int nfields,
+                   cudaStream_t s) {
+  Step3D<T> a;
+  fill3d<T>(p, &a);
+  for (int f = 0; f < nfields; ++f) {
+    a.u_in = (const T*)u_in + (int64_t)f * p->J;
+    a.u_out = (T*)u_out + (int64_t)f * p->J;
+    a.snap = (T*)snap;
+    cudaError_t e = fk_launch_step3d<T>(a, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 fk_status enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void* snap,
                        int nfields, cudaStream_t s) {
   cudaError_t e;
+  if (p->grid.dim == 3) {
+    e = p->prec == FK_FP32 ? step3d<float>(p, u_in, u_out, snap, nfields, s)
+                           : step3d<double>(p, u_in, u_out, snap, nfields, s);
+    return cuda_status(e);
+  }
   if (p->grid.dim == 2) {
     if (p->prec == FK_FP32) {
       Step2D<float> a;
@@ -757,7 +808,8 @@ fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void
   const int steps = n_from - n_to;
   if (steps == 0) {
     if (!u_in) return cuda_status(fk_launch_fill_chi(u_out, p->grid.dim, p->grid.n[0],
-                                                      p->grid.n[1], p->elem, s, p->periodic_x));
+                                                      p->grid.n[1], p->elem, s, p->periodic_x,
+                                                      p->grid.n[2]));
     if (u_in != u_out) return cuda_status(fk_launch_copy(u_out, u_in, bytes, s));
     return FK_OK;
   }
@@ -786,7 +838,7 @@ fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void
   if (!src) {
     void* buf = first_to_out ? p->scratch : u_out;
     fk_status st = cuda_status(fk_launch_fill_chi(buf, p->grid.dim, p->grid.n[0], p->grid.n[1],
-                                                  p->elem, s, p->periodic_x));
+                                                  p->elem, s, p->periodic_x, p->grid.n[2]));
     if (st != FK_OK) return st;
     src = buf;
   } else if (src == u_out && first_to_out) {
@@ -937,6 +989,24 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
     delete p;
     return FK_ERR_UNSUPPORTED;
   }
+  if (grid->dim == 3) {
+    // window width: the points of one axis span gs (a_{Q-1} - a_0) cells
+    // and touch at most floor(span) + 2 cells, W = floor(span) + 3 nodes
+    // (a small margin covers rounding of the positions)
+    int w = 3;
+    for (int m = 0; m < 3; ++m) {
+      const double span = sg * (p->gh_a[q_per_dim - 1] - p->gh_a[0]) / p->h[m];
+      w = std::max(w, (int)floor(span * (1.0 + 1e-6) + 1e-3) + 3);
+    }
+    bool fits = w <= FK_MAXW_3D;
+    for (int m = 0; m < 3; ++m) fits = fits && grid->n[m] >= w;
+    if (!fits) {
+      free_coords(p);
+      delete p;
+      return FK_ERR_UNSUPPORTED;
+    }
+    p->w3 = w;
+  }
   window_eligibility(p);
   masked_eligibility(p);
   cudaError_t e = cudaGetDevice(&p->device);
@@ -949,7 +1019,7 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   // the CSR path launches no step kernel: a halo too wide for any tile only
   // concerns the matrix-free path
   if (st == FK_ERR_UNSUPPORTED && path == FK_PATH_CSR) st = FK_OK;
-  if (st == FK_OK && path == FK_PATH_MATRIX_FREE)
+  if (st == FK_OK && path == FK_PATH_MATRIX_FREE && grid->dim != 3)
     st = cuda_status(fk_prepare_step_kernels(grid->dim, q_per_dim, p->elem));
   if (st == FK_OK && grid->dim == 1) {
     // The whole 1D march in one launch: FP32 in one CTA when the field, its
@@ -981,6 +1051,8 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   if (st == FK_OK) st = fk_dev_alloc(p, (void**)&p->d_err, sizeof(unsigned));
   if (st == FK_OK) st = cuda_status(cudaMemset(p->d_err, 0, sizeof(unsigned)));
   if (st == FK_OK) st = fk_dev_alloc(p, &p->scratch, (size_t)(p->J * p->elem));
+  if (st == FK_OK && grid->dim == 3)
+    st = fk_dev_alloc(p, &p->rec3d, (size_t)(4 * p->J * p->elem));
   if (st == FK_OK) st = (prec == FK_FP32) ? upload_tables<float>(p) : upload_tables<double>(p);
   if (st == FK_OK && p->nu)
     st = (prec == FK_FP32) ? upload_coords<float>(p) : upload_coords<double>(p);
@@ -1019,6 +1091,7 @@ fk_status fk_plan_destroy(fk_plan* p) {
   if (p->graph) cudaGraphExecDestroy(p->graph);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   fk_dev_free(p->scratch);
+  fk_dev_free(p->rec3d);
   fk_dev_free(p->col_tab);
   fk_dev_free(p->row_tab);
   fk_dev_free(p->d_err);
@@ -1056,11 +1129,12 @@ fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
   }
   info->csr_nnz = p->csr_nnz;
   info->workspace_bytes = p->workspace_bytes;
-  info->window_rows = p->use_masked ? p->mwin : p->win;
+  info->window_rows = p->grid.dim == 3 ? p->w3 : (p->use_masked ? p->mwin : p->win);
   info->periodic_x = p->periodic_x;
   info->nonuniform = p->nu;
-  info->step_kernel = p->grid.dim == 1 ? (p->resident1d ? 2 + p->resident1d : 0)
-                                        : current_kernel(p);
+  info->step_kernel = p->grid.dim == 1   ? (p->resident1d ? 2 + p->resident1d : 0)
+                      : p->grid.dim == 3 ? 5
+                                         : current_kernel(p);
   info->batch_mode = fk_batch_mode(p);
   info->adjoint_kernel = p->adj_kernel;
   return FK_OK;
@@ -1140,7 +1214,7 @@ fk_status fk_solve_horizons(fk_plan* p, const void* u_terminal, void* p_out,
   char* buf[2] = {(char*)p_out, (char*)p->hz_ws};
   fk_status st = cuda_status(fk_launch_fill_fields(buf[0], buf[1], u_terminal, p->grid.dim,
                                                    p->grid.n[0], p->grid.n[1], p->elem, N,
-                                                   stream, p->periodic_x));
+                                                   stream, p->periodic_x, p->grid.n[2]));
   const int kMaxFields = 65535;  // grid z limit
   for (int n = N; n >= 1 && st == FK_OK; --n) {
     const int par = n & 1;

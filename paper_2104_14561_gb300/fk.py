@@ -2,8 +2,9 @@
 
 PyTorch supplies device memory and streams; every step of the march runs
 in libfk_gb300's CUDA kernels.  Fields are tensors of shape (n[1], n[0])
-in 2D (x fastest) or (n[0],) in 1D, dtype float32 or float64 matching the
-plan's precision, on the plan's CUDA device.
+in 2D (x fastest), (n[2], n[1], n[0]) in 3D or (n[0],) in 1D, dtype
+float32 or float64 matching the plan's precision, on the plan's CUDA
+device.
 """
 from __future__ import annotations
 
@@ -98,7 +99,8 @@ class Plan:
                 "tile": list(i.tile), "reach_cells": list(i.reach_cells),
                 "csr_nnz": i.csr_nnz, "workspace_bytes": i.workspace_bytes,
                 "window_rows": i.window_rows,
-                "step_kernel": ("direct", "window", "masked", "resident", "cluster")[i.step_kernel],
+                "step_kernel": ("direct", "window", "masked", "resident", "cluster",
+                                "window3d")[i.step_kernel],
                 "batch_mode": ("none", "persistent", "streams")[i.batch_mode],
                 "adjoint_kernel": ("none", "scatter", "masked")[i.adjoint_kernel],
                 "periodic_x": bool(i.periodic_x), "nonuniform": bool(i.nonuniform)}

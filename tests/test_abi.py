@@ -76,7 +76,14 @@ CASES = [
     (dict(q=9), 2),
     (dict(faces=0x3), 2),
     (dict(path=1), 2),             # CSR with a time-dependent drift
-    (dict(dim=3, n=(5, 5, 5)), 2),
+    (dict(dim=3, n=(5, 5, 5)), 1),  # the cellular flow is two-dimensional
+    # d = 3: constant drift, uniform, absorbing, matrix-free, narrow point spread
+    (dict(dim=3, n=(9, 9, 9), family=0, p=(0.1, 0, 0, 1.0), faces=0x3C), 2),
+    (dict(dim=3, n=(9, 9, 9), family=0, p=(0.1, 0, 0, 1.0), path=1), 2),
+    (dict(dim=3, n=(5, 5, 5), family=0, p=(0.1, 0, 0, 1.0),
+          axes=(None, None, [0.0, 0.1, 0.5, 0.7, 1.0])), 2),
+    (dict(dim=3, n=(9, 9, 9), family=0, p=(0.1, 0, 0, 1.0), dt=0.05), 2),  # span > 6 cells
+    (dict(dim=3, n=(4, 33, 33), family=0, p=(0.1, 0, 0, 0.3), dt=2e-3), 2),  # n < W on x
     (dict(dim=1, n=(33,)), 1),     # the cellular flow is two-dimensional
     (dict(family=2, dim=1, n=(33,), p=(10.0, 2.0, 0.15, 0.6)), 1),  # so is the paper's
     (dict(faces=0x3C, dim=1, n=(33,), family=0, p=(0.1, 0, 0, 1.0)), 2),  # periodic x in 1D

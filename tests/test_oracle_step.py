@@ -43,7 +43,7 @@ def _affine_field(g, c0, c):
     return c0 + sum(c[m] * coords[m] for m in range(g.dim)), coords
 
 
-@pytest.mark.parametrize("case", ["const1d", "const2d", "cell2d"])
+@pytest.mark.parametrize("case", ["const1d", "const2d", "cell2d", "const3d"])
 def test_affine_maps_to_shifted_affine(case, oracle):
     rng = np.random.default_rng(1)
     dt = 2e-3
@@ -53,6 +53,9 @@ def test_affine_maps_to_shifted_affine(case, oracle):
     elif case == "const2d":
         g = oracle.Grid((31, 21), (-2.0, -1.0), (2.0, 1.0))
         fam, p = oracle.CONST_DRIFT, [-0.4, 0.9, 0, 0.5]
+    elif case == "const3d":
+        g = oracle.Grid((17, 13, 11), (-2.0, -1.0, 0.0), (2.0, 1.0, 1.0))
+        fam, p = oracle.CONST_DRIFT, [0.6, -0.8, 0.3, 0.4]
     else:
         g = oracle.Grid((41, 21), (-1.0, -1.0), (3.0, 2.0))
         fam, p = oracle.CELLULAR_FLOW, [1.3, 0.4, 2 * math.pi, 0.02]
@@ -140,6 +143,58 @@ def test_dense_matrix_form_2d(oracle):
     want[0, :] = want[-1, :] = 1.0
     want[:, 0] = want[:, -1] = 1.0
     got = oracle.march(g, oracle.CELLULAR_FLOW, p, q, dt, n + 1, n, u)
+    np.testing.assert_allclose(got, want, atol=1e-14)
+
+
+def test_dense_matrix_form_3d(oracle):
+    """The same matrix form in 3D: every column of Psi is a product of three
+    1D cardinal functions, with a node's value or one of its three first
+    partials (Eq. (Lag11) carries no mixed partials)."""
+    rng = np.random.default_rng(4)
+    n = (5, 4, 4)
+    g = oracle.Grid(n, (0.0, -1.0, 0.0), (2.0, 1.0, 1.5))
+    p = [0.4, -0.3, 0.2, 0.6]
+    dt, q = 0.01, 3
+    u = rng.uniform(0, 1, g.shape)  # (nz, ny, nx)
+    h = [g.h(m) for m in range(3)]
+    du = [_slopes_indep(u, h[0], axis=2), _slopes_indep(u, h[1], axis=1),
+          _slopes_indep(u, h[2], axis=0)]
+    a, w = oracle.gauss_hermite(q)
+    ax = [g.axis(m) for m in range(3)]
+    want = np.zeros(g.shape)
+    for l in range(n[2]):
+        for k in range(n[1]):
+            for i in range(n[0]):
+                x = (ax[0][i], ax[1][k], ax[2][l])
+                acc = 0.0
+                for r in range(q):
+                    for qq in range(q):
+                        for pp in range(q):
+                            z = [x[m] + p[m] * dt + p[3] * math.sqrt(2 * dt) * a[(pp, qq, r)[m]]
+                                 for m in range(3)]
+                            wt = w[pp] * w[qq] * w[r]
+                            if not all(g.lo[m] <= z[m] <= g.hi[m] for m in range(3)):
+                                acc += wt
+                                continue
+                            val = 0.0
+                            for ll in range(n[2]):
+                                vz, dz = _cardinal(ax[2][ll], h[2], z[2])
+                                if vz == 0.0 and dz == 0.0:
+                                    continue
+                                for kk in range(n[1]):
+                                    vy, dy = _cardinal(ax[1][kk], h[1], z[1])
+                                    for ii in range(n[0]):
+                                        vx, dx = _cardinal(ax[0][ii], h[0], z[0])
+                                        c = (ll, kk, ii)
+                                        val += (vx * vy * vz * u[c] + dx * vy * vz * du[0][c]
+                                                + vx * dy * vz * du[1][c]
+                                                + vx * vy * dz * du[2][c])
+                            acc += wt * val
+                want[l, k, i] = acc
+    want[0], want[-1] = 1.0, 1.0
+    want[:, 0], want[:, -1] = 1.0, 1.0
+    want[:, :, 0], want[:, :, -1] = 1.0, 1.0
+    got = oracle.march(g, oracle.CONST_DRIFT, p, q, dt, 1, 0, u)
     np.testing.assert_allclose(got, want, atol=1e-14)
 
 
