@@ -126,8 +126,7 @@ def test_3d_horizons_and_snapshots(fk, oracle):
 def test_3d_workload_sampled_step(fk, oracle):
     """The 129^3 benchmark workload (FP32, 4^3 points): one step from a random
     field at sampled nodes against the oracle's step there; the whole march
-    stays in [0, 1] and is symmetric where the problem is (none of the drift
-    components vanishes, so only bounds and the device error word apply)."""
+    stays in [0, 1]."""
     import torch
     w = fk_inputs.workload("drift3d_129")
     shape = tuple(reversed(w["n"]))
@@ -148,7 +147,9 @@ def test_3d_workload_sampled_step(fk, oracle):
     assert plan.last_device_error() == 0
     plan.close()
     assert full.min() >= -1e-6 and full.max() <= 1 + 1e-6
-    assert 0.05 < full[64, 64, 64] < 0.95
+    # the centre is ~3 standard deviations from every face: 1 - prod of the
+    # 1D survivals there is 0.037
+    assert 0.02 < full[64, 64, 64] < 0.06
 
 
 def test_3d_full_march_vs_product_form(fk, oracle):
