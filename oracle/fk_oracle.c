@@ -28,6 +28,12 @@
  * the n - 1 distinct nodes, slopes and shifted points wrap around, and no
  * point exits through that axis.
  *
+ * The runaway-electron model of Sec. 4.3 counts only exits through
+ * p = p_max (value 1).  Its other faces follow the face rules of
+ * face_rule() below: an exit through p = p_min or r = 1 takes the value 0,
+ * and the faces xi = +-1 and r = 0, which the process does not cross,
+ * mirror a shifted point back into the box.
+ *
  * Readings where the paper is silent or garbled are documented next to the
  * code that takes them.  Coefficient time is the left end t_n = n dt
  * (Eq. (ref-X)).  Every floating-point value is IEEE binary64; the library
@@ -46,6 +52,7 @@
 #define FKO_CONST_DRIFT 0
 #define FKO_CELLULAR_FLOW 1
 #define FKO_PAPER_CELLULAR 2
+#define FKO_RUNAWAY 3
 
 static const double FKO_PI = 3.14159265358979323846264338327950288;
 
@@ -103,11 +110,38 @@ static void grid_canonical(const fko_grid *g, int *idx) {
     if (axis_periodic(g, m) && idx[m] == g->n[m] - 1) idx[m] = 0;
 }
 
-/* Nodes on a face of a non-periodic axis are boundary nodes. */
-static int grid_is_boundary(const fko_grid *g, const int *idx) {
-  for (int m = 0; m < g->dim; ++m)
-    if (!axis_periodic(g, m) && (idx[m] == 0 || idx[m] == g->n[m] - 1)) return 1;
-  return 0;
+/* What a face does to the process.  Every face of a non-periodic axis is
+ * absorbing with exit value 1 (Eq. (e24)), except in the runaway-electron
+ * model of Sec. 4.3, where only p = p_max (the upper face of axis 0) counts
+ * as runaway: p = p_min and the wall r = 1 absorb with value 0, and the
+ * faces xi = -1, xi = 1 and r = 0, which the process does not cross (the xi
+ * diffusion vanishes there and the drift points inwards; r = 0 is the
+ * axis), reflect. */
+enum { FACE_EXIT0 = 0, FACE_EXIT1 = 1, FACE_REFLECT = 2 };
+static int face_rule(int family, int m, int upper) {
+  if (family != FKO_RUNAWAY) return FACE_EXIT1;
+  if (m == 0) return upper ? FACE_EXIT1 : FACE_EXIT0;
+  if (m == 1) return FACE_REFLECT;
+  return upper ? FACE_EXIT0 : FACE_REFLECT;
+}
+
+/* Nodes on an absorbing face are boundary nodes; they hold the face's exit
+ * value, 1 when any of their faces has value 1.  Returns -1 for a node the
+ * scheme updates. */
+static double boundary_value(const fko_grid *g, int family, const int *idx) {
+  int on = 0, one = 0;
+  for (int m = 0; m < g->dim; ++m) {
+    if (axis_periodic(g, m)) continue;
+    for (int up = 0; up < 2; ++up) {
+      if (idx[m] != (up ? g->n[m] - 1 : 0)) continue;
+      int rule = face_rule(family, m, up);
+      if (rule == FACE_REFLECT) continue;
+      on = 1;
+      if (rule == FACE_EXIT1) one = 1;
+    }
+  }
+  if (!on) return -1.0;
+  return one ? 1.0 : 0.0;
 }
 
 static int grid_check(const fko_grid *g) {
@@ -129,6 +163,53 @@ static int grid_check(const fko_grid *g) {
 }
 
 /* -------------------------------------------------------- coefficients -- */
+
+/*
+ * FKO_RUNAWAY (d = 3), x = (p, xi, r) (momentum, cosine of the pitch angle,
+ * minor radius), parameters
+ *   p = (E, tau, Z, delta, nu_ee, v_T, r_D, W, Delta_p, V_0, D_0):
+ * Eq. (ex32d) of Sec. 4.3 with the collision functions
+ *   C_A = nu v_T^2 psi(y) / y,
+ *   C_B = (1/2) nu v_T^2 (1/y) [Z + phi(y) - psi(y) + y^2 delta^4 / 2],
+ *   C_F = 2 nu v_T psi(y),
+ *   phi = erf, psi(y) = [phi(y) - y phi'(y)] / (2 y^2),
+ *   y = p / gamma, gamma = sqrt(1 + (delta p)^2),
+ * and V(r) = V_0 1{r > r_D}, D(r, p) = (D_0/2)(1 + tanh((r - r_D)/W))
+ * exp(-(p/Delta_p)^2).  The drift of p carries the derivative
+ * (1/p^2) d/dp (p^2 C_A), written out by the chain rule:
+ *   d/dp [p^2 psi(y) / y] = 2 p psi / y + p^2 (psi'/y - psi/y^2) dy/dp,
+ *   dy/dp = 1/gamma^3,  psi'(y) = phi'(y) - 2 psi(y) / y.
+ * sigma is diagonal: sqrt(2 C_A), sqrt(2 C_B) sqrt(1 - xi^2) / p,
+ * sqrt(2 D).  The coefficients do not depend on t.
+ */
+static void runaway_coefficients(const double *p, const double *x, double *b, double *sig) {
+  const double E = p[0], tau = p[1], Z = p[2], delta = p[3], nu = p[4], vT = p[5];
+  const double rD = p[6], Wr = p[7], Dp = p[8], V0 = p[9], D0 = p[10];
+  const double mom = x[0], xi = x[1], r = x[2];
+  const double gam = sqrt(1.0 + (delta * mom) * (delta * mom));
+  const double y = mom / gam;
+  const double phi = erf(y);
+  const double dphi = 2.0 / sqrt(FKO_PI) * exp(-y * y);
+  const double psi = (phi - y * dphi) / (2.0 * y * y);
+  const double dpsi = dphi - 2.0 * psi / y;
+  const double CA = nu * vT * vT * psi / y;
+  const double CB = 0.5 * nu * vT * vT / y * (Z + phi - psi + 0.5 * y * y * pow(delta, 4.0));
+  const double CF = 2.0 * nu * vT * psi;
+  const double dy = 1.0 / (gam * gam * gam);
+  const double df = 2.0 * mom * psi / y + mom * mom * (dpsi / y - psi / (y * y)) * dy;
+  const double dp2CA = nu * vT * vT * df; /* d/dp (p^2 C_A) */
+  const double one_m = 1.0 - xi * xi;
+  b[0] = E * xi - gam * mom / tau * one_m - CF + dp2CA / (mom * mom);
+  b[1] = E * one_m / mom - xi * one_m / (tau * gam) - 2.0 * xi * CB / (mom * mom);
+  const double th = tanh((r - rD) / Wr);
+  const double ep = exp(-(mom / Dp) * (mom / Dp));
+  const double D = 0.5 * D0 * (1.0 + th) * ep;
+  const double dD = 0.5 * D0 * (1.0 - th * th) / Wr * ep;
+  b[2] = (r > rD ? V0 : 0.0) + dD;
+  sig[0] = sqrt(2.0 * CA);
+  sig[4] = sqrt(2.0 * CB) * sqrt(one_m) / mom;
+  sig[8] = sqrt(2.0 * D);
+}
 
 /*
  * Drift b(t,x) and diffusion matrix sigma(t,x) (d x d, row-major) of the
@@ -156,6 +237,10 @@ void fko_coefficients(int family, const double *p, int dim, double t,
       b[m] = p[m];
       sig[m * dim + m] = p[3];
     }
+    return;
+  }
+  if (family == FKO_RUNAWAY) {
+    runaway_coefficients(p, x, b, sig);
     return;
   }
   if (family == FKO_PAPER_CELLULAR) {
@@ -188,6 +273,7 @@ static int family_check(int family, int dim, const double *p) {
   if (family == FKO_CONST_DRIFT) return !(p[3] >= 0.0);
   if (family == FKO_CELLULAR_FLOW) return dim != 2 || !(p[3] >= 0.0);
   if (family == FKO_PAPER_CELLULAR) return dim != 2;
+  if (family == FKO_RUNAWAY) return dim != 3;
   return 1;
 }
 
@@ -348,7 +434,7 @@ static double node_update(const fko_grid *g, int family, const double *p,
       wq *= w[q[m]];
     }
     double z[FKO_MAXDIM];
-    int outside = 0;
+    int outside = 0, exit_one = 0;
     for (int m = 0; m < d; ++m) {
       double noise = 0.0;
       for (int k = 0; k < d; ++k) noise += sig[m * d + k] * a[q[k]];
@@ -360,10 +446,20 @@ static double node_update(const fko_grid *g, int family, const double *p,
         if (r < 0.0) r += L;
         z[m] = g->lo[m] + r;
       } else if (z[m] < g->lo[m] || z[m] > g->hi[m]) {
-        outside = 1;
+        int up = z[m] > g->hi[m];
+        int rule = face_rule(family, m, up);
+        if (rule == FACE_REFLECT) {
+          /* mirror image in the face (once; the step is far shorter than the box) */
+          z[m] = up ? 2.0 * g->hi[m] - z[m] : 2.0 * g->lo[m] - z[m];
+        } else {
+          outside = 1;
+          if (rule == FACE_EXIT1) exit_one = 1;
+        }
       }
     }
-    double val = outside ? 1.0 : interpolate(g, u, du, z);
+    /* an exit takes its face's value; value 1 wins when a point leaves
+     * through several faces at once */
+    double val = outside ? (exit_one ? 1.0 : 0.0) : interpolate(g, u, du, z);
     sum += wq * val;
   }
   return sum;
@@ -402,8 +498,9 @@ int fko_march(const fko_grid *g, int family, const double *p, int nq,
       int idx[FKO_MAXDIM];
       grid_unflatten(g, j, idx);
       grid_canonical(g, idx);
-      if (boundary_rule && grid_is_boundary(g, idx))
-        nxt[j] = 1.0;
+      double bv = boundary_rule ? boundary_value(g, family, idx) : -1.0;
+      if (bv >= 0.0)
+        nxt[j] = bv;
       else
         nxt[j] = node_update(g, family, p, nq, a, w, dt, tn, cur, du, idx);
     }
@@ -436,8 +533,9 @@ int fko_step_nodes(const fko_grid *g, int family, const double *p, int nq,
     int idx[FKO_MAXDIM];
     grid_unflatten(g, nodes[k], idx);
     grid_canonical(g, idx);
-    if (boundary_rule && grid_is_boundary(g, idx))
-      out[k] = 1.0;
+    double bv = boundary_rule ? boundary_value(g, family, idx) : -1.0;
+    if (bv >= 0.0)
+      out[k] = bv;
     else
       out[k] = node_update(g, family, p, nq, a, w, dt, tn, u_next, du, idx);
   }
@@ -578,7 +676,8 @@ int fko_adjoint(const fko_grid *g, int family, const double *p, int nq,
                 double *dtheta, double *du_terminal) {
   if (grid_check(g) || family_check(family, g->dim, p)) return 1;
   if (nq < 1 || !(dt > 0.0) || n_steps < 1) return 1;
-  if (g->periodic || family == FKO_PAPER_CELLULAR) return 3; /* not differentiated */
+  if (g->periodic || family == FKO_PAPER_CELLULAR || family == FKO_RUNAWAY)
+    return 3; /* not differentiated */
   for (int m = 0; m < g->dim; ++m)
     if (g->axis[m]) return 3; /* uniform meshes only */
   int d = g->dim;
@@ -612,7 +711,7 @@ int fko_adjoint(const fko_grid *g, int family, const double *p, int nq,
     for (int64_t j = 0; j < J; ++j) {
       int idx[FKO_MAXDIM];
       grid_unflatten(g, j, idx);
-      if (grid_is_boundary(g, idx) || lam[j] == 0.0) continue;
+      if (boundary_value(g, family, idx) >= 0.0 || lam[j] == 0.0) continue;
       double x[FKO_MAXDIM], b[FKO_MAXDIM], sig[FKO_MAXDIM * FKO_MAXDIM];
       double db[4][FKO_MAXDIM], ds[4];
       for (int m = 0; m < d; ++m) x[m] = grid_x(g, m, idx[m]);

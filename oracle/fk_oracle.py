@@ -44,6 +44,9 @@ _LIB = os.path.join(_HERE, "libfk_oracle.so")
 CONST_DRIFT = 0
 CELLULAR_FLOW = 1
 PAPER_CELLULAR = 2   # the paper's own example of Sec. 4.2: p = (Pe, n, eps, omega), sigma = I
+RUNAWAY = 3          # the runaway-electron model of Sec. 4.3 (d = 3, x = (p, xi, r)):
+#                      params (E, tau, Z, delta, nu_ee, v_T, r_D, W, Delta_p, V_0, D_0)
+RUNAWAY_PARAMS = (0.3, 1e5, 1.0, 0.042, 1.0, 1.0, 0.7, 1e-2, 20.0, 0.003, 1e-4)  # Sec. 4.3
 
 
 def build(force: bool = False) -> str:
@@ -160,7 +163,7 @@ class Grid:
 
 
 def _params(p: Sequence[float]) -> np.ndarray:
-    out = np.zeros(8, dtype=np.float64)
+    out = np.zeros(16, dtype=np.float64)
     out[: len(p)] = p
     return out
 
@@ -186,10 +189,14 @@ def gauss_hermite(q: int):
 
 # ------------------------------------------------------------- fields ----
 
-def terminal_indicator(grid: Grid) -> np.ndarray:
+def terminal_indicator(grid: Grid, family: int = CONST_DRIFT) -> np.ndarray:
     """chi of Sec. 3.2: 0 at interior nodes, 1 at boundary nodes (the faces
-    of the non-periodic axes)."""
+    of the non-periodic axes).  The runaway model counts only p = p_max
+    (the upper face of axis 0): chi is 1 there and 0 elsewhere."""
     chi = np.zeros(grid.shape, dtype=np.float64)
+    if family == RUNAWAY:
+        chi[..., -1] = 1.0
+        return chi
     for ax in range(chi.ndim):
         if (grid.periodic >> (chi.ndim - 1 - ax)) & 1:
             continue
@@ -240,7 +247,7 @@ def march(grid: Grid, family: int, params, q: int, dt: float, n_from: int,
     lib = _load()
     a, w = gauss_hermite(q)
     if u_in is None:
-        u_in = terminal_indicator(grid)
+        u_in = terminal_indicator(grid, family)
     uu = np.ascontiguousarray(u_in, dtype=np.float64).reshape(-1)
     if uu.size != grid.size:
         raise ValueError("u_in has the wrong size")
