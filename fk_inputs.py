@@ -36,6 +36,10 @@ Workloads (the paper has no datasets; every input is defined by formulas):
                               towards every face (non-uniform axes).
 * ``horizons_1025x513``    -- every horizon t_k = k dt, k = 1..200, of the
                               cellular flow (Algorithm 1).
+* ``runaway_97x65x41``     -- the runaway-electron model of Sec. 4.3 at the
+                              paper's parameters on (2, 50) x (-1, 1) x
+                              (0, 1), 97 x 65 x 41 nodes, 4 x 4 x 4 points,
+                              dt = 5e-3, 4800 steps (T = 24), FP32.
 * ``drift3d_129``          -- d = 3: Brownian motion with drift
                               b = (0.3, -0.2, 0.1), sigma = 0.5 in (-1, 1)^3,
                               129^3 nodes, 4 x 4 x 4 points, dt = 1e-3,
@@ -85,6 +89,14 @@ WORKLOADS = {
     "drift3d_129": dict(n=(129, 129, 129), lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0),
                         family="const_drift", params=(0.3, -0.2, 0.1, 0.5), q=4, dt=1e-3,
                         n_steps=500, precision="fp32"),
+    # the runaway-electron model of Sec. 4.3 at the paper's parameters,
+    # p in (2, 50), xi in (-1, 1), r in (0, 1), uniform mesh, T = 24 (the
+    # first time of the paper's figures)
+    "runaway_97x65x41": dict(n=(97, 65, 41), lo=(2.0, -1.0, 0.0), hi=(50.0, 1.0, 1.0),
+                             family="runaway",
+                             params=(0.3, 1e5, 1.0, 0.042, 1.0, 1.0, 0.7, 1e-2, 20.0, 0.003,
+                                     1e-4),
+                             q=4, dt=5e-3, n_steps=4800, precision="fp32"),
     # every horizon t_k = k dt, k = 1..200, of the time-dependent flow (Algorithm 1)
     "horizons_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
                               family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),

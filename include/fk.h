@@ -76,8 +76,25 @@ typedef enum fk_path { FK_PATH_MATRIX_FREE = 0, FK_PATH_CSR = 1 } fk_path;
  *                       v_2 =  n sin(pi x_2)[cos(n x_1) - eps f sin(n x_1)],
  *                     f = cos(omega t), sigma = I.  Usually with the region
  *                     FK_PERIODIC_X on [-pi, pi] x [0, 1].  Matrix-free
- *                     path only; fk_adjoint returns FK_ERR_UNSUPPORTED. */
-enum { FK_CONST_DRIFT = 0, FK_CELLULAR_FLOW = 1, FK_PAPER_CELLULAR = 2 };
+ *                     path only; fk_adjoint returns FK_ERR_UNSUPPORTED.
+ *  FK_RUNAWAY_3D      d = 3, x = (p, xi, r): the runaway-electron model of
+ *                     Sec. 4.3, Eq. (ex32d), with
+ *                     p = {E, tau, Z, delta, nu_ee, v_T, r_D, W, Delta_p,
+ *                          V_0, D_0} (the paper's values: 0.3, 1e5, 1,
+ *                     0.042, 1, 1, 0.7, 1e-2, 20, 0.003, 1e-4).  The box is
+ *                     [p_min, p_max] x [xi_lo, xi_hi] x [r_lo, r_hi] with
+ *                     p_min > 0, -1 <= xi_lo < xi_hi <= 1, r_lo >= 0.  The
+ *                     faces act as follows (the region must be
+ *                     FK_ALL_FACES_ABSORBING; this family fixes them): an
+ *                     exit through p = p_max takes 1 (runaway), through
+ *                     p = p_min or r = r_hi (the wall) 0, and the faces of
+ *                     xi and r = r_lo mirror a shifted point back into the
+ *                     box; nodes on those faces are updated, nodes on the
+ *                     absorbing faces hold their value (1 on p = p_max).
+ *                     The terminal indicator is 1 on p = p_max only.
+ *                     Uniform mesh, matrix-free; fk_adjoint, batching and
+ *                     the static entry return FK_ERR_UNSUPPORTED. */
+enum { FK_CONST_DRIFT = 0, FK_CELLULAR_FLOW = 1, FK_PAPER_CELLULAR = 2, FK_RUNAWAY_3D = 3 };
 
 /* Cartesian mesh S (Sec. 3.1.2): n[m] >= 3 nodes on [lo[m], hi[m]] for
  * m < dim; entries for m >= dim are ignored.  axis[m] = NULL gives the
@@ -115,7 +132,7 @@ typedef struct fk_region {
 
 typedef struct fk_coeffs {
   int family;
-  double p[8];
+  double p[16];   /* family parameters; unused entries are ignored but must be finite */
 } fk_coeffs;
 
 typedef struct fk_plan fk_plan;
@@ -165,11 +182,14 @@ typedef struct fk_plan_info {
  *   path       FK_PATH_CSR needs a family whose coefficients do not depend
  *              on t (FK_CONST_DRIFT, or FK_CELLULAR_FLOW with eps = 0),
  *              else FK_ERR_UNSUPPORTED.
- *   dim = 3    FK_CONST_DRIFT on a uniform mesh (axis[] NULL), every face
- *              absorbing, FK_PATH_MATRIX_FREE, n[m] <= 65535; the points
- *              of one axis must span fewer than 6 cells (sigma sqrt(2 dt)
- *              (a_{q-1} - a_0) / h_m < 6) and n[m] must be at least the
- *              window width floor(span) + 3; else FK_ERR_UNSUPPORTED.
+ *   dim = 3    FK_CONST_DRIFT or FK_RUNAWAY_3D on a uniform mesh (axis[]
+ *              NULL), FK_ALL_FACES_ABSORBING, FK_PATH_MATRIX_FREE,
+ *              n[m] <= 65535.  The node window W must be at most 8 and at
+ *              most every n[m]: W = floor(span) + 3 with span the largest
+ *              sigma_m sqrt(2 dt) (a_{q-1} - a_0) / h_m over the nodes (for
+ *              the runaway model also at least floor(|b_m| dt / h_m +
+ *              span / 2) + 2, so that mirrored points stay in the window);
+ *              else FK_ERR_UNSUPPORTED.
  *              fk_solve_batched, fk_adjoint and fk_solve_static take
  *              dim = 2 plans only (FK_ERR_UNSUPPORTED).
  * The plan allocates its own device workspace on the current CUDA device

@@ -17,7 +17,7 @@ STATUS = {0: "FK_OK", 1: "FK_ERR_INVALID_ARG", 2: "FK_ERR_UNSUPPORTED", 3: "FK_E
 
 FK_FP32, FK_FP64 = 0, 1
 FK_PATH_MATRIX_FREE, FK_PATH_CSR = 0, 1
-FK_CONST_DRIFT, FK_CELLULAR_FLOW, FK_PAPER_CELLULAR = 0, 1, 2
+FK_CONST_DRIFT, FK_CELLULAR_FLOW, FK_PAPER_CELLULAR, FK_RUNAWAY_3D = 0, 1, 2, 3
 FK_ALL_FACES_ABSORBING = 0x3F
 FK_PERIODIC_X = 0x3C
 
@@ -44,7 +44,7 @@ class Region(ctypes.Structure):
 
 
 class Coeffs(ctypes.Structure):
-    _fields_ = [("family", ctypes.c_int), ("p", ctypes.c_double * 8)]
+    _fields_ = [("family", ctypes.c_int), ("p", ctypes.c_double * 16)]
 
 
 class PlanInfo(ctypes.Structure):

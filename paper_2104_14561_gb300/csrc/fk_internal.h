@@ -127,10 +127,28 @@ struct Step3D {
   T gs[3];           // sigma sqrt(2 dt) / h per axis
   T ga[FK_MAXQ_2D], gw[FK_MAXQ_2D];  // abscissae (ascending) and weights
   unsigned* err;
+  // the runaway-electron family (FK_RUNAWAY_3D): per-node coefficients from
+  // the node coordinates x_m = lo[m] + i h[m] (FP64, as the mesh is defined)
+  int family;
+  double lo[3], h[3];
+  double rp[11];     // E, tau, Z, delta, nu_ee, v_T, r_D, W, Delta_p, V_0, D_0
+  T dt, sq2dt;       // dt and sqrt(2 dt)
+  // face rules per axis (lower, upper): 0 exit value 0, 1 exit value 1,
+  // 2 reflect; and the nodes the scheme updates: first[m] .. first[m] +
+  // count[m] - 1 (the nodes of reflecting faces included)
+  int face[3][2];
+  int first[3], count[3];
 };
 template <typename T>
 cudaError_t fk_launch_step3d(const Step3D<T>& a, cudaStream_t s);
+// The terminal indicator of a 3D plan: 1 on the faces whose exit value is
+// 1, 0 elsewhere.
+template <typename T>
+cudaError_t fk_launch_chi3d(const Step3D<T>& a, T* u, cudaStream_t s);
 #define FK_MAXW_3D 8
+#define FK_FACE_EXIT0 0
+#define FK_FACE_EXIT1 1
+#define FK_FACE_REFLECT 2
 
 // Shared memory bytes of one 2D step CTA (nu: plus the staged node
 // coordinates of a non-uniform mesh).

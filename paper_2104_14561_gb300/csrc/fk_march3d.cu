@@ -30,6 +30,16 @@
 //    consecutive x-nodes read overlapping, contiguous windows).
 // Positions are taken relative to the node in cells: point p of axis m is
 // at i_m + rel_p with rel_p = b_m dt / h_m + sigma_m sqrt(2 dt) a_p / h_m.
+//
+// The runaway-electron model of Sec. 4.3 (FK_RUNAWAY_3D, x = (p, xi, r))
+// takes its drift and diagonal sigma per node (Eq. (ex32d)) and its own face
+// rules: an exit through p = p_max takes 1, through p = p_min or the wall
+// r = r_hi 0, and a point beyond a face of xi or r = r_lo is mirrored back
+// into the box (those faces' nodes are updated like interior ones).  The
+// mirror keeps the sum separable (it acts on one coordinate), and the two
+// kinds of exit split each axis's dropped weight into E1_m and E0_m: a
+// point takes 1 when any coordinate leaves through a value-1 face, so
+//   u^n = sum_inside + 1 - prod_m (1 - E1_m).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -47,6 +57,26 @@ template <>
 __device__ __forceinline__ float floor_t<float>(float x) { return floorf(x); }
 template <>
 __device__ __forceinline__ double floor_t<double>(double x) { return floor(x); }
+
+// The value a node on an absorbing face holds (Eq. (e3)): 1 when one of
+// its faces has exit value 1, else 0; -1 for a node the scheme updates.
+template <typename T>
+__device__ __forceinline__ T held_value(const Step3D<T>& a, int i, int j, int k) {
+  const int at[3] = {i, j, k}, n3[3] = {a.nx, a.ny, a.nz};
+  bool on = false, one = false;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+#pragma unroll
+    for (int up = 0; up < 2; ++up) {
+      const int rule = a.face[m][up];
+      if (at[m] == (up ? n3[m] - 1 : 0) && rule != FK_FACE_REFLECT) {
+        on = true;
+        one = one || rule == FK_FACE_EXIT1;
+      }
+    }
+  }
+  return on ? (one ? T(1) : T(0)) : T(-1);
+}
 
 // Records and boundary values of one field.
 template <typename T>
@@ -70,37 +100,69 @@ __global__ void __launch_bounds__(kRecThreads) k_rec3d(const Step3D<T> a) {
   r.z = slope(j, a.ny, sy);
   r.w = slope(k, a.nz, sz);
   a.rec[node] = r;
-  if (i == 0 || i == a.nx - 1 || j == 0 || j == a.ny - 1 || k == 0 || k == a.nz - 1) {
-    a.u_out[node] = T(1);
-    if (a.snap) a.snap[node] = T(1);
+  const T held = held_value(a, i, j, k);
+  if (held >= T(0)) {
+    a.u_out[node] = held;
+    if (a.snap) a.snap[node] = held;
   }
 }
 
+// Terminal indicator: 1 on the faces whose exit value is 1, 0 elsewhere.
+template <typename T>
+__global__ void __launch_bounds__(kRecThreads) k_chi3d(const Step3D<T> a, T* u) {
+  const int i = blockIdx.x * kRecThreads + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  if (i >= a.nx) return;
+  const int at[3] = {i, j, k}, n3[3] = {a.nx, a.ny, a.nz};
+  bool one = false;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    one = one || (at[m] == 0 && a.face[m][0] == FK_FACE_EXIT1) ||
+          (at[m] == n3[m] - 1 && a.face[m][1] == FK_FACE_EXIT1);
+  }
+  u[((int64_t)k * a.ny + j) * a.nx + i] = one ? T(1) : T(0);
+}
+
 // The 1D weights of one axis over its window [org, org + W): node i of n,
-// points at i + sh + gs a_q.  Returns the exit weight E; sets bad when an
-// inside point's cell falls outside the window (cannot happen for the W the
-// plan chooses; the check keeps every read in bounds regardless).
-template <typename T, int W>
-__device__ __forceinline__ T axis_weights(const Step3D<T>& a, int i, int n, T sh, T gs,
-                                          T (&V)[W], T (&D)[W], int& org, unsigned& bad) {
+// points at i + sh + gs a_q.  Returns the weight of the points that exit
+// with value 1 (E1) and with value 0 (E0, the runaway faces only); with RE
+// a point beyond a reflecting face is mirrored into the box first.  Sets
+// bad when an inside point's cell falls outside the window (the plan's W
+// rules this out; the check keeps every read in bounds regardless).
+template <typename T, int W, bool RE>
+__device__ __forceinline__ void axis_weights(const Step3D<T>& a, int m, int i, int n, T sh, T gs,
+                                             T (&V)[W], T (&D)[W], T& E1, T& E0, int& org,
+                                             unsigned& bad) {
 #pragma unroll
   for (int t = 0; t < W; ++t) {
     V[t] = T(0);
     D[t] = T(0);
   }
-  T E = T(0);
+  E1 = T(0);
+  E0 = T(0);
   const T lo = T(-i), hi = T(n - 1 - i);  // the box, relative to the node
   // the abscissae ascend and gs >= 0: point 0 is the leftmost
   int o = i + (int)floor_t(sh + gs * a.ga[0]);
   o = o < 0 ? 0 : o;
   o = o > n - W ? n - W : o;
   org = o;
+  int rlo = FK_FACE_EXIT1, rhi = FK_FACE_EXIT1;
+  if constexpr (RE) {
+    rlo = a.face[m][0];
+    rhi = a.face[m][1];
+  }
 #pragma unroll
   for (int q = 0; q < FK_MAXQ_2D; ++q) {
     if (q < a.q) {
-      const T rel = sh + gs * a.ga[q];
+      T rel = sh + gs * a.ga[q];
       const T wq = a.gw[q];
-      const bool in = !(rel < lo || rel > hi);
+      if constexpr (RE) {
+        // mirror image in a reflecting face
+        if (rel < lo && rlo == FK_FACE_REFLECT) rel = T(2) * lo - rel;
+        if (rel > hi && rhi == FK_FACE_REFLECT) rel = T(2) * hi - rel;
+      }
+      const bool below = rel < lo, above = rel > hi;
+      const bool in = !(below || above);
       const T fl = floor_t(rel);
       int c = i + (int)fl;
       T s = rel - fl;
@@ -111,7 +173,9 @@ __device__ __forceinline__ T axis_weights(const Step3D<T>& a, int i, int n, T sh
       const int off = c - o;
       const bool ok = off >= 0 && off <= W - 2;
       if (in && !ok) bad = 1u;
-      E += in ? T(0) : wq;
+      const int rule = below ? rlo : rhi;
+      E1 += (!in && rule == FK_FACE_EXIT1) ? wq : T(0);
+      if constexpr (RE) E0 += (!in && rule == FK_FACE_EXIT0) ? wq : T(0);
       const T wi = (in && ok) ? wq : T(0);
       // cubic Hermite basis on a unit cell (Sec. 3.1.3)
       const T s2 = s * s, r1 = T(1) - s;
@@ -124,31 +188,115 @@ __device__ __forceinline__ T axis_weights(const Step3D<T>& a, int i, int n, T sh
       }
     }
   }
-  return E;
 }
 
-template <typename T, int W>
+// Entry t of a register array indexed by a runtime value (a select per
+// entry keeps the array in registers).
+template <int W, typename T>
+__device__ __forceinline__ T pick(const T (&v)[W], int t) {
+  T r = v[0];
+#pragma unroll
+  for (int e = 1; e < W; ++e) r = (e == t) ? v[e] : r;
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T erf_t(T x);
+template <>
+__device__ __forceinline__ float erf_t<float>(float x) { return erff(x); }
+template <>
+__device__ __forceinline__ double erf_t<double>(double x) { return erf(x); }
+
+// Drift and diagonal sigma of the runaway-electron model at node (i, j, k)
+// (Eq. (ex32d) of Sec. 4.3), returned as the point shift sh = b dt / h and
+// scale gs = sigma sqrt(2 dt) / h per axis, in cells.  Collision functions
+// C_A = nu v_T^2 psi(y)/y, C_B = (nu v_T^2 / 2y)[Z + phi(y) - psi(y) +
+// y^2 delta^4 / 2], C_F = 2 nu v_T psi(y) with phi = erf, psi(y) =
+// (phi - y phi') / (2 y^2), y = p / gamma, gamma = sqrt(1 + (delta p)^2);
+// the p drift carries (1/p^2) d/dp (p^2 C_A) by the chain rule (dy/dp =
+// 1/gamma^3, psi' = phi' - 2 psi / y).  The node coordinates are formed in
+// FP64 without contraction, and the step V(r) = V_0 1{r > r_D} is decided
+// there; the rest runs in T.
+template <typename T>
+__device__ __forceinline__ void runaway_coef(const Step3D<T>& a, int i, int j, int k, T (&sh)[3],
+                                             T (&gs)[3]) {
+  const double xp = __dadd_rn(a.lo[0], __dmul_rn((double)i, a.h[0]));
+  const double xx = __dadd_rn(a.lo[1], __dmul_rn((double)j, a.h[1]));
+  const double xr = __dadd_rn(a.lo[2], __dmul_rn((double)k, a.h[2]));
+  const bool beyond = xr > a.rp[6];
+  const T mom = (T)xp, xi = (T)xx, r = (T)xr;
+  const T E = (T)a.rp[0], tau = (T)a.rp[1], Z = (T)a.rp[2], delta = (T)a.rp[3];
+  const T nu = (T)a.rp[4], vT = (T)a.rp[5], rD = (T)a.rp[6], Wr = (T)a.rp[7];
+  const T Dp = (T)a.rp[8], V0 = (T)a.rp[9], D0 = (T)a.rp[10];
+  const T dm = delta * mom;
+  const T gam = sqrt(T(1) + dm * dm);
+  const T y = mom / gam;
+  const T phi = erf_t(y);
+  const T dphi = T(1.1283791670955126) * exp(-y * y);  // 2 / sqrt(pi) exp(-y^2)
+  const T psi = (phi - y * dphi) / (T(2) * y * y);
+  const T dpsi = dphi - T(2) * psi / y;
+  const T nv2 = nu * vT * vT;
+  const T CA = nv2 * psi / y;
+  const T d2 = delta * delta;
+  const T CB = T(0.5) * nv2 / y * (Z + phi - psi + T(0.5) * y * y * (d2 * d2));
+  const T CF = T(2) * nu * vT * psi;
+  const T dy = T(1) / (gam * gam * gam);
+  const T df = T(2) * mom * psi / y + mom * mom * (dpsi / y - psi / (y * y)) * dy;
+  const T om = T(1) - xi * xi;
+  const T b0 = E * xi - gam * mom / tau * om - CF + nv2 * df / (mom * mom);
+  const T b1 = E * om / mom - xi * om / (tau * gam) - T(2) * xi * CB / (mom * mom);
+  const T th = tanh((r - rD) / Wr);
+  const T q = mom / Dp;
+  const T ep = exp(-q * q);
+  const T Dr = T(0.5) * D0 * (T(1) + th) * ep;
+  const T b2 = (beyond ? V0 : T(0)) + T(0.5) * D0 * (T(1) - th * th) / Wr * ep;
+  const T s0 = sqrt(T(2) * CA);
+  const T s1 = sqrt(T(2) * CB) * sqrt(om > T(0) ? om : T(0)) / mom;
+  const T s2 = sqrt(T(2) * Dr);
+  const T b[3] = {b0, b1, b2}, sg[3] = {s0, s1, s2};
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    sh[m] = b[m] * a.dt / (T)a.h[m];
+    gs[m] = sg[m] * a.sq2dt / (T)a.h[m];
+  }
+}
+
+template <typename T, int W, bool RE>
 __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
-  const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = 1 + blockIdx.y, k = 1 + blockIdx.z;
-  if (i > a.nx - 2) return;
+  const int i = a.first[0] + blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = a.first[1] + blockIdx.y, k = a.first[2] + blockIdx.z;
+  if (i >= a.first[0] + a.count[0]) return;
   const int64_t sy = a.nx, sz = (int64_t)a.nx * a.ny;
   const int64_t node = (int64_t)k * sz + (int64_t)j * sy + i;
 
-  // 1D weights per axis (constant drift: shift and scale are plan constants)
+  // shift and scale of the points per axis, in cells: plan constants for
+  // the constant drift, per node for the runaway model
+  T sh[3], gs[3];
+  if constexpr (RE) {
+    runaway_coef(a, i, j, k, sh, gs);
+  } else {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      sh[m] = a.cd[m];
+      gs[m] = a.gs[m];
+    }
+  }
+
+  // 1D weights per axis
   T Vx[W], Dx[W], Vy[W], Dy[W], Vz[W], Dz[W];
+  T E1x, E0x, E1y, E0y, E1z, E0z;
   int ox, oy, oz;
   unsigned bad = 0;
-  const T Ex = axis_weights<T, W>(a, i, a.nx, a.cd[0], a.gs[0], Vx, Dx, ox, bad);
-  const T Ey = axis_weights<T, W>(a, j, a.ny, a.cd[1], a.gs[1], Vy, Dy, oy, bad);
-  const T Ez = axis_weights<T, W>(a, k, a.nz, a.cd[2], a.gs[2], Vz, Dz, oz, bad);
+  axis_weights<T, W, RE>(a, 0, i, a.nx, sh[0], gs[0], Vx, Dx, E1x, E0x, ox, bad);
+  axis_weights<T, W, RE>(a, 1, j, a.ny, sh[1], gs[1], Vy, Dy, E1y, E0y, oy, bad);
+  axis_weights<T, W, RE>(a, 2, k, a.nz, sh[2], gs[2], Vz, Dz, E1z, E0z, oz, bad);
 
   const V4<T>* R = a.rec;
   const T uj = R[node].x;
   T acc = T(0);
-#pragma unroll
+#pragma unroll 1
   for (int c = 0; c < W; ++c) {
-    const T vz = Vz[c], dz = Dz[c];
+    const T vz = pick<W>(Vz, c), dz = pick<W>(Dz, c);
     const V4<T>* plane = R + (int64_t)(oz + c) * sz + (int64_t)oy * sy + ox;
     T P = T(0), Pz = T(0);
 #pragma unroll
@@ -167,9 +315,18 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
     }
     acc += vz * P + dz * Pz;
   }
-  // exit mass 1 - (1 - Ex)(1 - Ey)(1 - Ez), exactly 0 when no point exits
-  const T ex = Ex + (T(1) - Ex) * (Ey + (T(1) - Ey) * Ez);
-  const T un = uj + acc + (T(1) - uj) * ex;
+  // value-1 exit mass 1 - (1 - E1x)(1 - E1y)(1 - E1z), exactly 0 when no
+  // point exits; the window part is u_j + sum w (Itilde - u_j) over the
+  // inside points, whose weight is (1 - Ex)(1 - Ey)(1 - Ez)
+  const T ex1 = E1x + (T(1) - E1x) * (E1y + (T(1) - E1y) * E1z);
+  T un;
+  if constexpr (RE) {
+    const T Ex = E1x + E0x, Ey = E1y + E0y, Ez = E1z + E0z;
+    const T exall = Ex + (T(1) - Ex) * (Ey + (T(1) - Ey) * Ez);
+    un = uj + acc + (ex1 - uj * exall);
+  } else {
+    un = uj + acc + (T(1) - uj) * ex1;
+  }
   a.u_out[node] = un;
   if (a.snap) a.snap[node] = un;
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
@@ -177,10 +334,13 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
 
 template <typename T, int W>
 cudaError_t launch_w(const Step3D<T>& a, cudaStream_t s) {
-  const int in = a.nx - 2;
+  const int in = a.count[0];
   const int bx = in <= 32 ? 32 : (in <= 64 ? 64 : kRecThreads);
-  const dim3 grid((unsigned)((in + bx - 1) / bx), (unsigned)(a.ny - 2), (unsigned)(a.nz - 2));
-  k_step3d<T, W><<<grid, bx, 0, s>>>(a);
+  const dim3 grid((unsigned)((in + bx - 1) / bx), (unsigned)a.count[1], (unsigned)a.count[2]);
+  if (a.family == FK_RUNAWAY_3D)
+    k_step3d<T, W, true><<<grid, bx, 0, s>>>(a);
+  else
+    k_step3d<T, W, false><<<grid, bx, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -206,5 +366,15 @@ cudaError_t fk_launch_step3d(const Step3D<T>& a, cudaStream_t s) {
   }
 }
 
+template <typename T>
+cudaError_t fk_launch_chi3d(const Step3D<T>& a, T* u, cudaStream_t s) {
+  const dim3 grid((unsigned)((a.nx + kRecThreads - 1) / kRecThreads), (unsigned)a.ny,
+                  (unsigned)a.nz);
+  k_chi3d<T><<<grid, kRecThreads, 0, s>>>(a, u);
+  return cudaGetLastError();
+}
+
 template cudaError_t fk_launch_step3d<float>(const Step3D<float>&, cudaStream_t);
 template cudaError_t fk_launch_step3d<double>(const Step3D<double>&, cudaStream_t);
+template cudaError_t fk_launch_chi3d<float>(const Step3D<float>&, float*, cudaStream_t);
+template cudaError_t fk_launch_chi3d<double>(const Step3D<double>&, double*, cudaStream_t);

@@ -98,6 +98,7 @@ bool finite(double v) { return v == v && v - v == 0.0; }
 // Largest |b| over the box (drift bound used to size the tile halo).
 void drift_bound(const fk_coeffs* c, int dim, double* bmax) {
   for (int m = 0; m < 3; ++m) bmax[m] = 0.0;
+  if (c->family == FK_RUNAWAY_3D) return;  // per-node bounds: runaway_bounds()
   if (c->family == FK_CONST_DRIFT) {
     for (int m = 0; m < dim; ++m) bmax[m] = fabs(c->p[m]);
   } else if (c->family == FK_PAPER_CELLULAR) {
@@ -113,7 +114,55 @@ void drift_bound(const fk_coeffs* c, int dim, double* bmax) {
 
 double sigma_of(const fk_coeffs* c) {
   if (c->family == FK_PAPER_CELLULAR) return 1.0;  // unit Brownian motions
+  if (c->family == FK_RUNAWAY_3D) return 0.0;      // per node: runaway_bounds()
   return c->family == FK_CONST_DRIFT ? c->p[3] : sqrt(2.0 * c->p[3]);
+}
+
+// Drift and diagonal sigma of the runaway-electron model at one node (the
+// host's copy of Eq. (ex32d), for the plan's window bounds only).
+void runaway_host(const double* q, double mom, double xi, double r, double* b, double* s) {
+  const double E = q[0], tau = q[1], Z = q[2], delta = q[3], nu = q[4], vT = q[5];
+  const double rD = q[6], Wr = q[7], Dp = q[8], V0 = q[9], D0 = q[10];
+  const double gam = sqrt(1.0 + (delta * mom) * (delta * mom)), y = mom / gam;
+  const double phi = erf(y), dphi = 2.0 / sqrt(kPi) * exp(-y * y);
+  const double psi = (phi - y * dphi) / (2.0 * y * y), dpsi = dphi - 2.0 * psi / y;
+  const double nv2 = nu * vT * vT;
+  const double CA = nv2 * psi / y;
+  const double CB = 0.5 * nv2 / y * (Z + phi - psi + 0.5 * y * y * pow(delta, 4.0));
+  const double CF = 2.0 * nu * vT * psi;
+  const double df = 2.0 * mom * psi / y +
+                    mom * mom * (dpsi / y - psi / (y * y)) / (gam * gam * gam);
+  const double om = 1.0 - xi * xi;
+  b[0] = E * xi - gam * mom / tau * om - CF + nv2 * df / (mom * mom);
+  b[1] = E * om / mom - xi * om / (tau * gam) - 2.0 * xi * CB / (mom * mom);
+  const double th = tanh((r - rD) / Wr), ep = exp(-(mom / Dp) * (mom / Dp));
+  b[2] = (r > rD ? V0 : 0.0) + 0.5 * D0 * (1.0 - th * th) / Wr * ep;
+  s[0] = sqrt(2.0 * CA);
+  s[1] = sqrt(2.0 * CB) * sqrt(om > 0.0 ? om : 0.0) / mom;
+  s[2] = sqrt(D0 * (1.0 + th) * ep);
+}
+
+// Largest sigma_m and |b_m| over the nodes of a runaway plan (sigma_p and
+// b depend on (p, xi) and (p, r) only, so the pairs of axis nodes cover them).
+void runaway_bounds(const fk_plan* p, double* smax, double* bmax) {
+  for (int m = 0; m < 3; ++m) smax[m] = bmax[m] = 0.0;
+  const int n0 = p->grid.n[0], n1 = p->grid.n[1], n2 = p->grid.n[2];
+  auto x = [&](int m, int i) { return p->grid.lo[m] + (double)i * p->h[m]; };
+  double b[3], s[3];
+  for (int i = 0; i < n0; ++i) {
+    for (int j = 0; j < n1; ++j) {
+      runaway_host(p->coeffs.p, x(0, i), x(1, j), x(2, 0), b, s);
+      for (int m = 0; m < 2; ++m) {
+        smax[m] = std::max(smax[m], s[m]);
+        bmax[m] = std::max(bmax[m], fabs(b[m]));
+      }
+    }
+    for (int k = 0; k < n2; ++k) {
+      runaway_host(p->coeffs.p, x(0, i), 0.0, x(2, k), b, s);
+      smax[2] = std::max(smax[2], s[2]);
+      bmax[2] = std::max(bmax[2], fabs(b[2]));
+    }
+  }
 }
 
 fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int q, double dt,
@@ -128,18 +177,32 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
   if (prec != FK_FP32 && prec != FK_FP64) return FK_ERR_INVALID_ARG;
   if (path != FK_PATH_MATRIX_FREE && path != FK_PATH_CSR) return FK_ERR_INVALID_ARG;
   if (c->family != FK_CONST_DRIFT && c->family != FK_CELLULAR_FLOW &&
-      c->family != FK_PAPER_CELLULAR)
+      c->family != FK_PAPER_CELLULAR && c->family != FK_RUNAWAY_3D)
     return FK_ERR_INVALID_ARG;
-  for (int k = 0; k < 8; ++k)
+  for (int k = 0; k < 16; ++k)
     if (!finite(c->p[k])) return FK_ERR_INVALID_ARG;
   if (c->family == FK_CONST_DRIFT && !(c->p[3] >= 0.0)) return FK_ERR_INVALID_ARG;
   if (c->family == FK_CELLULAR_FLOW && !(c->p[3] >= 0.0)) return FK_ERR_INVALID_ARG;
   if ((c->family == FK_CELLULAR_FLOW || c->family == FK_PAPER_CELLULAR) && g->dim != 2)
     return FK_ERR_INVALID_ARG;
+  if (c->family == FK_RUNAWAY_3D) {
+    // x = (p, xi, r): p > 0, xi in [-1, 1], r >= 0; tau, W, Delta_p > 0,
+    // the other rates non-negative
+    if (g->dim != 3) return FK_ERR_INVALID_ARG;
+    if (!(g->lo[0] > 0.0) || !(g->lo[1] >= -1.0) || !(g->hi[1] <= 1.0) || !(g->lo[2] >= 0.0))
+      return FK_ERR_INVALID_ARG;
+    const double* q8 = c->p;
+    if (!(q8[1] > 0.0) || !(q8[7] > 0.0) || !(q8[8] > 0.0)) return FK_ERR_INVALID_ARG;
+    if (!(q8[2] >= 0.0) || !(q8[3] >= 0.0) || !(q8[4] >= 0.0) || !(q8[5] >= 0.0) ||
+        !(q8[10] >= 0.0))
+      return FK_ERR_INVALID_ARG;
+  }
   if (g->dim == 3) {
-    // d = 3: constant drift on a uniform mesh with every face absorbing,
+    // d = 3: constant drift or the runaway model on a uniform mesh,
     // matrix-free (the window kernel of fk_march3d.cu)
-    if (c->family != FK_CONST_DRIFT || path != FK_PATH_MATRIX_FREE) return FK_ERR_UNSUPPORTED;
+    if ((c->family != FK_CONST_DRIFT && c->family != FK_RUNAWAY_3D) ||
+        path != FK_PATH_MATRIX_FREE)
+      return FK_ERR_UNSUPPORTED;
     if (r && r->absorbing_faces != FK_ALL_FACES_ABSORBING) return FK_ERR_UNSUPPORTED;
     for (int m = 0; m < 3; ++m)
       if (g->axis[m] || g->n[m] > 65535) return FK_ERR_UNSUPPORTED;
@@ -713,6 +776,38 @@ void fill3d(const fk_plan* p, Step3D<T>* a) {
     a->gw[q] = (T)p->gh_w[q];
   }
   a->err = p->d_err;
+  a->family = p->coeffs.family;
+  const bool re = a->family == FK_RUNAWAY_3D;
+  for (int m = 0; m < 3; ++m) {
+    a->lo[m] = p->grid.lo[m];
+    a->h[m] = p->h[m];
+    // faces: every one exits with 1, except in the runaway model (p_max 1,
+    // p_min and the wall 0, xi and r = r_lo reflect)
+    a->face[m][0] = !re ? FK_FACE_EXIT1 : (m == 0 ? FK_FACE_EXIT0 : FK_FACE_REFLECT);
+    a->face[m][1] = !re ? FK_FACE_EXIT1
+                        : (m == 0 ? FK_FACE_EXIT1 : (m == 1 ? FK_FACE_REFLECT : FK_FACE_EXIT0));
+    a->first[m] = a->face[m][0] == FK_FACE_REFLECT ? 0 : 1;
+    const int last = a->face[m][1] == FK_FACE_REFLECT ? p->grid.n[m] - 1 : p->grid.n[m] - 2;
+    a->count[m] = last - a->first[m] + 1;
+  }
+  for (int k = 0; k < 11; ++k) a->rp[k] = p->coeffs.p[k];
+  a->dt = (T)p->dt;
+  a->sq2dt = (T)sqrt(2.0 * p->dt);
+}
+
+// The terminal indicator of a 3D plan into u (device, J values).
+fk_status chi3d(const fk_plan* p, void* u, cudaStream_t s) {
+  cudaError_t e;
+  if (p->prec == FK_FP32) {
+    Step3D<float> a;
+    fill3d<float>(p, &a);
+    e = fk_launch_chi3d<float>(a, (float*)u, s);
+  } else {
+    Step3D<double> a;
+    fill3d<double>(p, &a);
+    e = fk_launch_chi3d<double>(a, (double*)u, s);
+  }
+  return cuda_status(e);
 }
 
 // One step of each of nfields fields (J values apart): the record pass and
@@ -807,9 +902,11 @@ fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void
   const int64_t bytes = p->J * p->elem;
   const int steps = n_from - n_to;
   if (steps == 0) {
-    if (!u_in) return cuda_status(fk_launch_fill_chi(u_out, p->grid.dim, p->grid.n[0],
-                                                      p->grid.n[1], p->elem, s, p->periodic_x,
-                                                      p->grid.n[2]));
+    if (!u_in) {
+      if (p->grid.dim == 3) return chi3d(p, u_out, s);
+      return cuda_status(fk_launch_fill_chi(u_out, p->grid.dim, p->grid.n[0], p->grid.n[1],
+                                            p->elem, s, p->periodic_x));
+    }
     if (u_in != u_out) return cuda_status(fk_launch_copy(u_out, u_in, bytes, s));
     return FK_OK;
   }
@@ -837,8 +934,10 @@ fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void
   const void* src = u_in;
   if (!src) {
     void* buf = first_to_out ? p->scratch : u_out;
-    fk_status st = cuda_status(fk_launch_fill_chi(buf, p->grid.dim, p->grid.n[0], p->grid.n[1],
-                                                  p->elem, s, p->periodic_x, p->grid.n[2]));
+    fk_status st = p->grid.dim == 3
+                       ? chi3d(p, buf, s)
+                       : cuda_status(fk_launch_fill_chi(buf, p->grid.dim, p->grid.n[0],
+                                                        p->grid.n[1], p->elem, s, p->periodic_x));
     if (st != FK_OK) return st;
     src = buf;
   } else if (src == u_out && first_to_out) {
@@ -992,11 +1091,28 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   if (grid->dim == 3) {
     // window width: the points of one axis span gs (a_{Q-1} - a_0) cells
     // and touch at most floor(span) + 2 cells, W = floor(span) + 3 nodes
-    // (a small margin covers rounding of the positions)
+    // (a small margin covers rounding of the positions).  The runaway
+    // model takes the largest span over the nodes, and its mirrored points
+    // reach |shift| + span / 2 cells into the box from a reflecting face.
     int w = 3;
+    double smax[3], bmax3[3];
+    if (coeffs->family == FK_RUNAWAY_3D) {
+      runaway_bounds(p, smax, bmax3);
+    } else {
+      for (int m = 0; m < 3; ++m) {
+        smax[m] = sigma_of(coeffs);
+        bmax3[m] = fabs(coeffs->p[m]);
+      }
+    }
     for (int m = 0; m < 3; ++m) {
-      const double span = sg * (p->gh_a[q_per_dim - 1] - p->gh_a[0]) / p->h[m];
+      const double span = smax[m] * sqrt(2.0 * dt) * (p->gh_a[q_per_dim - 1] - p->gh_a[0]) /
+                          p->h[m];
+      const double shift = bmax3[m] * dt / p->h[m];
       w = std::max(w, (int)floor(span * (1.0 + 1e-6) + 1e-3) + 3);
+      if (coeffs->family == FK_RUNAWAY_3D)
+        w = std::max(w, (int)floor((shift + 0.5 * span) * (1.0 + 1e-6) + 1e-3) + 2);
+      p->reach[m] = shift + 0.5 * span;
+      p->halo[m] = (int)ceil(p->reach[m]) + 1;
     }
     bool fits = w <= FK_MAXW_3D;
     for (int m = 0; m < 3; ++m) fits = fits && grid->n[m] >= w;
@@ -1212,9 +1328,16 @@ fk_status fk_solve_horizons(fk_plan* p, const void* u_terminal, void* p_out,
     p->hz_bytes = (int64_t)N * fb;
   }
   char* buf[2] = {(char*)p_out, (char*)p->hz_ws};
-  fk_status st = cuda_status(fk_launch_fill_fields(buf[0], buf[1], u_terminal, p->grid.dim,
-                                                   p->grid.n[0], p->grid.n[1], p->elem, N,
-                                                   stream, p->periodic_x, p->grid.n[2]));
+  fk_status st = FK_OK;
+  if (p->grid.dim == 3 && !u_terminal) {
+    // the 3D indicator depends on the faces' exit values: form it once
+    st = chi3d(p, p->scratch, stream);
+    u_terminal = p->scratch;
+  }
+  if (st == FK_OK)
+    st = cuda_status(fk_launch_fill_fields(buf[0], buf[1], u_terminal, p->grid.dim,
+                                           p->grid.n[0], p->grid.n[1], p->elem, N, stream,
+                                           p->periodic_x, p->grid.n[2]));
   const int kMaxFields = 65535;  // grid z limit
   for (int n = N; n >= 1 && st == FK_OK; --n) {
     const int par = n & 1;

@@ -101,7 +101,7 @@ extern "C" fk_status fk_solve_static(const fk_grid* grid, const fk_coeffs* coeff
   if (prec != FK_FP32 && prec != FK_FP64) return FK_ERR_INVALID_ARG;
   if (coeffs->family != FK_CONST_DRIFT && coeffs->family != FK_CELLULAR_FLOW)
     return FK_ERR_INVALID_ARG;
-  for (int k = 0; k < 8; ++k)
+  for (int k = 0; k < 16; ++k)
     if (!finite_d(coeffs->p[k])) return FK_ERR_INVALID_ARG;
   if (!(coeffs->p[3] >= 0.0)) return FK_ERR_INVALID_ARG;
   if (q_per_dim < 1 || q_per_dim > FK_MAXQ_2D) return FK_ERR_UNSUPPORTED;

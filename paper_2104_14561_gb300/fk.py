@@ -20,7 +20,7 @@ _DTYPE = {"fp32": torch.float32, "fp64": torch.float64}
 _PREC = {"fp32": L.FK_FP32, "fp64": L.FK_FP64}
 _PATH = {"matrix_free": L.FK_PATH_MATRIX_FREE, "csr": L.FK_PATH_CSR}
 _FAMILY = {"const_drift": L.FK_CONST_DRIFT, "cellular_flow": L.FK_CELLULAR_FLOW,
-           "paper_cellular": L.FK_PAPER_CELLULAR}
+           "paper_cellular": L.FK_PAPER_CELLULAR, "runaway": L.FK_RUNAWAY_3D}
 
 
 def _ptr(t: torch.Tensor | None):

@@ -44,8 +44,8 @@ def _args(L, **kw):
     n = kw.get("n", (33, 17))
     for m in range(len(n)):
         g.n[m] = n[m]
-        g.lo[m] = 0.0
-        g.hi[m] = (2.0, 1.0, 1.0)[m]
+        g.lo[m] = kw.get("lo", (0.0, 0.0, 0.0))[m]
+        g.hi[m] = kw.get("hi", (2.0, 1.0, 1.0))[m]
     for m, ax in enumerate(kw.get("axes", ())):
         if ax is not None:
             arr = (ctypes.c_double * len(ax))(*ax)
@@ -58,6 +58,8 @@ def _args(L, **kw):
         c.p[k] = v
     return g, r, c
 
+
+RUNAWAY = (0.3, 1e5, 1.0, 0.042, 1.0, 1.0, 0.7, 1e-2, 20.0, 0.003, 1e-4)
 
 CASES = [
     (dict(dim=0), 1),
@@ -84,6 +86,16 @@ CASES = [
           axes=(None, None, [0.0, 0.1, 0.5, 0.7, 1.0])), 2),
     (dict(dim=3, n=(9, 9, 9), family=0, p=(0.1, 0, 0, 1.0), dt=0.05), 2),  # span > 6 cells
     (dict(dim=3, n=(4, 33, 33), family=0, p=(0.1, 0, 0, 0.3), dt=2e-3), 2),  # n < W on x
+    # the runaway model: d = 3, p > 0, xi within [-1, 1], positive scales
+    (dict(family=3, p=RUNAWAY), 1),  # two-dimensional grid
+    (dict(dim=3, n=(9, 9, 9), family=3, p=RUNAWAY, lo=(0.0, -1.0, 0.0), hi=(50, 1, 1)), 1),
+    (dict(dim=3, n=(9, 9, 9), family=3, p=RUNAWAY, lo=(2.0, -1.5, 0.0), hi=(50, 1, 1)), 1),
+    (dict(dim=3, n=(9, 9, 9), family=3, p=RUNAWAY[:1] + (0.0,) + RUNAWAY[2:],
+          lo=(2.0, -1.0, 0.0), hi=(50, 1, 1)), 1),  # tau = 0
+    (dict(dim=3, n=(9, 9, 9), family=3, p=RUNAWAY, lo=(2.0, -1.0, 0.0), hi=(50, 1, 1),
+          path=1), 2),
+    (dict(dim=3, n=(9, 65, 9), family=3, p=RUNAWAY, lo=(2.0, -1.0, 0.0), hi=(50, 1, 1),
+          dt=0.5), 2),  # the xi points span more than 6 cells
     (dict(dim=1, n=(33,)), 1),     # the cellular flow is two-dimensional
     (dict(family=2, dim=1, n=(33,), p=(10.0, 2.0, 0.15, 0.6)), 1),  # so is the paper's
     (dict(faces=0x3C, dim=1, n=(33,), family=0, p=(0.1, 0, 0, 1.0)), 2),  # periodic x in 1D

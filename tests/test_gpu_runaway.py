@@ -1,0 +1,135 @@
+"""The runaway-electron model of Sec. 4.3 (Eq. (ex32d), d = 3, x = (p, xi,
+r)) on the GPU, through the C ABI, against the FP64 oracle on the same
+seeded inputs.  Tolerances (max-abs): 1e-12 FP64, 1e-5 FP32.
+
+* whole marches on small meshes at the paper's parameters and at a set with
+  a strong field, radiation and radial transport (every face rule at work:
+  runaway exit at p_max, value 0 at p_min and at the wall, mirrors at
+  xi = +-1 and r = 0);
+* one step from a random field (every face's nodes included);
+* every horizon (Algorithm 1) from the runaway indicator;
+* the 97 x 65 x 41 benchmark workload over one step at sampled nodes.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import fk_inputs
+
+pytestmark = pytest.mark.gpu
+NCPU = os.cpu_count() or 1
+PAPER = (0.3, 1e5, 1.0, 0.042, 1.0, 1.0, 0.7, 1e-2, 20.0, 0.003, 1e-4)
+STRONG = (3.0, 50.0, 1.0, 0.042, 1.0, 1.0, 0.5, 0.05, 20.0, 0.05, 0.02)
+
+
+@pytest.fixture(scope="module")
+def fk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2104_14561_gb300 as fk
+    fk.load()
+    return fk
+
+
+def _w(n, params, hi_p, dt, n_steps, precision="fp64", q=4):
+    return dict(n=n, lo=(2.0, -1.0, 0.0), hi=(hi_p, 1.0, 1.0), family="runaway",
+                params=params, q=q, dt=dt, n_steps=n_steps, precision=precision)
+
+
+def _spec(fk, w):
+    return fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family="runaway", params=w["params"],
+                       q=w["q"], dt=w["dt"], n_steps=w["n_steps"], precision=w["precision"])
+
+
+def _grid(oracle, w):
+    return oracle.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]))
+
+
+def _oracle(oracle, w, k=None, u0=None):
+    return oracle.march(_grid(oracle, w), oracle.RUNAWAY, list(w["params"]), w["q"], w["dt"],
+                        k or w["n_steps"], 0, u0, nthreads=NCPU)
+
+
+def _solve(fk, w, u0=None):
+    import torch
+    plan = fk.Plan(_spec(fk, w))
+    ut = None if u0 is None else torch.tensor(u0, dtype=plan.dtype, device="cuda")
+    out = plan.solve(ut)
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    info = plan.info()
+    res = out.double().cpu().numpy()
+    plan.close()
+    return res, info
+
+
+@pytest.mark.parametrize("case", ["paper", "strong"])
+def test_runaway_fp64_vs_oracle(fk, oracle, case):
+    if case == "paper":
+        w = _w((25, 17, 13), PAPER, 50.0, 0.02, 25)
+    else:
+        w = _w((21, 17, 11), STRONG, 12.0, 0.02, 40)
+    got, info = _solve(fk, w)
+    assert info["step_kernel"] == "window3d"
+    want = _oracle(oracle, w)
+    assert np.abs(got - want).max() <= 1e-12
+    assert got[..., -1].min() == 1.0 and got[..., 0].max() == 0.0
+    if case == "strong":
+        assert 0.05 < got[5, 12, 12] < 0.999  # the march moved a front into the box
+
+
+def test_runaway_fp32_random_field_step(fk, oracle):
+    w = _w((21, 17, 11), STRONG, 12.0, 0.05, 3, precision="fp32")
+    u1 = fk_inputs.random_field((11, 17, 21), seed=71, boundary_one=False)
+    got, _ = _solve(fk, w, u1)
+    assert np.abs(got - _oracle(oracle, w, u0=u1)).max() <= 1e-5
+
+
+def test_runaway_fp64_random_field_one_step(fk, oracle):
+    import torch
+    w = _w((21, 17, 11), STRONG[:9] + (0.05, 0.3), 12.0, 0.02, 2)
+    u1 = fk_inputs.random_field((11, 17, 21), seed=72, boundary_one=False)
+    plan = fk.Plan(_spec(fk, w))
+    got = plan.march(1, 0, torch.tensor(u1, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    plan.close()
+    want = oracle.march(_grid(oracle, w), oracle.RUNAWAY, list(w["params"]), 4, w["dt"], 1, 0, u1)
+    assert np.abs(got.cpu().numpy() - want).max() <= 1e-12
+
+
+def test_runaway_horizons(fk, oracle):
+    import torch
+    w = _w((21, 17, 11), STRONG, 12.0, 0.05, 5)
+    plan = fk.Plan(_spec(fk, w))
+    hz = plan.solve_horizons()
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    hz = hz.cpu().numpy()
+    plan.close()
+    for k in (1, 3, 5):
+        assert np.abs(hz[k - 1] - _oracle(oracle, w, k)).max() <= 1e-12, k
+
+
+def test_runaway_workload_sampled_step(fk, oracle):
+    """The 97 x 65 x 41 workload at the paper's parameters (FP32, 4^3
+    points): one step from a random field at sampled nodes (every face
+    included) against the oracle's step there."""
+    import torch
+    w = fk_inputs.workload("runaway_97x65x41")
+    shape = tuple(reversed(w["n"]))
+    plan = fk.Plan(_spec(fk, w))
+    assert plan.info()["window_rows"] <= 8
+    u1 = fk_inputs.random_field(shape, seed=73, boundary_one=False)
+    n = 100
+    got = plan.march(n + 1, n, torch.tensor(u1, dtype=torch.float32, device="cuda"))
+    got = got.double().cpu().numpy().reshape(-1)
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    plan.close()
+    nodes = fk_inputs.sample_nodes(shape, 3000, seed=13)
+    want = oracle.step_nodes(_grid(oracle, w), oracle.RUNAWAY, list(w["params"]), w["q"],
+                             w["dt"], n, u1, nodes, nthreads=NCPU)
+    assert np.abs(got[nodes] - want).max() <= 1e-5
