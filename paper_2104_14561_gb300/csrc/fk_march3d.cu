@@ -245,11 +245,15 @@ __device__ __forceinline__ void runaway_coef(const Step3D<T>& a, int i, int j, i
   const T om = T(1) - xi * xi;
   const T b0 = E * xi - gam * mom / tau * om - CF + nv2 * df / (mom * mom);
   const T b1 = E * om / mom - xi * om / (tau * gam) - T(2) * xi * CB / (mom * mom);
-  const T th = tanh((r - rD) / Wr);
+  // 1 + tanh z = 2 / (1 + e^{-2z}) and 1 - tanh z = 2 / (1 + e^{2z}): no
+  // cancellation where tanh is near -1 (in FP32, 1 + tanhf(-10) is 0, which
+  // would drop a radial diffusion that FP64 keeps)
+  const T z = (r - rD) / Wr;
+  const T onep = T(2) / (T(1) + exp(T(-2) * z)), onem = T(2) / (T(1) + exp(T(2) * z));
   const T q = mom / Dp;
   const T ep = exp(-q * q);
-  const T Dr = T(0.5) * D0 * (T(1) + th) * ep;
-  const T b2 = (beyond ? V0 : T(0)) + T(0.5) * D0 * (T(1) - th * th) / Wr * ep;
+  const T Dr = T(0.5) * D0 * onep * ep;
+  const T b2 = (beyond ? V0 : T(0)) + T(0.5) * D0 * onep * onem / Wr * ep;
   const T s0 = sqrt(T(2) * CA);
   const T s1 = sqrt(T(2) * CB) * sqrt(om > T(0) ? om : T(0)) / mom;
   const T s2 = sqrt(T(2) * Dr);

@@ -76,8 +76,9 @@ def test_runaway_fp64_vs_oracle(fk, oracle, case):
     want = _oracle(oracle, w)
     assert np.abs(got - want).max() <= 1e-12
     assert got[..., -1].min() == 1.0 and got[..., 0].max() == 0.0
-    if case == "strong":
-        assert 0.05 < got[5, 12, 12] < 0.999  # the march moved a front into the box
+    if case == "strong":  # T = 0.8 carried a runaway front into the box (129 nodes)
+        inner = got[1:-1, 1:-1, 1:-1]
+        assert np.count_nonzero((inner > 0.05) & (inner < 0.95)) > 50
 
 
 def test_runaway_fp32_random_field_step(fk, oracle):
