@@ -297,10 +297,8 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
 
   const V4<T>* R = a.rec;
   const T uj = R[node].x;
-  T acc = T(0);
-#pragma unroll 1
-  for (int c = 0; c < W; ++c) {
-    const T vz = pick<W>(Vz, c), dz = pick<W>(Dz, c);
+  // one plane c of the window: its W x W records against the x and y weights
+  auto plane_sum = [&](int c, T vz, T dz) {
     const V4<T>* plane = R + (int64_t)(oz + c) * sz + (int64_t)oy * sy + ox;
     T P = T(0), Pz = T(0);
 #pragma unroll
@@ -317,7 +315,17 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
       P += Vy[b] * s1 + Dy[b] * s2;
       Pz += Vy[b] * s3;
     }
-    acc += vz * P + dz * Pz;
+    return vz * P + dz * Pz;
+  };
+  T acc = T(0);
+  if constexpr (RE) {
+    // planes in a loop (the runaway instantiations would double the build
+    // time if unrolled as well)
+#pragma unroll 1
+    for (int c = 0; c < W; ++c) acc += plane_sum(c, pick<W>(Vz, c), pick<W>(Dz, c));
+  } else {
+#pragma unroll
+    for (int c = 0; c < W; ++c) acc += plane_sum(c, Vz[c], Dz[c]);
   }
   // value-1 exit mass 1 - (1 - E1x)(1 - E1y)(1 - E1z), exactly 0 when no
   // point exits; the window part is u_j + sum w (Itilde - u_j) over the
