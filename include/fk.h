@@ -93,8 +93,22 @@ typedef enum fk_path { FK_PATH_MATRIX_FREE = 0, FK_PATH_CSR = 1 } fk_path;
  *                     absorbing faces hold their value (1 on p = p_max).
  *                     The terminal indicator is 1 on p = p_max only.
  *                     Uniform mesh, matrix-free; fk_adjoint, batching and
- *                     the static entry return FK_ERR_UNSUPPORTED. */
-enum { FK_CONST_DRIFT = 0, FK_CELLULAR_FLOW = 1, FK_PAPER_CELLULAR = 2, FK_RUNAWAY_3D = 3 };
+ *                     the static entry return FK_ERR_UNSUPPORTED.
+ *  FK_RUNAWAY_QUENCH_3D  the time-dependent variant at the end of Sec. 4.3
+ *                     (a thermal quench), p = {E_0, tau, Z, T0, Tf, Ttilde,
+ *                     t_star, r_D, W, Delta_p, V_0, D_0, mc2}; at time t the
+ *                     FK_RUNAWAY_3D model runs with the constants that
+ *                     fk_runaway_quench_params returns for t (the paper's
+ *                     values: 1e-3, 6000, 1, 3, 0.005, 3, t_star, 0, 1e-4,
+ *                     2, 0, D_0, with temperatures in keV and mc2 = 511).
+ *                     Same box, faces and restrictions as FK_RUNAWAY_3D. */
+enum {
+  FK_CONST_DRIFT = 0,
+  FK_CELLULAR_FLOW = 1,
+  FK_PAPER_CELLULAR = 2,
+  FK_RUNAWAY_3D = 3,
+  FK_RUNAWAY_QUENCH_3D = 4
+};
 
 /* Cartesian mesh S (Sec. 3.1.2): n[m] >= 3 nodes on [lo[m], hi[m]] for
  * m < dim; entries for m >= dim are ignored.  axis[m] = NULL gives the
@@ -215,6 +229,22 @@ fk_status fk_plan_get_info(const fk_plan *plan, fk_plan_info *info);
  * sum w = 1.  Host arrays of length q, 1 <= q <= 16.  Host-only call.
  * ---------------------------------------------------------------------- */
 fk_status fk_gauss_hermite(int q, double *a, double *w);
+
+/* ------------------------------------------------------------------------
+ * fk_runaway_quench_params -- the constants of the runaway model at time t
+ * of the thermal-quench variant (end of Sec. 4.3): with
+ *   T(t) = Tf + (T0 - Tf) exp(-t / t_star),
+ *   ln Lambda(T) = 14.9 - (1/2) ln 0.28 + ln T,
+ * it writes p11 = {E_0 (T0/T)^{3/2}, tau, Z, sqrt(2 T / mc2),
+ * (Ttilde/T)^{3/2} ln Lambda(T) / ln Lambda(Ttilde), sqrt(T / Ttilde), r_D,
+ * W, Delta_p, V_0, D_0}, the FK_RUNAWAY_3D parameter block.
+ *   p13  host array of the 13 FK_RUNAWAY_QUENCH_3D parameters.
+ *   t    time.
+ *   p11  host array of 11 doubles, written.
+ * Host-only call.  FK_ERR_INVALID_ARG for NULL pointers, a non-finite t, or
+ * T0, Tf, Ttilde, t_star or mc2 not positive.
+ * ---------------------------------------------------------------------- */
+fk_status fk_runaway_quench_params(const double *p13, double t, double *p11);
 
 /* ------------------------------------------------------------------------
  * fk_solve -- Scheme 1 from n = N to n = 0: u_out <- u^0 = P(T, x_j).

@@ -53,6 +53,7 @@
 #define FKO_CELLULAR_FLOW 1
 #define FKO_PAPER_CELLULAR 2
 #define FKO_RUNAWAY 3
+#define FKO_RUNAWAY_QUENCH 4
 
 static const double FKO_PI = 3.14159265358979323846264338327950288;
 
@@ -119,7 +120,7 @@ static void grid_canonical(const fko_grid *g, int *idx) {
  * axis), reflect. */
 enum { FACE_EXIT0 = 0, FACE_EXIT1 = 1, FACE_REFLECT = 2 };
 static int face_rule(int family, int m, int upper) {
-  if (family != FKO_RUNAWAY) return FACE_EXIT1;
+  if (family != FKO_RUNAWAY && family != FKO_RUNAWAY_QUENCH) return FACE_EXIT1;
   if (m == 0) return upper ? FACE_EXIT1 : FACE_EXIT0;
   if (m == 1) return FACE_REFLECT;
   return upper ? FACE_EXIT0 : FACE_REFLECT;
@@ -163,6 +164,37 @@ static int grid_check(const fko_grid *g) {
 }
 
 /* -------------------------------------------------------- coefficients -- */
+
+/*
+ * FKO_RUNAWAY_QUENCH (d = 3): the time-dependent runaway model at the end
+ * of Sec. 4.3, p = (E_0, tau, Z, T0, Tf, Ttilde, t_star, r_D, W, Delta_p,
+ * V_0, D_0, mc2).  The plasma temperature falls as
+ *   T(t) = Tf + (T0 - Tf) exp(-t / t_star),
+ * and with ln Lambda(T) = 14.9 - (1/2) ln 0.28 + ln T the constants of the
+ * static model become
+ *   v_T = sqrt(T / Ttilde),  nu_ee = (Ttilde / T)^{3/2} ln Lambda(T) / ln Lambda(Ttilde),
+ *   delta = sqrt(2 T / mc2),  E = E_0 (T0 / T)^{3/2};
+ * the remaining ones are taken as given.  Temperatures and mc2 share one
+ * unit (keV: mc2 = 511).
+ */
+static void quench_static_params(const double *q, double t, double *p11) {
+  const double T = q[4] + (q[3] - q[4]) * exp(-t / q[6]);
+  const double lnL = 14.9 - 0.5 * log(0.28) + log(T);
+  const double lnLt = 14.9 - 0.5 * log(0.28) + log(q[5]);
+  p11[0] = q[0] * pow(q[3] / T, 1.5);          /* E */
+  p11[1] = q[1];                               /* tau */
+  p11[2] = q[2];                               /* Z */
+  p11[3] = sqrt(2.0 * T / q[12]);              /* delta */
+  p11[4] = pow(q[5] / T, 1.5) * lnL / lnLt;    /* nu_ee */
+  p11[5] = sqrt(T / q[5]);                     /* v_T */
+  p11[6] = q[7];                               /* r_D */
+  p11[7] = q[8];                               /* W */
+  p11[8] = q[9];                               /* Delta_p */
+  p11[9] = q[10];                              /* V_0 */
+  p11[10] = q[11];                             /* D_0 */
+}
+
+void fko_quench_params(const double *q, double t, double *p11) { quench_static_params(q, t, p11); }
 
 /*
  * FKO_RUNAWAY (d = 3), x = (p, xi, r) (momentum, cosine of the pitch angle,
@@ -243,6 +275,12 @@ void fko_coefficients(int family, const double *p, int dim, double t,
     runaway_coefficients(p, x, b, sig);
     return;
   }
+  if (family == FKO_RUNAWAY_QUENCH) {
+    double p11[11];
+    quench_static_params(p, t, p11);
+    runaway_coefficients(p11, x, b, sig);
+    return;
+  }
   if (family == FKO_PAPER_CELLULAR) {
     double Pe = p[0], nn = p[1], eps = p[2], omega = p[3];
     double f = cos(omega * t);
@@ -273,7 +311,7 @@ static int family_check(int family, int dim, const double *p) {
   if (family == FKO_CONST_DRIFT) return !(p[3] >= 0.0);
   if (family == FKO_CELLULAR_FLOW) return dim != 2 || !(p[3] >= 0.0);
   if (family == FKO_PAPER_CELLULAR) return dim != 2;
-  if (family == FKO_RUNAWAY) return dim != 3;
+  if (family == FKO_RUNAWAY || family == FKO_RUNAWAY_QUENCH) return dim != 3;
   return 1;
 }
 
@@ -676,7 +714,8 @@ int fko_adjoint(const fko_grid *g, int family, const double *p, int nq,
                 double *dtheta, double *du_terminal) {
   if (grid_check(g) || family_check(family, g->dim, p)) return 1;
   if (nq < 1 || !(dt > 0.0) || n_steps < 1) return 1;
-  if (g->periodic || family == FKO_PAPER_CELLULAR || family == FKO_RUNAWAY)
+  if (g->periodic || family == FKO_PAPER_CELLULAR || family == FKO_RUNAWAY ||
+      family == FKO_RUNAWAY_QUENCH)
     return 3; /* not differentiated */
   for (int m = 0; m < g->dim; ++m)
     if (g->axis[m]) return 3; /* uniform meshes only */

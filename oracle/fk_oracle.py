@@ -47,6 +47,8 @@ PAPER_CELLULAR = 2   # the paper's own example of Sec. 4.2: p = (Pe, n, eps, ome
 RUNAWAY = 3          # the runaway-electron model of Sec. 4.3 (d = 3, x = (p, xi, r)):
 #                      params (E, tau, Z, delta, nu_ee, v_T, r_D, W, Delta_p, V_0, D_0)
 RUNAWAY_PARAMS = (0.3, 1e5, 1.0, 0.042, 1.0, 1.0, 0.7, 1e-2, 20.0, 0.003, 1e-4)  # Sec. 4.3
+RUNAWAY_QUENCH = 4   # the thermal-quench (time-dependent) variant, params
+#                      (E_0, tau, Z, T0, Tf, Ttilde, t_star, r_D, W, Delta_p, V_0, D_0, mc2)
 
 
 def build(force: bool = False) -> str:
@@ -94,6 +96,8 @@ def _load():
         lib.fko_coefficients.argtypes = [ctypes.c_int, dp, ctypes.c_int,
                                          ctypes.c_double, dp, dp, dp]
         lib.fko_coefficients.restype = None
+        lib.fko_quench_params.argtypes = [dp, ctypes.c_double, dp]
+        lib.fko_quench_params.restype = None
         lib.fko_adjoint.argtypes = [gp, ctypes.c_int, dp, ctypes.c_int, dp, dp, ctypes.c_double,
                                     ctypes.c_int, dp, dp, dp, dp]
         _lib = lib
@@ -194,7 +198,7 @@ def terminal_indicator(grid: Grid, family: int = CONST_DRIFT) -> np.ndarray:
     of the non-periodic axes).  The runaway model counts only p = p_max
     (the upper face of axis 0): chi is 1 there and 0 elsewhere."""
     chi = np.zeros(grid.shape, dtype=np.float64)
-    if family == RUNAWAY:
+    if family in (RUNAWAY, RUNAWAY_QUENCH):
         chi[..., -1] = 1.0
         return chi
     for ax in range(chi.ndim):
@@ -216,6 +220,15 @@ def coefficients(family: int, params, dim: int, t: float, x) -> tuple:
     s = np.zeros(dim * dim)
     lib.fko_coefficients(family, _dp(p), dim, float(t), _dp(xx), _dp(b), _dp(s))
     return b, s.reshape(dim, dim)
+
+
+def quench_params(params, t: float) -> np.ndarray:
+    """The static runaway parameters (E, tau, Z, delta, nu_ee, v_T, r_D, W,
+    Delta_p, V_0, D_0) of the thermal-quench model at time t."""
+    lib = _load()
+    out = np.zeros(11)
+    lib.fko_quench_params(_dp(_params(params)), float(t), _dp(out))
+    return out
 
 
 def slopes(grid: Grid, u: np.ndarray) -> np.ndarray:

@@ -18,13 +18,15 @@ STATUS = {0: "FK_OK", 1: "FK_ERR_INVALID_ARG", 2: "FK_ERR_UNSUPPORTED", 3: "FK_E
 FK_FP32, FK_FP64 = 0, 1
 FK_PATH_MATRIX_FREE, FK_PATH_CSR = 0, 1
 FK_CONST_DRIFT, FK_CELLULAR_FLOW, FK_PAPER_CELLULAR, FK_RUNAWAY_3D = 0, 1, 2, 3
+FK_RUNAWAY_QUENCH_3D = 4
 FK_ALL_FACES_ABSORBING = 0x3F
 FK_PERIODIC_X = 0x3C
 
 # every symbol include/fk.h declares
 EXPORTS = ("fk_plan_create", "fk_plan_destroy", "fk_plan_get_info", "fk_gauss_hermite",
            "fk_solve", "fk_march", "fk_solve_horizons", "fk_solve_batched", "fk_adjoint",
-           "fk_status_string", "fk_last_device_error", "fk_solve_static")
+           "fk_status_string", "fk_last_device_error", "fk_solve_static",
+           "fk_runaway_quench_params")
 
 
 class FkError(RuntimeError):
@@ -88,6 +90,9 @@ def load(build_if_missing: bool = False):
     lib.fk_gauss_hermite.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]
     lib.fk_gauss_hermite.restype = st
+    lib.fk_runaway_quench_params.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_double)]
+    lib.fk_runaway_quench_params.restype = st
     lib.fk_solve.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp]
     lib.fk_solve.restype = st
     lib.fk_march.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]

@@ -98,7 +98,8 @@ bool finite(double v) { return v == v && v - v == 0.0; }
 // Largest |b| over the box (drift bound used to size the tile halo).
 void drift_bound(const fk_coeffs* c, int dim, double* bmax) {
   for (int m = 0; m < 3; ++m) bmax[m] = 0.0;
-  if (c->family == FK_RUNAWAY_3D) return;  // per-node bounds: runaway_bounds()
+  if (c->family == FK_RUNAWAY_3D || c->family == FK_RUNAWAY_QUENCH_3D)
+    return;  // per-node bounds: runaway_bounds()
   if (c->family == FK_CONST_DRIFT) {
     for (int m = 0; m < dim; ++m) bmax[m] = fabs(c->p[m]);
   } else if (c->family == FK_PAPER_CELLULAR) {
@@ -114,7 +115,8 @@ void drift_bound(const fk_coeffs* c, int dim, double* bmax) {
 
 double sigma_of(const fk_coeffs* c) {
   if (c->family == FK_PAPER_CELLULAR) return 1.0;  // unit Brownian motions
-  if (c->family == FK_RUNAWAY_3D) return 0.0;      // per node: runaway_bounds()
+  if (c->family == FK_RUNAWAY_3D || c->family == FK_RUNAWAY_QUENCH_3D)
+    return 0.0;  // per node: runaway_bounds()
   return c->family == FK_CONST_DRIFT ? c->p[3] : sqrt(2.0 * c->p[3]);
 }
 
@@ -142,26 +144,65 @@ void runaway_host(const double* q, double mom, double xi, double r, double* b, d
   s[2] = sqrt(D0 * (1.0 + th) * ep);
 }
 
-// Largest sigma_m and |b_m| over the nodes of a runaway plan (sigma_p and
-// b depend on (p, xi) and (p, r) only, so the pairs of axis nodes cover them).
-void runaway_bounds(const fk_plan* p, double* smax, double* bmax) {
-  for (int m = 0; m < 3; ++m) smax[m] = bmax[m] = 0.0;
+// The thermal-quench schedule (end of Sec. 4.3): the static runaway
+// constants at time t (see fk_runaway_quench_params in fk.h).
+void quench_params(const double* q, double t, double* p11) {
+  const double T = q[4] + (q[3] - q[4]) * exp(-t / q[6]);
+  const double c = 14.9 - 0.5 * log(0.28);
+  const double lam = c + log(T), lam_ref = c + log(q[5]);
+  p11[0] = q[0] * pow(q[3] / T, 1.5);
+  p11[1] = q[1];
+  p11[2] = q[2];
+  p11[3] = sqrt(2.0 * T / q[12]);
+  p11[4] = pow(q[5] / T, 1.5) * lam / lam_ref;
+  p11[5] = sqrt(T / q[5]);
+  for (int k = 6; k < 11; ++k) p11[k] = q[k + 1];
+}
+
+bool quench_family(int family) { return family == FK_RUNAWAY_QUENCH_3D; }
+bool runaway_family(int family) {
+  return family == FK_RUNAWAY_3D || family == FK_RUNAWAY_QUENCH_3D;
+}
+
+// The static runaway constants of plan p at step n (t_n = n dt).
+void runaway_params_at(const fk_plan* p, int n, double* p11) {
+  if (quench_family(p->coeffs.family))
+    quench_params(p->coeffs.p, n * p->dt, p11);
+  else
+    for (int k = 0; k < 11; ++k) p11[k] = p->coeffs.p[k];
+}
+
+// Largest sigma_m and |b_m| over the nodes for the constants q11 (sigma_p
+// and b depend on (p, xi) and (p, r) only, so the pairs of axis nodes cover
+// the mesh); running maxima in smax, bmax.
+void runaway_bounds_at(const fk_plan* p, const double* q11, double* smax, double* bmax) {
   const int n0 = p->grid.n[0], n1 = p->grid.n[1], n2 = p->grid.n[2];
   auto x = [&](int m, int i) { return p->grid.lo[m] + (double)i * p->h[m]; };
   double b[3], s[3];
   for (int i = 0; i < n0; ++i) {
     for (int j = 0; j < n1; ++j) {
-      runaway_host(p->coeffs.p, x(0, i), x(1, j), x(2, 0), b, s);
+      runaway_host(q11, x(0, i), x(1, j), x(2, 0), b, s);
       for (int m = 0; m < 2; ++m) {
         smax[m] = std::max(smax[m], s[m]);
         bmax[m] = std::max(bmax[m], fabs(b[m]));
       }
     }
     for (int k = 0; k < n2; ++k) {
-      runaway_host(p->coeffs.p, x(0, i), 0.0, x(2, k), b, s);
+      runaway_host(q11, x(0, i), 0.0, x(2, k), b, s);
       smax[2] = std::max(smax[2], s[2]);
       bmax[2] = std::max(bmax[2], fabs(b[2]));
     }
+  }
+}
+
+// The same over every time step of a quench plan.
+void runaway_bounds(const fk_plan* p, double* smax, double* bmax) {
+  for (int m = 0; m < 3; ++m) smax[m] = bmax[m] = 0.0;
+  const int times = quench_family(p->coeffs.family) ? p->n_steps : 1;
+  for (int n = 0; n < times; ++n) {
+    double q11[11];
+    runaway_params_at(p, n, q11);
+    runaway_bounds_at(p, q11, smax, bmax);
   }
 }
 
@@ -177,7 +218,7 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
   if (prec != FK_FP32 && prec != FK_FP64) return FK_ERR_INVALID_ARG;
   if (path != FK_PATH_MATRIX_FREE && path != FK_PATH_CSR) return FK_ERR_INVALID_ARG;
   if (c->family != FK_CONST_DRIFT && c->family != FK_CELLULAR_FLOW &&
-      c->family != FK_PAPER_CELLULAR && c->family != FK_RUNAWAY_3D)
+      c->family != FK_PAPER_CELLULAR && !runaway_family(c->family))
     return FK_ERR_INVALID_ARG;
   for (int k = 0; k < 16; ++k)
     if (!finite(c->p[k])) return FK_ERR_INVALID_ARG;
@@ -185,22 +226,32 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
   if (c->family == FK_CELLULAR_FLOW && !(c->p[3] >= 0.0)) return FK_ERR_INVALID_ARG;
   if ((c->family == FK_CELLULAR_FLOW || c->family == FK_PAPER_CELLULAR) && g->dim != 2)
     return FK_ERR_INVALID_ARG;
-  if (c->family == FK_RUNAWAY_3D) {
+  if (runaway_family(c->family)) {
     // x = (p, xi, r): p > 0, xi in [-1, 1], r >= 0; tau, W, Delta_p > 0,
-    // the other rates non-negative
+    // the other rates non-negative (the quench variant: at t = 0; its
+    // temperatures, t_star and mc2 positive)
     if (g->dim != 3) return FK_ERR_INVALID_ARG;
     if (!(g->lo[0] > 0.0) || !(g->lo[1] >= -1.0) || !(g->hi[1] <= 1.0) || !(g->lo[2] >= 0.0))
       return FK_ERR_INVALID_ARG;
-    const double* q8 = c->p;
-    if (!(q8[1] > 0.0) || !(q8[7] > 0.0) || !(q8[8] > 0.0)) return FK_ERR_INVALID_ARG;
-    if (!(q8[2] >= 0.0) || !(q8[3] >= 0.0) || !(q8[4] >= 0.0) || !(q8[5] >= 0.0) ||
-        !(q8[10] >= 0.0))
+    const double* q = c->p;
+    if (quench_family(c->family)) {
+      for (int k : {3, 4, 5, 6, 12})
+        if (!(q[k] > 0.0)) return FK_ERR_INVALID_ARG;
+    }
+    double q11[11];
+    if (quench_family(c->family))
+      quench_params(q, 0.0, q11);
+    else
+      for (int k = 0; k < 11; ++k) q11[k] = q[k];
+    if (!(q11[1] > 0.0) || !(q11[7] > 0.0) || !(q11[8] > 0.0)) return FK_ERR_INVALID_ARG;
+    if (!(q11[2] >= 0.0) || !(q11[3] >= 0.0) || !(q11[4] >= 0.0) || !(q11[5] >= 0.0) ||
+        !(q11[10] >= 0.0))
       return FK_ERR_INVALID_ARG;
   }
   if (g->dim == 3) {
     // d = 3: constant drift or the runaway model on a uniform mesh,
     // matrix-free (the window kernel of fk_march3d.cu)
-    if ((c->family != FK_CONST_DRIFT && c->family != FK_RUNAWAY_3D) ||
+    if ((c->family != FK_CONST_DRIFT && !runaway_family(c->family)) ||
         path != FK_PATH_MATRIX_FREE)
       return FK_ERR_UNSUPPORTED;
     if (r && r->absorbing_faces != FK_ALL_FACES_ABSORBING) return FK_ERR_UNSUPPORTED;
@@ -758,7 +809,7 @@ void fk_fill_step2d_f64(const fk_plan* p, int n, Step2D<double>* a) { fill2d<dou
 
 namespace {
 template <typename T>
-void fill3d(const fk_plan* p, Step3D<T>* a) {
+void fill3d(const fk_plan* p, int n, Step3D<T>* a) {
   memset(a, 0, sizeof(*a));
   a->rec = (V4<T>*)p->rec3d;
   a->nx = p->grid.n[0];
@@ -776,8 +827,10 @@ void fill3d(const fk_plan* p, Step3D<T>* a) {
     a->gw[q] = (T)p->gh_w[q];
   }
   a->err = p->d_err;
-  a->family = p->coeffs.family;
-  const bool re = a->family == FK_RUNAWAY_3D;
+  // both runaway variants run the runaway kernel; the quench variant with
+  // the constants of t_n = n dt
+  const bool re = runaway_family(p->coeffs.family);
+  a->family = re ? FK_RUNAWAY_3D : p->coeffs.family;
   for (int m = 0; m < 3; ++m) {
     a->lo[m] = p->grid.lo[m];
     a->h[m] = p->h[m];
@@ -790,7 +843,7 @@ void fill3d(const fk_plan* p, Step3D<T>* a) {
     const int last = a->face[m][1] == FK_FACE_REFLECT ? p->grid.n[m] - 1 : p->grid.n[m] - 2;
     a->count[m] = last - a->first[m] + 1;
   }
-  for (int k = 0; k < 11; ++k) a->rp[k] = p->coeffs.p[k];
+  if (re) runaway_params_at(p, n, a->rp);
   a->dt = (T)p->dt;
   a->sq2dt = (T)sqrt(2.0 * p->dt);
 }
@@ -800,11 +853,11 @@ fk_status chi3d(const fk_plan* p, void* u, cudaStream_t s) {
   cudaError_t e;
   if (p->prec == FK_FP32) {
     Step3D<float> a;
-    fill3d<float>(p, &a);
+    fill3d<float>(p, 0, &a);
     e = fk_launch_chi3d<float>(a, (float*)u, s);
   } else {
     Step3D<double> a;
-    fill3d<double>(p, &a);
+    fill3d<double>(p, 0, &a);
     e = fk_launch_chi3d<double>(a, (double*)u, s);
   }
   return cuda_status(e);
@@ -813,10 +866,10 @@ fk_status chi3d(const fk_plan* p, void* u, cudaStream_t s) {
 // One step of each of nfields fields (J values apart): the record pass and
 // the window pass per field (the records are one field's workspace).
 template <typename T>
-cudaError_t step3d(const fk_plan* p, const void* u_in, void* u_out, void* snap, int nfields,
+cudaError_t step3d(const fk_plan* p, int n, const void* u_in, void* u_out, void* snap, int nfields,
                    cudaStream_t s) {
   Step3D<T> a;
-  fill3d<T>(p, &a);
+  fill3d<T>(p, n, &a);
   for (int f = 0; f < nfields; ++f) {
     a.u_in = (const T*)u_in + (int64_t)f * p->J;
     a.u_out = (T*)u_out + (int64_t)f * p->J;
@@ -831,8 +884,8 @@ fk_status enqueue_step(fk_plan* p, int n, const void* u_in, void* u_out, void* s
                        int nfields, cudaStream_t s) {
   cudaError_t e;
   if (p->grid.dim == 3) {
-    e = p->prec == FK_FP32 ? step3d<float>(p, u_in, u_out, snap, nfields, s)
-                           : step3d<double>(p, u_in, u_out, snap, nfields, s);
+    e = p->prec == FK_FP32 ? step3d<float>(p, n, u_in, u_out, snap, nfields, s)
+                           : step3d<double>(p, n, u_in, u_out, snap, nfields, s);
     return cuda_status(e);
   }
   if (p->grid.dim == 2) {
@@ -982,6 +1035,15 @@ fk_status fk_gauss_hermite(int q, double* a, double* w) {
   return gauss_hermite(q, a, w) ? FK_OK : FK_ERR_INVALID_ARG;
 }
 
+fk_status fk_runaway_quench_params(const double* p13, double t, double* p11) {
+  auto fin = [](double v) { return v == v && v - v == 0.0; };
+  if (!p13 || !p11 || !fin(t)) return FK_ERR_INVALID_ARG;
+  for (int k : {3, 4, 5, 6, 12})
+    if (!(p13[k] > 0.0) || !fin(p13[k])) return FK_ERR_INVALID_ARG;
+  quench_params(p13, t, p11);
+  return FK_OK;
+}
+
 fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* region,
                          const fk_coeffs* coeffs, int q_per_dim, double dt, int n_steps,
                          fk_precision prec, fk_path path) {
@@ -1096,7 +1158,7 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
     // reach |shift| + span / 2 cells into the box from a reflecting face.
     int w = 3;
     double smax[3], bmax3[3];
-    if (coeffs->family == FK_RUNAWAY_3D) {
+    if (runaway_family(coeffs->family)) {
       runaway_bounds(p, smax, bmax3);
     } else {
       for (int m = 0; m < 3; ++m) {
@@ -1109,7 +1171,7 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
                           p->h[m];
       const double shift = bmax3[m] * dt / p->h[m];
       w = std::max(w, (int)floor(span * (1.0 + 1e-6) + 1e-3) + 3);
-      if (coeffs->family == FK_RUNAWAY_3D)
+      if (runaway_family(coeffs->family))
         w = std::max(w, (int)floor((shift + 0.5 * span) * (1.0 + 1e-6) + 1e-3) + 2);
       p->reach[m] = shift + 0.5 * span;
       p->halo[m] = (int)ceil(p->reach[m]) + 1;

@@ -20,7 +20,8 @@ _DTYPE = {"fp32": torch.float32, "fp64": torch.float64}
 _PREC = {"fp32": L.FK_FP32, "fp64": L.FK_FP64}
 _PATH = {"matrix_free": L.FK_PATH_MATRIX_FREE, "csr": L.FK_PATH_CSR}
 _FAMILY = {"const_drift": L.FK_CONST_DRIFT, "cellular_flow": L.FK_CELLULAR_FLOW,
-           "paper_cellular": L.FK_PAPER_CELLULAR, "runaway": L.FK_RUNAWAY_3D}
+           "paper_cellular": L.FK_PAPER_CELLULAR, "runaway": L.FK_RUNAWAY_3D,
+           "runaway_quench": L.FK_RUNAWAY_QUENCH_3D}
 
 
 def _ptr(t: torch.Tensor | None):
@@ -39,6 +40,18 @@ def gauss_hermite(q: int):
     w = (ctypes.c_double * q)()
     L.check("fk_gauss_hermite", lib.fk_gauss_hermite(q, a, w))
     return list(a), list(w)
+
+
+def runaway_quench_params(params, t: float):
+    """The runaway-model constants (E, tau, Z, delta, nu_ee, v_T, r_D, W,
+    Delta_p, V_0, D_0) at time t of the thermal-quench variant with the 13
+    parameters (E_0, tau, Z, T0, Tf, Ttilde, t_star, r_D, W, Delta_p, V_0,
+    D_0, mc2)."""
+    lib = L.load()
+    q = (ctypes.c_double * 16)(*[float(v) for v in params])
+    out = (ctypes.c_double * 11)()
+    L.check("fk_runaway_quench_params", lib.fk_runaway_quench_params(q, float(t), out))
+    return list(out)
 
 
 @dataclass

@@ -6,6 +6,7 @@ import math
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -162,3 +163,36 @@ def test_static_entry_rejects_axes(L):
     st = lib.fk_solve_static(ctypes.byref(g), ctypes.byref(c), 4, 1e-3, 5, 0, None,
                              ctypes.c_void_p(256), None)
     assert st == 2
+
+
+QUENCH = (0.1, 6000.0, 1.0, 3.0, 0.005, 3.0, 0.5, 0.0, 1e-4, 2.0, 0.0, 0.01, 511.0)
+
+
+def test_runaway_quench_params_match_oracle(L, oracle):
+    """The library's thermal-quench schedule (host code, no GPU) against the
+    oracle's, written separately: the same constants at every time."""
+    lib = L.load()
+    q = (ctypes.c_double * 16)(*QUENCH)
+    out = (ctypes.c_double * 11)()
+    for t in (0.0, 0.05, 0.7, 3.0, 40.0):
+        assert lib.fk_runaway_quench_params(q, t, out) == 0
+        np.testing.assert_allclose(list(out), oracle.quench_params(QUENCH, t), rtol=1e-15,
+                                   atol=0.0)
+    assert lib.fk_runaway_quench_params(None, 0.0, out) == 1
+    assert lib.fk_runaway_quench_params(q, float("nan"), out) == 1
+    bad = (ctypes.c_double * 16)(*QUENCH)
+    bad[6] = 0.0  # t_star
+    assert lib.fk_runaway_quench_params(bad, 0.0, out) == 1
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(family=4, p=QUENCH), 1),  # two-dimensional grid
+    (dict(dim=3, n=(9, 9, 9), family=4, p=QUENCH[:3] + (0.0,) + QUENCH[4:],
+          lo=(2.0, -1.0, 0.0), hi=(8.0, 1.0, 1.0)), 1),  # T0 = 0
+    (dict(dim=3, n=(9, 9, 9), family=4, p=QUENCH[:12] + (-511.0,),
+          lo=(2.0, -1.0, 0.0), hi=(8.0, 1.0, 1.0)), 1),  # mc2 < 0
+    (dict(dim=3, n=(9, 9, 9), family=4, p=QUENCH, lo=(2.0, -1.0, 0.0), hi=(8.0, 1.0, 1.0),
+          path=1), 2),
+])
+def test_plan_create_rejects_quench(L, kw, status):
+    test_plan_create_rejects(L, kw, status)

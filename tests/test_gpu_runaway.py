@@ -134,3 +134,53 @@ def test_runaway_workload_sampled_step(fk, oracle):
     want = oracle.step_nodes(_grid(oracle, w), oracle.RUNAWAY, list(w["params"]), w["q"],
                              w["dt"], n, u1, nodes, nthreads=NCPU)
     assert np.abs(got[nodes] - want).max() <= 1e-5
+
+
+# the thermal-quench variant (end of Sec. 4.3): the paper's constants with
+# E_0 = 0.1 and t_star = 0.5, on p in (2, 8), so that the field grows and
+# the collisions with it over the march
+QUENCH = (0.1, 6000.0, 1.0, 3.0, 0.005, 3.0, 0.5, 0.0, 1e-4, 2.0, 0.0, 0.01, 511.0)
+
+
+def _wq(precision="fp64", n_steps=25):
+    return dict(n=(21, 17, 11), lo=(2.0, -1.0, 0.0), hi=(8.0, 1.0, 1.0),
+                family="runaway_quench", params=QUENCH, q=4, dt=0.02, n_steps=n_steps,
+                precision=precision)
+
+
+def _spec_q(fk, w):
+    return fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family="runaway_quench",
+                       params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
+                       precision=w["precision"])
+
+
+def _oracle_q(oracle, w, k=None):
+    return oracle.march(_grid(oracle, w), oracle.RUNAWAY_QUENCH, list(w["params"]), w["q"],
+                        w["dt"], k or w["n_steps"], 0, nthreads=NCPU)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_quench_vs_oracle(fk, oracle, precision, tol):
+    import torch
+    w = _wq(precision)
+    plan = fk.Plan(_spec_q(fk, w))
+    got = plan.solve().double().cpu().numpy()
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    plan.close()
+    assert np.abs(got - _oracle_q(oracle, w)).max() <= tol
+
+
+def test_quench_horizons(fk, oracle):
+    """Every horizon of the non-autonomous model (Algorithm 1): horizon k
+    marches k steps with the constants of t_{k-1}, ..., t_0."""
+    import torch
+    w = _wq(n_steps=12)
+    plan = fk.Plan(_spec_q(fk, w))
+    hz = plan.solve_horizons()
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    hz = hz.cpu().numpy()
+    plan.close()
+    for k in (1, 6, 12):
+        assert np.abs(hz[k - 1] - _oracle_q(oracle, w, k)).max() <= 1e-12, k

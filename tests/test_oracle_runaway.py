@@ -238,3 +238,54 @@ def _face_rule_nodes(oracle, g, n, u, params, dt, q, a, w, crossed):
                 want.append(acc)
     got = oracle.step_nodes(g, oracle.RUNAWAY, params, q, dt, 0, u, np.array(nodes))
     np.testing.assert_allclose(got, want, atol=1e-14)
+
+
+# ------------------------------------------------ the thermal-quench variant
+
+QUENCH = (0.1, 6000.0, 1.0, 3.0, 0.005, 3.0, 0.5, 0.0, 1e-4, 2.0, 0.0, 0.01, 511.0)
+
+
+def test_quench_schedule_limits(oracle):
+    """At t = 0 with T0 = Ttilde the model is in its normalised units
+    (v_T = nu_ee = 1, E = E_0, delta = sqrt(2 T0 / mc2)); long after the
+    quench T = Tf; the temperature falls monotonically in between."""
+    p0 = oracle.quench_params(QUENCH, 0.0)
+    assert p0[0] == pytest.approx(0.1, rel=1e-15) and p0[5] == pytest.approx(1.0, rel=1e-15)
+    assert p0[4] == pytest.approx(1.0, rel=1e-15)
+    assert p0[3] == pytest.approx(math.sqrt(6.0 / 511.0), rel=1e-15)
+    assert list(p0[[1, 2, 6, 7, 8, 9, 10]]) == [6000.0, 1.0, 0.0, 1e-4, 2.0, 0.0, 0.01]
+    late = oracle.quench_params(QUENCH, 60.0)  # 120 cooling times
+    Tf = 0.005
+    assert late[5] == pytest.approx(math.sqrt(Tf / 3.0), rel=1e-12)
+    assert late[0] == pytest.approx(0.1 * (3.0 / Tf) ** 1.5, rel=1e-12)
+    assert late[3] == pytest.approx(math.sqrt(2 * Tf / 511.0), rel=1e-12)
+    vt = [oracle.quench_params(QUENCH, t)[5] for t in np.linspace(0, 5, 41)]
+    assert all(a > b for a, b in zip(vt, vt[1:]))
+
+
+def test_quench_step_uses_t_n(oracle):
+    """Step n of the quench variant is the static model's step with the
+    constants of t_n = n dt: the same numbers, node by node."""
+    g = oracle.Grid((13, 9, 7), (2.0, -1.0, 0.0), (8.0, 1.0, 1.0))
+    u = np.random.default_rng(3).uniform(0, 1, g.shape)
+    dt = 0.02
+    for n in (0, 7, 30):
+        got = oracle.march(g, oracle.RUNAWAY_QUENCH, list(QUENCH), 3, dt, n + 1, n, u)
+        want = oracle.march(g, oracle.RUNAWAY, list(oracle.quench_params(QUENCH, n * dt)), 3, dt,
+                            n + 1, n, u)
+        assert np.array_equal(got, want), n
+
+
+def test_quench_without_cooling_is_static(oracle):
+    """With t_star -> infinity the temperature stays at T0 and the quench
+    march is the static march with the t = 0 constants."""
+    q = list(QUENCH)
+    q[6] = 1e300
+    g = oracle.Grid((13, 9, 7), (2.0, -1.0, 0.0), (8.0, 1.0, 1.0))
+    a = oracle.march(g, oracle.RUNAWAY_QUENCH, q, 3, 0.02, 15, 0, nthreads=4)
+    b = oracle.march(g, oracle.RUNAWAY, list(oracle.quench_params(q, 0.0)), 3, 0.02, 15, 0,
+                     nthreads=4)
+    assert np.abs(a - b).max() <= 1e-14
+    # with cooling the answer moves away from the frozen one
+    c = oracle.march(g, oracle.RUNAWAY_QUENCH, list(QUENCH), 3, 0.02, 15, 0, nthreads=4)
+    assert np.abs(c - b).max() > 1e-3
