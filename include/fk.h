@@ -101,7 +101,11 @@ typedef enum fk_path { FK_PATH_MATRIX_FREE = 0, FK_PATH_CSR = 1 } fk_path;
  *                     fk_runaway_quench_params returns for t (the paper's
  *                     values: 1e-3, 6000, 1, 3, 0.005, 3, t_star, 0, 1e-4,
  *                     2, 0, D_0, with temperatures in keV and mc2 = 511).
- *                     Same box, faces and restrictions as FK_RUNAWAY_3D. */
+ *                     Same box, faces and restrictions as FK_RUNAWAY_3D;
+ *                     T0, Tf, Ttilde, t_star and mc2 must be positive and
+ *                     ln Lambda(T) positive at T0, Tf and Ttilde
+ *                     (FK_ERR_INVALID_ARG).  Plan creation evaluates the
+ *                     coefficients at every time step to bound the window. */
 enum {
   FK_CONST_DRIFT = 0,
   FK_CELLULAR_FLOW = 1,

@@ -237,6 +237,11 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
     if (quench_family(c->family)) {
       for (int k : {3, 4, 5, 6, 12})
         if (!(q[k] > 0.0)) return FK_ERR_INVALID_ARG;
+      // ln Lambda must stay positive at every temperature the schedule
+      // passes (T between T0 and Tf) and at Ttilde
+      const double c0 = 14.9 - 0.5 * log(0.28);
+      for (int k : {3, 4, 5})
+        if (!(c0 + log(q[k]) > 0.0)) return FK_ERR_INVALID_ARG;
     }
     double q11[11];
     if (quench_family(c->family))

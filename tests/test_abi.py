@@ -191,6 +191,8 @@ def test_runaway_quench_params_match_oracle(L, oracle):
           lo=(2.0, -1.0, 0.0), hi=(8.0, 1.0, 1.0)), 1),  # T0 = 0
     (dict(dim=3, n=(9, 9, 9), family=4, p=QUENCH[:12] + (-511.0,),
           lo=(2.0, -1.0, 0.0), hi=(8.0, 1.0, 1.0)), 1),  # mc2 < 0
+    (dict(dim=3, n=(9, 9, 9), family=4, p=QUENCH[:4] + (1e-8,) + QUENCH[5:],
+          lo=(2.0, -1.0, 0.0), hi=(8.0, 1.0, 1.0)), 1),  # ln Lambda(Tf) < 0
     (dict(dim=3, n=(9, 9, 9), family=4, p=QUENCH, lo=(2.0, -1.0, 0.0), hi=(8.0, 1.0, 1.0),
           path=1), 2),
 ])
