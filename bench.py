@@ -185,7 +185,8 @@ def oracle_rate(w, max_seconds: float = 20.0):
     workload's march (consecutive time steps from the terminal field)."""
     from oracle import fk_oracle as O
     fam = {"const_drift": O.CONST_DRIFT, "cellular_flow": O.CELLULAR_FLOW,
-           "paper_cellular": O.PAPER_CELLULAR}[w["family"]]
+           "paper_cellular": O.PAPER_CELLULAR, "runaway": O.RUNAWAY,
+           "runaway_quench": O.RUNAWAY_QUENCH}[w["family"]]
     g = O.Grid(tuple(w["n"]), tuple(w["lo"]), tuple(w["hi"]), int(w.get("periodic_x", False)),
                fk_inputs.axes_of(w))
     cores = os.cpu_count() or 1
@@ -211,7 +212,8 @@ def run_reference(args, rank: int):
     from oracle import fk_oracle as O
     O.build()
     fams = {"const_drift": O.CONST_DRIFT, "cellular_flow": O.CELLULAR_FLOW,
-            "paper_cellular": O.PAPER_CELLULAR}
+            "paper_cellular": O.PAPER_CELLULAR, "runaway": O.RUNAWAY,
+            "runaway_quench": O.RUNAWAY_QUENCH}
     # one benchmark step of the reference arm = one time step of the march
     # (of every instance, for the batched sweep): a bounded sample of the
     # workload, so that K + W steps take seconds to a minute
