@@ -100,12 +100,19 @@ def workload_of(args):
 
 def units_per_solve(w) -> float:
     """Node-quadrature updates of one march: the updated nodes (interior
-    ones; a periodic x axis has n - 1 distinct columns, all updated) times
-    the points per node times the steps."""
-    interior = 1
+    ones; a periodic x axis has n - 1 distinct columns, all updated; the
+    runaway model also updates the nodes of its mirroring faces, every xi
+    node and r = 0) times the points per node times the steps."""
+    updated = 1
+    runaway = w["family"] in ("runaway", "runaway_quench")
     for m, n in enumerate(w["n"]):
-        interior *= (n - 1) if (m == 0 and w.get("periodic_x")) else (n - 2)
-    return float(interior) * (w["q"] ** len(w["n"])) * w["n_steps"]
+        if m == 0 and w.get("periodic_x"):
+            updated *= n - 1
+        elif runaway and m > 0:
+            updated *= n if m == 1 else n - 1
+        else:
+            updated *= n - 2
+    return float(updated) * (w["q"] ** len(w["n"])) * w["n_steps"]
 
 
 def l2_note(w) -> str:
