@@ -46,7 +46,7 @@ extern "C" {
 typedef enum fk_status {
   FK_OK = 0,
   FK_ERR_INVALID_ARG = 1, /* a NULL, out-of-range or inconsistent argument */
-  FK_ERR_UNSUPPORTED = 2, /* valid, but not a case this build implements  */
+  FK_ERR_UNSUPPORTED = 2, /* valid, but not a case the library implements */
   FK_ERR_OOM = 3,         /* device allocation failed                     */
   FK_ERR_CUDA = 4,        /* a CUDA runtime call failed                   */
   FK_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up           */
