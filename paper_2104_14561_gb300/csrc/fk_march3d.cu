@@ -23,9 +23,10 @@
 // Two launches per step:
 //  * k_rec3d writes one record {u, hx u_x, hy u_y, hz u_z} per node (the
 //    scaled PCHIP slopes of Eq. (e300) with the end rule that gives node 0
-//    the slope of node 1 and node n-1 that of node n-2), and 1 into u^n at
-//    every boundary node (Eq. (e3));
-//  * k_step3d forms each interior node's 1D weights in registers and sums
+//    the slope of node 1 and node n-1 that of node n-2), and the held value
+//    into u^n at every node of an absorbing face (Eq. (e3): 1, or the face's
+//    exit value in the runaway model);
+//  * k_step3d forms each updated node's 1D weights in registers and sums
 //    the W^3 records of its window, read through L1/L2 (a warp's 32
 //    consecutive x-nodes read overlapping, contiguous windows).
 // Positions are taken relative to the node in cells: point p of axis m is
