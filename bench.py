@@ -42,8 +42,6 @@ UNIT = "node-quadrature updates/s"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FLOP_PER_UPDATE = 26                # 13 multiply-adds per query: 12 Hermite terms + the weighted sum
 FLOP_PER_UPDATE_3D = 66             # 33 multiply-adds: 8 corners x (value + 3 partials) + the sum
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (profiling recipe)
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 HBM_FALLBACK_GBS = 6800.0
 
@@ -55,6 +53,26 @@ def hbm_peak():
         return v, "measured"
     except (OSError, ValueError, KeyError):
         return HBM_FALLBACK_GBS, "fallback"
+
+
+def measure_alu_peaks(fk, stream, local_rank: int) -> dict:
+    """FP32 and FP64 fused multiply-add throughput of this GPU, measured with
+    the library's register-resident FMA-chain kernel (CUDA events), with the
+    SM clock sampled while it runs.  The FP32 peak is the larger of the
+    scalar and the packed f32x2 rates (the step kernels use both forms)."""
+    import torch
+    props = torch.cuda.get_device_properties(local_rank)
+    clk = ClockSampler(local_rank)
+    clk.start()
+    f32 = fk.measure_fma_rate("fp32", False, 0.25, stream)
+    f32x2 = fk.measure_fma_rate("fp32", True, 0.25, stream)
+    f64 = fk.measure_fma_rate("fp64", False, 0.25, stream)
+    clocks = clk.stop()
+    return {"fp32_tflops": max(f32, f32x2) / 1e12, "fp32_scalar_tflops": f32 / 1e12,
+            "fp32_packed_tflops": f32x2 / 1e12, "fp64_tflops": f64 / 1e12,
+            "sm_count": props.multi_processor_count, "sm_mhz_median": clocks.get("sm_mhz"),
+            "how": "fk_measure_fma_rate: 8 independent FMA chains per thread on every thread "
+                   "slot of every SM, CUDA-event timed (about 0.25 s per precision)"}
 
 
 def csr_bytes_per_step(w, nnz: int) -> float:
@@ -77,6 +95,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cellular_1025x513")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 march and the adjoint beside the headline march")
     # profiling aids: a smaller case of the same workload (not a benchmark line)
     ap.add_argument("--time-steps", type=int, default=None,
                     help="override the workload's number of time steps")
@@ -85,6 +105,12 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default=None,
                     help="override the workload's precision")
     return ap.parse_args()
+
+
+def headline(args) -> bool:
+    """The workload the metric is quoted on, unmodified."""
+    return (args.workload == "cellular_1025x513" and not args.time_steps and not args.grid
+            and not args.precision)
 
 
 def workload_of(args):
@@ -296,22 +322,7 @@ def run_batched(args, rank: int, world: int, local_rank: int):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def timed(fn):
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                fn()
-        stream.synchronize()
-        ms = []
-        with torch.cuda.stream(stream):
-            for i in range(args.steps):
-                flush.fill_(float(i))
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                fn()
-                b.record(stream)
-                b.synchronize()
-                ms.append(a.elapsed_time(b))
-        return sum(ms) / len(ms)
+        return timed_ms(fn, stream, flush, args.warmup, args.steps)
 
     def batched():
         fk.solve_batched(plans, None, outs, stream=stream)
@@ -385,22 +396,7 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
     units = units_per_solve(w)
 
     def timed(fn):
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                fn()
-        stream.synchronize()
-        ms = []
-        with torch.cuda.stream(stream):
-            for i in range(args.steps):
-                flush.fill_(float(i))
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                fn()
-                b.record(stream)
-                b.synchronize()
-                ms.append(a.elapsed_time(b))
-        return sum(ms) / len(ms)
+        return timed_ms(fn, stream, flush, args.warmup, args.steps)
 
     clk = ClockSampler(local_rank)
     clk.start()
@@ -452,23 +448,9 @@ def run_horizons(args, rank: int, world: int, local_rank: int):
     units = units_per_solve(w) / N * field_steps
 
     def timed(fn):
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                fn()
-        stream.synchronize()
-        ms = []
-        with torch.cuda.stream(stream):
-            for i in range(args.steps):
-                flush.fill_(float(i))
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                fn()
-                b.record(stream)
-                b.synchronize()
-                ms.append(a.elapsed_time(b))
-        return sum(ms) / len(ms)
+        return timed_ms(fn, stream, flush, args.warmup, args.steps)
 
+    peaks = measure_alu_peaks(fk, stream, local_rank)
     clk = ClockSampler(local_rank)
     clk.start()
     ms_h = timed(lambda: plan.solve_horizons(None, out_all, stream=stream))
@@ -483,7 +465,7 @@ def run_horizons(args, rank: int, world: int, local_rank: int):
         plan.close()
         return
     flop = FLOP_PER_UPDATE * units
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = peaks["fp32_tflops"]
     achieved = flop / (ms_h * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": whole_job_rate(units, world, ms_max), "unit": UNIT,
@@ -496,8 +478,9 @@ def run_horizons(args, rank: int, world: int, local_rank: int):
                    "l2": "flushed (512 MB write) before every timed call; the "
                          f"{2 * N * math.prod(w['n']) * 4 / 1e9:.1f} GB of fields exceed the L2"},
         "roofline": {"kernel": "k_step2dm (all horizons of a step per launch)", "bound": "alu",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None},
+                     "achieved": achieved, "peak": peak, "peak_source": "measured",
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None},
+        "alu_peaks": peaks,
         "single_march_ms": ms_single,
         "field_step_us": ms_h * 1e3 / field_steps,
         "single_step_us": ms_single * 1e3 / N,
@@ -508,7 +491,110 @@ def run_horizons(args, rank: int, world: int, local_rank: int):
     plan.close()
 
 
-# ------------------------------------------------------------ ranks -----
+def timed_ms(fn, stream, flush, warmup: int, steps: int) -> float:
+    """Mean CUDA-event time (ms) of fn() on `stream` over `steps` calls after
+    `warmup` untimed ones, with L2 flushed (a write larger than L2) before
+    each timed call."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+    stream.synchronize()
+    ms = []
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(float(i))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+    return sum(ms) / len(ms)
+
+
+def plan_of(fk, w, **over):
+    """A plan of workload w (entries of `over` replace the workload's)."""
+    w = dict(w, **over)
+    return fk.Plan(fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
+                               params=w["params"], q=w["q"], dt=w["dt"], n_steps=w["n_steps"],
+                               precision=w["precision"], path=w.get("path", "matrix_free"),
+                               periodic_x=w.get("periodic_x", False),
+                               axes=fk_inputs.axes_of(w)))
+
+
+def fp64_line(fk, w, stream, flush, steps: int, peaks: dict) -> dict:
+    """The same march in FP64 (the metric's FP64 half): whole marches timed
+    with CUDA events, rate, algorithmic HBM bytes and the ALU roofline
+    against the measured FP64 FMA rate."""
+    plan = plan_of(fk, w, precision="fp64")
+    out = plan.empty()
+    ms = timed_ms(lambda: plan.solve(None, out, stream=stream), stream, flush, 1, steps)
+    if plan.last_device_error() != 0:
+        raise RuntimeError("device-side range check fired in the FP64 march")
+    info = plan.info()
+    plan.close()
+    w64 = dict(w, precision="fp64")
+    units = units_per_solve(w64)
+    launch_ms = ms / w["n_steps"]
+    flop_launch = FLOP_PER_UPDATE * units / w["n_steps"]
+    achieved = flop_launch / (launch_ms * 1e-3) / 1e12
+    peak = peaks["fp64_tflops"]
+    kname = {"direct": "k_step2d", "window": "k_step2dw", "masked": "k_step2dm"}.get(
+        info.get("step_kernel"), info.get("step_kernel"))
+    return {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "warmup": 1, "dtype": "f64",
+            "hbm_gbs_algorithmic": hbm_bytes_per_solve(w64) / (ms * 1e-3) / 1e9,
+            "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
+                         "peak_source": "measured", "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": profile_traffic(kname, "cellular_1025x513_fp64"),
+                         "flop_per_launch": flop_launch, "launch_ms": launch_ms,
+                         "step_kernel": info.get("step_kernel")}}
+
+
+def adjoint_line(fk, w, stream, flush, steps: int, peaks: dict, forward_ms: float) -> dict:
+    """The adjoint of the same march (the metric's adjoint/forward): dL/d(A,
+    eps, omega, D) and dL/du^N of the mean of u^0 over the interior nodes,
+    checkpoints every 50 steps, FP32 march with the FP64 gradient
+    reduction.  One call = forward pass with checkpoints, segment recompute
+    and the backward pass; the backward-step kernel's launches are timed
+    live with CUDA events around each launch (fk_adjoint_kernel_times)."""
+    import torch
+    plan = plan_of(fk, w)
+    ny, nx = plan.shape
+    cot = torch.zeros(plan.shape, dtype=torch.float64, device=plan.device)
+    cot[1:-1, 1:-1] = 1.0 / ((nx - 2) * (ny - 2))
+    call = lambda: plan.adjoint(cot, None, checkpoint_every=50, stream=stream)  # noqa: E731
+    ms = timed_ms(call, stream, flush, 1, steps)
+    plan.adjoint_kernel_times(True)
+    call()
+    kms, launches = plan.adjoint_kernel_times(False)
+    if plan.last_device_error() != 0:
+        raise RuntimeError("device-side range check fired in the adjoint")
+    info = plan.info()
+    plan.close()
+    units = units_per_solve(w)
+    kname = {"scatter": "k_adj_scatter", "masked": "k_adj_masked"}.get(info.get("adjoint_kernel"),
+                                                                       "?")
+    launch_ms = kms / max(launches, 1)
+    # the transposed step applies the transpose of the step's linear map: the
+    # same 13 multiply-adds per node-quadrature update as the forward step
+    flop_launch = FLOP_PER_UPDATE * units / w["n_steps"]
+    achieved = flop_launch / (launch_ms * 1e-3) / 1e12
+    peak = peaks["fp32_tflops"]
+    return {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "warmup": 1, "adjoint_over_forward": ms / forward_ms, "checkpoint_every": 50,
+            "objective": "mean of u^0 over interior nodes; gradients in (A, eps, omega, D) "
+                         "and u^N",
+            "backward_kernel_ms_per_launch": launch_ms, "backward_launches": launches,
+            "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
+                         "peak_source": "measured", "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": profile_traffic(kname, "adjoint_1025x513"),
+                         "flop_per_launch": flop_launch, "launch_ms": launch_ms}}
+
+
+# ------------------------------------------------------------- ranks -----
 def max_over_ranks(value: float, dist=None, device=None) -> float:
     """The largest per-rank figure over all ranks (the value itself when the
     job has one rank)."""
@@ -550,6 +636,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if dist is not None:
             dist.barrier()
 
+    peaks = measure_alu_peaks(fk, stream, local_rank)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             plan.solve(None, out, stream=stream)
@@ -603,6 +690,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     e2e_value = whole_job_rate(units, world, max_over_ranks(sum(e_ms) / len(e_ms), dist, dev))
     field_bytes = int(host_in.numel() * host_in.element_size())
 
+    # the metric's FP64 and adjoint/forward halves, on the headline workload
+    extras = {}
+    if rank == 0 and headline(args) and not args.no_extras:
+        k = max(1, min(args.steps, 3))
+        extras["fp64"] = fp64_line(fk, w, stream, flush, k, peaks)
+        extras["adjoint"] = adjoint_line(fk, w, stream, flush, k, peaks, ms_step)
+
     if rank != 0:
         return
     info = plan.info()
@@ -620,11 +714,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         # two launches per time step (records, then the window sums); the
         # time of both is charged to the step, so the fraction is a floor
         flops_launch = FLOP_PER_UPDATE_3D * units / w["n_steps"]
-        peak_flops = (SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 if w["precision"] == "fp32"
-                      else FP64_PEAK_TFLOPS * 1e12)
+        peak_flops = 1e12 * (peaks["fp32_tflops"] if w["precision"] == "fp32"
+                             else peaks["fp64_tflops"])
         achieved = flops_launch / (launch_ms * 1e-3)
         roofline = {"kernel": "k_step3d (with k_rec3d: one time step)", "bound": "alu",
-                    "achieved": achieved / 1e12, "peak": peak_flops / 1e12, "unit": "TFLOP/s",
+                    "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
+                    "peak_source": "measured", "unit": "TFLOP/s",
                     "frac": achieved / peak_flops,
                     "traffic": profile_traffic("k_step3d", args.workload),
                     "flop_per_launch": flops_launch, "launch_ms": launch_ms,
@@ -632,8 +727,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                     "step_kernel": info.get("step_kernel")}
     else:
         flops_launch = FLOP_PER_UPDATE * units / w["n_steps"]
-        peak_flops = (SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 if w["precision"] == "fp32"
-                      else FP64_PEAK_TFLOPS * 1e12)
+        peak_flops = 1e12 * (peaks["fp32_tflops"] if w["precision"] == "fp32"
+                             else peaks["fp64_tflops"])
         achieved = flops_launch / (launch_ms * 1e-3)
         kname = ({"resident": "k_march1d", "cluster": "k_march1d_cluster"}.get(
                      info.get("step_kernel"), "k_step1d")
@@ -641,7 +736,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                  {"direct": "k_step2d", "window": "k_step2dw",
                   "masked": "k_step2dm"}[info.get("step_kernel", "direct")])
         roofline = {"kernel": kname, "bound": "alu", "achieved": achieved / 1e12,
-                    "peak": peak_flops / 1e12, "unit": "TFLOP/s", "frac": achieved / peak_flops,
+                    "peak": peak_flops / 1e12, "peak_source": "measured", "unit": "TFLOP/s",
+                    "frac": achieved / peak_flops,
                     "traffic": profile_traffic(kname, args.workload),
                     "flop_per_launch": flops_launch, "launch_ms": launch_ms,
                     "window_rows": info.get("window_rows", 0),
@@ -665,6 +761,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                       * w["n_steps"] + 1),
         "clocks": clocks,
         "wall_s_timed_region": wall,
+        "alu_peaks": peaks,
+        **extras,
     }
     if not args.no_cpu_baseline:
         try:

@@ -335,6 +335,19 @@ fk_status fk_adjoint(fk_plan *plan, const void *u_terminal,
                      void *du_terminal, int checkpoint_every,
                      cudaStream_t stream);
 
+/* fk_adjoint_kernel_times -- a measurement aid (no counterpart in the
+ * paper).  With record = 1, later fk_adjoint calls on this plan record a
+ * CUDA event on their stream right before and right after each launch of
+ * the backward-step kernel (the transposed step; the slope transpose that
+ * follows it is outside the pair); with record = 0 they stop.  Each call of
+ * this function first waits for the events of the last recorded fk_adjoint
+ * and writes their summed elapsed time (ms) to *kernel_ms and the number of
+ * pairs to *launches (0 and 0 if nothing was recorded; either pointer may
+ * be NULL), then sets the recording state.  The events are created by the
+ * first recorded fk_adjoint (2 N of them) and freed with the plan. */
+fk_status fk_adjoint_kernel_times(fk_plan *plan, int record, double *kernel_ms,
+                                  int *launches);
+
 /* Text for a status code (static storage). */
 const char *fk_status_string(fk_status status);
 
@@ -348,10 +361,8 @@ fk_status fk_last_device_error(fk_plan *plan);
  * problem, for callers that cannot allocate device memory.  The paper has no
  * counterpart; this exists only for such callers: applications whose own
  * pool allocator owns all device memory and forbids libraries from calling
- * cudaMalloc beside it, code that enqueues work while a stream is being
- * captured into a CUDA graph (where an allocation is refused or breaks the
- * capture), and latency-bound loops that cannot afford the device-wide
- * synchronisation of cudaMalloc / cudaFree.
+ * cudaMalloc beside it, and latency-bound loops that cannot afford the
+ * device-wide synchronisation of cudaMalloc / cudaFree.
  *
  * It calls no cudaMalloc, cudaFree or other allocating routine, host or
  * device.  Everything besides the caller's buffers (one scratch field, the
@@ -359,28 +370,58 @@ fk_status fk_last_device_error(fk_plan *plan);
  * 16 MiB, which every GPU that loads this library holds until the process
  * exits.
  *   grid, coeffs, q_per_dim, dt, n_steps, prec  as for fk_plan_create, with
- *               grid->dim = 2, a uniform mesh (axis[] NULL) and the box's
- *               faces all absorbing (else FK_ERR_UNSUPPORTED); families
- *               FK_CONST_DRIFT and FK_CELLULAR_FLOW.
+ *               grid->dim = 2 and a uniform mesh (axis[] NULL); families
+ *               FK_CONST_DRIFT and FK_CELLULAR_FLOW.  There is no region
+ *               argument: every face of the box absorbs.
  *   u_terminal  device pointer to u^N, or NULL for chi; may equal u_out.
  *   u_out       device pointer, receives u^0.
  * Size limit: 256 + 4 n[0] e + 2 n[1] e + n[0] n[1] e bytes (e = 4 for FP32,
  * 8 for FP64; each of the three tables rounded up to 256 B) must fit in
  * 16 MiB -- about 4.1 million nodes in FP32, 2.09 million in FP64.  Larger
  * problems get FK_ERR_INVALID_ARG before anything is enqueued.
+ * A CUDA error already pending in the calling thread (from earlier work of
+ * the caller) gives FK_ERR_CUDA before anything is enqueued; the error is
+ * left pending for the caller.
  * The first call on each device does a one-time set-up on that device (it
  * looks up the device address of the static array and opts the step kernels
  * into large shared memory); make that first call before any stream
- * capture.  Every call on a device uses the same array and overwrites what
- * the previous call left there: calls whose work overlaps on the GPU (two
- * streams, two host threads) race and corrupt each other's results.  The
- * device error word is cleared by each call but not reported; use a plan
- * and fk_last_device_error to see range checks.
+ * capture.  The set-up is kept for the life of the process: resetting the
+ * device (cudaDeviceReset) after the first call is not supported.  Every
+ * call on a device uses the same array and overwrites what the previous
+ * call left there: calls whose work overlaps on the GPU (two streams, two
+ * host threads) race and corrupt each other's results.
  * ---------------------------------------------------------------------- */
 fk_status fk_solve_static(const fk_grid *grid, const fk_coeffs *coeffs,
                           int q_per_dim, double dt, int n_steps,
                           fk_precision prec, const void *u_terminal,
                           void *u_out, cudaStream_t stream);
+
+/* fk_static_last_device_error -- the device error word of fk_solve_static
+ * calls on the current device (like fk_last_device_error for a plan; no
+ * counterpart in the paper).  It waits for all work on the current device
+ * (cudaDeviceSynchronize), then reads and clears the word in the static
+ * array: FK_OK, FK_ERR_DEVICE (a step kernel's range check fired: a
+ * shifted point fell outside its tile's halo, and that result is wrong) or
+ * FK_ERR_CUDA.  Each fk_solve_static call clears the word at the start of
+ * its own work on the GPU, so the answer covers the last call.  Allocates
+ * nothing; not for use during stream capture. */
+fk_status fk_static_last_device_error(void);
+
+/* ------------------------------------------------------------------------
+ * fk_measure_fma_rate -- a measurement aid with no counterpart in the
+ * paper: the fused multiply-add throughput of the current device, the
+ * denominator of the march kernels' ALU rooflines.  Every thread slot of
+ * every SM runs eight independent FMA chains from registers; the kernel is
+ * timed with CUDA events on `stream` and the call waits for it.
+ *   prec     FK_FP32 or FK_FP64.
+ *   packed   FK_FP32 only: 1 times the packed f32x2 form (two FMAs per
+ *            instruction), 0 the scalar form.
+ *   seconds  target duration of the timed launch, (0, 10].
+ *   flop_per_s  receives 2 x FMAs per second (0 on error).
+ * Errors: FK_ERR_INVALID_ARG, FK_ERR_CUDA.  Allocates nothing.
+ * ---------------------------------------------------------------------- */
+fk_status fk_measure_fma_rate(fk_precision prec, int packed, double seconds,
+                              double *flop_per_s, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

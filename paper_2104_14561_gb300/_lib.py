@@ -26,7 +26,8 @@ FK_PERIODIC_X = 0x3C
 EXPORTS = ("fk_plan_create", "fk_plan_destroy", "fk_plan_get_info", "fk_gauss_hermite",
            "fk_solve", "fk_march", "fk_solve_horizons", "fk_solve_batched", "fk_adjoint",
            "fk_status_string", "fk_last_device_error", "fk_solve_static",
-           "fk_runaway_quench_params")
+           "fk_static_last_device_error", "fk_runaway_quench_params", "fk_measure_fma_rate",
+           "fk_adjoint_kernel_times")
 
 
 class FkError(RuntimeError):
@@ -108,6 +109,14 @@ def load(build_if_missing: bool = False):
     lib.fk_status_string.restype = ctypes.c_char_p
     lib.fk_last_device_error.argtypes = [vp]
     lib.fk_last_device_error.restype = st
+    lib.fk_static_last_device_error.argtypes = []
+    lib.fk_static_last_device_error.restype = st
+    lib.fk_measure_fma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_double), vp]
+    lib.fk_measure_fma_rate.restype = st
+    lib.fk_adjoint_kernel_times.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_int)]
+    lib.fk_adjoint_kernel_times.restype = st
     _lib = lib
     return lib
 

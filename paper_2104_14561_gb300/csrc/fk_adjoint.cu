@@ -973,8 +973,15 @@ cudaError_t launch_adj_masked(const AdjArgs<float>& g, int q, cudaStream_t s) {
 // Whether the backward steps of plan p use the masked window form (FP32
 // plans eligible for the masked step kernel; FK_ADJ_KERNEL=scatter|masked
 // chooses explicitly where both apply), and its tile height.
+bool adj_masked_built(int q, int w) {
+#define FK_M(QQ, WW) \
+  if (q == QQ && w == WW) return true;
+  FK_MASKED_LIST(FK_M)
+#undef FK_M
+  return false;
+}
 bool adj_use_masked(const fk_plan* p) {
-  if (p->prec != FK_FP32 || p->mwin <= 0) return false;
+  if (p->prec != FK_FP32 || p->mwin <= 0 || !adj_masked_built(p->q, p->mwin)) return false;
   const char* k = getenv("FK_ADJ_KERNEL");
   return !(k && strcmp(k, "scatter") == 0);
 }
@@ -1037,6 +1044,13 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
     g.cn = (T)(p->coeffs.p[3] > 0.0 ? 1.0 / p->coeffs.p[3] : 0.0);  // sigma = s
   }
   cudaError_t e;
+  // fk_adjoint_kernel_times: an event pair around the backward-step kernel
+  cudaEvent_t* ev = nullptr;
+  if (p->adj_rec && p->adj_ev_used + 2 <= p->adj_ev_cap) {
+    ev = p->adj_ev + p->adj_ev_used;
+    p->adj_ev_used += 2;
+    if (cudaEventRecord(ev[0], s) != cudaSuccess) return FK_ERR_CUDA;
+  }
   if constexpr (sizeof(T) == 4) {
     if (adj_use_masked(p)) {
       // the masked window's layout: halo, row-major records, cell offsets
@@ -1066,6 +1080,7 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
     e = launch_adj<T>(g, p->q, s);
   }
   if (e != cudaSuccess) return FK_ERR_CUDA;
+  if (ev && cudaEventRecord(ev[1], s) != cudaSuccess) return FK_ERR_CUDA;
   const dim3 b(32, 8), gr((p->grid.n[0] + 31) / 32, (p->grid.n[1] + 7) / 8);
   k_adj_slopes_t<T><<<gr, b, 0, s>>>((const T*)u_in, (const T*)g.mu, (T*)lam_out, mu_next,
                                      p->grid.n[0], p->grid.n[1]);
@@ -1165,6 +1180,18 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
       k_cast_in<double><<<blocks, 256, 0, s>>>(cotangent_u0, (double*)lam[cur], p->J);
     if (cudaGetLastError() != cudaSuccess) return FK_ERR_CUDA;
   }
+  // events for the backward-step kernels (fk_adjoint_kernel_times)
+  p->adj_ev_used = 0;
+  if (p->adj_rec && p->adj_ev_cap < 2 * N) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FK_ERR_CUDA;
+    cudaEvent_t* grown = (cudaEvent_t*)realloc(p->adj_ev, sizeof(cudaEvent_t) * 2 * N);
+    if (!grown) return FK_ERR_OOM;
+    p->adj_ev = grown;
+    while (p->adj_ev_cap < 2 * N) {
+      if (cudaEventCreate(&p->adj_ev[p->adj_ev_cap]) != cudaSuccess) return FK_ERR_CUDA;
+      ++p->adj_ev_cap;
+    }
+  }
   // backward over segments [mK, top)
   for (int m = 0; m < M; ++m) {
     FkRange seg_range("fk_adjoint segment");
@@ -1187,5 +1214,25 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
     }
   }
   if (du_terminal && fk_launch_copy(du_terminal, lam[cur], fb, s) != cudaSuccess) return FK_ERR_CUDA;
+  return FK_OK;
+}
+
+extern "C" fk_status fk_adjoint_kernel_times(fk_plan* p, int record, double* kernel_ms,
+                                             int* launches) {
+  if (!p || (record != 0 && record != 1)) return FK_ERR_INVALID_ARG;
+  if (kernel_ms) *kernel_ms = 0.0;
+  if (launches) *launches = 0;
+  double total = 0.0;
+  const int pairs = p->adj_ev_used / 2;
+  for (int i = 0; i < pairs; ++i) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p->adj_ev[2 * i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, p->adj_ev[2 * i], p->adj_ev[2 * i + 1]) != cudaSuccess)
+      return FK_ERR_CUDA;
+    total += ms;
+  }
+  if (kernel_ms) *kernel_ms = total;
+  if (launches) *launches = pairs;
+  p->adj_rec = record;
   return FK_OK;
 }

@@ -90,7 +90,57 @@ struct Step2D {
   const T* xc;
   const T* yc;
   T blo[2], bhi[2];
+  // masked tensor window (mode 2): index of the cell-offset pattern m_q
+  // among those of (Q, W) (fk_mpat), and g_q - m_q per axis
+  int mpat;
+  T gmx[FK_MAXQ_2D], gmy[FK_MAXQ_2D];
 };
+
+// Cell-offset patterns of the masked tensor-window kernel.  With the 1D
+// Gauss-Hermite abscissae a_q of the rule of Q points and c = sigma
+// sqrt(2 dt) / h (the spread of the points in cells), point q lies
+// m_q = floor(c (a_q - a_0)) cells after point 0's cell, up to one more
+// cell; the window spans W = m_{Q-1} + 3 nodes.  The rows below list every
+// pattern m that some c > 0 produces with W <= 9, for Q = 4, 6 and 8
+// (found by walking c across the breakpoints j / (a_q - a_0)), numbered
+// k = 0, 1, ... within each (Q, W).  fk_mpat returns m_q of pattern k of
+// (Q, W), or -1 past the last pattern; fk_npat the number of patterns.
+__host__ __device__ constexpr int fk_mpat(int Q, int W, int k, int q) {
+  const signed char t[57][11] = {
+      {4, 3, 0, 0, 0, 0, 0},          {4, 4, 0, 0, 0, 0, 1},          {4, 4, 1, 0, 0, 1, 1},
+      {4, 5, 0, 0, 0, 1, 2},          {4, 5, 1, 0, 1, 1, 2},          {4, 6, 0, 0, 1, 1, 3},
+      {4, 6, 1, 0, 1, 2, 3},          {4, 7, 0, 0, 1, 2, 4},          {4, 7, 1, 0, 1, 3, 4},
+      {4, 8, 0, 0, 1, 3, 5},          {4, 8, 1, 0, 2, 3, 5},          {4, 9, 0, 0, 2, 3, 6},
+      {4, 9, 1, 0, 2, 4, 6},
+      {6, 3, 0, 0, 0, 0, 0, 0, 0},    {6, 4, 0, 0, 0, 0, 0, 0, 1},    {6, 4, 1, 0, 0, 0, 0, 1, 1},
+      {6, 4, 2, 0, 0, 0, 1, 1, 1},    {6, 5, 0, 0, 0, 0, 1, 1, 2},    {6, 5, 1, 0, 0, 1, 1, 1, 2},
+      {6, 5, 2, 0, 0, 1, 1, 2, 2},    {6, 6, 0, 0, 0, 1, 1, 2, 3},    {6, 6, 1, 0, 0, 1, 2, 2, 3},
+      {6, 6, 2, 0, 0, 1, 2, 3, 3},    {6, 7, 0, 0, 0, 1, 2, 3, 4},    {6, 7, 1, 0, 1, 1, 2, 3, 4},
+      {6, 7, 2, 0, 1, 2, 2, 3, 4},    {6, 8, 0, 0, 1, 2, 2, 3, 5},    {6, 8, 1, 0, 1, 2, 3, 3, 5},
+      {6, 8, 2, 0, 1, 2, 3, 4, 5},    {6, 9, 0, 0, 1, 2, 3, 4, 6},    {6, 9, 1, 0, 1, 2, 3, 5, 6},
+      {6, 9, 2, 0, 1, 2, 4, 5, 6},
+      {8, 3, 0, 0, 0, 0, 0, 0, 0, 0, 0}, {8, 4, 0, 0, 0, 0, 0, 0, 0, 0, 1},
+      {8, 4, 1, 0, 0, 0, 0, 0, 0, 1, 1}, {8, 4, 2, 0, 0, 0, 0, 0, 1, 1, 1},
+      {8, 4, 3, 0, 0, 0, 0, 1, 1, 1, 1}, {8, 5, 0, 0, 0, 0, 0, 1, 1, 1, 2},
+      {8, 5, 1, 0, 0, 0, 1, 1, 1, 1, 2}, {8, 5, 2, 0, 0, 0, 1, 1, 1, 2, 2},
+      {8, 5, 3, 0, 0, 0, 1, 1, 2, 2, 2}, {8, 6, 0, 0, 0, 0, 1, 1, 2, 2, 3},
+      {8, 6, 1, 0, 0, 1, 1, 1, 2, 2, 3}, {8, 6, 2, 0, 0, 1, 1, 2, 2, 2, 3},
+      {8, 6, 3, 0, 0, 1, 1, 2, 2, 3, 3}, {8, 7, 0, 0, 0, 1, 1, 2, 2, 3, 4},
+      {8, 7, 1, 0, 0, 1, 1, 2, 3, 3, 4}, {8, 7, 2, 0, 0, 1, 2, 2, 3, 3, 4},
+      {8, 7, 3, 0, 0, 1, 2, 2, 3, 4, 4}, {8, 8, 0, 0, 0, 1, 2, 2, 3, 4, 5},
+      {8, 8, 1, 0, 0, 1, 2, 3, 3, 4, 5}, {8, 8, 2, 0, 0, 1, 2, 3, 4, 4, 5},
+      {8, 8, 3, 0, 0, 1, 2, 3, 4, 5, 5}, {8, 9, 0, 0, 0, 1, 2, 3, 4, 5, 6},
+      {8, 9, 1, 0, 1, 1, 2, 3, 4, 5, 6}, {8, 9, 2, 0, 1, 2, 2, 3, 4, 5, 6},
+      {8, 9, 3, 0, 1, 2, 3, 3, 4, 5, 6}};
+  for (int r = 0; r < 57; ++r)
+    if (t[r][0] == Q && t[r][1] == W && t[r][2] == k) return (q >= 0 && q < Q) ? t[r][3 + q] : -1;
+  return -1;
+}
+__host__ __device__ constexpr int fk_npat(int Q, int W) {
+  int n = 0;
+  while (fk_mpat(Q, W, n, 0) >= 0) ++n;
+  return n;
+}
 
 template <typename T>
 struct Step1D {
@@ -169,11 +219,25 @@ bool fk_window_available(int q, int w);
 // memory of one CTA, availability for (q, W), and the large-shared-memory
 // opt-in (plan creation only).
 cudaError_t fk_launch_step2dm(const Step2D<float>& a, int q, cudaStream_t s);
-size_t fk_step2dm_smem(int ly, int lp);  // ly staged rows of pitch lp
+size_t fk_step2dm_smem(int ly, int lx);  // ly staged rows of lx nodes
+// staged columns of a masked-window tile: 32 output columns, the halo on
+// both sides, one node on each side for the slopes, and one more column
+// when W is odd (the window is read in pairs of columns)
+int fk_step2dm_lx(int hx, int w);
 bool fk_masked_available(int q, int w);
+// index k of the pattern m[0..q-1] among those of (q, w), or -1
+int fk_masked_pattern(int q, int w, const int* m);
 cudaError_t fk_prepare_masked_kernels(int q);
-// (Q, W) pairs built: the window form pays off while W^2 cells stay below
-// the direct form's 4 Q^2 corner reads and its weights fit in registers.
+// per rule size (fk_window_q4.cu, fk_window_q6.cu, fk_window_q8.cu)
+cudaError_t fk_launch_step2dm_q4(const Step2D<float>& a, cudaStream_t s);
+cudaError_t fk_launch_step2dm_q6(const Step2D<float>& a, cudaStream_t s);
+cudaError_t fk_launch_step2dm_q8(const Step2D<float>& a, cudaStream_t s);
+cudaError_t fk_prepare_masked_q4();
+cudaError_t fk_prepare_masked_q6();
+cudaError_t fk_prepare_masked_q8();
+// (Q, W) pairs of the masked-window adjoint kernel (fk_adjoint.cu): the
+// window form pays off while W^2 cells stay below the direct form's 4 Q^2
+// corner reads and its weights fit in registers.
 #define FK_MASKED_LIST(X)                                                  \
   X(4, 3) X(4, 4) X(4, 5) X(4, 6) X(4, 7)                                  \
   X(6, 3) X(6, 4) X(6, 5) X(6, 6) X(6, 7) X(6, 8) X(6, 9)                  \
@@ -227,6 +291,7 @@ struct fk_plan {
   int mwin;          // window width of the masked tensor-window kernel (0: not eligible)
   int mwm[FK_MAXQ_2D];  // its cell offsets floor(g_q - g_0), equal on both axes
   int mhalo[2];      // its halo per axis
+  int mpat;          // index of its cell-offset pattern among those of (q, mwin)
   int use_masked;    // the masked kernel is the step kernel
   int resident1d;    // 1D: 0 one launch per step, 1 the whole march in one CTA,
                      // 2 in one cluster of cluster1d CTAs (fk_march1d.cu)
@@ -275,6 +340,12 @@ struct fk_plan {
   void* adj_tab;     // piecewise-cubic weight tables of the masked adjoint (device, float4)
   float adj_break[2][FK_MAXQ_2D];  // their piece boundaries per axis, unused ones 2
   float adj_last[2];               // g_{Q-1} - g_0 per axis
+  // fk_adjoint_kernel_times: CUDA events around each backward-step kernel
+  // launch of the recorded fk_adjoint calls (pairs; host array)
+  int adj_rec;        // recording on
+  cudaEvent_t* adj_ev;
+  int adj_ev_cap;     // events created
+  int adj_ev_used;    // events recorded by the last fk_adjoint
 };
 
 void fk_batch_release(fk_plan* p);

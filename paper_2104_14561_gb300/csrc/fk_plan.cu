@@ -435,12 +435,17 @@ void fill2d(const fk_plan* p, int n, Step2D<T>* a) {
     a->win = p->mwin;
     a->hx = p->mhalo[0];
     a->hy = p->mhalo[1];
-    a->lx = a->tx + 2 * a->hx + 2;
+    a->lx = fk_step2dm_lx(a->hx, a->win);
     a->ly = a->ty + 2 * a->hy + 2;
-    a->lyr = a->lx | 1;  // row pitch of the row-major records
+    a->lyr = a->lx;  // row pitch of the records
+    a->mpat = p->mpat;
     for (int q = 0; q < p->q; ++q) {
       a->wm[q] = p->mwm[q];
       a->wmf[q] = (T)p->mwm[q];
+      // g_q - m_q from the rounded offsets g_q (exact: m_q is an integer no
+      // larger than the spread), so that the points stay symmetric
+      a->gmx[q] = a->gx[q] - (T)p->mwm[q];
+      a->gmy[q] = a->gy[q] - (T)p->mwm[q];
     }
   }
 }
@@ -491,8 +496,8 @@ bool kernel_eligible(const fk_plan* p, int kern) {
 bool cand_fits(const fk_plan* p, const TileCand& c, int dev_smem, int kern = kDirect) {
   if (p->elem == 8 && c.variant != 0) return false;
   if (kern == kMasked) {
-    const int lx = 32 + 2 * p->mhalo[0] + 2, ly = c.ty + 2 * p->mhalo[1] + 2;
-    return fk_step2dm_smem(ly, lx | 1) <= (size_t)dev_smem;
+    const int lx = fk_step2dm_lx(p->mhalo[0], p->mwin), ly = c.ty + 2 * p->mhalo[1] + 2;
+    return fk_step2dm_smem(ly, lx) <= (size_t)dev_smem;
   }
   const int hy = p->halo[1] + (kern == kRowWindow ? 1 : 0);
   const int lx = 32 + 2 * p->halo[0] + 2, ly = c.ty + 2 * hy + 2;
@@ -567,13 +572,17 @@ void masked_eligibility(fk_plan* p) {
   }
   const int W = p->mwm[p->q - 1] + 3;
   if (!fk_masked_available(p->q, W)) return;
+  p->mpat = fk_masked_pattern(p->q, W, p->mwm);
+  if (p->mpat < 0) return;
   for (int m = 0; m < 2; ++m) {
     // |error of an FP32 position difference| <= 2 ulp(reach + 1) << margin
     if ((p->reach[m] + 1.0) * 4.8e-7 > 0.5 * kMargin) return;
     const double r = p->reach[m] * (1.0 + 1e-6) + 1e-3;
     p->mhalo[m] = (int)floor(r) + 2;
   }
-  if (32 + 2 * p->mhalo[0] + 2 > 2 + FK_THREADS) return;  // one column per thread in the sweep
+  if (32 + 2 * p->mhalo[0] + 2 > 2 + FK_THREADS) return;  // adjoint: one column per thread
+  // step: the staging sweeps cover the pair columns with 31 per warp
+  if (fk_step2dm_lx(p->mhalo[0], W) - 3 > 31 * (FK_THREADS / 32)) return;
   p->mwin = W;
 }
 
@@ -1290,6 +1299,8 @@ fk_status fk_plan_destroy(fk_plan* p) {
   free_coords(p);
   fk_dev_free(p->adj_ws);
   fk_dev_free(p->adj_tab);
+  for (int i = 0; i < p->adj_ev_cap; ++i) cudaEventDestroy(p->adj_ev[i]);
+  free(p->adj_ev);
   fk_batch_release(p);
   delete p;
   return FK_OK;

@@ -2,15 +2,14 @@
 //
 // Some callers cannot call cudaMalloc: applications that hand every byte of
 // device memory to their own pool allocator and forbid libraries from
-// allocating beside it, code that enqueues work while a stream is being
-// captured into a CUDA graph (an allocation there is either rejected or
-// breaks the capture), and latency-bound loops that cannot afford the
+// allocating beside it, and latency-bound loops that cannot afford the
 // implicit device synchronisation of cudaMalloc / cudaFree.  For them this
 // entry point keeps everything the march needs besides the caller's input
 // and output -- the ping-pong field, the per-row and per-column coefficient
 // tables and the device error word -- in one file-scope __device__ array of
 // FK_STATIC_SCRATCH_BYTES, which every GPU that loads the library holds
-// until the process exits.
+// until the process exits.  fk_static_last_device_error reads the error
+// word back (it synchronises the device, so it is for after the work).
 //
 // The step kernel is the same one fk_solve launches; only where its
 // scratch lives differs.
@@ -145,6 +144,10 @@ extern "C" fk_status fk_solve_static(const fk_grid* grid, const fk_coeffs* coeff
   const size_t need = off_fld + (size_t)p.J * p.elem;
   if (need > FK_STATIC_SCRATCH_BYTES) return FK_ERR_INVALID_ARG;
 
+  // ---- a CUDA error left pending by the caller's earlier work is not ours
+  // to clear or to blame on this call's launches: report it, enqueue nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return FK_ERR_CUDA;
+
   // ---- device set-up (first call on each device) and tile choice
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FK_ERR_CUDA;
@@ -215,4 +218,22 @@ extern "C" fk_status fk_solve_static(const fk_grid* grid, const fk_coeffs* coeff
     src = dst;
   }
   return FK_OK;
+}
+
+extern "C" fk_status fk_static_last_device_error(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FK_ERR_CUDA;
+  unsigned char* base = nullptr;
+  fk_status st = setup_device(dev, &base);
+  if (st != FK_OK) return st;
+  // the calls are asynchronous on the caller's streams, which need not
+  // synchronise with the legacy default stream: wait for the whole device
+  if (cudaDeviceSynchronize() != cudaSuccess) return FK_ERR_CUDA;
+  unsigned word = 0;
+  const unsigned zero = 0;
+  if (cudaMemcpy(&word, base, sizeof(word), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(base, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+    return FK_ERR_CUDA;
+  if (word & FK_DEVERR_TIMEOUT) return FK_ERR_TIMEOUT;
+  return word ? FK_ERR_DEVICE : FK_OK;
 }

@@ -1,0 +1,383 @@
+// Masked tensor-window step of Scheme 1 (Sec. 3.1.5), FP32, for sm_103a.
+//
+// The same u^n as the direct kernel, from a factorisation of the quadrature
+// sum.  For node j = (i, k) the tensor Gauss-Hermite points of Eq. (e31) are
+// X_p x Y_q: their x coordinate does not depend on q nor their y coordinate
+// on p, because the drift and sigma are evaluated at the node.  The
+// zero-twist bicubic Hermite interpolant of Eq. (Lag11) is a sum over the
+// four corners of a cell of (value, h u_x, h u_y) times products of 1D
+// Hermite functions, so
+//
+//   sum_{p,q} w_p w_q Itilde(X_p, Y_q)
+//     = sum_{c,r} u_{c,r} phi_c Phi_r + h u_x(c,r) psi_c Phi_r + h u_y(c,r) phi_c Psi_r
+//
+// with 1D weights phi_c = sum_p w_p H(value basis of node c at X_p), psi_c
+// the same with the slope basis, and Phi_r, Psi_r along y.  The nodes with
+// a non-zero weight lie in a W x W window: point q falls in cell
+// c_0 + m_q + beta_q, where m_q = floor(g_q - g_0) is a plan constant (one
+// of the patterns fk_mpat lists) and beta_q is 0 or 1, so W = m_{Q-1} + 3.
+// The kernel is compiled for every pattern of its (Q, W) and takes the
+// plan's with one uniform branch, so each point's weights land in fixed
+// registers.
+//
+// Exits (Eq. (e24)): point (p, q) takes the value 1 when X_p or Y_q is
+// outside the closed box.  Dropping such points from the 1D weights keeps
+// the sum separable:
+//
+//   u^n_j = u_j + sum_{c,r} [(u_{c,r} - u_j) phi_c Phi_r + ...]      (masked weights)
+//             + (1 - u_j) (E_x + E_y - E_x E_y),
+//
+// where E_x and E_y are the weights of the dropped x- and y-points.  The
+// exit term is exactly 0 for a node whose points all stay inside, and the
+// window part is in the increment form u_j + sum w (Itilde - u_j), so that
+// rounding scales with the per-step change.  Rows of nodes whose points
+// cannot leave the box (tiles at least a halo away from the x faces, rows
+// at least a halo away from the y faces) skip the exit tests.
+//
+// Per CTA (32 x ty output nodes): stage u^{n+1} over the tile plus halo
+// with cp.async, form the scaled PCHIP slopes of Eq. (e300) and store, for
+// every staged node c, the pair records {u_c, u_{c+1}, h u_x(c),
+// h u_x(c+1)} and {h u_y(c), h u_y(c+1)}; then per node: the x and y
+// weights as f32x2 pairs (both axes at once), and the window read as pairs
+// of columns, so that each f32x2 multiply-add covers two nodes of the
+// window.  (Tiled TMA copies cannot stage these fields: a row of 2^k + 1
+// FP32 values is not a multiple of 16 bytes long.)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fk_device.cuh"
+#include "fk_internal.h"
+
+namespace {
+
+// Pair records of the staged tile (lx x ly nodes, row pitch lx): P[r][c] =
+// {u_c, u_{c+1}, h u_x(c), h u_x(c+1)} and Y[r][c] = {h u_y(c), h u_y(c+1)}
+// for staged columns c = 1 .. lx-3 and rows r = 1 .. ly-2; U holds u^{n+1}
+// itself (zero outside the mesh).  Ends with the records visible to the
+// whole CTA.
+template <bool MF>
+__device__ __forceinline__ void stage_pairs(const Step2D<float>& a, float* U, float4* P,
+                                            float2* Y, int gi0, int gk0) {
+  const int lx = a.lx, ly = a.ly;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // 1. u^{n+1} over the tile and halo: rows by warp, columns by lane, so
+  // global reads are coalesced and shared-memory writes consecutive
+  {
+    const uint32_t sU = (uint32_t)__cvta_generic_to_shared(U);
+    for (int r = warp; r < ly; r += FK_THREADS / 32) {
+      const int gk = gk0 + r;
+      const bool rowin = (unsigned)gk < (unsigned)a.ny;
+      const float* src = field_in<MF>(a) + (int64_t)(rowin ? gk : 0) * a.nx;
+      const uint32_t drow = sU + (uint32_t)(r * lx) * 4u;
+      for (int c = lane; c < lx; c += 32) {
+        const int gi = gi0 + c;
+        const bool in = rowin && (unsigned)gi < (unsigned)a.nx;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c),
+                     "l"(in ? src + gi : field_in<MF>(a)), "r"(in ? 4 : 0));
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+  }
+  // 2. vertical sweeps: warp group g takes staged columns 1 + 31 g + lane
+  // (lane 31 lends its values to lane 30 and stores nothing) over one
+  // segment of rows, carrying u of the rows above and below in registers;
+  // the partner column's values come by shuffle.  The end rule stated after
+  // Eq. (e300) gives node 0 the slope of node 1 and node n-1 that of node
+  // n-2 (the harmonic mean is symmetric): an end column takes its
+  // x-differences one column inwards, and the end rows copy the y-slopes of
+  // their neighbour row afterwards.  Nodes outside the mesh get finite
+  // values from the zero fill; they only ever carry weight 0.
+  {
+    const int groups = (lx - 3 + 30) / 31;
+    const int segs = (FK_THREADS / 32) / groups;
+    const int g = warp % groups, seg = warp / groups;
+    if (seg < segs) {
+      const int c = 1 + 31 * g + lane;
+      const bool have = c <= lx - 2;  // slopes exist for staged columns 1 .. lx-2
+      const bool emit = lane < 31 && c <= lx - 3;
+      const int hr = ly - 2;
+      const int len = (hr + segs - 1) / segs;
+      const int r0 = 1 + seg * len, r1 = min(r0 + len, hr + 1);
+      const int gi = gi0 + c;
+      const int ax = c + (gi == 0) - (gi == a.nx - 1);
+      const int cc = have ? c : 1, axc = have ? ax : 1;  // idle lanes read in range
+      const float* col = U + cc;
+      const float* colx = U + axc;
+      float up = r0 <= hr ? col[(r0 - 1) * lx] : 0.f, uc = r0 <= hr ? col[r0 * lx] : 0.f;
+      for (int r = r0; r < r1; ++r) {
+        const float un = col[(r + 1) * lx];
+        const float* rx = colx + r * lx;
+        const float X = pchip_fast(rx[0] - rx[-1], rx[1] - rx[0]);
+        const float Yv = pchip_fast(uc - up, un - uc);
+        const float u1 = __shfl_down_sync(0xffffffffu, uc, 1);
+        const float X1 = __shfl_down_sync(0xffffffffu, X, 1);
+        const float Y1 = __shfl_down_sync(0xffffffffu, Yv, 1);
+        if (emit) {
+          P[r * lx + c] = make_float4(uc, u1, X, X1);
+          Y[r * lx + c] = make_float2(Yv, Y1);
+        }
+        up = uc;
+        uc = un;
+      }
+    }
+    __syncthreads();
+    // y end rule: staged rows of mesh rows 0 and ny-1 take their neighbour's y-slopes
+    const int rb = -gk0, rt = a.ny - 1 - gk0;
+    const bool fb = rb >= 1 && rb <= ly - 3, ft = rt >= 2 && rt <= ly - 2;
+    if (fb || ft) {
+      for (int e = tid; e < lx - 3; e += FK_THREADS) {
+        if (fb) Y[rb * lx + 1 + e] = Y[(rb + 1) * lx + 1 + e];
+        if (ft) Y[rt * lx + 1 + e] = Y[(rt - 1) * lx + 1 + e];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// The 1D weights of points q .. Q-1 of pattern K of (Q, W), x in .x and y
+// in .y: PH[s] += (phi_s, Phi_s), PS[s] += (psi_s, Psi_s).  qc[q] = {G_x,
+// G_y, w_q, w_q} with G = g_q - m_q.  Z: the drift after the window
+// origin, so that point q sits at Z + g_q = Z + G + m_q.  With EXIT, a point outside [LO, HI] (positions
+// after the window origin) is dropped and its weight added to E.
+template <int Q, int W, int K, bool EXIT, int q>
+struct PointWeights {
+  template <int S>
+  __device__ __forceinline__ static void run(const float4* qc, float2 Z, float2 LO, float2 HI,
+                                             float2 (&PH)[S], float2 (&PS)[S], float2& E) {
+    if constexpr (q < Q) {
+      constexpr int M = fk_mpat(Q, W, K, q);
+      static_assert(M >= 0 && M + 2 < S, "pattern slot outside the window");
+      const float4 c0 = qc[q];
+      const float2 one = f2(1.f, 1.f);
+      const float2 tp = add2(Z, f2(c0.x, c0.y));  // in [0, 2): cells M and M + 1, up to rounding
+      float2 w1 = f2(c0.z, c0.w);
+      if constexpr (EXIT) {
+        const float2 sq = add2(tp, f2((float)M, (float)M));
+        const float2 ex = f2((sq.x < LO.x || sq.x > HI.x) ? w1.x : 0.f,
+                             (sq.y < LO.y || sq.y > HI.y) ? w1.y : 0.f);
+        E = add2(E, ex);
+        w1 = add2(w1, f2(-ex.x, -ex.y));  // weight, 0 if the point exits
+      }
+      // (tp may round a hair outside [0, 2) at a cell face: the cubic is
+      // continuous there, so the compare only has to pick one of the cells)
+      const float2 beta = f2(tp.x >= 1.f ? 1.f : 0.f, tp.y >= 1.f ? 1.f : 0.f);
+      const float2 t = add2(tp, f2(-beta.x, -beta.y));
+      const float2 nb = add2(one, f2(-beta.x, -beta.y));
+      // cubic Hermite basis at t, weighted: values v0 = w h00, v1 = w h01,
+      // slopes s0 = w h10, s1 = w h11.  h01 = t^2 (3 - 2t) is formed before
+      // the weight is applied: 3 - 2t is exact, while a rounded 3 w would
+      // shift the same sliver of weight from node to node at every node and
+      // step, a bias that adds up over a march.
+      const float2 tt = mul2(t, t);
+      const float2 om = add2(t, f2(-1.f, -1.f));
+      const float2 v1 = mul2(w1, mul2(tt, fma2(f2(-2.f, -2.f), t, f2(3.f, 3.f))));
+      const float2 v0 = add2(w1, f2(-v1.x, -v1.y));
+      const float2 wto = mul2(mul2(w1, t), om);
+      const float2 s0 = mul2(wto, om);
+      const float2 s1 = mul2(wto, t);
+      // beta = 1 moves the pair one node up: slots (M, M+1, M+2) get
+      // ((1-beta) v0, beta v0 + (1-beta) v1, beta v1)
+      PH[M] = fma2(nb, v0, PH[M]);
+      PH[M + 1] = fma2(beta, v0, fma2(nb, v1, PH[M + 1]));
+      PH[M + 2] = fma2(beta, v1, PH[M + 2]);
+      PS[M] = fma2(nb, s0, PS[M]);
+      PS[M + 1] = fma2(beta, s0, fma2(nb, s1, PS[M + 1]));
+      PS[M + 2] = fma2(beta, s1, PS[M + 2]);
+      PointWeights<Q, W, K, EXIT, q + 1>::run(qc, Z, LO, HI, PH, PS, E);
+    }
+  }
+};
+
+// Pattern `pat` of (Q, W), taken from K upwards (one uniform branch).
+template <int Q, int W, int K, int S>
+__device__ __forceinline__ void weights_of(int pat, bool exits, const float4* qc, float2 Z,
+                                           float2 LO, float2 HI, float2 (&PH)[S], float2 (&PS)[S],
+                                           float2& E) {
+  if constexpr (K < fk_npat(Q, W)) {
+    if (pat == K) {
+      if (exits)
+        PointWeights<Q, W, K, true, 0>::run(qc, Z, LO, HI, PH, PS, E);
+      else
+        PointWeights<Q, W, K, false, 0>::run(qc, Z, LO, HI, PH, PS, E);
+    } else {
+      weights_of<Q, W, K + 1>(pat, exits, qc, Z, LO, HI, PH, PS, E);
+    }
+  }
+}
+
+// MINB: CTAs of 256 threads per SM the register budget is sized for
+// (3 -> 80 registers, 2 -> 128; variant 0 and 1 of the plan).
+// MF: several fields per launch (blockIdx.z), for Algorithm 1.
+template <int Q, int W, int MINB, bool MF>
+__global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float> a) {
+  constexpr int NP = (W + 1) / 2;  // column pairs of the window
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lx = a.lx, ly = a.ly;
+  float4* QC = reinterpret_cast<float4*>(smem);
+  float4* P = QC + FK_MAXQ_2D;
+  float2* Yr = reinterpret_cast<float2*>(P + ly * lx);
+  float* U = reinterpret_cast<float*>(Yr + ly * lx);
+  const int tid = threadIdx.x;
+  if (tid < Q) QC[tid] = make_float4(a.gmx[tid], a.gmy[tid], a.w[tid], a.w[tid]);
+  const int i0 = 1 + blockIdx.x * 32, k0 = 1 + blockIdx.y * a.ty;
+  const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;  // global node of staged (0, 0)
+
+  stage_pairs<MF>(a, U, P, Yr, gi0, gk0);
+
+  // 3. one output node per thread and pass: column i0 + lane, row k0 + warp + 8 m
+  const int lane = tid & 31, warp = tid >> 5;
+  const int i = i0 + lane;
+  if (i > a.nx - 2) return;
+  const int li = i - gi0;
+  // no point of a node in this tile's columns can leave through an x face
+  // (the halo exceeds the reach of every point)
+  const bool xsafe = i0 - a.hx >= 0 && i0 + 31 + a.hx <= a.nx - 1;
+  // column factors of the cellular drift: A sin(pi x) + e1 sin(2 pi x) and
+  // A cos(pi x) + e2 cos(2 pi x) (constant drift: 1, the row factor is the drift)
+  float fcx = 1.f, fcy = 1.f;
+  if (a.family == FK_CELLULAR_FLOW) {
+    const float* ct = a.col_tab + 4 * (int64_t)i;
+    fcx = a.A * ct[0] + a.e1 * ct[1];
+    fcy = a.A * ct[2] + a.e2 * ct[3];
+  }
+  unsigned bad = 0;
+#pragma unroll 1
+  for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
+    const int k = k0 + ty;
+    if (k > a.ny - 2) break;
+    const int lk = k - gk0;
+    const float uj = U[lk * lx + li];
+    float dx, dy;
+    if (a.family == FK_CELLULAR_FLOW) {
+      const float* rt = a.row_tab + 2 * (int64_t)k;
+      dx = a.kx * rt[0] * fcx;
+      dy = a.ky * rt[1] * fcy;
+    } else {
+      dx = a.cdx * fcx;
+      dy = a.cdy * fcy;
+    }
+    // window origin F0: the cell of point 0 on each axis; positions after
+    // it are Z + g_q with Z = D - F0 (the points keep the rule's symmetric
+    // offsets g_q, so FP32 rounding of the offsets cannot add up to a drift),
+    // and a point exits when it leaves [LO, HI] (the box in the same
+    // coordinates)
+    const float fx0 = floorf(dx + a.gx[0]), fy0 = floorf(dy + a.gy[0]);
+    int wx = li + (int)fx0, wy = lk + (int)fy0;
+    if (wx < 1 || wx + 2 * NP - 1 > lx - 2 || wy < 1 || wy + W - 1 > ly - 2) {
+      bad = 1u;  // halo too small for this drift: flag, read an in-range window
+      wx = 1;
+      wy = 1;
+    }
+    const float2 Z = f2(dx - fx0, dy - fy0);
+    const float2 LO = f2(-(float)i - fx0, -(float)k - fy0);
+    const float2 HI = f2((float)(a.nx - 1 - i) - fx0, (float)(a.ny - 1 - k) - fy0);
+    const bool exits = !(xsafe && k - a.hy >= 0 && k + a.hy <= a.ny - 1);
+    // 1D weights, x in .x and y in .y: PH[s] = (phi_s, Phi_s), PS[s] = (psi_s, Psi_s)
+    float2 PH[2 * NP], PS[2 * NP];
+#pragma unroll
+    for (int r = 0; r < 2 * NP; ++r) PH[r] = PS[r] = f2(0.f, 0.f);
+    float2 E = f2(0.f, 0.f);
+    weights_of<Q, W, 0>(a.mpat, exits, QC + opaque_zero(), Z, LO, HI, PH, PS, E);
+    // W x W record window, row by row, two columns per f32x2 operation:
+    //   (AE_r, AX_r) = sum_c (phi_c (u - u_j), psi_c h u_x),  B_r = sum_c phi_c h u_y,
+    //   acc += Phi_r (AE_r + AX_r) + Psi_r B_r
+    float2 XP[NP], XS[NP];  // (phi_c, phi_c+1), (psi_c, psi_c+1), c = 2 j
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      XP[j] = f2(PH[2 * j].x, PH[2 * j + 1].x);
+      XS[j] = f2(PS[2 * j].x, PS[2 * j + 1].x);
+    }
+    const float4* pwin = P + (wy * lx + wx);
+    const float2* ywin = Yr + (wy * lx + wx);
+    const float2 nuj = f2(-uj, -uj);
+    float acc = 0.f;
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      const float4* pr = pwin + r * lx;
+      const float2* yr = ywin + r * lx;
+      float2 AE, AX, B;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const float4 p = pr[2 * j];
+        const float2 y = yr[2 * j];
+        const float2 du = add2(f2(p.x, p.y), nuj);
+        if (j == 0) {
+          AE = mul2(XP[0], du);
+          AX = mul2(XS[0], f2(p.z, p.w));
+          B = mul2(XP[0], y);
+        } else {
+          AE = fma2(XP[j], du, AE);
+          AX = fma2(XS[j], f2(p.z, p.w), AX);
+          B = fma2(XP[j], y, B);
+        }
+      }
+      const float2 T = add2(AE, AX);
+      acc = fmaf(PH[r].y, T.x + T.y, fmaf(PS[r].y, B.x + B.y, acc));
+    }
+    const float ext = (1.f - uj) * (E.x + E.y - E.x * E.y);
+    const float un = uj + (acc + ext);
+    const int64_t j = (int64_t)k * a.nx + i;
+    field_out<MF>(a)[j] = un;
+    if (a.snap) a.snap[j] = un;
+    write_adjacent_boundary<MF>(a, i, k);
+  }
+  if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
+}
+
+// Several fields run the 3-CTA/SM register budget whatever the variant.
+template <int Q, int W, int MINB>
+cudaError_t launch_m(const Step2D<float>& a, cudaStream_t s) {
+  const size_t smem = fk_step2dm_smem(a.ly, a.lx);
+  const int nf = a.ncols > 1 ? a.ncols : 1;
+  dim3 grid((a.nx - 2 + 31) / 32, (a.ny - 2 + a.ty - 1) / a.ty, nf);
+  if (nf > 1)
+    k_step2dm<Q, W, 3, true><<<grid, FK_THREADS, smem, s>>>(a);
+  else
+    k_step2dm<Q, W, MINB, false><<<grid, FK_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int Q, int W>
+cudaError_t attr_m() {
+  const int big = 227 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_step2dm<Q, W, 3, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step2dm<Q, W, 2, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step2dm<Q, W, 3, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  return e;
+}
+
+}  // namespace
+
+// Launcher and shared-memory opt-in of the masked kernels of one rule size.
+#define FK_DEFINE_MASKED_Q(QQ)                                                          \
+  cudaError_t fk_launch_step2dm_q##QQ(const Step2D<float>& a, cudaStream_t s) {         \
+    switch (a.win) {                                                                    \
+      case 3: return a.variant == 1 ? launch_m<QQ, 3, 2>(a, s) : launch_m<QQ, 3, 3>(a, s); \
+      case 4: return a.variant == 1 ? launch_m<QQ, 4, 2>(a, s) : launch_m<QQ, 4, 3>(a, s); \
+      case 5: return a.variant == 1 ? launch_m<QQ, 5, 2>(a, s) : launch_m<QQ, 5, 3>(a, s); \
+      case 6: return a.variant == 1 ? launch_m<QQ, 6, 2>(a, s) : launch_m<QQ, 6, 3>(a, s); \
+      case 7: return a.variant == 1 ? launch_m<QQ, 7, 2>(a, s) : launch_m<QQ, 7, 3>(a, s); \
+      case 8: return a.variant == 1 ? launch_m<QQ, 8, 2>(a, s) : launch_m<QQ, 8, 3>(a, s); \
+      case 9: return a.variant == 1 ? launch_m<QQ, 9, 2>(a, s) : launch_m<QQ, 9, 3>(a, s); \
+      default: return cudaErrorInvalidValue;                                            \
+    }                                                                                   \
+  }                                                                                     \
+  cudaError_t fk_prepare_masked_q##QQ() {                                               \
+    cudaError_t e = attr_m<QQ, 3>();                                                    \
+    if (e == cudaSuccess) e = attr_m<QQ, 4>();                                          \
+    if (e == cudaSuccess) e = attr_m<QQ, 5>();                                          \
+    if (e == cudaSuccess) e = attr_m<QQ, 6>();                                          \
+    if (e == cudaSuccess) e = attr_m<QQ, 7>();                                          \
+    if (e == cudaSuccess) e = attr_m<QQ, 8>();                                          \
+    if (e == cudaSuccess) e = attr_m<QQ, 9>();                                          \
+    return e;                                                                           \
+  }

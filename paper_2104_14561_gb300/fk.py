@@ -54,6 +54,18 @@ def runaway_quench_params(params, t: float):
     return list(out)
 
 
+def measure_fma_rate(precision: str = "fp32", packed: bool = False, seconds: float = 0.05,
+                     stream=None) -> float:
+    """FMA throughput of the current device in flop/s (2 x FMAs per second):
+    the denominator of the march kernels' ALU rooflines."""
+    lib = L.load()
+    out = ctypes.c_double()
+    L.check("fk_measure_fma_rate",
+            lib.fk_measure_fma_rate(_PREC[precision], int(packed), float(seconds),
+                                    ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
 @dataclass
 class PlanSpec:
     n: tuple
@@ -189,6 +201,18 @@ class Plan:
                                                    _ptr(du), int(checkpoint_every),
                                                    _stream(stream)))
         return dtheta, du
+
+    def adjoint_kernel_times(self, record: bool):
+        """(summed ms, launches) of the backward-step kernel over the last
+        recorded adjoint call, then recording on (True) or off (False) for
+        later calls (fk_adjoint_kernel_times: CUDA events around each
+        launch)."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int()
+        L.check("fk_adjoint_kernel_times",
+                self._lib.fk_adjoint_kernel_times(self._h, int(record), ctypes.byref(ms),
+                                                  ctypes.byref(n)))
+        return ms.value, n.value
 
     def last_device_error(self) -> int:
         return self._lib.fk_last_device_error(self._h)

@@ -1,13 +1,14 @@
 """fk_solve_static: the march for callers that cannot allocate device memory.
 
 Such callers (a host application whose pool allocator owns all device
-memory, code that enqueues work during CUDA-graph capture, latency-bound
-loops that cannot absorb cudaMalloc's synchronisation) get an entry point
-whose scratch lives in a static device array instead of plan memory.  Its
-results must equal fk_solve's within the parity tolerances (1e-5 FP32,
-1e-12 FP64), on two calls in a row (the second call reuses the array the
-first one left behind).  This file is collected last so that a failure here
-does not hide the other tests.
+memory, latency-bound loops that cannot absorb cudaMalloc's
+synchronisation) get an entry point whose scratch lives in a static device
+array instead of plan memory.  Its results must equal fk_solve's within the
+parity tolerances (1e-5 FP32, 1e-12 FP64), on two calls in a row (the second
+call reuses the array the first one left behind); its error word, read back
+with fk_static_last_device_error, must be clear; and a call after the
+one-time set-up must leave the device's free memory unchanged.  This file is
+collected last so that a failure here does not hide the other tests.
 """
 import ctypes
 import math
@@ -31,6 +32,8 @@ def env():
                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p]
     lib.fk_solve_static.restype = ctypes.c_int
+    lib.fk_static_last_device_error.argtypes = []
+    lib.fk_static_last_device_error.restype = ctypes.c_int
     return torch, L, fk, lib
 
 
@@ -67,6 +70,7 @@ def test_static_scratch_matches_fk_solve(env, precision, n_steps):
                                  ctypes.c_void_p(stream.cuda_stream))
         assert st == 0, L.STATUS.get(st, st)
         torch.cuda.synchronize()
+        assert L.STATUS[lib.fk_static_last_device_error()] == "FK_OK"
         err = (out.double() - ref.double()).abs().max().item()
         assert err <= TOL[precision], (call, err)
 
@@ -100,3 +104,28 @@ def test_static_scratch_rejects_oversize(env):
     st = lib.fk_solve_static(ctypes.byref(g), ctypes.byref(c), 8, 5e-4, 10, L.FK_FP32, None,
                              ctypes.c_void_p(out.data_ptr()), None)
     assert L.STATUS[st] == "FK_ERR_INVALID_ARG"
+
+
+def test_static_scratch_allocates_nothing(env):
+    """After the first call on the device (the one-time set-up), a call must
+    not change the device's free memory: every byte it uses is the static
+    array or the caller's buffers."""
+    torch, L, fk, lib = env
+    n, q, dt, n_steps = (257, 129), 6, 1e-3, 20
+    params = (1.0, 0.2, 2 * math.pi, 1e-3)
+    g, c = _structs(L, n, params)
+    out = torch.empty((n[1], n[0]), dtype=torch.float32, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call():
+        st = lib.fk_solve_static(ctypes.byref(g), ctypes.byref(c), q, dt, n_steps, L.FK_FP32,
+                                 None, ctypes.c_void_p(out.data_ptr()), stream)
+        assert st == 0, L.STATUS.get(st, st)
+        torch.cuda.synchronize()
+
+    call()  # set-up, if no earlier test made it
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        call()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert L.STATUS[lib.fk_static_last_device_error()] == "FK_OK"
