@@ -63,6 +63,19 @@ __device__ __forceinline__ float pchip_fast<float>(float dl, float dr) {
   return p > 0.f ? __fdividef(2.f * p, dl + dr) : 0.f;
 }
 
+// The FP32 slope of Eq. (e300) with the hardware reciprocal approximation
+// (rcp.approx: relative error below 2^-22) times 2 p: the quotient is a
+// few ulp, inside the FP32 parity budget like pchip_fast.  When p > 0 both
+// differences have the same sign and are normal, so their sum is normal
+// and flushing subnormal inputs changes nothing.
+__device__ __forceinline__ float pchip_rcp(float dl, float dr) {
+  const float p = dl * dr;
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(dl + dr));
+  const float h = p * r;
+  return p > 0.f ? h + h : 0.f;
+}
+
 // Boundary nodes adjacent to interior node (i, k) hold 1 (Eq. (e3)).  On a
 // mesh with 3 nodes along an axis the single interior line is next to both
 // faces of that axis, so every flag is tested on its own.

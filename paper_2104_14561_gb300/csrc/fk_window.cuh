@@ -64,19 +64,33 @@ __device__ __forceinline__ void stage_pairs(const Step2D<float>& a, float* U, fl
   const int lx = a.lx, ly = a.ly;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // 1. u^{n+1} over the tile and halo: rows by warp, columns by lane, so
-  // global reads are coalesced and shared-memory writes consecutive
+  // global reads are coalesced and shared-memory writes consecutive.  A lane
+  // holds columns lane and lane + 32 (more only for halos over 14 nodes);
+  // reads outside the mesh are clamped to a mesh node and copy 0 bytes (zero
+  // fill)
   {
     const uint32_t sU = (uint32_t)__cvta_generic_to_shared(U);
+    const int c1 = lane + 32;
+    const int g0 = gi0 + lane, g1 = gi0 + c1;
+    const bool x0 = (unsigned)g0 < (unsigned)a.nx, x1 = c1 < lx && (unsigned)g1 < (unsigned)a.nx;
+    const int cx0 = min(max(g0, 0), a.nx - 1), cx1 = min(max(g1, 0), a.nx - 1);
+    const float* base = field_in<MF>(a);
+#pragma unroll 1
     for (int r = warp; r < ly; r += FK_THREADS / 32) {
       const int gk = gk0 + r;
       const bool rowin = (unsigned)gk < (unsigned)a.ny;
-      const float* src = field_in<MF>(a) + (int64_t)(rowin ? gk : 0) * a.nx;
+      const float* src = base + (int64_t)min(max(gk, 0), a.ny - 1) * a.nx;
       const uint32_t drow = sU + (uint32_t)(r * lx) * 4u;
-      for (int c = lane; c < lx; c += 32) {
-        const int gi = gi0 + c;
-        const bool in = rowin && (unsigned)gi < (unsigned)a.nx;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * lane),
+                   "l"(src + cx0), "r"(rowin && x0 ? 4 : 0));
+      if (c1 < lx)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c1),
+                     "l"(src + cx1), "r"(rowin && x1 ? 4 : 0));
+      for (int c = lane + 64; c < lx; c += 32) {  // wide halos only
+        const int g = gi0 + c;
+        const bool in = rowin && (unsigned)g < (unsigned)a.nx;
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c),
-                     "l"(in ? src + gi : field_in<MF>(a)), "r"(in ? 4 : 0));
+                     "l"(src + min(max(g, 0), a.nx - 1)), "r"(in ? 4 : 0));
       }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -111,8 +125,8 @@ __device__ __forceinline__ void stage_pairs(const Step2D<float>& a, float* U, fl
       for (int r = r0; r < r1; ++r) {
         const float un = col[(r + 1) * lx];
         const float* rx = colx + r * lx;
-        const float X = pchip_fast(rx[0] - rx[-1], rx[1] - rx[0]);
-        const float Yv = pchip_fast(uc - up, un - uc);
+        const float X = pchip_rcp(rx[0] - rx[-1], rx[1] - rx[0]);
+        const float Yv = pchip_rcp(uc - up, un - uc);
         const float u1 = __shfl_down_sync(0xffffffffu, uc, 1);
         const float X1 = __shfl_down_sync(0xffffffffu, X, 1);
         const float Y1 = __shfl_down_sync(0xffffffffu, Yv, 1);
@@ -143,6 +157,21 @@ __device__ __forceinline__ void stage_pairs(const Step2D<float>& a, float* U, fl
 // G_y, w_q, w_q} with G = g_q - m_q.  Z: the drift after the window
 // origin, so that point q sits at Z + g_q = Z + G + m_q.  With EXIT, a point outside [LO, HI] (positions
 // after the window origin) is dropped and its weight added to E.
+// The first point of pattern K of (Q, W) whose cell pair touches window
+// slot s (point q touches slots m_q .. m_q + 2), or Q if none does.
+__host__ __device__ constexpr int first_point(int Q, int W, int K, int s) {
+  for (int q = 0; q < Q; ++q)
+    if (fk_mpat(Q, W, K, q) <= s && s <= fk_mpat(Q, W, K, q) + 2) return q;
+  return Q;
+}
+
+// a * b + c, or a * b where point q is the first to reach the slot
+template <bool FIRST>
+__device__ __forceinline__ float2 acc2(float2 a, float2 b, float2 c) {
+  if constexpr (FIRST) return mul2(a, b);
+  else return fma2(a, b, c);
+}
+
 template <int Q, int W, int K, bool EXIT, int q>
 struct PointWeights {
   template <int S>
@@ -181,12 +210,15 @@ struct PointWeights {
       const float2 s1 = mul2(wto, t);
       // beta = 1 moves the pair one node up: slots (M, M+1, M+2) get
       // ((1-beta) v0, beta v0 + (1-beta) v1, beta v1)
-      PH[M] = fma2(nb, v0, PH[M]);
-      PH[M + 1] = fma2(beta, v0, fma2(nb, v1, PH[M + 1]));
-      PH[M + 2] = fma2(beta, v1, PH[M + 2]);
-      PS[M] = fma2(nb, s0, PS[M]);
-      PS[M + 1] = fma2(beta, s0, fma2(nb, s1, PS[M + 1]));
-      PS[M + 2] = fma2(beta, s1, PS[M + 2]);
+      // (a slot's first contribution is a product: no zero fill needed)
+      constexpr bool F0 = first_point(Q, W, K, M) == q, F1 = first_point(Q, W, K, M + 1) == q,
+                     F2 = first_point(Q, W, K, M + 2) == q;
+      PH[M] = acc2<F0>(nb, v0, PH[M]);
+      PH[M + 1] = fma2(beta, v0, acc2<F1>(nb, v1, PH[M + 1]));
+      PH[M + 2] = acc2<F2>(beta, v1, PH[M + 2]);
+      PS[M] = acc2<F0>(nb, s0, PS[M]);
+      PS[M + 1] = fma2(beta, s0, acc2<F1>(nb, s1, PS[M + 1]));
+      PS[M + 2] = acc2<F2>(beta, s1, PS[M + 2]);
       PointWeights<Q, W, K, EXIT, q + 1>::run(qc, Z, LO, HI, PH, PS, E);
     }
   }
@@ -277,9 +309,11 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float
     const float2 HI = f2((float)(a.nx - 1 - i) - fx0, (float)(a.ny - 1 - k) - fy0);
     const bool exits = !(xsafe && k - a.hy >= 0 && k + a.hy <= a.ny - 1);
     // 1D weights, x in .x and y in .y: PH[s] = (phi_s, Phi_s), PS[s] = (psi_s, Psi_s)
+    // (slots 0 .. W-1 all receive a first contribution; the padding slot
+    // of an odd W stays 0)
     float2 PH[2 * NP], PS[2 * NP];
 #pragma unroll
-    for (int r = 0; r < 2 * NP; ++r) PH[r] = PS[r] = f2(0.f, 0.f);
+    for (int r = W; r < 2 * NP; ++r) PH[r] = PS[r] = f2(0.f, 0.f);
     float2 E = f2(0.f, 0.f);
     weights_of<Q, W, 0>(a.mpat, exits, QC + opaque_zero(), Z, LO, HI, PH, PS, E);
     // W x W record window, row by row, two columns per f32x2 operation:
