@@ -541,7 +541,7 @@ def fp64_line(fk, w, stream, flush, steps: int, peaks: dict) -> dict:
     flop_launch = FLOP_PER_UPDATE * units / w["n_steps"]
     achieved = flop_launch / (launch_ms * 1e-3) / 1e12
     peak = peaks["fp64_tflops"]
-    kname = {"direct": "k_step2d", "window": "k_step2dw", "masked": "k_step2dm"}.get(
+    kname = {"direct": "k_step2d", "window": "k_step2dw", "masked": "k_step2dm64"}.get(
         info.get("step_kernel"), info.get("step_kernel"))
     return {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "warmup": 1, "dtype": "f64",
@@ -734,7 +734,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                      info.get("step_kernel"), "k_step1d")
                  if len(w["n"]) == 1 else
                  {"direct": "k_step2d", "window": "k_step2dw",
-                  "masked": "k_step2dm"}[info.get("step_kernel", "direct")])
+                  "masked": "k_step2dm" if w["precision"] == "fp32" else "k_step2dm64"}[
+                     info.get("step_kernel", "direct")])
         roofline = {"kernel": kname, "bound": "alu", "achieved": achieved / 1e12,
                     "peak": peak_flops / 1e12, "peak_source": "measured", "unit": "TFLOP/s",
                     "frac": achieved / peak_flops,

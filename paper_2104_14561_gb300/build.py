@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libfk_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fk_plan.cu", "fk_march.cu", "fk_window.cu", "fk_window_q4.cu", "fk_window_q6.cu",
-           "fk_window_q8.cu", "fk_march1d.cu", "fk_csr.cu",
+           "fk_window_q8.cu", "fk_window64.cu", "fk_march1d.cu", "fk_csr.cu",
            "fk_static.cu", "fk_batched.cu", "fk_adjoint.cu", "fk_march3d.cu", "fk_peak.cu"]
 
 

@@ -225,6 +225,12 @@ size_t fk_step2dm_smem(int ly, int lx);  // ly staged rows of lx nodes
 // when W is odd (the window is read in pairs of columns)
 int fk_step2dm_lx(int hx, int w);
 bool fk_masked_available(int q, int w);
+// The FP64 masked tensor-window kernel (fk_window64.cu): launcher, shared
+// memory of one CTA (ly staged rows of lx nodes) and the large-shared-memory
+// opt-in (plan creation only).
+cudaError_t fk_launch_step2dm64(const Step2D<double>& a, int q, cudaStream_t s);
+size_t fk_step2dm64_smem(int ly, int lx);
+cudaError_t fk_prepare_masked64(int q);
 // index k of the pattern m[0..q-1] among those of (q, w), or -1
 int fk_masked_pattern(int q, int w, const int* m);
 cudaError_t fk_prepare_masked_kernels(int q);

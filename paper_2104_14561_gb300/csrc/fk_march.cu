@@ -952,6 +952,9 @@ bool fk_window_available(int q, int w) {
 
 template <typename T>
 cudaError_t fk_launch_step2d(const Step2D<T>& a, int q, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    if (a.mode == 2) return fk_launch_step2dm64(a, q, s);  // masked tensor window, FP64
+  }
   if constexpr (sizeof(T) == 4) {
     if (a.mode == 2) return fk_launch_step2dm(a, q, s);  // masked tensor window
     if (a.win > 0) {
@@ -1000,6 +1003,10 @@ cudaError_t fk_launch_step1d(const Step1D<T>& a, int q, cudaStream_t s) {
 }
 
 cudaError_t fk_prepare_step_kernels(int dim, int q, int elem) {
+  if (dim == 2 && elem == 8) {
+    cudaError_t em = fk_prepare_masked64(q);
+    if (em != cudaSuccess) return em;
+  }
   if (dim == 2 && elem == 4) {
     cudaError_t em = fk_prepare_masked_kernels(q);
     if (em != cudaSuccess) return em;

@@ -430,7 +430,7 @@ void fill2d(const fk_plan* p, int n, Step2D<T>* a) {
     a->nb_lo = (a->row_lo - 1 + a->ty - 1) / a->ty;
     for (int q = 0; q < p->q; ++q) a->wm[q] = p->wm[q];
   }
-  if (sizeof(T) == 4 && p->use_masked && p->mwin > 0) {
+  if (p->use_masked && p->mwin > 0) {
     a->mode = 2;
     a->win = p->mwin;
     a->hx = p->mhalo[0];
@@ -497,7 +497,8 @@ bool cand_fits(const fk_plan* p, const TileCand& c, int dev_smem, int kern = kDi
   if (p->elem == 8 && c.variant != 0) return false;
   if (kern == kMasked) {
     const int lx = fk_step2dm_lx(p->mhalo[0], p->mwin), ly = c.ty + 2 * p->mhalo[1] + 2;
-    return fk_step2dm_smem(ly, lx) <= (size_t)dev_smem;
+    const size_t bytes = p->elem == 8 ? fk_step2dm64_smem(ly, lx) : fk_step2dm_smem(ly, lx);
+    return bytes <= (size_t)dev_smem;
   }
   const int hy = p->halo[1] + (kern == kRowWindow ? 1 : 0);
   const int lx = 32 + 2 * p->halo[0] + 2, ly = c.ty + 2 * hy + 2;
@@ -543,7 +544,7 @@ void window_eligibility(fk_plan* p) {
   p->win_max = W;
 }
 
-// The masked tensor-window kernel (FP32, 2D, matrix-free) needs: the cell
+// The masked tensor-window kernels (FP32 and FP64, 2D, matrix-free) need: the cell
 // offsets m_q = floor(g_q - g_0) the same on both axes (one uniform scatter
 // pattern for the x and the y weights) with the fractional part of
 // g_q - g_0 away from 0 and 1 by a margin that the FP32 rounding of the
@@ -554,17 +555,21 @@ void window_eligibility(fk_plan* p) {
 void masked_eligibility(fk_plan* p) {
   const double kMargin = 1e-4;
   p->mwin = 0;
-  if (p->grid.dim != 2 || p->prec != FK_FP32 || p->path != FK_PATH_MATRIX_FREE) return;
+  if (p->grid.dim != 2 || p->path != FK_PATH_MATRIX_FREE) return;
   if (p->periodic_x || p->nu) return;  // periodic x, non-uniform: the direct kernel only
   const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * p->dt);
-  float gx[FK_MAXQ_2D], gy[FK_MAXQ_2D];
+  double gx[FK_MAXQ_2D], gy[FK_MAXQ_2D];  // the offsets as the kernel holds them
   for (int q = 0; q < p->q; ++q) {
-    gx[q] = (float)(sg * p->gh_a[q] / p->h[0]);
-    gy[q] = (float)(sg * p->gh_a[q] / p->h[1]);
+    gx[q] = sg * p->gh_a[q] / p->h[0];
+    gy[q] = sg * p->gh_a[q] / p->h[1];
+    if (p->prec == FK_FP32) {
+      gx[q] = (double)(float)gx[q];
+      gy[q] = (double)(float)gy[q];
+    }
   }
   p->mwm[0] = 0;
   for (int q = 1; q < p->q; ++q) {
-    const double dx = (double)gx[q] - (double)gx[0], dy = (double)gy[q] - (double)gy[0];
+    const double dx = gx[q] - gx[0], dy = gy[q] - gy[0];
     const double fx = dx - floor(dx), fy = dy - floor(dy);
     if (fx < kMargin || fx > 1.0 - kMargin || fy < kMargin || fy > 1.0 - kMargin) return;
     if (floor(dx) != floor(dy)) return;
@@ -575,8 +580,9 @@ void masked_eligibility(fk_plan* p) {
   p->mpat = fk_masked_pattern(p->q, W, p->mwm);
   if (p->mpat < 0) return;
   for (int m = 0; m < 2; ++m) {
-    // |error of an FP32 position difference| <= 2 ulp(reach + 1) << margin
-    if ((p->reach[m] + 1.0) * 4.8e-7 > 0.5 * kMargin) return;
+    // |error of a position difference| <= 2 ulp(reach + 1) << margin
+    const double ulp2 = p->prec == FK_FP32 ? 4.8e-7 : 4.5e-16;
+    if ((p->reach[m] + 1.0) * ulp2 > 0.5 * kMargin) return;
     const double r = p->reach[m] * (1.0 + 1e-6) + 1e-3;
     p->mhalo[m] = (int)floor(r) + 2;
   }
