@@ -250,7 +250,7 @@ def run_reference(args, rank: int):
     # one benchmark step of the reference arm = one time step of the march
     # (of every instance, for the batched sweep): a bounded sample of the
     # workload, so that K + W steps take seconds to a minute
-    ws = (fk_inputs.batched_instances() if args.workload == "batched_64"
+    ws = (fk_inputs.batch(args.workload) if args.workload in fk_inputs.BATCHES
           else [fk_inputs.workload(args.workload)])
     w = ws[0]
     cores = os.cpu_count() or 1
@@ -309,7 +309,7 @@ def run_batched(args, rank: int, world: int, local_rank: int):
     import paper_2104_14561_gb300 as fk
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    ws = fk_inputs.batched_instances()
+    ws = fk_inputs.batch(args.workload)
     if args.time_steps:
         ws = [dict(x, n_steps=args.time_steps) for x in ws]
     plans = [fk.Plan(fk.PlanSpec(n=w["n"], lo=w["lo"], hi=w["hi"], family=w["family"],
@@ -355,14 +355,14 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "batched_64", "instances": len(ws), "nodes": nodes,
+        "config": {"workload": args.workload, "instances": len(ws), "nodes": nodes,
                    "q_per_dim": 6, "time_steps": ws[0]["n_steps"], "dt": 1e-3,
                    "l2": "flushed (512 MB write) before every timed march"},
         "batch_mode": mode,
         "persistent_kernel": {"value": units / (ms_k * 1e-3), "ms_per_step": ms_k,
                               "how": "the cooperative persistent kernel, forced"},
         "plain_march": {"value": units / (ms_p * 1e-3), "ms_per_step": ms_p,
-                        "how": "64 fk_solve calls (one CUDA graph each) on one stream"},
+                        "how": f"{len(ws)} fk_solve calls (one CUDA graph each) on one stream"},
         "gpu_launches": args.steps * (sum(w["n_steps"] + 1 for w in ws) if mode == "streams"
                                       else 1 + len(ws)),
         "clocks": clocks,
@@ -788,7 +788,7 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        if args.workload == "batched_64":
+        if args.workload in fk_inputs.BATCHES:
             run_batched(args, rank, world, local_rank)
         elif args.workload == "adjoint_1025x513":
             run_adjoint(args, rank, world, local_rank)

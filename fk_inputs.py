@@ -97,6 +97,19 @@ WORKLOADS = {
                              params=(0.3, 1e5, 1.0, 0.042, 1.0, 1.0, 0.7, 1e-2, 20.0, 0.003,
                                      1e-4),
                              q=4, dt=5e-3, n_steps=4800, precision="fp32"),
+    # the thermal-quench variant at the end of Sec. 4.3 at the constants the
+    # paper prints there (E_0 = 1e-3, tau = 6000, Z = 1, T0 = 3, Tf = 0.005,
+    # Ttilde = 3 keV, r_D = 0, W = 1e-4, Delta_p = 2, V_0 = 0) with the free
+    # pair D_0 = 0.01 (the value of the paper's figure) and t_star = 2, mc2 =
+    # 511 keV; the static model's box, T = 12.  As the plasma cools the
+    # collision rates grow as T^{-3/2} (pitch-angle scattering reaches
+    # sigma_xi ~ 1.9), so the xi axis has 33 nodes and dt = 1e-3 to keep
+    # every shifted point within the 3D node window
+    "runaway_quench_97x33x41": dict(n=(97, 33, 41), lo=(2.0, -1.0, 0.0), hi=(50.0, 1.0, 1.0),
+                                    family="runaway_quench",
+                                    params=(1e-3, 6000.0, 1.0, 3.0, 0.005, 3.0, 2.0, 0.0, 1e-4,
+                                            2.0, 0.0, 0.01, 511.0),
+                                    q=4, dt=1e-3, n_steps=12000, precision="fp32"),
     # every horizon t_k = k dt, k = 1..200, of the time-dependent flow (Algorithm 1)
     "horizons_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
                               family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
@@ -147,6 +160,17 @@ def batched_instances(count: int = 64, seed: int = BATCH_SEED, nx_range=(257, 20
                         params=(A, 0.2, TWO_PI, D), q=6, dt=1e-3, n_steps=1000,
                         precision="fp32"))
     return out
+
+
+# batched workloads: the 64-instance sweep, and a launch-bound batch of 256
+# small instances (nx in [33, 129]) drawn the same way
+BATCHES = {"batched_64": dict(count=64, nx_range=(257, 2049)),
+           "batched_small_256": dict(count=256, nx_range=(33, 129))}
+
+
+def batch(name: str):
+    """The instances of a named batched workload."""
+    return batched_instances(**BATCHES[name])
 
 
 def random_field(shape, seed: int, modes: int = 6, boundary_one: bool = True) -> np.ndarray:

@@ -27,8 +27,10 @@
 //    into u^n at every node of an absorbing face (Eq. (e3): 1, or the face's
 //    exit value in the runaway model);
 //  * k_step3d forms each updated node's 1D weights in registers and sums
-//    the W^3 records of its window, read through L1/L2 (a warp's 32
-//    consecutive x-nodes read overlapping, contiguous windows).
+//    the records of its window, read through L1/L2 (a warp's 32
+//    consecutive x-nodes read overlapping, contiguous windows); with
+//    per-node coefficients, only the planes, rows and cells its own points
+//    reach, often far fewer than the W^3 the widest node needs.
 // Positions are taken relative to the node in cells: point p of axis m is
 // at i_m + rel_p with rel_p = b_m dt / h_m + sigma_m sqrt(2 dt) a_p / h_m.
 //
@@ -129,11 +131,16 @@ __global__ void __launch_bounds__(kRecThreads) k_chi3d(const Step3D<T> a, T* u) 
 // with value 1 (E1) and with value 0 (E0, the runaway faces only); with RE
 // a point beyond a reflecting face is mirrored into the box first.  Sets
 // bad when an inside point's cell falls outside the window (the plan's W
-// rules this out; the check keeps every read in bounds regardless).
+// rules this out; the check keeps every read in bounds regardless).  The
+// slots that can carry weight are [tlo, thi] (empty, tlo > thi, when every
+// point exits): W covers the widest spread on the mesh, and a node whose
+// points spread less needs fewer of the window's records.
 template <typename T, int W, bool RE>
 __device__ __forceinline__ void axis_weights(const Step3D<T>& a, int m, int i, int n, T sh, T gs,
                                              T (&V)[W], T (&D)[W], T& E1, T& E0, int& org,
-                                             unsigned& bad) {
+                                             int& tlo, int& thi, unsigned& bad) {
+  tlo = W;
+  thi = -1;
 #pragma unroll
   for (int t = 0; t < W; ++t) {
     V[t] = T(0);
@@ -178,6 +185,10 @@ __device__ __forceinline__ void axis_weights(const Step3D<T>& a, int m, int i, i
       E1 += (!in && rule == FK_FACE_EXIT1) ? wq : T(0);
       if constexpr (RE) E0 += (!in && rule == FK_FACE_EXIT0) ? wq : T(0);
       const T wi = (in && ok) ? wq : T(0);
+      if (in && ok) {
+        tlo = off < tlo ? off : tlo;
+        thi = off + 1 > thi ? off + 1 : thi;
+      }
       // cubic Hermite basis on a unit cell (Sec. 3.1.3)
       const T s2 = s * s, r1 = T(1) - s;
       const T h00 = (T(1) + T(2) * s) * r1 * r1, h01 = s2 * (T(3) - T(2) * s);
@@ -290,28 +301,35 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
   // 1D weights per axis
   T Vx[W], Dx[W], Vy[W], Dy[W], Vz[W], Dz[W];
   T E1x, E0x, E1y, E0y, E1z, E0z;
-  int ox, oy, oz;
+  int ox, oy, oz, xlo, xhi, ylo, yhi, zlo, zhi;
   unsigned bad = 0;
-  axis_weights<T, W, RE>(a, 0, i, a.nx, sh[0], gs[0], Vx, Dx, E1x, E0x, ox, bad);
-  axis_weights<T, W, RE>(a, 1, j, a.ny, sh[1], gs[1], Vy, Dy, E1y, E0y, oy, bad);
-  axis_weights<T, W, RE>(a, 2, k, a.nz, sh[2], gs[2], Vz, Dz, E1z, E0z, oz, bad);
+  axis_weights<T, W, RE>(a, 0, i, a.nx, sh[0], gs[0], Vx, Dx, E1x, E0x, ox, xlo, xhi, bad);
+  axis_weights<T, W, RE>(a, 1, j, a.ny, sh[1], gs[1], Vy, Dy, E1y, E0y, oy, ylo, yhi, bad);
+  axis_weights<T, W, RE>(a, 2, k, a.nz, sh[2], gs[2], Vz, Dz, E1z, E0z, oz, zlo, zhi, bad);
 
   const V4<T>* R = a.rec;
   const T uj = R[node].x;
-  // one plane c of the window: its W x W records against the x and y weights
+  // one plane c of the window: its W x W records against the x and y
+  // weights.  With per-node coefficients (RE) only the rows [ylo, yhi] and
+  // cells [xlo, xhi] that can carry weight are read (the others would add
+  // exact zeros); with constant coefficients every node reaches the whole
+  // window, and the unconditional loops schedule better.
   auto plane_sum = [&](int c, T vz, T dz) {
     const V4<T>* plane = R + (int64_t)(oz + c) * sz + (int64_t)oy * sy + ox;
     T P = T(0), Pz = T(0);
 #pragma unroll
     for (int b = 0; b < W; ++b) {
+      if (RE && (b < ylo || b > yhi)) continue;
       const V4<T>* row = plane + (int64_t)b * sy;
       T s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
       for (int t = 0; t < W; ++t) {
-        const V4<T> r = row[t];
-        s1 += Vx[t] * (r.x - uj) + Dx[t] * r.y;
-        s2 += Vx[t] * r.z;
-        s3 += Vx[t] * r.w;
+        if (!RE || (t >= xlo && t <= xhi)) {
+          const V4<T> r = row[t];
+          s1 += Vx[t] * (r.x - uj) + Dx[t] * r.y;
+          s2 += Vx[t] * r.z;
+          s3 += Vx[t] * r.w;
+        }
       }
       P += Vy[b] * s1 + Dy[b] * s2;
       Pz += Vy[b] * s3;
@@ -320,10 +338,10 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
   };
   T acc = T(0);
   if constexpr (RE) {
-    // planes in a loop (the runaway instantiations would double the build
-    // time if unrolled as well)
+    // planes in a loop over the reached ones (the runaway instantiations
+    // would double the build time if unrolled as well)
 #pragma unroll 1
-    for (int c = 0; c < W; ++c) acc += plane_sum(c, pick<W>(Vz, c), pick<W>(Dz, c));
+    for (int c = zlo; c <= zhi; ++c) acc += plane_sum(c, pick<W>(Vz, c), pick<W>(Dz, c));
   } else {
 #pragma unroll
     for (int c = 0; c < W; ++c) acc += plane_sum(c, Vz[c], Dz[c]);

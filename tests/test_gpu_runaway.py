@@ -8,7 +8,10 @@ seeded inputs.  Tolerances (max-abs): 1e-12 FP64, 1e-5 FP32.
   xi = +-1 and r = 0);
 * one step from a random field (every face's nodes included);
 * every horizon (Algorithm 1) from the runaway indicator;
-* the 97 x 65 x 41 benchmark workload over one step at sampled nodes.
+* the 97 x 65 x 41 benchmark workload over one step at sampled nodes;
+* the thermal-quench variant: whole marches at a strong-field test set and
+  at the constants the paper prints for it (p up to 50), every horizon, and
+  one late step of its 97 x 33 x 41 workload at sampled nodes.
 """
 import os
 
@@ -184,3 +187,49 @@ def test_quench_horizons(fk, oracle):
     plan.close()
     for k in (1, 6, 12):
         assert np.abs(hz[k - 1] - _oracle_q(oracle, w, k)).max() <= 1e-12, k
+
+
+# the constants the paper prints for the quench (E_0 = 1e-3, tau = 6000,
+# r_D = 0, W = 1e-4, Delta_p = 2, V_0 = 0), D_0 = 0.01, t_star = 2
+QUENCH_PAPER = fk_inputs.workload("runaway_quench_97x33x41")["params"]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_quench_paper_parameters_vs_oracle(fk, oracle, precision, tol):
+    """A whole march to T = 10 at the paper's quench constants on p in (2,
+    50): the temperature falls from 3 keV to about 25 eV and the field grows
+    from 1e-3 to about 1.3, so that a runaway probability spreads from the
+    p_max face into the interior."""
+    import torch
+    w = dict(n=(25, 9, 11), lo=(2.0, -1.0, 0.0), hi=(50.0, 1.0, 1.0), family="runaway_quench",
+             params=QUENCH_PAPER, q=4, dt=0.01, n_steps=1000, precision=precision)
+    plan = fk.Plan(_spec_q(fk, w))
+    got = plan.solve().double().cpu().numpy()
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    plan.close()
+    want = _oracle_q(oracle, w)
+    assert want[:, :, :-1].max() > 1e-3  # off the p_max face
+    assert np.abs(got - want).max() <= tol
+
+
+def test_quench_workload_sampled_late_step(fk, oracle):
+    """The 97 x 33 x 41 quench workload (FP32): one step at n = 8000 (t =
+    8, about 35 eV) from a random field, at sampled nodes against the
+    oracle's step there."""
+    import torch
+    w = fk_inputs.workload("runaway_quench_97x33x41")
+    shape = tuple(reversed(w["n"]))
+    plan = fk.Plan(_spec_q(fk, w))
+    assert plan.info()["window_rows"] <= 8
+    u1 = fk_inputs.random_field(shape, seed=79, boundary_one=False)
+    n = 8000
+    got = plan.march(n + 1, n, torch.tensor(u1, dtype=torch.float32, device="cuda"))
+    got = got.double().cpu().numpy().reshape(-1)
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    plan.close()
+    nodes = fk_inputs.sample_nodes(shape, 3000, seed=17)
+    want = oracle.step_nodes(_grid(oracle, w), oracle.RUNAWAY_QUENCH, list(w["params"]), w["q"],
+                             w["dt"], n, u1, nodes, nthreads=NCPU)
+    assert np.abs(got[nodes] - want).max() <= 1e-5
