@@ -110,6 +110,13 @@ WORKLOADS = {
                                     params=(1e-3, 6000.0, 1.0, 3.0, 0.005, 3.0, 2.0, 0.0, 1e-4,
                                             2.0, 0.0, 0.01, 511.0),
                                     q=4, dt=1e-3, n_steps=12000, precision="fp32"),
+    # the same model on the paper's non-uniform radial grid (Sec. 4.3): r
+    # spaced 0.1 on [0, r_D] and 0.0025 on [r_D, 1] (8 + 120 cells), which
+    # resolves the boundary layer at r_D = 0.7
+    "runaway_nonuniform_97x65x128": dict(
+        n=(97, 65, 128), lo=(2.0, -1.0, 0.0), hi=(50.0, 1.0, 1.0), family="runaway",
+        params=(0.3, 1e5, 1.0, 0.042, 1.0, 1.0, 0.7, 1e-2, 20.0, 0.003, 1e-4),
+        q=4, dt=5e-3, n_steps=4800, precision="fp32", r_axis=(0.7, 0.1, 0.0025)),
     # every horizon t_k = k dt, k = 1..200, of the time-dependent flow (Algorithm 1)
     "horizons_1025x513": dict(n=(1025, 513), lo=(0.0, 0.0), hi=(2.0, 1.0),
                               family="cellular_flow", params=(1.0, 0.2, TWO_PI, 1e-3),
@@ -129,8 +136,21 @@ def graded_axis(lo: float, hi: float, n: int, strength: float) -> np.ndarray:
     return x
 
 
+def two_spacing_axis(lo: float, mid: float, hi: float, coarse: float, fine: float) -> np.ndarray:
+    """Coordinates spaced `coarse` on [lo, mid] and `fine` on [mid, hi] (the
+    shape of the paper's non-uniform radial grid of Sec. 4.3)."""
+    a = lo + np.arange(0, int(round((mid - lo) / coarse))) * coarse
+    b = mid + np.arange(0, int(round((hi - mid) / fine)) + 1) * fine
+    x = np.concatenate([a, b])
+    x[0], x[-1] = lo, hi
+    return x
+
+
 def axes_of(w: dict):
-    """The node coordinates of a workload with graded axes, else None."""
+    """The node coordinates of a workload with graded or explicit axes, else
+    None (uniform)."""
+    if w.get("axes") is not None:
+        return tuple(None if a is None else np.asarray(a, dtype=np.float64) for a in w["axes"])
     if not w.get("graded"):
         return None
     return tuple(graded_axis(w["lo"][m], w["hi"][m], w["n"][m], w["graded"][m])
@@ -141,6 +161,11 @@ def workload(name: str, **override) -> dict:
     w = dict(WORKLOADS[name])
     w.setdefault("path", "matrix_free")
     w.update(override)
+    if w.get("r_axis") and w.get("axes") is None:
+        mid, coarse, fine = w["r_axis"]
+        r = two_spacing_axis(w["lo"][2], mid, w["hi"][2], coarse, fine)
+        assert len(r) == w["n"][2], (len(r), w["n"][2])
+        w["axes"] = (None, None, r)
     return w
 
 

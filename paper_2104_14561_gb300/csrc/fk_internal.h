@@ -188,6 +188,13 @@ struct Step3D {
   // count[m] - 1 (the nodes of reflecting faces included)
   int face[3][2];
   int first[3], count[3];
+  // non-uniform axes (nu): node coordinates per axis in T (positions of the
+  // shifted points, cells, widths) and in FP64 (the runaway coefficients);
+  // cd and gs are then physical lengths b dt and sigma sqrt(2 dt), the
+  // records hold raw derivatives {u, u_x, u_y, u_z}
+  int nu;
+  const T* xc[3];
+  const double* xd[3];
 };
 template <typename T>
 cudaError_t fk_launch_step3d(const Step3D<T>& a, cudaStream_t s);
@@ -329,8 +336,9 @@ struct fk_plan {
   int batch_grid;    // CTAs of the last batched launch
   int periodic_x;    // the x faces are identified (region FK_PERIODIC_X)
   int nu;            // non-uniform axes: node coordinates per axis
-  double* hcoord[2]; // host copies (malloc) and device copies in the plan's precision
-  void* dcoord[2];
+  double* hcoord[3]; // host copies (malloc) and device copies in the plan's precision
+  void* dcoord[3];
+  void* dcoord64[3]; // d = 3, FP32 plans: FP64 device copies (runaway coefficients)
   // d = 3: the node records of the step and the window width
   void* rec3d;
   int w3;

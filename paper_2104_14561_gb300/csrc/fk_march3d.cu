@@ -90,18 +90,24 @@ __global__ void __launch_bounds__(kRecThreads) k_rec3d(const Step3D<T> a) {
   const int64_t sy = a.nx, sz = (int64_t)a.nx * a.ny;
   const int64_t node = (int64_t)k * sz + (int64_t)j * sy + i;
   const T* u = a.u_in;
-  // slope of Eq. (e300) along one axis at index idx (n nodes, stride st)
-  auto slope = [&](int idx, int n, int64_t st) {
+  // slope of Eq. (e300) along axis m at index idx (n nodes, stride st):
+  // scaled by the cell on a uniform mesh, a raw derivative from the
+  // divided differences over the actual spacings on a non-uniform one
+  auto slope = [&](int m, int idx, int n, int64_t st) {
     const int c = idx < 1 ? 1 : (idx > n - 2 ? n - 2 : idx);
     const T* b = u + node + (int64_t)(c - idx) * st;
     const T um = b[-st], u0 = b[0], up = b[st];
+    if (a.nu) {
+      const T* x = a.xc[m];
+      return pchip_fast((u0 - um) / (x[c] - x[c - 1]), (up - u0) / (x[c + 1] - x[c]));
+    }
     return pchip_fast(u0 - um, up - u0);
   };
   V4<T> r;
   r.x = u[node];
-  r.y = slope(i, a.nx, 1);
-  r.z = slope(j, a.ny, sy);
-  r.w = slope(k, a.nz, sz);
+  r.y = slope(0, i, a.nx, 1);
+  r.z = slope(1, j, a.ny, sy);
+  r.w = slope(2, k, a.nz, sz);
   a.rec[node] = r;
   const T held = held_value(a, i, j, k);
   if (held >= T(0)) {
@@ -202,6 +208,88 @@ __device__ __forceinline__ void axis_weights(const Step3D<T>& a, int m, int i, i
   }
 }
 
+// The same 1D weights on a non-uniform axis (node coordinates x[0..n-1]):
+// points at x_i + sh + gs a_q in physical lengths (sh = b dt, gs = sigma
+// sqrt(2 dt)), each located by walking from the node's cell (the last node
+// at or left of the point, clamped to a cell, as the oracle's bisection
+// finds it), the cell's own width scaling the slope basis (the records hold
+// raw derivatives).  The window starts at the lowest cell an inside point
+// reaches (mirrored points included), clamped to [0, n - W].
+template <typename T, int W, bool RE>
+__device__ __forceinline__ void axis_weights_nu(const Step3D<T>& a, int m, int i, int n, T sh,
+                                                T gs, T (&V)[W], T (&D)[W], T& E1, T& E0,
+                                                int& org, int& tlo, int& thi, unsigned& bad) {
+  const T* __restrict__ x = a.xc[m];
+#pragma unroll
+  for (int t = 0; t < W; ++t) {
+    V[t] = T(0);
+    D[t] = T(0);
+  }
+  E1 = T(0);
+  E0 = T(0);
+  tlo = W;
+  thi = -1;
+  const T lo = x[0], hi = x[n - 1], xi = x[i];
+  int rlo = FK_FACE_EXIT1, rhi = FK_FACE_EXIT1;
+  if constexpr (RE) {
+    rlo = a.face[m][0];
+    rhi = a.face[m][1];
+  }
+  T z[FK_MAXQ_2D];
+  int cq[FK_MAXQ_2D];
+  int cmin = n;
+#pragma unroll
+  for (int q = 0; q < FK_MAXQ_2D; ++q) {
+    if (q < a.q) {
+      T v = xi + sh + gs * a.ga[q];
+      if constexpr (RE) {
+        if (v < lo && rlo == FK_FACE_REFLECT) v = T(2) * lo - v;
+        if (v > hi && rhi == FK_FACE_REFLECT) v = T(2) * hi - v;
+      }
+      int c = i < n - 2 ? i : n - 2;
+      while (c > 0 && x[c] > v) --c;
+      while (c < n - 2 && x[c + 1] <= v) ++c;
+      z[q] = v;
+      cq[q] = c;
+      if (!(v < lo || v > hi)) cmin = c < cmin ? c : cmin;
+    }
+  }
+  int o = cmin > n - W ? n - W : cmin;
+  o = o < 0 ? 0 : o;
+  org = o;
+#pragma unroll
+  for (int q = 0; q < FK_MAXQ_2D; ++q) {
+    if (q < a.q) {
+      const T v = z[q];
+      const T wq = a.gw[q];
+      const bool below = v < lo, above = v > hi;
+      const bool in = !(below || above);
+      const int c = cq[q];
+      const T h = x[c + 1] - x[c];
+      const T s = (v - x[c]) / h;
+      const int off = c - o;
+      const bool ok = off >= 0 && off <= W - 2;
+      if (in && !ok) bad = 1u;
+      const int rule = below ? rlo : rhi;
+      E1 += (!in && rule == FK_FACE_EXIT1) ? wq : T(0);
+      if constexpr (RE) E0 += (!in && rule == FK_FACE_EXIT0) ? wq : T(0);
+      const T wi = (in && ok) ? wq : T(0);
+      if (in && ok) {
+        tlo = off < tlo ? off : tlo;
+        thi = off + 1 > thi ? off + 1 : thi;
+      }
+      const T s2 = s * s, r1 = T(1) - s;
+      const T h00 = (T(1) + T(2) * s) * r1 * r1, h01 = s2 * (T(3) - T(2) * s);
+      const T h10 = h * (s * r1 * r1), h11 = -h * (s2 * r1);
+#pragma unroll
+      for (int t = 0; t < W; ++t) {
+        V[t] += (t == off) ? wi * h00 : ((t == off + 1) ? wi * h01 : T(0));
+        D[t] += (t == off) ? wi * h10 : ((t == off + 1) ? wi * h11 : T(0));
+      }
+    }
+  }
+}
+
 // Entry t of a register array indexed by a runtime value (a select per
 // entry keeps the array in registers).
 template <int W, typename T>
@@ -221,7 +309,8 @@ __device__ __forceinline__ double erf_t<double>(double x) { return erf(x); }
 
 // Drift and diagonal sigma of the runaway-electron model at node (i, j, k)
 // (Eq. (ex32d) of Sec. 4.3), returned as the point shift sh = b dt / h and
-// scale gs = sigma sqrt(2 dt) / h per axis, in cells.  Collision functions
+// scale gs = sigma sqrt(2 dt) / h per axis, in cells (NU: physical lengths
+// b dt and sigma sqrt(2 dt), at the plan's FP64 node coordinates).  Collision functions
 // C_A = nu v_T^2 psi(y)/y, C_B = (nu v_T^2 / 2y)[Z + phi(y) - psi(y) +
 // y^2 delta^4 / 2], C_F = 2 nu v_T psi(y) with phi = erf, psi(y) =
 // (phi - y phi') / (2 y^2), y = p / gamma, gamma = sqrt(1 + (delta p)^2);
@@ -229,12 +318,19 @@ __device__ __forceinline__ double erf_t<double>(double x) { return erf(x); }
 // 1/gamma^3, psi' = phi' - 2 psi / y).  The node coordinates are formed in
 // FP64 without contraction, and the step V(r) = V_0 1{r > r_D} is decided
 // there; the rest runs in T.
-template <typename T>
+template <typename T, bool NU>
 __device__ __forceinline__ void runaway_coef(const Step3D<T>& a, int i, int j, int k, T (&sh)[3],
                                              T (&gs)[3]) {
-  const double xp = __dadd_rn(a.lo[0], __dmul_rn((double)i, a.h[0]));
-  const double xx = __dadd_rn(a.lo[1], __dmul_rn((double)j, a.h[1]));
-  const double xr = __dadd_rn(a.lo[2], __dmul_rn((double)k, a.h[2]));
+  double xp, xx, xr;
+  if constexpr (NU) {  // the FP64 node coordinates of the plan
+    xp = a.xd[0][i];
+    xx = a.xd[1][j];
+    xr = a.xd[2][k];
+  } else {
+    xp = __dadd_rn(a.lo[0], __dmul_rn((double)i, a.h[0]));
+    xx = __dadd_rn(a.lo[1], __dmul_rn((double)j, a.h[1]));
+    xr = __dadd_rn(a.lo[2], __dmul_rn((double)k, a.h[2]));
+  }
   const bool beyond = xr > a.rp[6];
   const T mom = (T)xp, xi = (T)xx, r = (T)xr;
   const T E = (T)a.rp[0], tau = (T)a.rp[1], Z = (T)a.rp[2], delta = (T)a.rp[3];
@@ -272,12 +368,17 @@ __device__ __forceinline__ void runaway_coef(const Step3D<T>& a, int i, int j, i
   const T b[3] = {b0, b1, b2}, sg[3] = {s0, s1, s2};
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    sh[m] = b[m] * a.dt / (T)a.h[m];
-    gs[m] = sg[m] * a.sq2dt / (T)a.h[m];
+    if constexpr (NU) {  // physical lengths
+      sh[m] = b[m] * a.dt;
+      gs[m] = sg[m] * a.sq2dt;
+    } else {
+      sh[m] = b[m] * a.dt / (T)a.h[m];
+      gs[m] = sg[m] * a.sq2dt / (T)a.h[m];
+    }
   }
 }
 
-template <typename T, int W, bool RE>
+template <typename T, int W, bool RE, bool NU>
 __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
   const int i = a.first[0] + blockIdx.x * blockDim.x + threadIdx.x;
   const int j = a.first[1] + blockIdx.y, k = a.first[2] + blockIdx.z;
@@ -289,7 +390,7 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
   // the constant drift, per node for the runaway model
   T sh[3], gs[3];
   if constexpr (RE) {
-    runaway_coef(a, i, j, k, sh, gs);
+    runaway_coef<T, NU>(a, i, j, k, sh, gs);
   } else {
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -303,9 +404,15 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
   T E1x, E0x, E1y, E0y, E1z, E0z;
   int ox, oy, oz, xlo, xhi, ylo, yhi, zlo, zhi;
   unsigned bad = 0;
-  axis_weights<T, W, RE>(a, 0, i, a.nx, sh[0], gs[0], Vx, Dx, E1x, E0x, ox, xlo, xhi, bad);
-  axis_weights<T, W, RE>(a, 1, j, a.ny, sh[1], gs[1], Vy, Dy, E1y, E0y, oy, ylo, yhi, bad);
-  axis_weights<T, W, RE>(a, 2, k, a.nz, sh[2], gs[2], Vz, Dz, E1z, E0z, oz, zlo, zhi, bad);
+  if constexpr (NU) {
+    axis_weights_nu<T, W, RE>(a, 0, i, a.nx, sh[0], gs[0], Vx, Dx, E1x, E0x, ox, xlo, xhi, bad);
+    axis_weights_nu<T, W, RE>(a, 1, j, a.ny, sh[1], gs[1], Vy, Dy, E1y, E0y, oy, ylo, yhi, bad);
+    axis_weights_nu<T, W, RE>(a, 2, k, a.nz, sh[2], gs[2], Vz, Dz, E1z, E0z, oz, zlo, zhi, bad);
+  } else {
+    axis_weights<T, W, RE>(a, 0, i, a.nx, sh[0], gs[0], Vx, Dx, E1x, E0x, ox, xlo, xhi, bad);
+    axis_weights<T, W, RE>(a, 1, j, a.ny, sh[1], gs[1], Vy, Dy, E1y, E0y, oy, ylo, yhi, bad);
+    axis_weights<T, W, RE>(a, 2, k, a.nz, sh[2], gs[2], Vz, Dz, E1z, E0z, oz, zlo, zhi, bad);
+  }
 
   const V4<T>* R = a.rec;
   const T uj = R[node].x;
@@ -319,12 +426,12 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
     T P = T(0), Pz = T(0);
 #pragma unroll
     for (int b = 0; b < W; ++b) {
-      if (RE && (b < ylo || b > yhi)) continue;
+      if ((RE || NU) && (b < ylo || b > yhi)) continue;
       const V4<T>* row = plane + (int64_t)b * sy;
       T s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
       for (int t = 0; t < W; ++t) {
-        if (!RE || (t >= xlo && t <= xhi)) {
+        if (!(RE || NU) || (t >= xlo && t <= xhi)) {
           const V4<T> r = row[t];
           s1 += Vx[t] * (r.x - uj) + Dx[t] * r.y;
           s2 += Vx[t] * r.z;
@@ -337,7 +444,7 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
     return vz * P + dz * Pz;
   };
   T acc = T(0);
-  if constexpr (RE) {
+  if constexpr (RE || NU) {
     // planes in a loop over the reached ones (the runaway instantiations
     // would double the build time if unrolled as well)
 #pragma unroll 1
@@ -368,10 +475,17 @@ cudaError_t launch_w(const Step3D<T>& a, cudaStream_t s) {
   const int in = a.count[0];
   const int bx = in <= 32 ? 32 : (in <= 64 ? 64 : kRecThreads);
   const dim3 grid((unsigned)((in + bx - 1) / bx), (unsigned)a.count[1], (unsigned)a.count[2]);
-  if (a.family == FK_RUNAWAY_3D)
-    k_step3d<T, W, true><<<grid, bx, 0, s>>>(a);
-  else
-    k_step3d<T, W, false><<<grid, bx, 0, s>>>(a);
+  const bool re = a.family == FK_RUNAWAY_3D;
+  if (a.nu) {
+    if (re)
+      k_step3d<T, W, true, true><<<grid, bx, 0, s>>>(a);
+    else
+      k_step3d<T, W, false, true><<<grid, bx, 0, s>>>(a);
+  } else if (re) {
+    k_step3d<T, W, true, false><<<grid, bx, 0, s>>>(a);
+  } else {
+    k_step3d<T, W, false, false><<<grid, bx, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

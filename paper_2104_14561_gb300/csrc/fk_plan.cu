@@ -177,7 +177,9 @@ void runaway_params_at(const fk_plan* p, int n, double* p11) {
 // the mesh); running maxima in smax, bmax.
 void runaway_bounds_at(const fk_plan* p, const double* q11, double* smax, double* bmax) {
   const int n0 = p->grid.n[0], n1 = p->grid.n[1], n2 = p->grid.n[2];
-  auto x = [&](int m, int i) { return p->grid.lo[m] + (double)i * p->h[m]; };
+  auto x = [&](int m, int i) {
+    return p->nu ? p->hcoord[m][i] : p->grid.lo[m] + (double)i * p->h[m];
+  };
   double b[3], s[3];
   for (int i = 0; i < n0; ++i) {
     for (int j = 0; j < n1; ++j) {
@@ -261,7 +263,7 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
       return FK_ERR_UNSUPPORTED;
     if (r && r->absorbing_faces != FK_ALL_FACES_ABSORBING) return FK_ERR_UNSUPPORTED;
     for (int m = 0; m < 3; ++m)
-      if (g->axis[m] || g->n[m] > 65535) return FK_ERR_UNSUPPORTED;
+      if (g->n[m] > 65535) return FK_ERR_UNSUPPORTED;
   }
   if (q < 1 || q > (g->dim == 1 ? FK_MAXQ : FK_MAXQ_2D)) return FK_ERR_UNSUPPORTED;
   if (r && r->absorbing_faces != FK_ALL_FACES_ABSORBING) {
@@ -291,7 +293,7 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
 }
 
 void free_coords(fk_plan* p) {
-  for (int m = 0; m < 2; ++m) {
+  for (int m = 0; m < 3; ++m) {
     free(p->hcoord[m]);
     p->hcoord[m] = nullptr;
   }
@@ -303,7 +305,9 @@ fk_status cuda_status(cudaError_t e) {
   return FK_ERR_CUDA;
 }
 
-// Node coordinates of a non-uniform plan, in the plan's precision.
+// Node coordinates of a non-uniform plan, in the plan's precision (and, for
+// an FP32 plan in d = 3, in FP64 as well: the runaway coefficients are
+// evaluated at the FP64 node coordinates).
 template <typename T>
 fk_status upload_coords(fk_plan* p) {
   for (int m = 0; m < p->grid.dim; ++m) {
@@ -313,6 +317,12 @@ fk_status upload_coords(fk_plan* p) {
     fk_status st = fk_dev_alloc(p, &p->dcoord[m], sizeof(T) * nm);
     if (st == FK_OK)
       st = cuda_status(cudaMemcpy(p->dcoord[m], c.data(), sizeof(T) * nm, cudaMemcpyHostToDevice));
+    if (st == FK_OK && p->grid.dim == 3 && sizeof(T) == 4) {
+      st = fk_dev_alloc(p, &p->dcoord64[m], sizeof(double) * nm);
+      if (st == FK_OK)
+        st = cuda_status(cudaMemcpy(p->dcoord64[m], p->hcoord[m], sizeof(double) * nm,
+                                    cudaMemcpyHostToDevice));
+    }
     if (st != FK_OK) return st;
   }
   return FK_OK;
@@ -839,8 +849,17 @@ void fill3d(const fk_plan* p, int n, Step3D<T>* a) {
   a->w3 = p->w3;
   const double sg = sigma_of(&p->coeffs) * sqrt(2.0 * p->dt);
   for (int m = 0; m < 3; ++m) {
-    a->cd[m] = (T)(p->coeffs.p[m] * p->dt / p->h[m]);
-    a->gs[m] = (T)(sg / p->h[m]);
+    // in cells of a uniform mesh, physical lengths on a non-uniform one
+    const double hm = p->nu ? 1.0 : p->h[m];
+    a->cd[m] = (T)(p->coeffs.p[m] * p->dt / hm);
+    a->gs[m] = (T)(sg / hm);
+  }
+  if (p->nu) {
+    a->nu = 1;
+    for (int m = 0; m < 3; ++m) {
+      a->xc[m] = (const T*)p->dcoord[m];
+      a->xd[m] = (const double*)(sizeof(T) == 8 ? p->dcoord[m] : p->dcoord64[m]);
+    }
   }
   for (int q = 0; q < p->q; ++q) {
     a->ga[q] = (T)p->gh_a[q];
@@ -1187,6 +1206,34 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
       }
     }
     for (int m = 0; m < 3; ++m) {
+      if (p->nu) {
+        // non-uniform axis: every point of node i (mirrored ones included)
+        // lies within R of x_i and in the box, so its window covers the
+        // cells of [max(lo, x_i - R), min(hi, x_i + R)] and their right
+        // nodes
+        const double* x = p->hcoord[m];
+        const int nm = grid->n[m];
+        const double L = x[nm - 1] - x[0];
+        const double R = (bmax3[m] * dt + 0.5 * smax[m] * sqrt(2.0 * dt) *
+                                              (p->gh_a[q_per_dim - 1] - p->gh_a[0])) *
+                             (1.0 + 1e-6) + 1e-6 * L;
+        auto cell = [&](double z) {
+          int lo = 0, up = nm - 1;
+          while (up - lo > 1) {
+            const int mid = (lo + up) / 2;
+            if (x[mid] <= z) lo = mid; else up = mid;
+          }
+          return lo;  // in [0, nm-2]
+        };
+        int cells = 1;
+        for (int i = 0; i < nm; ++i)
+          cells = std::max(cells, cell(std::min(x[nm - 1], x[i] + R)) -
+                                      cell(std::max(x[0], x[i] - R)) + 1);
+        w = std::max(w, cells + 1);
+        p->reach[m] = 0.5 * cells;
+        p->halo[m] = cells + 1;
+        continue;
+      }
       const double span = smax[m] * sqrt(2.0 * dt) * (p->gh_a[q_per_dim - 1] - p->gh_a[0]) /
                           p->h[m];
       const double shift = bmax3[m] * dt / p->h[m];
@@ -1300,8 +1347,10 @@ fk_status fk_plan_destroy(fk_plan* p) {
   fk_dev_free(p->stack);
   fk_dev_free(p->batch_rec);
   fk_dev_free(p->hz_ws);
-  fk_dev_free(p->dcoord[0]);
-  fk_dev_free(p->dcoord[1]);
+  for (int m = 0; m < 3; ++m) {
+    fk_dev_free(p->dcoord[m]);
+    fk_dev_free(p->dcoord64[m]);
+  }
   free_coords(p);
   fk_dev_free(p->adj_ws);
   fk_dev_free(p->adj_tab);

@@ -84,7 +84,7 @@ CASES = [
     (dict(dim=3, n=(9, 9, 9), family=0, p=(0.1, 0, 0, 1.0), faces=0x3C), 2),
     (dict(dim=3, n=(9, 9, 9), family=0, p=(0.1, 0, 0, 1.0), path=1), 2),
     (dict(dim=3, n=(5, 5, 5), family=0, p=(0.1, 0, 0, 1.0),
-          axes=(None, None, [0.0, 0.1, 0.5, 0.7, 1.0])), 2),
+          axes=(None, None, [0.0, 0.1, 0.5, 0.7, 1.1])), 1),  # last coordinate != hi
     (dict(dim=3, n=(9, 9, 9), family=0, p=(0.1, 0, 0, 1.0), dt=0.05), 2),  # span > 6 cells
     (dict(dim=3, n=(4, 33, 33), family=0, p=(0.1, 0, 0, 0.3), dt=2e-3), 2),  # n < W on x
     # the runaway model: d = 3, p > 0, xi within [-1, 1], positive scales
