@@ -186,6 +186,12 @@ typedef struct fk_plan_info {
                                tensor window                             */
   int periodic_x;           /* 1: region FK_PERIODIC_X                   */
   int nonuniform;           /* 1: some axis has explicit coordinates     */
+  int march_mode;           /* whole marches without snapshots: 0 one
+                               launch per step, 1 one persistent launch
+                               for every step (2D FP32 masked kernel:
+                               tiles wait on their 3 x 3 neighbourhood's
+                               step counters, chosen at plan creation
+                               when a timed 16-step march is faster)     */
 } fk_plan_info;
 
 /* ------------------------------------------------------------------------

@@ -443,8 +443,12 @@ fk_status run_streams(int n, fk_plan* const* plans, const void* const* u_termina
   const bool whole = n_from == plans[0]->n_steps && n_to == 0;
   for (int b = 0; b < n && st == FK_OK; ++b) {
     cudaStream_t sb = bw->side[which[b]];
+    // no persistent march here: its CTAs wait on one another, which the
+    // plans running concurrently on other streams must not stand in for
+    plans[b]->no_persist = 1;
     st = whole ? fk_solve(plans[b], u_terminal[b], u_out[b], nullptr, 0, sb)
                : fk_march(plans[b], n_from, n_to, u_terminal[b], u_out[b], sb);
+    plans[b]->no_persist = 0;
   }
   // join every side stream, also after a failed enqueue
   for (int k = 0; k < K; ++k) {

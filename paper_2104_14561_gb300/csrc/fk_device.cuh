@@ -76,9 +76,30 @@ __device__ __forceinline__ float pchip_rcp(float dl, float dr) {
   return p > 0.f ? h + h : 0.f;
 }
 
-// Boundary nodes adjacent to interior node (i, k) hold 1 (Eq. (e3)).  On a
-// mesh with 3 nodes along an axis the single interior line is next to both
-// faces of that axis, so every flag is tested on its own.
+// Boundary nodes adjacent to interior node (i, k) hold 1 (Eq. (e3)), in
+// out (and snap when given).  On a mesh with 3 nodes along an axis the
+// single interior line is next to both faces of that axis, so every flag is
+// tested on its own.
+template <typename T>
+__device__ __forceinline__ void boundary_ones(T* out, T* snap, int nx_, int ny_, int i, int k) {
+  const int64_t nx = nx_;
+  const bool L = (i == 1), Rt = (i == nx_ - 2), B = (k == 1), Tp = (k == ny_ - 2);
+  if (L | Rt | B | Tp) {
+    const int64_t top = (int64_t)(ny_ - 1) * nx, row = (int64_t)k * nx;
+    auto one = [&](int64_t j) {
+      out[j] = T(1);
+      if (snap) snap[j] = T(1);
+    };
+    if (L) one(row);
+    if (Rt) one(row + nx - 1);
+    if (B) one(i);
+    if (Tp) one(top + i);
+    if (L & B) one(0);
+    if (Rt & B) one(nx - 1);
+    if (L & Tp) one(top);
+    if (Rt & Tp) one(top + nx - 1);
+  }
+}
 template <bool MF, typename T>
 __device__ __forceinline__ void write_adjacent_boundary(const Step2D<T>& a, int i, int k) {
   const int64_t nx = a.nx;

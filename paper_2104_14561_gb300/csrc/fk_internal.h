@@ -248,6 +248,29 @@ cudaError_t fk_launch_step2dm_q8(const Step2D<float>& a, cudaStream_t s);
 cudaError_t fk_prepare_masked_q4();
 cudaError_t fk_prepare_masked_q6();
 cudaError_t fk_prepare_masked_q8();
+// The persistent march of the FP32 masked kernel (fk_window.cuh): the steps
+// n_from-1 .. n_from-steps of one field in one cooperative launch, one CTA
+// per tile; step m reads u_first (m = 1) or buf[(steps - m + 1) & 1] and
+// writes buf[(steps - m) & 1].  flags (one word per tile) and abort must be
+// zero at launch.
+struct MaskedMarch {
+  const float* u_first;
+  float* buf[2];
+  const float2* e12;  // per time index n: the cellular flow's eps sin(omega t_n) factors
+  unsigned* flags;
+  unsigned* abort;
+  int n_from, steps;
+  int silent;  // tile that never publishes its step count (test hook; -1 none)
+};
+cudaError_t fk_launch_march2dm(const Step2D<float>& a, const MaskedMarch& m, int q,
+                               cudaStream_t s);
+bool fk_march2dm_fits(const Step2D<float>& a, int q);  // all tiles resident at once
+cudaError_t fk_launch_march2dm_q4(const Step2D<float>& a, const MaskedMarch& m, cudaStream_t s);
+cudaError_t fk_launch_march2dm_q6(const Step2D<float>& a, const MaskedMarch& m, cudaStream_t s);
+cudaError_t fk_launch_march2dm_q8(const Step2D<float>& a, const MaskedMarch& m, cudaStream_t s);
+bool fk_march2dm_fits_q4(const Step2D<float>& a);
+bool fk_march2dm_fits_q6(const Step2D<float>& a);
+bool fk_march2dm_fits_q8(const Step2D<float>& a);
 // (Q, W) pairs of the masked-window adjoint kernel (fk_adjoint.cu): the
 // window form pays off while W^2 cells stay below the direct form's 4 Q^2
 // corner reads and its weights fit in registers.
@@ -305,6 +328,16 @@ struct fk_plan {
   int mwm[FK_MAXQ_2D];  // its cell offsets floor(g_q - g_0), equal on both axes
   int mhalo[2];      // its halo per axis
   int mpat;          // index of its cell-offset pattern among those of (q, mwin)
+  // the persistent march of the masked kernel (fk_window.cuh): whether
+  // whole marches use it (1), its tile flags and abort word, and the
+  // per-step drift factors; batch: the batched call forbids it while its
+  // plans run concurrently
+  int persist;
+  unsigned* mflags;
+  int64_t mflags_n;
+  float2* me12;
+  int no_persist;
+  int g_persist;     // the cached graph was built with the persistent march
   int use_masked;    // the masked kernel is the step kernel
   int resident1d;    // 1D: 0 one launch per step, 1 the whole march in one CTA,
                      // 2 in one cluster of cluster1d CTAs (fk_march1d.cu)

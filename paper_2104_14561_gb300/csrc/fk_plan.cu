@@ -798,6 +798,90 @@ fk_status autotune(fk_plan* p) {
   return st;
 }
 
+fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void* u_out,
+                        void* snaps, int stride, cudaStream_t s);
+bool use_persistent(const fk_plan* p, const void* snaps, int steps);
+
+// The persistent march's workspace: one flag per tile of the shortest tile
+// candidate (4 rows) and the abort word, and the per-step drift factors
+// (the same values the per-step launches receive).
+fk_status persist_workspace(fk_plan* p) {
+  p->mflags_n = (int64_t)((p->grid.n[0] - 2 + 31) / 32) * ((p->grid.n[1] - 2 + 3) / 4) + 1;
+  fk_status st = fk_dev_alloc(p, (void**)&p->mflags, sizeof(unsigned) * p->mflags_n);
+  if (st == FK_OK) st = fk_dev_alloc(p, (void**)&p->me12, sizeof(float2) * p->n_steps);
+  if (st != FK_OK) return st;
+  std::vector<float2> e(p->n_steps);
+  for (int n = 0; n < p->n_steps; ++n) {
+    Step2D<float> a;
+    fill2d<float>(p, n, &a);
+    e[n] = make_float2(a.e1, a.e2);
+  }
+  return cuda_status(
+      cudaMemcpy(p->me12, e.data(), sizeof(float2) * p->n_steps, cudaMemcpyHostToDevice));
+}
+
+// Whole marches of a masked-kernel plan: the persistent march or one
+// launch per step, whichever a short timed march (min(N, 16) steps from
+// chi) finds faster.  FK_MARCH=persistent|steps chooses explicitly.
+fk_status tune_persist(fk_plan* p) {
+  p->persist = 0;
+  if (!p->mflags || !p->use_masked || p->mwin <= 0) return FK_OK;
+  const char* f = getenv("FK_MARCH");
+  if (f && strcmp(f, "steps") == 0) return FK_OK;
+  const int steps = p->n_steps < 16 ? p->n_steps : 16;
+  p->persist = 1;
+  if (!use_persistent(p, nullptr, steps)) {
+    p->persist = 0;
+    return FK_OK;
+  }
+  if (f && strcmp(f, "persistent") == 0) return FK_OK;
+  void* tmp = nullptr;
+  if (cudaMalloc(&tmp, (size_t)(p->J * p->elem)) != cudaSuccess) {
+    cudaGetLastError();
+    p->persist = 0;
+    return FK_OK;
+  }
+  cudaStream_t s = p->cap_stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float ms[2] = {1e30f, 1e30f};
+  fk_status st = FK_OK;
+  const bool log = getenv("FK_TUNE_LOG") != nullptr;
+  for (int mode = 0; mode < 2 && st == FK_OK; ++mode) {
+    p->persist = mode;
+    for (int rep = 0; rep < 2 && st == FK_OK; ++rep) {  // the first is a warm-up
+      st = cuda_status(fk_launch_fill_chi(p->scratch, 2, p->grid.n[0], p->grid.n[1], p->elem, s));
+      cudaEventRecord(e0, s);
+      if (st == FK_OK) st = enqueue_march(p, p->n_steps, p->n_steps - steps, p->scratch, tmp, nullptr, 0, s);
+      cudaEventRecord(e1, s);
+      if (st == FK_OK && cudaEventSynchronize(e1) != cudaSuccess) st = FK_ERR_CUDA;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep == 1) ms[mode] = t;
+    }
+    if (st != FK_OK && mode == 1) {
+      // a persistent launch that the device refuses (resources): keep the
+      // per-step launches
+      const cudaError_t e = cudaGetLastError();
+      if (log) fprintf(stderr, "fk march tune: persistent march refused (%s)\n", cudaGetErrorString(e));
+      cudaStreamSynchronize(s);
+      st = FK_OK;
+      ms[1] = 1e30f;
+    }
+  }
+  if (log)
+    fprintf(stderr, "fk march tune %dx%d: %d steps, per-step launches %.1f us, persistent %.1f us\n",
+            p->grid.n[0], p->grid.n[1], steps, ms[0] * 1e3f, ms[1] * 1e3f);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  cudaMemset(p->d_err, 0, sizeof(unsigned));
+  p->persist = (st == FK_OK && ms[1] < ms[0]) ? 1 : 0;
+  return st;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ internal --
@@ -989,6 +1073,23 @@ namespace {
 // Steps n_from-1 .. n_to from u_in (NULL = chi) into u_out, ping-ponging
 // between u_out and the plan's scratch field so that the last step lands in
 // u_out; snapshots as documented for fk_solve when snaps != NULL.
+// Whether a march of `steps` steps runs as the masked kernel's persistent
+// march: an FP32 2D plan on the masked kernel that chose it, no snapshots,
+// not inside a batch, tiles taller than their halo, and every tile
+// resident at once.
+bool use_persistent(const fk_plan* p, const void* snaps, int steps) {
+  if (!p->persist || p->no_persist || snaps || steps < 2 || !p->use_masked || p->mwin <= 0 ||
+      p->prec != FK_FP32 || p->grid.dim != 2 || !p->mflags || !p->me12)
+    return false;
+  Step2D<float> a;
+  fill2d<float>(p, 0, &a);
+  // a tile waits for the 3 x 3 block of tiles around it only: its staged
+  // halo must stay within that block
+  if (a.hy + 1 > a.ty || a.hx + 1 > 32) return false;
+  const int64_t tiles = (int64_t)((a.nx - 2 + 31) / 32) * ((a.ny - 2 + a.ty - 1) / a.ty);
+  return tiles + 1 <= p->mflags_n && fk_march2dm_fits(a, p->q);
+}
+
 fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void* u_out,
                         void* snaps, int stride, cudaStream_t s) {
   const int64_t bytes = p->J * p->elem;
@@ -1036,6 +1137,27 @@ fk_status enqueue_march(fk_plan* p, int n_from, int n_to, const void* u_in, void
     fk_status st = cuda_status(fk_launch_copy(p->scratch, src, bytes, s));
     if (st != FK_OK) return st;
     src = p->scratch;
+  }
+  if (use_persistent(p, snaps, steps)) {
+    // the whole march in one launch (fk_window.cuh): tile flags and the
+    // abort word start at zero
+    Step2D<float> a;
+    fill2d<float>(p, n_from - 1, &a);
+    MaskedMarch mm;
+    mm.u_first = (const float*)src;
+    mm.buf[0] = (float*)u_out;
+    mm.buf[1] = (float*)p->scratch;
+    mm.e12 = p->me12;
+    mm.flags = p->mflags;
+    mm.abort = p->mflags + p->mflags_n - 1;
+    mm.n_from = n_from;
+    mm.steps = steps;
+    // test hook: tile 0 never publishes a step, so the tiles around it run
+    // into their wait limit (the timeout path)
+    mm.silent = getenv("FK_TEST_STALL_MARCH") ? 0 : -1;
+    cudaError_t e = cudaMemsetAsync(p->mflags, 0, sizeof(unsigned) * p->mflags_n, s);
+    if (e == cudaSuccess) e = fk_launch_march2dm(a, mm, p->q, s);
+    return cuda_status(e);
   }
   for (int m = 1; m <= steps; ++m) {
     const int n = n_from - m;
@@ -1302,7 +1424,9 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   if (st == FK_OK && p->nu)
     st = (prec == FK_FP32) ? upload_coords<float>(p) : upload_coords<double>(p);
   if (st == FK_OK) st = cuda_status(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  if (st == FK_OK && p->mwin > 0 && prec == FK_FP32 && grid->dim == 2) st = persist_workspace(p);
   if (st == FK_OK) st = autotune(p);
+  if (st == FK_OK) st = tune_persist(p);
   if (st == FK_OK) {
     // explicit choice of the 2D step kernel (tests exercise both paths)
     const char* k = getenv("FK_STEP_KERNEL");
@@ -1354,6 +1478,8 @@ fk_status fk_plan_destroy(fk_plan* p) {
   free_coords(p);
   fk_dev_free(p->adj_ws);
   fk_dev_free(p->adj_tab);
+  fk_dev_free(p->mflags);
+  fk_dev_free(p->me12);
   for (int i = 0; i < p->adj_ev_cap; ++i) cudaEventDestroy(p->adj_ev[i]);
   free(p->adj_ev);
   fk_batch_release(p);
@@ -1386,6 +1512,7 @@ fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
                                          : current_kernel(p);
   info->batch_mode = fk_batch_mode(p);
   info->adjoint_kernel = p->adj_kernel;
+  info->march_mode = p->persist ? 1 : 0;
   return FK_OK;
 }
 
@@ -1403,8 +1530,10 @@ fk_status fk_solve(fk_plan* p, const void* u_terminal, void* u_out, void* snapsh
   if (!p || !u_out) return FK_ERR_INVALID_ARG;
   if (snapshots && snapshot_stride < 1) return FK_ERR_INVALID_ARG;
   if (!snapshots) snapshot_stride = 0;
+  const int pers = p->persist && !p->no_persist;
   const bool hit = p->graph && p->g_in == u_terminal && p->g_out == u_out &&
-                   p->g_snap == snapshots && p->g_stride == snapshot_stride;
+                   p->g_snap == snapshots && p->g_stride == snapshot_stride &&
+                   p->g_persist == pers;
   if (!hit) {
     if (p->graph) {
       cudaGraphExecDestroy(p->graph);
@@ -1430,6 +1559,7 @@ fk_status fk_solve(fk_plan* p, const void* u_terminal, void* u_out, void* snapsh
     p->g_out = u_out;
     p->g_snap = snapshots;
     p->g_stride = snapshot_stride;
+    p->g_persist = pers;
   }
   return cuda_status(cudaGraphLaunch(p->graph, stream));
 }

@@ -42,3 +42,22 @@ cudaError_t fk_prepare_masked_kernels(int q) {
     default: return cudaSuccess;
   }
 }
+
+cudaError_t fk_launch_march2dm(const Step2D<float>& a, const MaskedMarch& m, int q,
+                               cudaStream_t s) {
+  switch (q) {
+    case 4: return fk_launch_march2dm_q4(a, m, s);
+    case 6: return fk_launch_march2dm_q6(a, m, s);
+    case 8: return fk_launch_march2dm_q8(a, m, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool fk_march2dm_fits(const Step2D<float>& a, int q) {
+  switch (q) {
+    case 4: return fk_march2dm_fits_q4(a);
+    case 6: return fk_march2dm_fits_q6(a);
+    case 8: return fk_march2dm_fits_q8(a);
+    default: return false;
+  }
+}

@@ -58,9 +58,12 @@ namespace {
 // for staged columns c = 1 .. lx-3 and rows r = 1 .. ly-2; U holds u^{n+1}
 // itself (zero outside the mesh).  Ends with the records visible to the
 // whole CTA.
-template <bool MF>
-__device__ __forceinline__ void stage_pairs(const Step2D<float>& a, float* U, float4* P,
-                                            float2* Y, int gi0, int gk0) {
+// field: u^{n+1}.  L2: read it through L2 only (ld.global.cg + st.shared):
+// in the persistent march other CTAs rewrite the field during the launch,
+// and L1 is not coherent with their stores.
+template <bool L2>
+__device__ __forceinline__ void stage_pairs(const Step2D<float>& a, const float* field, float* U,
+                                            float4* P, float2* Y, int gi0, int gk0) {
   const int lx = a.lx, ly = a.ly;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // 1. u^{n+1} over the tile and halo: rows by warp, columns by lane, so
@@ -74,26 +77,40 @@ __device__ __forceinline__ void stage_pairs(const Step2D<float>& a, float* U, fl
     const int g0 = gi0 + lane, g1 = gi0 + c1;
     const bool x0 = (unsigned)g0 < (unsigned)a.nx, x1 = c1 < lx && (unsigned)g1 < (unsigned)a.nx;
     const int cx0 = min(max(g0, 0), a.nx - 1), cx1 = min(max(g1, 0), a.nx - 1);
-    const float* base = field_in<MF>(a);
+    const float* base = field;
 #pragma unroll 1
     for (int r = warp; r < ly; r += FK_THREADS / 32) {
       const int gk = gk0 + r;
       const bool rowin = (unsigned)gk < (unsigned)a.ny;
       const float* src = base + (int64_t)min(max(gk, 0), a.ny - 1) * a.nx;
       const uint32_t drow = sU + (uint32_t)(r * lx) * 4u;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * lane),
-                   "l"(src + cx0), "r"(rowin && x0 ? 4 : 0));
-      if (c1 < lx)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c1),
-                     "l"(src + cx1), "r"(rowin && x1 ? 4 : 0));
-      for (int c = lane + 64; c < lx; c += 32) {  // wide halos only
-        const int g = gi0 + c;
-        const bool in = rowin && (unsigned)g < (unsigned)a.nx;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c),
-                     "l"(src + min(max(g, 0), a.nx - 1)), "r"(in ? 4 : 0));
+      if constexpr (L2) {
+        float v0, v1 = 0.f;
+        asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v0) : "l"(src + cx0));
+        if (c1 < lx) asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v1) : "l"(src + cx1));
+        U[r * lx + lane] = rowin && x0 ? v0 : 0.f;
+        if (c1 < lx) U[r * lx + c1] = rowin && x1 ? v1 : 0.f;
+        for (int c = lane + 64; c < lx; c += 32) {  // wide halos only
+          const int g = gi0 + c;
+          float v;
+          asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(src + min(max(g, 0), a.nx - 1)));
+          U[r * lx + c] = rowin && (unsigned)g < (unsigned)a.nx ? v : 0.f;
+        }
+      } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * lane),
+                     "l"(src + cx0), "r"(rowin && x0 ? 4 : 0));
+        if (c1 < lx)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c1),
+                       "l"(src + cx1), "r"(rowin && x1 ? 4 : 0));
+        for (int c = lane + 64; c < lx; c += 32) {  // wide halos only
+          const int g = gi0 + c;
+          const bool in = rowin && (unsigned)g < (unsigned)a.nx;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c),
+                       "l"(src + min(max(g, 0), a.nx - 1)), "r"(in ? 4 : 0));
+        }
       }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    if constexpr (!L2) asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
   }
   // 2. vertical sweeps: warp group g takes staged columns 1 + 31 g + lane
@@ -241,13 +258,15 @@ __device__ __forceinline__ void weights_of(int pat, bool exits, const float4* qc
   }
 }
 
-// MINB: CTAs of 256 threads per SM the register budget is sized for
-// (3 -> 80 registers, 2 -> 128; variant 0 and 1 of the plan).
-// MF: several fields per launch (blockIdx.z), for Algorithm 1.
-template <int Q, int W, int MINB, bool MF>
-__global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float> a) {
+// One tile (bx, by) of one step: u_in -> u_out (and a.snap), with the
+// per-step drift factors e1, e2 of the cellular flow.  MF: u_in and u_out
+// are the field of blockIdx.z.  L2: stage through L2 only (persistent
+// march).  Sets bad when a halo range check fires.
+template <int Q, int W, bool MF, bool L2>
+__device__ __forceinline__ void masked_tile(const Step2D<float>& a, const float* u_in,
+                                            float* u_out, float e1, float e2, int bx, int by,
+                                            unsigned char* smem, unsigned& bad) {
   constexpr int NP = (W + 1) / 2;  // column pairs of the window
-  extern __shared__ __align__(16) unsigned char smem[];
   const int lx = a.lx, ly = a.ly;
   float4* QC = reinterpret_cast<float4*>(smem);
   float4* P = QC + FK_MAXQ_2D;
@@ -255,15 +274,15 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float
   float* U = reinterpret_cast<float*>(Yr + ly * lx);
   const int tid = threadIdx.x;
   if (tid < Q) QC[tid] = make_float4(a.gmx[tid], a.gmy[tid], a.w[tid], a.w[tid]);
-  const int i0 = 1 + blockIdx.x * 32, k0 = 1 + blockIdx.y * a.ty;
+  const int i0 = 1 + bx * 32, k0 = 1 + by * a.ty;
   const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;  // global node of staged (0, 0)
 
-  stage_pairs<MF>(a, U, P, Yr, gi0, gk0);
+  stage_pairs<L2>(a, u_in, U, P, Yr, gi0, gk0);
 
   // 3. one output node per thread and pass: column i0 + lane, row k0 + warp + 8 m
   const int lane = tid & 31, warp = tid >> 5;
   const int i = i0 + lane;
-  if (i > a.nx - 2) return;
+  if (i > a.nx - 2) return;  // (no barrier follows in the tile)
   const int li = i - gi0;
   // no point of a node in this tile's columns can leave through an x face
   // (the halo exceeds the reach of every point)
@@ -273,10 +292,9 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float
   float fcx = 1.f, fcy = 1.f;
   if (a.family == FK_CELLULAR_FLOW) {
     const float* ct = a.col_tab + 4 * (int64_t)i;
-    fcx = a.A * ct[0] + a.e1 * ct[1];
-    fcy = a.A * ct[2] + a.e2 * ct[3];
+    fcx = a.A * ct[0] + e1 * ct[1];
+    fcy = a.A * ct[2] + e2 * ct[3];
   }
-  unsigned bad = 0;
 #pragma unroll 1
   for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
     const int k = k0 + ty;
@@ -355,9 +373,100 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float
     const float ext = (1.f - uj) * (E.x + E.y - E.x * E.y);
     const float un = uj + (acc + ext);
     const int64_t j = (int64_t)k * a.nx + i;
-    field_out<MF>(a)[j] = un;
+    u_out[j] = un;
     if (a.snap) a.snap[j] = un;
-    write_adjacent_boundary<MF>(a, i, k);
+    boundary_ones(u_out, a.snap, a.nx, a.ny, i, k);
+  }
+}
+
+// MINB: CTAs of 256 threads per SM the register budget is sized for
+// (3 -> 80 registers, 2 -> 128; variant 0 and 1 of the plan).
+// MF: several fields per launch (blockIdx.z), for Algorithm 1.
+template <int Q, int W, int MINB, bool MF>
+__global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned bad = 0;
+  masked_tile<Q, W, MF, false>(a, field_in<MF>(a), field_out<MF>(a), a.e1, a.e2, blockIdx.x,
+                               blockIdx.y, smem, bad);
+  if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
+}
+
+// The persistent march: steps n_from-1 .. n_to of Scheme 1 in one launch,
+// one CTA per tile (all co-resident: a cooperative launch).  A tile starts
+// step m once the tiles around it (the 3 x 3 block: its halo is smaller
+// than a tile) have finished step m-1, signalled by a per-tile count of
+// finished steps (release after the CTA's stores, acquire before staging).
+// No tile is ever more than one step ahead of a neighbour, so two buffers
+// suffice: step m writes buf[(steps - m) & 1] while every tile that still
+// reads that buffer's previous contents has finished.  Staging of one
+// tile overlaps the compute of others, and no step waits for the slowest
+// CTA of the grid or for a launch.  A wait is bounded: after 1 s (or 2^24
+// polls) the CTA records FK_DEVERR_TIMEOUT and raises the abort word, and
+// every CTA leaves at its next wait.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <int Q, int W, int MINB>
+__global__ void __launch_bounds__(FK_THREADS, MINB) k_march2dm(const Step2D<float> a,
+                                                               const MaskedMarch m) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int go;
+  const int bx = blockIdx.x, by = blockIdx.y, tx = gridDim.x, tyn = gridDim.y;
+  unsigned bad = 0;
+  for (int s = 1; s <= m.steps; ++s) {
+    // wait for the 3 x 3 block of tiles to have finished step s - 1
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      if (s > 1) {
+        const unsigned long long t0 = global_timer_ns();
+        unsigned polls = 0;
+        for (int dy = -1; dy <= 1 && ok; ++dy) {
+          for (int dx = -1; dx <= 1 && ok; ++dx) {
+            const int nx_ = bx + dx, ny_ = by + dy;
+            if ((dx | dy) == 0 || nx_ < 0 || ny_ < 0 || nx_ >= tx || ny_ >= tyn) continue;
+            const unsigned* f = m.flags + ny_ * tx + nx_;
+            while (ld_acquire(f) < (unsigned)(s - 1)) {
+              if (ld_acquire(m.abort)) {
+                ok = 0;
+                break;
+              }
+              if (global_timer_ns() - t0 > 1000000000ull || ++polls > (1u << 24)) {
+                atomicOr(a.err, FK_DEVERR_TIMEOUT);
+                atomicExch(m.abort, 1u);
+                ok = 0;
+                break;
+              }
+              __nanosleep(32);
+            }
+          }
+        }
+      }
+      go = ok;
+    }
+    __syncthreads();
+    if (!go) break;
+    const int n = m.n_from - s;
+    const bool odd = (m.steps - s) & 1;  // (selects, not an indexed parameter array)
+    const float* src = s == 1 ? m.u_first : (odd ? m.buf[0] : m.buf[1]);
+    float* dst = odd ? m.buf[1] : m.buf[0];
+    const float2 e = m.e12[n];  // (e1, e2) at t_n
+    masked_tile<Q, W, false, true>(a, src, dst, e.x, e.y, bx, by, smem, bad);
+    __syncthreads();  // every store of the tile is issued
+    if (threadIdx.x == 0 && by * tx + bx != m.silent) {
+      __threadfence();
+      st_release(m.flags + by * tx + bx, (unsigned)s);
+    }
   }
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
@@ -375,6 +484,48 @@ cudaError_t launch_m(const Step2D<float>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The persistent march of a single-field plan (variant 0: 3 CTAs/SM, 1:
+// 2); cudaErrorCooperativeLaunchTooLarge when the tiles cannot all be
+// resident at once.
+template <int Q, int W>
+cudaError_t launch_march_m(const Step2D<float>& a, const MaskedMarch& m, cudaStream_t s) {
+  const size_t smem = fk_step2dm_smem(a.ly, a.lx);
+  const dim3 grid((a.nx - 2 + 31) / 32, (a.ny - 2 + a.ty - 1) / a.ty);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(FK_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (a.variant == 1) return cudaLaunchKernelEx(&cfg, k_march2dm<Q, W, 2>, a, m);
+  return cudaLaunchKernelEx(&cfg, k_march2dm<Q, W, 3>, a, m);
+}
+
+// Whether every tile of the persistent march can be resident at once.
+template <int Q, int W>
+bool march_fits_m(const Step2D<float>& a) {
+  const size_t smem = fk_step2dm_smem(a.ly, a.lx);
+  const int tiles = ((a.nx - 2 + 31) / 32) * ((a.ny - 2 + a.ty - 1) / a.ty);
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  cudaError_t e = a.variant == 1
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 2>,
+                                                                      FK_THREADS, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 3>,
+                                                                      FK_THREADS, smem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (int64_t)per * sms >= tiles;
+}
+
 template <int Q, int W>
 cudaError_t attr_m() {
   const int big = 227 * 1024;
@@ -386,6 +537,13 @@ cudaError_t attr_m() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_step2dm<Q, W, 3, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  // (the persistent march keeps a word of static shared memory beside the dynamic part)
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_march2dm<Q, W, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             big - 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_march2dm<Q, W, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             big - 1024);
   return e;
 }
 
@@ -403,6 +561,31 @@ cudaError_t attr_m() {
       case 8: return a.variant == 1 ? launch_m<QQ, 8, 2>(a, s) : launch_m<QQ, 8, 3>(a, s); \
       case 9: return a.variant == 1 ? launch_m<QQ, 9, 2>(a, s) : launch_m<QQ, 9, 3>(a, s); \
       default: return cudaErrorInvalidValue;                                            \
+    }                                                                                   \
+  }                                                                                     \
+  cudaError_t fk_launch_march2dm_q##QQ(const Step2D<float>& a, const MaskedMarch& m,   \
+                                       cudaStream_t s) {                                \
+    switch (a.win) {                                                                    \
+      case 3: return launch_march_m<QQ, 3>(a, m, s);                                    \
+      case 4: return launch_march_m<QQ, 4>(a, m, s);                                    \
+      case 5: return launch_march_m<QQ, 5>(a, m, s);                                    \
+      case 6: return launch_march_m<QQ, 6>(a, m, s);                                    \
+      case 7: return launch_march_m<QQ, 7>(a, m, s);                                    \
+      case 8: return launch_march_m<QQ, 8>(a, m, s);                                    \
+      case 9: return launch_march_m<QQ, 9>(a, m, s);                                    \
+      default: return cudaErrorInvalidValue;                                            \
+    }                                                                                   \
+  }                                                                                     \
+  bool fk_march2dm_fits_q##QQ(const Step2D<float>& a) {                                 \
+    switch (a.win) {                                                                    \
+      case 3: return march_fits_m<QQ, 3>(a);                                            \
+      case 4: return march_fits_m<QQ, 4>(a);                                            \
+      case 5: return march_fits_m<QQ, 5>(a);                                            \
+      case 6: return march_fits_m<QQ, 6>(a);                                            \
+      case 7: return march_fits_m<QQ, 7>(a);                                            \
+      case 8: return march_fits_m<QQ, 8>(a);                                            \
+      case 9: return march_fits_m<QQ, 9>(a);                                            \
+      default: return false;                                                            \
     }                                                                                   \
   }                                                                                     \
   cudaError_t fk_prepare_masked_q##QQ() {                                               \

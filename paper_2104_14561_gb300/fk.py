@@ -128,7 +128,8 @@ class Plan:
                                 "window3d")[i.step_kernel],
                 "batch_mode": ("none", "persistent", "streams")[i.batch_mode],
                 "adjoint_kernel": ("none", "scatter", "masked")[i.adjoint_kernel],
-                "periodic_x": bool(i.periodic_x), "nonuniform": bool(i.nonuniform)}
+                "periodic_x": bool(i.periodic_x), "nonuniform": bool(i.nonuniform),
+                "march_mode": ("steps", "persistent")[i.march_mode]}
 
     def _check_field(self, t: torch.Tensor, name: str):
         if t.dtype != self.dtype or t.device.type != "cuda" or tuple(t.shape) != self.shape \
