@@ -18,9 +18,11 @@ BUILD = os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libfk_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fk_plan.cu", "fk_march.cu", "fk_window.cu", "fk_window_q4.cu", "fk_window_q6.cu",
-           "fk_window_q8.cu", "fk_window64.cu", "fk_march1d.cu", "fk_csr.cu",
-           "fk_static.cu", "fk_batched.cu", "fk_adjoint.cu", "fk_march3d.cu", "fk_peak.cu"]
+# (longest compiles first: the parallel build starts them in this order)
+SOURCES = ["fk_march3d_f64.cu", "fk_march3d_f32.cu", "fk_march.cu", "fk_window_q8a.cu",
+           "fk_window_q8b.cu", "fk_window_q8c.cu", "fk_window_q6a.cu", "fk_window_q6b.cu", "fk_window64.cu",
+           "fk_window_q4.cu", "fk_adjoint.cu", "fk_march1d.cu", "fk_csr.cu", "fk_batched.cu",
+           "fk_plan.cu", "fk_window.cu", "fk_static.cu", "fk_peak.cu"]
 
 
 def nvcc() -> str:

@@ -49,7 +49,7 @@ struct Step2D {
   int nx, ny;
   int tx, ty;      // output tile (interior nodes) per CTA: tx = 32, ty = 8 m
   int variant;     // register-budget variant (FP32 direct and row window: 0 -> 4
-                   // CTAs/SM, 1 -> 3; masked window: 0 -> 3, 1 -> 2)
+                   // CTAs/SM, 1 -> 3; masked window: 0 -> 3, 1 -> 2, 2 -> 4)
   int hx, hy;      // halo in cells
   int lx, ly;      // staged value tile: tx + 2 hx + 2, ty + 2 hy + 2
   int lyr;         // odd pitch of the record tiles: column pitch of the column-major
@@ -163,7 +163,7 @@ struct Step1D {
   __device__ __forceinline__ T* out() const { return u_out + (int64_t)blockIdx.z * zstride; }
 };
 
-// One 3D step (fk_march3d.cu): uniform mesh, lengths in cells as in Step2D.
+// One 3D step (fk_march3d.cuh): uniform mesh, lengths in cells as in Step2D.
 template <typename T>
 struct Step3D {
   const T* u_in;
@@ -241,13 +241,6 @@ cudaError_t fk_prepare_masked64(int q);
 // index k of the pattern m[0..q-1] among those of (q, w), or -1
 int fk_masked_pattern(int q, int w, const int* m);
 cudaError_t fk_prepare_masked_kernels(int q);
-// per rule size (fk_window_q4.cu, fk_window_q6.cu, fk_window_q8.cu)
-cudaError_t fk_launch_step2dm_q4(const Step2D<float>& a, cudaStream_t s);
-cudaError_t fk_launch_step2dm_q6(const Step2D<float>& a, cudaStream_t s);
-cudaError_t fk_launch_step2dm_q8(const Step2D<float>& a, cudaStream_t s);
-cudaError_t fk_prepare_masked_q4();
-cudaError_t fk_prepare_masked_q6();
-cudaError_t fk_prepare_masked_q8();
 // The persistent march of the FP32 masked kernel (fk_window.cuh): the steps
 // n_from-1 .. n_from-steps of one field in one cooperative launch, one CTA
 // per tile; step m reads u_first (m = 1) or buf[(steps - m + 1) & 1] and
@@ -265,12 +258,20 @@ struct MaskedMarch {
 cudaError_t fk_launch_march2dm(const Step2D<float>& a, const MaskedMarch& m, int q,
                                cudaStream_t s);
 bool fk_march2dm_fits(const Step2D<float>& a, int q);  // all tiles resident at once
-cudaError_t fk_launch_march2dm_q4(const Step2D<float>& a, const MaskedMarch& m, cudaStream_t s);
-cudaError_t fk_launch_march2dm_q6(const Step2D<float>& a, const MaskedMarch& m, cudaStream_t s);
-cudaError_t fk_launch_march2dm_q8(const Step2D<float>& a, const MaskedMarch& m, cudaStream_t s);
-bool fk_march2dm_fits_q4(const Step2D<float>& a);
-bool fk_march2dm_fits_q6(const Step2D<float>& a);
-bool fk_march2dm_fits_q8(const Step2D<float>& a);
+// Every (rule size, window width) the FP32 masked kernels are built for, and
+// their entry points (fk_window_q*.cu, a few widths per translation unit so
+// that the parallel build stays short).
+#define FK_MASKED_ALL(X)                                  \
+  X(4, 3) X(4, 4) X(4, 5) X(4, 6) X(4, 7) X(4, 8) X(4, 9) \
+  X(6, 3) X(6, 4) X(6, 5) X(6, 6) X(6, 7) X(6, 8) X(6, 9) \
+  X(8, 3) X(8, 4) X(8, 5) X(8, 6) X(8, 7) X(8, 8) X(8, 9)
+#define FK_DECLARE_MASKED_QW(QQ, WW)                                                        \
+  cudaError_t fk_launch_step2dm_q##QQ##w##WW(const Step2D<float>& a, cudaStream_t s);       \
+  cudaError_t fk_launch_march2dm_q##QQ##w##WW(const Step2D<float>& a, const MaskedMarch& m, \
+                                              cudaStream_t s);                              \
+  bool fk_march2dm_fits_q##QQ##w##WW(const Step2D<float>& a);                               \
+  cudaError_t fk_prepare_masked_q##QQ##w##WW();
+FK_MASKED_ALL(FK_DECLARE_MASKED_QW)
 // (Q, W) pairs of the masked-window adjoint kernel (fk_adjoint.cu): the
 // window form pays off while W^2 cells stay below the direct form's 4 Q^2
 // corner reads and its weights fit in registers.

@@ -43,6 +43,12 @@
 // kinds of exit split each axis's dropped weight into E1_m and E0_m: a
 // point takes 1 when any coordinate leaves through a value-1 face, so
 //   u^n = sum_inside + 1 - prod_m (1 - E1_m).
+//
+// The kernels and their launchers are templates on the precision; the
+// translation units fk_march3d_f32.cu and fk_march3d_f64.cu instantiate one
+// precision each, so that the parallel build compiles them side by side.
+#pragma once
+
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -518,8 +524,3 @@ cudaError_t fk_launch_chi3d(const Step3D<T>& a, T* u, cudaStream_t s) {
   k_chi3d<T><<<grid, kRecThreads, 0, s>>>(a, u);
   return cudaGetLastError();
 }
-
-template cudaError_t fk_launch_step3d<float>(const Step3D<float>&, cudaStream_t);
-template cudaError_t fk_launch_step3d<double>(const Step3D<double>&, cudaStream_t);
-template cudaError_t fk_launch_chi3d<float>(const Step3D<float>&, float*, cudaStream_t);
-template cudaError_t fk_launch_chi3d<double>(const Step3D<double>&, double*, cudaStream_t);

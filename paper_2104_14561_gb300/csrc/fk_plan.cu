@@ -257,7 +257,7 @@ fk_status validate(const fk_grid* g, const fk_region* r, const fk_coeffs* c, int
   }
   if (g->dim == 3) {
     // d = 3: constant drift or the runaway model on a uniform mesh,
-    // matrix-free (the window kernel of fk_march3d.cu)
+    // matrix-free (the window kernel of fk_march3d.cuh)
     if ((c->family != FK_CONST_DRIFT && !runaway_family(c->family)) ||
         path != FK_PATH_MATRIX_FREE)
       return FK_ERR_UNSUPPORTED;
@@ -505,6 +505,7 @@ bool kernel_eligible(const fk_plan* p, int kern) {
 
 bool cand_fits(const fk_plan* p, const TileCand& c, int dev_smem, int kern = kDirect) {
   if (p->elem == 8 && c.variant != 0) return false;
+  if (c.variant == 2 && kern != kMasked) return false;  // (4 CTAs/SM: masked FP32 only)
   if (kern == kMasked) {
     const int lx = fk_step2dm_lx(p->mhalo[0], p->mwin), ly = c.ty + 2 * p->mhalo[1] + 2;
     const size_t bytes = p->elem == 8 ? fk_step2dm64_smem(ly, lx) : fk_step2dm_smem(ly, lx);
@@ -657,17 +658,19 @@ void refit_tile(fk_plan* p) {
   set_kernel(p, kDirect);
 }
 
-// Tile candidates of the masked kernel: the fixed list plus tile heights
-// that make the number of tiles just fit 1-4 waves of resident CTAs (3 per
-// SM for variant 0, 2 for variant 1), so that the last wave is not short.
+// Tile candidates of the masked kernel: the fixed list, three heights of
+// variant 2, and tile heights that make the number of tiles just fit 1-4
+// waves of resident CTAs (3 per SM for variant 0, 2 for variant 1, 4 for
+// variant 2), so that the last wave is not short.
 std::vector<TileCand> masked_cands(const fk_plan* p) {
   std::vector<TileCand> v(std::begin(kCands), std::end(kCands));
+  v.insert(v.end(), {TileCand{16, 2}, TileCand{24, 2}, TileCand{32, 2}});
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
     sms = 152;
   const int nxt = (p->grid.n[0] - 2 + 31) / 32, rows = p->grid.n[1] - 2;
-  for (int var = 0; var < 2; ++var) {
-    const int per_sm = var == 0 ? 3 : 2;
+  for (int var = 0; var < 3; ++var) {
+    const int per_sm = var == 0 ? 3 : var == 1 ? 2 : 4;
     for (int waves = 1; waves <= 4; ++waves) {
       const int row_tiles = waves * sms * per_sm / nxt;
       if (row_tiles < 1) continue;
@@ -688,7 +691,7 @@ fk_status autotune(fk_plan* p) {
   if (const char* t = getenv("FK_STEP_TILE")) {
     int ty = 0, var = 0, kern = 0;
     if (sscanf(t, "%d,%d,%d", &ty, &var, &kern) >= 1 && ty >= 4 && ty <= 64 &&
-        (var == 0 || var == 1) && kern >= 0 && kern <= 2) {
+        (var >= 0 && var <= 2) && kern >= 0 && kern <= 2) {
       if (kern != kMasked && ty % 8 != 0) ty = (ty + 7) / 8 * 8;
       int dev_smem = 0;
       cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);

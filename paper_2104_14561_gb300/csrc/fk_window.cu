@@ -25,39 +25,37 @@ int fk_masked_pattern(int q, int w, const int* m) {
   return -1;
 }
 
+// (each macro expands to one test per (Q, W) of FK_MASKED_ALL)
 cudaError_t fk_launch_step2dm(const Step2D<float>& a, int q, cudaStream_t s) {
-  switch (q) {
-    case 4: return fk_launch_step2dm_q4(a, s);
-    case 6: return fk_launch_step2dm_q6(a, s);
-    case 8: return fk_launch_step2dm_q8(a, s);
-    default: return cudaErrorInvalidValue;
-  }
+#define FK_CASE(QQ, WW) \
+  if (q == QQ && a.win == WW) return fk_launch_step2dm_q##QQ##w##WW(a, s);
+  FK_MASKED_ALL(FK_CASE)
+#undef FK_CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t fk_prepare_masked_kernels(int q) {
-  switch (q) {
-    case 4: return fk_prepare_masked_q4();
-    case 6: return fk_prepare_masked_q6();
-    case 8: return fk_prepare_masked_q8();
-    default: return cudaSuccess;
-  }
+  cudaError_t e = cudaSuccess;
+#define FK_CASE(QQ, WW) \
+  if (q == QQ && e == cudaSuccess) e = fk_prepare_masked_q##QQ##w##WW();
+  FK_MASKED_ALL(FK_CASE)
+#undef FK_CASE
+  return e;
 }
 
 cudaError_t fk_launch_march2dm(const Step2D<float>& a, const MaskedMarch& m, int q,
                                cudaStream_t s) {
-  switch (q) {
-    case 4: return fk_launch_march2dm_q4(a, m, s);
-    case 6: return fk_launch_march2dm_q6(a, m, s);
-    case 8: return fk_launch_march2dm_q8(a, m, s);
-    default: return cudaErrorInvalidValue;
-  }
+#define FK_CASE(QQ, WW) \
+  if (q == QQ && a.win == WW) return fk_launch_march2dm_q##QQ##w##WW(a, m, s);
+  FK_MASKED_ALL(FK_CASE)
+#undef FK_CASE
+  return cudaErrorInvalidValue;
 }
 
 bool fk_march2dm_fits(const Step2D<float>& a, int q) {
-  switch (q) {
-    case 4: return fk_march2dm_fits_q4(a);
-    case 6: return fk_march2dm_fits_q6(a);
-    case 8: return fk_march2dm_fits_q8(a);
-    default: return false;
-  }
+#define FK_CASE(QQ, WW) \
+  if (q == QQ && a.win == WW) return fk_march2dm_fits_q##QQ##w##WW(a);
+  FK_MASKED_ALL(FK_CASE)
+#undef FK_CASE
+  return false;
 }

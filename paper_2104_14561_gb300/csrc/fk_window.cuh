@@ -425,48 +425,44 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_march2dm(const Step2D<floa
   const int bx = blockIdx.x, by = blockIdx.y, tx = gridDim.x, tyn = gridDim.y;
   unsigned bad = 0;
   for (int s = 1; s <= m.steps; ++s) {
-    // wait for the 3 x 3 block of tiles to have finished step s - 1
-    if (threadIdx.x == 0) {
+    // wait for the 3 x 3 block of tiles to have finished step s - 1: lane
+    // 3 (dy + 1) + dx + 1 of warp 0 polls neighbour (dx, dy), all at once
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x, dx = lane % 3 - 1, dy = lane / 3 - 1;
+      const int nx_ = bx + dx, ny_ = by + dy;
       int ok = 1;
-      if (s > 1) {
+      if (s > 1 && lane < 9 && lane != 4 && nx_ >= 0 && ny_ >= 0 && nx_ < tx && ny_ < tyn) {
+        const unsigned* f = m.flags + ny_ * tx + nx_;
         const unsigned long long t0 = global_timer_ns();
         unsigned polls = 0;
-        for (int dy = -1; dy <= 1 && ok; ++dy) {
-          for (int dx = -1; dx <= 1 && ok; ++dx) {
-            const int nx_ = bx + dx, ny_ = by + dy;
-            if ((dx | dy) == 0 || nx_ < 0 || ny_ < 0 || nx_ >= tx || ny_ >= tyn) continue;
-            const unsigned* f = m.flags + ny_ * tx + nx_;
-            while (ld_acquire(f) < (unsigned)(s - 1)) {
-              if (ld_acquire(m.abort)) {
-                ok = 0;
-                break;
-              }
-              if (global_timer_ns() - t0 > 1000000000ull || ++polls > (1u << 24)) {
-                atomicOr(a.err, FK_DEVERR_TIMEOUT);
-                atomicExch(m.abort, 1u);
-                ok = 0;
-                break;
-              }
-              __nanosleep(32);
-            }
+        while (ld_acquire(f) < (unsigned)(s - 1)) {
+          if (ld_acquire(m.abort)) {
+            ok = 0;
+            break;
           }
+          if (global_timer_ns() - t0 > 1000000000ull || ++polls > (1u << 24)) {
+            atomicOr(a.err, FK_DEVERR_TIMEOUT);
+            atomicExch(m.abort, 1u);
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
         }
       }
-      go = ok;
+      ok = __all_sync(0xffffffffu, ok);
+      if (lane == 0) go = ok;
     }
-    __syncthreads();
+    __syncthreads();  // (orders every thread's staging after the acquires)
     if (!go) break;
     const int n = m.n_from - s;
     const bool odd = (m.steps - s) & 1;  // (selects, not an indexed parameter array)
     const float* src = s == 1 ? m.u_first : (odd ? m.buf[0] : m.buf[1]);
     float* dst = odd ? m.buf[1] : m.buf[0];
     const float2 e = m.e12[n];  // (e1, e2) at t_n
-    masked_tile<Q, W, false, true>(a, src, dst, e.x, e.y, bx, by, smem, bad);
+    masked_tile<Q, W, false, false>(a, src, dst, e.x, e.y, bx, by, smem, bad);
     __syncthreads();  // every store of the tile is issued
-    if (threadIdx.x == 0 && by * tx + bx != m.silent) {
-      __threadfence();
-      st_release(m.flags + by * tx + bx, (unsigned)s);
-    }
+    // the release is cumulative: it publishes the stores the barrier ordered before it
+    if (threadIdx.x == 0 && by * tx + bx != m.silent) st_release(m.flags + by * tx + bx, (unsigned)s);
   }
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
@@ -502,7 +498,19 @@ cudaError_t launch_march_m(const Step2D<float>& a, const MaskedMarch& m, cudaStr
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (a.variant == 1) return cudaLaunchKernelEx(&cfg, k_march2dm<Q, W, 2>, a, m);
+  if (a.variant == 2) return cudaLaunchKernelEx(&cfg, k_march2dm<Q, W, 4>, a, m);
   return cudaLaunchKernelEx(&cfg, k_march2dm<Q, W, 3>, a, m);
+}
+
+// The single-field step of register-budget variant a.variant (0: 3 CTAs/SM,
+// 1: 2, 2: 4).
+template <int Q, int W>
+cudaError_t launch_v(const Step2D<float>& a, cudaStream_t s) {
+  switch (a.variant) {
+    case 1: return launch_m<Q, W, 2>(a, s);
+    case 2: return launch_m<Q, W, 4>(a, s);
+    default: return launch_m<Q, W, 3>(a, s);
+  }
 }
 
 // Whether every tile of the persistent march can be resident at once.
@@ -514,11 +522,13 @@ bool march_fits_m(const Step2D<float>& a) {
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return false;
-  cudaError_t e = a.variant == 1
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 2>,
-                                                                      FK_THREADS, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 3>,
-                                                                      FK_THREADS, smem);
+  cudaError_t e =
+      a.variant == 1   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 2>,
+                                                                       FK_THREADS, smem)
+      : a.variant == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 4>,
+                                                                       FK_THREADS, smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 3>,
+                                                                       FK_THREADS, smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -535,6 +545,9 @@ cudaError_t attr_m() {
     e = cudaFuncSetAttribute(k_step2dm<Q, W, 2, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step2dm<Q, W, 4, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_step2dm<Q, W, 3, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   // (the persistent march keeps a word of static shared memory beside the dynamic part)
@@ -544,57 +557,25 @@ cudaError_t attr_m() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_march2dm<Q, W, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              big - 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_march2dm<Q, W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             big - 1024);
   return e;
 }
 
 }  // namespace
 
-// Launcher and shared-memory opt-in of the masked kernels of one rule size.
-#define FK_DEFINE_MASKED_Q(QQ)                                                          \
-  cudaError_t fk_launch_step2dm_q##QQ(const Step2D<float>& a, cudaStream_t s) {         \
-    switch (a.win) {                                                                    \
-      case 3: return a.variant == 1 ? launch_m<QQ, 3, 2>(a, s) : launch_m<QQ, 3, 3>(a, s); \
-      case 4: return a.variant == 1 ? launch_m<QQ, 4, 2>(a, s) : launch_m<QQ, 4, 3>(a, s); \
-      case 5: return a.variant == 1 ? launch_m<QQ, 5, 2>(a, s) : launch_m<QQ, 5, 3>(a, s); \
-      case 6: return a.variant == 1 ? launch_m<QQ, 6, 2>(a, s) : launch_m<QQ, 6, 3>(a, s); \
-      case 7: return a.variant == 1 ? launch_m<QQ, 7, 2>(a, s) : launch_m<QQ, 7, 3>(a, s); \
-      case 8: return a.variant == 1 ? launch_m<QQ, 8, 2>(a, s) : launch_m<QQ, 8, 3>(a, s); \
-      case 9: return a.variant == 1 ? launch_m<QQ, 9, 2>(a, s) : launch_m<QQ, 9, 3>(a, s); \
-      default: return cudaErrorInvalidValue;                                            \
-    }                                                                                   \
-  }                                                                                     \
-  cudaError_t fk_launch_march2dm_q##QQ(const Step2D<float>& a, const MaskedMarch& m,   \
-                                       cudaStream_t s) {                                \
-    switch (a.win) {                                                                    \
-      case 3: return launch_march_m<QQ, 3>(a, m, s);                                    \
-      case 4: return launch_march_m<QQ, 4>(a, m, s);                                    \
-      case 5: return launch_march_m<QQ, 5>(a, m, s);                                    \
-      case 6: return launch_march_m<QQ, 6>(a, m, s);                                    \
-      case 7: return launch_march_m<QQ, 7>(a, m, s);                                    \
-      case 8: return launch_march_m<QQ, 8>(a, m, s);                                    \
-      case 9: return launch_march_m<QQ, 9>(a, m, s);                                    \
-      default: return cudaErrorInvalidValue;                                            \
-    }                                                                                   \
-  }                                                                                     \
-  bool fk_march2dm_fits_q##QQ(const Step2D<float>& a) {                                 \
-    switch (a.win) {                                                                    \
-      case 3: return march_fits_m<QQ, 3>(a);                                            \
-      case 4: return march_fits_m<QQ, 4>(a);                                            \
-      case 5: return march_fits_m<QQ, 5>(a);                                            \
-      case 6: return march_fits_m<QQ, 6>(a);                                            \
-      case 7: return march_fits_m<QQ, 7>(a);                                            \
-      case 8: return march_fits_m<QQ, 8>(a);                                            \
-      case 9: return march_fits_m<QQ, 9>(a);                                            \
-      default: return false;                                                            \
-    }                                                                                   \
-  }                                                                                     \
-  cudaError_t fk_prepare_masked_q##QQ() {                                               \
-    cudaError_t e = attr_m<QQ, 3>();                                                    \
-    if (e == cudaSuccess) e = attr_m<QQ, 4>();                                          \
-    if (e == cudaSuccess) e = attr_m<QQ, 5>();                                          \
-    if (e == cudaSuccess) e = attr_m<QQ, 6>();                                          \
-    if (e == cudaSuccess) e = attr_m<QQ, 7>();                                          \
-    if (e == cudaSuccess) e = attr_m<QQ, 8>();                                          \
-    if (e == cudaSuccess) e = attr_m<QQ, 9>();                                          \
-    return e;                                                                           \
-  }
+// The entry points of one (rule size, window width): the single-field step,
+// the persistent march, its residency test and the shared-memory opt-in.
+#define FK_DEFINE_MASKED_QW(QQ, WW)                                                         \
+  cudaError_t fk_launch_step2dm_q##QQ##w##WW(const Step2D<float>& a, cudaStream_t s) {      \
+    return launch_v<QQ, WW>(a, s);                                                          \
+  }                                                                                         \
+  cudaError_t fk_launch_march2dm_q##QQ##w##WW(const Step2D<float>& a, const MaskedMarch& m, \
+                                              cudaStream_t s) {                             \
+    return launch_march_m<QQ, WW>(a, m, s);                                                 \
+  }                                                                                         \
+  bool fk_march2dm_fits_q##QQ##w##WW(const Step2D<float>& a) {                              \
+    return march_fits_m<QQ, WW>(a);                                                         \
+  }                                                                                         \
+  cudaError_t fk_prepare_masked_q##QQ##w##WW() { return attr_m<QQ, WW>(); }

@@ -1,7 +1,14 @@
-// Masked tensor-window step kernels for the rule of 4 points per axis
-// (window widths 3..9, every cell-offset pattern of each); the kernel is in
-// fk_window.cuh.  One translation unit per rule size keeps the parallel
+// Masked tensor-window step kernels for the rule of 4 points per axis,
+// window widths 3..9 (every cell-offset pattern of each): the single-field
+// step, the persistent march and their shared-memory opt-in.  The kernels are
+// in fk_window.cuh; a few widths per translation unit keep the parallel
 // build short.
 #include "fk_window.cuh"
 
-FK_DEFINE_MASKED_Q(4)
+FK_DEFINE_MASKED_QW(4, 3)
+FK_DEFINE_MASKED_QW(4, 4)
+FK_DEFINE_MASKED_QW(4, 5)
+FK_DEFINE_MASKED_QW(4, 6)
+FK_DEFINE_MASKED_QW(4, 7)
+FK_DEFINE_MASKED_QW(4, 8)
+FK_DEFINE_MASKED_QW(4, 9)
