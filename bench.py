@@ -285,17 +285,24 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def sources_sha256(paths) -> str:
+    """One digest over the given source files (repo-relative), in order."""
+    h = hashlib.sha256()
+    for rel in paths:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()
+
+
 def profile_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu
-    summary, or None when the kernel source changed since the capture."""
+    """DRAM bytes per launch of the kernel from the committed ncu summary,
+    or None when a source it was built from changed since the capture."""
     try:
         prof = json.load(open(os.path.join(PROFILE_DIR, f"{kernel}_{workload}.json")))
-        src = os.path.join(ROOT, prof["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if prof.get("source_sha256") != h:
+        srcs = prof.get("sources") or [prof["source"]]
+        if prof.get("source_sha256") != sources_sha256(srcs):
             return None
         return prof.get("dram_bytes_per_launch")
-    except (OSError, ValueError):
+    except (OSError, ValueError, KeyError):
         return None
 
 
@@ -700,7 +707,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if rank != 0:
         return
     info = plan.info()
-    launch_ms = ms_step / w["n_steps"]  # graph of back-to-back step kernels
+    # one launch for every step (the persistent march), or a graph of
+    # back-to-back step kernels
+    persistent = info.get("march_mode") == "persistent"
+    launch_ms = ms_step / w["n_steps"]
     if w["path"] == "csr":
         peak, peak_kind = hbm_peak()
         bytes_step = csr_bytes_per_step(w, info["csr_nnz"])
@@ -726,13 +736,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                     "window_rows": info.get("window_rows", 0),
                     "step_kernel": info.get("step_kernel")}
     else:
-        flops_launch = FLOP_PER_UPDATE * units / w["n_steps"]
+        if persistent:  # the whole march is one launch of the persistent kernel
+            launch_ms = ms_step
+        flops_launch = FLOP_PER_UPDATE * units / (1 if persistent else w["n_steps"])
         peak_flops = 1e12 * (peaks["fp32_tflops"] if w["precision"] == "fp32"
                              else peaks["fp64_tflops"])
         achieved = flops_launch / (launch_ms * 1e-3)
         kname = ({"resident": "k_march1d", "cluster": "k_march1d_cluster"}.get(
                      info.get("step_kernel"), "k_step1d")
-                 if len(w["n"]) == 1 else
+                 if len(w["n"]) == 1 else "k_march2dm" if persistent else
                  {"direct": "k_step2d", "window": "k_step2dw",
                   "masked": "k_step2dm" if w["precision"] == "fp32" else "k_step2dm64"}[
                      info.get("step_kernel", "direct")])
@@ -742,7 +754,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                     "traffic": profile_traffic(kname, args.workload),
                     "flop_per_launch": flops_launch, "launch_ms": launch_ms,
                     "window_rows": info.get("window_rows", 0),
-                    "step_kernel": info.get("step_kernel")}
+                    "step_kernel": info.get("step_kernel"),
+                    "march_mode": info.get("march_mode")}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
@@ -751,13 +764,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "config": {"workload": args.workload, "grid": list(w["n"]), "q_per_dim": w["q"],
                    "time_steps": w["n_steps"], "dt": w["dt"], "path": w["path"],
                    "tile": info["tile"][:2], "halo": info["halo"][:2],
-                   "l2": l2_note(w),
+                   "march": info.get("march_mode"), "l2": l2_note(w),
                    "parallelism": f"{world} independent instances (one per GPU)"},
         "hbm_gbs_algorithmic": hbm_bytes_per_solve(w) * world / (ms_step_max * 1e-3) / 1e9,
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,
                 "d2h_bytes_per_step": field_bytes},
         "gpu_launches": args.steps * (1 if info.get("step_kernel") in ("resident", "cluster") else
+                                      2 if persistent else
                                       (2 if w["path"] == "csr" or len(w["n"]) == 3 else 1)
                                       * w["n_steps"] + 1),
         "clocks": clocks,

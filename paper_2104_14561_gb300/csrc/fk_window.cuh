@@ -56,12 +56,10 @@ namespace {
 // Pair records of the staged tile (lx x ly nodes, row pitch lx): P[r][c] =
 // {u_c, u_{c+1}, h u_x(c), h u_x(c+1)} and Y[r][c] = {h u_y(c), h u_y(c+1)}
 // for staged columns c = 1 .. lx-3 and rows r = 1 .. ly-2; U holds u^{n+1}
-// itself (zero outside the mesh).  Ends with the records visible to the
-// whole CTA.
-// field: u^{n+1}.  L2: read it through L2 only (ld.global.cg + st.shared):
-// in the persistent march other CTAs rewrite the field during the launch,
-// and L1 is not coherent with their stores.
-template <bool L2>
+// itself (zero outside the mesh), from field = u^{n+1}.  Ends with the
+// records visible to the whole CTA.  (In the persistent march the copies
+// follow a gpu-scope acquire of the neighbours' step counts and a CTA
+// barrier, which is what makes the neighbours' stores visible to them.)
 __device__ __forceinline__ void stage_pairs(const Step2D<float>& a, const float* field, float* U,
                                             float4* P, float2* Y, int gi0, int gk0) {
   const int lx = a.lx, ly = a.ly;
@@ -84,33 +82,19 @@ __device__ __forceinline__ void stage_pairs(const Step2D<float>& a, const float*
       const bool rowin = (unsigned)gk < (unsigned)a.ny;
       const float* src = base + (int64_t)min(max(gk, 0), a.ny - 1) * a.nx;
       const uint32_t drow = sU + (uint32_t)(r * lx) * 4u;
-      if constexpr (L2) {
-        float v0, v1 = 0.f;
-        asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v0) : "l"(src + cx0));
-        if (c1 < lx) asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v1) : "l"(src + cx1));
-        U[r * lx + lane] = rowin && x0 ? v0 : 0.f;
-        if (c1 < lx) U[r * lx + c1] = rowin && x1 ? v1 : 0.f;
-        for (int c = lane + 64; c < lx; c += 32) {  // wide halos only
-          const int g = gi0 + c;
-          float v;
-          asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(src + min(max(g, 0), a.nx - 1)));
-          U[r * lx + c] = rowin && (unsigned)g < (unsigned)a.nx ? v : 0.f;
-        }
-      } else {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * lane),
-                     "l"(src + cx0), "r"(rowin && x0 ? 4 : 0));
-        if (c1 < lx)
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c1),
-                       "l"(src + cx1), "r"(rowin && x1 ? 4 : 0));
-        for (int c = lane + 64; c < lx; c += 32) {  // wide halos only
-          const int g = gi0 + c;
-          const bool in = rowin && (unsigned)g < (unsigned)a.nx;
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c),
-                       "l"(src + min(max(g, 0), a.nx - 1)), "r"(in ? 4 : 0));
-        }
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * lane),
+                   "l"(src + cx0), "r"(rowin && x0 ? 4 : 0));
+      if (c1 < lx)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c1),
+                     "l"(src + cx1), "r"(rowin && x1 ? 4 : 0));
+      for (int c = lane + 64; c < lx; c += 32) {  // wide halos only
+        const int g = gi0 + c;
+        const bool in = rowin && (unsigned)g < (unsigned)a.nx;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(drow + 4u * c),
+                     "l"(src + min(max(g, 0), a.nx - 1)), "r"(in ? 4 : 0));
       }
     }
-    if constexpr (!L2) asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
   }
   // 2. vertical sweeps: warp group g takes staged columns 1 + 31 g + lane
@@ -260,9 +244,8 @@ __device__ __forceinline__ void weights_of(int pat, bool exits, const float4* qc
 
 // One tile (bx, by) of one step: u_in -> u_out (and a.snap), with the
 // per-step drift factors e1, e2 of the cellular flow.  MF: u_in and u_out
-// are the field of blockIdx.z.  L2: stage through L2 only (persistent
-// march).  Sets bad when a halo range check fires.
-template <int Q, int W, bool MF, bool L2>
+// are the field of blockIdx.z.  Sets bad when a halo range check fires.
+template <int Q, int W, bool MF>
 __device__ __forceinline__ void masked_tile(const Step2D<float>& a, const float* u_in,
                                             float* u_out, float e1, float e2, int bx, int by,
                                             unsigned char* smem, unsigned& bad) {
@@ -277,7 +260,7 @@ __device__ __forceinline__ void masked_tile(const Step2D<float>& a, const float*
   const int i0 = 1 + bx * 32, k0 = 1 + by * a.ty;
   const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;  // global node of staged (0, 0)
 
-  stage_pairs<L2>(a, u_in, U, P, Yr, gi0, gk0);
+  stage_pairs(a, u_in, U, P, Yr, gi0, gk0);
 
   // 3. one output node per thread and pass: column i0 + lane, row k0 + warp + 8 m
   const int lane = tid & 31, warp = tid >> 5;
@@ -386,7 +369,7 @@ template <int Q, int W, int MINB, bool MF>
 __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned bad = 0;
-  masked_tile<Q, W, MF, false>(a, field_in<MF>(a), field_out<MF>(a), a.e1, a.e2, blockIdx.x,
+  masked_tile<Q, W, MF>(a, field_in<MF>(a), field_out<MF>(a), a.e1, a.e2, blockIdx.x,
                                blockIdx.y, smem, bad);
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
@@ -395,7 +378,9 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float
 // one CTA per tile (all co-resident: a cooperative launch).  A tile starts
 // step m once the tiles around it (the 3 x 3 block: its halo is smaller
 // than a tile) have finished step m-1, signalled by a per-tile count of
-// finished steps (release after the CTA's stores, acquire before staging).
+// finished steps (release after the CTA's stores, acquire before staging;
+// one lane per neighbour polls, so the wait costs one L2 round trip once
+// every neighbour is done).
 // No tile is ever more than one step ahead of a neighbour, so two buffers
 // suffice: step m writes buf[(steps - m) & 1] while every tile that still
 // reads that buffer's previous contents has finished.  Staging of one
@@ -459,7 +444,7 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_march2dm(const Step2D<floa
     const float* src = s == 1 ? m.u_first : (odd ? m.buf[0] : m.buf[1]);
     float* dst = odd ? m.buf[1] : m.buf[0];
     const float2 e = m.e12[n];  // (e1, e2) at t_n
-    masked_tile<Q, W, false, false>(a, src, dst, e.x, e.y, bx, by, smem, bad);
+    masked_tile<Q, W, false>(a, src, dst, e.x, e.y, bx, by, smem, bad);
     __syncthreads();  // every store of the tile is issued
     // the release is cumulative: it publishes the stores the barrier ordered before it
     if (threadIdx.x == 0 && by * tx + bx != m.silent) st_release(m.flags + by * tx + bx, (unsigned)s);
@@ -480,8 +465,8 @@ cudaError_t launch_m(const Step2D<float>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// The persistent march of a single-field plan (variant 0: 3 CTAs/SM, 1:
-// 2); cudaErrorCooperativeLaunchTooLarge when the tiles cannot all be
+// The persistent march of a single-field plan (variant 0: 3 CTAs/SM, 1: 2,
+// 2: 4); cudaErrorCooperativeLaunchTooLarge when the tiles cannot all be
 // resident at once.
 template <int Q, int W>
 cudaError_t launch_march_m(const Step2D<float>& a, const MaskedMarch& m, cudaStream_t s) {
