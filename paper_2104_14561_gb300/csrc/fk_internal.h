@@ -195,9 +195,19 @@ struct Step3D {
   int nu;
   const T* xc[3];
   const double* xd[3];
+  // the runaway model: the per-node shift and scale (sh[0..2], gs[0..2],
+  // six planes of J values, plan workspace) that k_step3d reads; filled once
+  // per plan by fk_launch_coef3d for the static model, and by the step itself
+  // (coef_per_step) for the quench variant, whose constants change with t_n
+  const T* coef;
+  int coef_per_step;
 };
 template <typename T>
 cudaError_t fk_launch_step3d(const Step3D<T>& a, cudaStream_t s);
+// The per-node runaway coefficients of every node the scheme updates into
+// coef (6 J values), from the same device code the step evaluates them with.
+template <typename T>
+cudaError_t fk_launch_coef3d(const Step3D<T>& a, T* coef, cudaStream_t s);
 // The terminal indicator of a 3D plan: 1 on the faces whose exit value is
 // 1, 0 elsewhere.
 template <typename T>
@@ -375,6 +385,7 @@ struct fk_plan {
   void* dcoord64[3]; // d = 3, FP32 plans: FP64 device copies (runaway coefficients)
   // d = 3: the node records of the step and the window width
   void* rec3d;
+  void* coef3d;      // the static runaway model's per-node coefficients (6 J values)
   int w3;
   // fk_solve_horizons: the second buffer of the N horizon fields
   void* hz_ws;

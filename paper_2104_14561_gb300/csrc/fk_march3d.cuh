@@ -31,6 +31,11 @@
 //    consecutive x-nodes read overlapping, contiguous windows); with
 //    per-node coefficients, only the planes, rows and cells its own points
 //    reach, often far fewer than the W^3 the widest node needs.
+// The runaway model's per-node drift and sigma (Eq. (ex32d): erf, four
+// exponentials, square roots) go into a table of six values per node that
+// k_step3d reads: k_coef3d fills it once per plan for the static model and
+// before each step for the quench variant, whose constants depend on t_n
+// (a third launch per step there).
 // Positions are taken relative to the node in cells: point p of axis m is
 // at i_m + rel_p with rel_p = b_m dt / h_m + sigma_m sqrt(2 dt) a_p / h_m.
 //
@@ -384,8 +389,21 @@ __device__ __forceinline__ void runaway_coef(const Step3D<T>& a, int i, int j, i
   }
 }
 
+// Resident CTAs per SM that k_step3d's register budget is set for.  FP32,
+// measured on a GB300 against the unbounded budget (132 registers at W = 8):
+// 4 for the wide uniform windows (the 97 x 65 x 41 runaway march 209 ->
+// 177 ms, the 129^3 constant drift 263 -> 223 ms), 5 for W <= 6 and
+// non-uniform axes (quench 332 -> 318 ms, the 97 x 65 x 128 non-uniform
+// runaway march 738 -> 664 ms), a few spilled bytes at most.  FP64 keeps
+// the compiler's budget.
+template <typename T, int W, bool NU>
+constexpr int step3d_min_blocks() {
+  return sizeof(T) == 8 ? 1 : (NU || W <= 6) ? 5 : 4;
+}
+
 template <typename T, int W, bool RE, bool NU>
-__global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
+__global__ void __launch_bounds__(kRecThreads, (step3d_min_blocks<T, W, NU>()))
+    k_step3d(const Step3D<T> a) {
   const int i = a.first[0] + blockIdx.x * blockDim.x + threadIdx.x;
   const int j = a.first[1] + blockIdx.y, k = a.first[2] + blockIdx.z;
   if (i >= a.first[0] + a.count[0]) return;
@@ -395,8 +413,13 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
   // shift and scale of the points per axis, in cells: plan constants for
   // the constant drift, per node for the runaway model
   T sh[3], gs[3];
-  if constexpr (RE) {
-    runaway_coef<T, NU>(a, i, j, k, sh, gs);
+  if constexpr (RE) {  // k_coef3d's table (once per plan, or this step's for the quench)
+    const int64_t J = sz * a.nz;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      sh[m] = a.coef[m * J + node];
+      gs[m] = a.coef[(3 + m) * J + node];
+    }
   } else {
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -476,6 +499,24 @@ __global__ void __launch_bounds__(kRecThreads) k_step3d(const Step3D<T> a) {
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
 
+// The runaway coefficients of every node k_step3d updates, once per plan
+// (the static model's do not depend on t).
+template <typename T, bool NU>
+__global__ void __launch_bounds__(kRecThreads) k_coef3d(const Step3D<T> a, T* coef) {
+  const int i = a.first[0] + blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = a.first[1] + blockIdx.y, k = a.first[2] + blockIdx.z;
+  if (i >= a.first[0] + a.count[0]) return;
+  const int64_t J = (int64_t)a.nx * a.ny * a.nz;
+  const int64_t node = ((int64_t)k * a.ny + j) * a.nx + i;
+  T sh[3], gs[3];
+  runaway_coef<T, NU>(a, i, j, k, sh, gs);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    coef[m * J + node] = sh[m];
+    coef[(3 + m) * J + node] = gs[m];
+  }
+}
+
 template <typename T, int W>
 cudaError_t launch_w(const Step3D<T>& a, cudaStream_t s) {
   const int in = a.count[0];
@@ -499,6 +540,10 @@ cudaError_t launch_w(const Step3D<T>& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t fk_launch_step3d(const Step3D<T>& a, cudaStream_t s) {
+  if (a.family == FK_RUNAWAY_3D && a.coef_per_step) {
+    cudaError_t e = fk_launch_coef3d<T>(a, const_cast<T*>(a.coef), s);
+    if (e != cudaSuccess) return e;
+  }
   {
     const dim3 grid((unsigned)((a.nx + kRecThreads - 1) / kRecThreads), (unsigned)a.ny,
                     (unsigned)a.nz);
@@ -515,6 +560,17 @@ cudaError_t fk_launch_step3d(const Step3D<T>& a, cudaStream_t s) {
     case 8: return launch_w<T, 8>(a, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <typename T>
+cudaError_t fk_launch_coef3d(const Step3D<T>& a, T* coef, cudaStream_t s) {
+  const dim3 grid((unsigned)((a.count[0] + kRecThreads - 1) / kRecThreads), (unsigned)a.count[1],
+                  (unsigned)a.count[2]);
+  if (a.nu)
+    k_coef3d<T, true><<<grid, kRecThreads, 0, s>>>(a, coef);
+  else
+    k_coef3d<T, false><<<grid, kRecThreads, 0, s>>>(a, coef);
+  return cudaGetLastError();
 }
 
 template <typename T>

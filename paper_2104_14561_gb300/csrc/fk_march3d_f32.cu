@@ -3,3 +3,4 @@
 
 template cudaError_t fk_launch_step3d<float>(const Step3D<float>&, cudaStream_t);
 template cudaError_t fk_launch_chi3d<float>(const Step3D<float>&, float*, cudaStream_t);
+template cudaError_t fk_launch_coef3d<float>(const Step3D<float>&, float*, cudaStream_t);

@@ -3,3 +3,4 @@
 
 template cudaError_t fk_launch_step3d<double>(const Step3D<double>&, cudaStream_t);
 template cudaError_t fk_launch_chi3d<double>(const Step3D<double>&, double*, cudaStream_t);
+template cudaError_t fk_launch_coef3d<double>(const Step3D<double>&, double*, cudaStream_t);

@@ -972,6 +972,22 @@ void fill3d(const fk_plan* p, int n, Step3D<T>* a) {
   if (re) runaway_params_at(p, n, a->rp);
   a->dt = (T)p->dt;
   a->sq2dt = (T)sqrt(2.0 * p->dt);
+  a->coef = (const T*)p->coef3d;
+  a->coef_per_step = quench_family(p->coeffs.family) ? 1 : 0;
+}
+
+// The runaway model's per-node coefficients (Eq. (ex32d)), six values per
+// node that the step reads: the static model's once per plan here, the
+// quench variant's by each step at its t_n.
+template <typename T>
+fk_status fill_coef3d(fk_plan* p) {
+  fk_status st = fk_dev_alloc(p, &p->coef3d, (size_t)(6 * p->J * p->elem));
+  if (st != FK_OK || quench_family(p->coeffs.family)) return st;
+  Step3D<T> a;
+  fill3d<T>(p, 0, &a);
+  st = cuda_status(fk_launch_coef3d<T>(a, (T*)p->coef3d, 0));
+  if (st == FK_OK) st = cuda_status(cudaDeviceSynchronize());
+  return st;
 }
 
 // The terminal indicator of a 3D plan into u (device, J values).
@@ -1426,6 +1442,8 @@ fk_status fk_plan_create(fk_plan** out, const fk_grid* grid, const fk_region* re
   if (st == FK_OK) st = (prec == FK_FP32) ? upload_tables<float>(p) : upload_tables<double>(p);
   if (st == FK_OK && p->nu)
     st = (prec == FK_FP32) ? upload_coords<float>(p) : upload_coords<double>(p);
+  if (st == FK_OK && grid->dim == 3 && runaway_family(p->coeffs.family))
+    st = (prec == FK_FP32) ? fill_coef3d<float>(p) : fill_coef3d<double>(p);
   if (st == FK_OK) st = cuda_status(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
   if (st == FK_OK && p->mwin > 0 && prec == FK_FP32 && grid->dim == 2) st = persist_workspace(p);
   if (st == FK_OK) st = autotune(p);
@@ -1464,6 +1482,7 @@ fk_status fk_plan_destroy(fk_plan* p) {
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   fk_dev_free(p->scratch);
   fk_dev_free(p->rec3d);
+  fk_dev_free(p->coef3d);
   fk_dev_free(p->col_tab);
   fk_dev_free(p->row_tab);
   fk_dev_free(p->d_err);
