@@ -111,7 +111,7 @@ WORKLOADS = {
                                             2.0, 0.0, 0.01, 511.0),
                                     q=4, dt=1e-3, n_steps=12000, precision="fp32"),
     # the same model on the paper's non-uniform radial grid (Sec. 4.3): r
-    # spaced 0.1 on [0, r_D] and 0.0025 on [r_D, 1] (8 + 120 cells), which
+    # spaced 0.1 on [0, r_D] and 0.0025 on [r_D, 1] (7 + 120 cells), which
     # resolves the boundary layer at r_D = 0.7
     "runaway_nonuniform_97x65x128": dict(
         n=(97, 65, 128), lo=(2.0, -1.0, 0.0), hi=(50.0, 1.0, 1.0), family="runaway",

@@ -13,6 +13,11 @@ width.
 * 1D drifted Brownian motion on a mesh graded towards both faces against
   discretely monitored Monte Carlo, to the tolerance the uniform mesh with
   twice the nodes meets.
+* d = 3: explicit uniform coordinates reproduce the uniform march, for
+  constant drift and for the runaway-electron model (its coefficients then
+  come from the given coordinates and act in physical lengths); affine data
+  on three graded axes is reproduced by the tricubic interpolant and shifted
+  by b dt by one step.
 """
 import math
 
@@ -72,3 +77,45 @@ def test_graded_1d_monte_carlo(oracle):
                                  seed=seed)
         tol = 4 * math.sqrt(mc * (1 - mc) / PATHS) + 2.5e-3
         assert abs(u[j] - mc) < tol, (x0, u[j], mc, tol)
+
+
+def test_explicit_uniform_axes_reproduce_uniform_3d(oracle):
+    runaway = fk_inputs.workload("runaway_97x65x41")["params"]
+    cases = (((13, 11, 9), (-1.0,) * 3, (1.0,) * 3, oracle.CONST_DRIFT, [0.3, -0.2, 0.1, 0.4],
+              2e-3),
+             ((13, 9, 11), (2.0, -1.0, 0.0), (12.0, 1.0, 1.0), oracle.RUNAWAY, list(runaway),
+              0.05))
+    for n, lo, hi, fam, p, dt in cases:
+        g = oracle.Grid(n, lo, hi)
+        ga = oracle.Grid(n, lo, hi, axes=tuple(g.axis(m) for m in range(3)))
+        u0 = fk_inputs.random_field(tuple(reversed(n)), seed=4, boundary_one=False) \
+            if fam == oracle.CONST_DRIFT else None
+        a = oracle.march(g, fam, p, 4, dt, 8, 0, u0)
+        b = oracle.march(ga, fam, p, 4, dt, 8, 0, u0)
+        assert np.abs(a).max() > 0.05
+        assert np.abs(a - b).max() <= 1e-13, fam
+
+
+def test_affine_data_on_graded_axes_3d(oracle):
+    axs = (_graded(-2.0, 2.0, 25, 0.9), _graded(-1.5, 1.5, 21, 0.85), _graded(-1.0, 1.0, 17, 0.8))
+    assert min(np.diff(a).max() / np.diff(a).min() for a in axs) > 4
+    g = oracle.Grid((25, 21, 17), (-2.0, -1.5, -1.0), (2.0, 1.5, 1.0), axes=axs)
+    Z, Y, X = np.meshgrid(axs[2], axs[1], axs[0], indexing="ij")
+    c = (0.3, 0.05, -0.07, 0.04)
+    u = c[0] + c[1] * X + c[2] * Y + c[3] * Z
+    b, s, dt = (0.6, -0.4, 0.3), 0.3, 0.01
+    got = oracle.march(g, oracle.CONST_DRIFT, [b[0], b[1], b[2], s], 4, dt, 1, 0, u,
+                       boundary_rule=False)
+    want = c[0] + c[1] * (X + b[0] * dt) + c[2] * (Y + b[1] * dt) + c[3] * (Z + b[2] * dt)
+    a, _ = oracle.gauss_hermite(4)
+    reach = max(abs(v) for v in b) * dt + s * math.sqrt(2 * dt) * abs(a).max()
+    inside = ((np.abs(X) < 2.0 - reach - 1e-9) & (np.abs(Y) < 1.5 - reach - 1e-9)
+              & (np.abs(Z) < 1.0 - reach - 1e-9))
+    assert inside.sum() > 3000
+    assert np.abs(got - want)[inside].max() <= 1e-13
+    rng = np.random.default_rng(2)
+    pts = np.stack([rng.uniform(-2, 2, 400), rng.uniform(-1.5, 1.5, 400),
+                    rng.uniform(-1, 1, 400)], axis=1)
+    vals = oracle.interp(g, u, pts)
+    ref = c[0] + c[1] * pts[:, 0] + c[2] * pts[:, 1] + c[3] * pts[:, 2]
+    assert np.abs(vals - ref).max() <= 1e-13
