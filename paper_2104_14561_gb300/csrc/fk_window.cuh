@@ -225,20 +225,138 @@ struct PointWeights {
   }
 };
 
-// Pattern `pat` of (Q, W), taken from K upwards (one uniform branch).
-template <int Q, int W, int K, int S>
-__device__ __forceinline__ void weights_of(int pat, bool exits, const float4* qc, float2 Z,
-                                           float2 LO, float2 HI, float2 (&PH)[S], float2 (&PS)[S],
-                                           float2& E) {
-  if constexpr (K < fk_npat(Q, W)) {
-    if (pat == K) {
-      if (exits)
-        PointWeights<Q, W, K, true, 0>::run(qc, Z, LO, HI, PH, PS, E);
-      else
-        PointWeights<Q, W, K, false, 0>::run(qc, Z, LO, HI, PH, PS, E);
-    } else {
-      weights_of<Q, W, K + 1>(pat, exits, qc, Z, LO, HI, PH, PS, E);
+// The tile geometry a node body needs: staged tile size, the staged node
+// (0, 0) as a global node, and the shared-memory tables.
+struct MaskedTileRefs {
+  const float4* QC;
+  const float4* P;
+  const float2* Yr;
+  const float* U;
+  int lx, ly, gi0, gk0;
+};
+
+// One output node (i, k) of pattern K of (Q, W): its 1D weights, the W x W
+// record window and the store.  Compiled per pattern and exit flag, so the
+// weights sit in fixed registers from their first contribution to the last
+// read, with no branch join in between.
+template <int Q, int W, int K, bool EXIT>
+__device__ __forceinline__ void masked_node(const Step2D<float>& a, const MaskedTileRefs& t,
+                                            float* u_out, int i, int k, float fcx, float fcy,
+                                            unsigned& bad) {
+  constexpr int NP = (W + 1) / 2;  // column pairs of the window
+  const int lx = t.lx, ly = t.ly;
+  const int li = i - t.gi0, lk = k - t.gk0;
+  const float uj = t.U[lk * lx + li];
+  float dx, dy;
+  if (a.family == FK_CELLULAR_FLOW) {
+    const float* rt = a.row_tab + 2 * (int64_t)k;
+    dx = a.kx * rt[0] * fcx;
+    dy = a.ky * rt[1] * fcy;
+  } else {
+    dx = a.cdx * fcx;
+    dy = a.cdy * fcy;
+  }
+  // window origin F0: the cell of point 0 on each axis; positions after
+  // it are Z + g_q with Z = D - F0 (the points keep the rule's symmetric
+  // offsets g_q, so FP32 rounding of the offsets cannot add up to a drift),
+  // and a point exits when it leaves [LO, HI] (the box in the same
+  // coordinates)
+  const float fx0 = floorf(dx + a.gx[0]), fy0 = floorf(dy + a.gy[0]);
+  int wx = li + (int)fx0, wy = lk + (int)fy0;
+  if (wx < 1 || wx + 2 * NP - 1 > lx - 2 || wy < 1 || wy + W - 1 > ly - 2) {
+    bad = 1u;  // halo too small for this drift: flag, read an in-range window
+    wx = 1;
+    wy = 1;
+  }
+  const float2 Z = f2(dx - fx0, dy - fy0);
+  float2 LO = f2(0.f, 0.f), HI = f2(0.f, 0.f);
+  if constexpr (EXIT) {
+    LO = f2(-(float)i - fx0, -(float)k - fy0);
+    HI = f2((float)(a.nx - 1 - i) - fx0, (float)(a.ny - 1 - k) - fy0);
+  }
+  // 1D weights, x in .x and y in .y: PH[s] = (phi_s, Phi_s), PS[s] = (psi_s, Psi_s)
+  // (slots 0 .. W-1 all receive a first contribution; the padding slot
+  // of an odd W stays 0)
+  float2 PH[2 * NP], PS[2 * NP];
+#pragma unroll
+  for (int r = W; r < 2 * NP; ++r) PH[r] = PS[r] = f2(0.f, 0.f);
+  float2 E = f2(0.f, 0.f);
+  PointWeights<Q, W, K, EXIT, 0>::run(t.QC + opaque_zero(), Z, LO, HI, PH, PS, E);
+  // W x W record window, row by row, two columns per f32x2 operation:
+  //   (AE_r, AX_r) = sum_c (phi_c (u - u_j), psi_c h u_x),  B_r = sum_c phi_c h u_y,
+  //   acc += Phi_r (AE_r + AX_r) + Psi_r B_r
+  float2 XP[NP], XS[NP];  // (phi_c, phi_c+1), (psi_c, psi_c+1), c = 2 j
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    XP[j] = f2(PH[2 * j].x, PH[2 * j + 1].x);
+    XS[j] = f2(PS[2 * j].x, PS[2 * j + 1].x);
+  }
+  const float4* pwin = t.P + (wy * lx + wx);
+  const float2* ywin = t.Yr + (wy * lx + wx);
+  const float2 nuj = f2(-uj, -uj);
+  float acc = 0.f;
+#pragma unroll
+  for (int r = 0; r < W; ++r) {
+    const float4* pr = pwin + r * lx;
+    const float2* yr = ywin + r * lx;
+    float2 AE, AX, B;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const float4 p = pr[2 * j];
+      const float2 y = yr[2 * j];
+      const float2 du = add2(f2(p.x, p.y), nuj);
+      if (j == 0) {
+        AE = mul2(XP[0], du);
+        AX = mul2(XS[0], f2(p.z, p.w));
+        B = mul2(XP[0], y);
+      } else {
+        AE = fma2(XP[j], du, AE);
+        AX = fma2(XS[j], f2(p.z, p.w), AX);
+        B = fma2(XP[j], y, B);
+      }
     }
+    const float2 T = add2(AE, AX);
+    acc = fmaf(PH[r].y, T.x + T.y, fmaf(PS[r].y, B.x + B.y, acc));
+  }
+  const float ext = EXIT ? (1.f - uj) * (E.x + E.y - E.x * E.y) : 0.f;
+  const float un = uj + (acc + ext);
+  const int64_t j = (int64_t)k * a.nx + i;
+  u_out[j] = un;
+  if (a.snap) a.snap[j] = un;
+  boundary_ones(u_out, a.snap, a.nx, a.ny, i, k);
+}
+
+// The rows of one tile column (one output node per thread and pass: column
+// i, rows k0 + warp + 8 m) with pattern K; a row whose points can leave the
+// box takes the exit tests.
+template <int Q, int W, int K>
+__device__ __forceinline__ void masked_rows(const Step2D<float>& a, const MaskedTileRefs& t,
+                                            float* u_out, int i, int k0, bool xsafe, float fcx,
+                                            float fcy, unsigned& bad) {
+  const int warp = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
+    const int k = k0 + ty;
+    if (k > a.ny - 2) break;
+    if (!(xsafe && k - a.hy >= 0 && k + a.hy <= a.ny - 1))
+      masked_node<Q, W, K, true>(a, t, u_out, i, k, fcx, fcy, bad);
+    else
+      masked_node<Q, W, K, false>(a, t, u_out, i, k, fcx, fcy, bad);
+  }
+}
+
+// The plan's pattern `pat` of (Q, W), taken from K upwards: one uniform
+// branch per tile, ahead of the row loop.
+template <int Q, int W, int K>
+__device__ __forceinline__ void masked_rows_of(int pat, const Step2D<float>& a,
+                                               const MaskedTileRefs& t, float* u_out, int i,
+                                               int k0, bool xsafe, float fcx, float fcy,
+                                               unsigned& bad) {
+  if constexpr (K < fk_npat(Q, W)) {
+    if (pat == K)
+      masked_rows<Q, W, K>(a, t, u_out, i, k0, xsafe, fcx, fcy, bad);
+    else
+      masked_rows_of<Q, W, K + 1>(pat, a, t, u_out, i, k0, xsafe, fcx, fcy, bad);
   }
 }
 
@@ -249,7 +367,6 @@ template <int Q, int W, bool MF>
 __device__ __forceinline__ void masked_tile(const Step2D<float>& a, const float* u_in,
                                             float* u_out, float e1, float e2, int bx, int by,
                                             unsigned char* smem, unsigned& bad) {
-  constexpr int NP = (W + 1) / 2;  // column pairs of the window
   const int lx = a.lx, ly = a.ly;
   float4* QC = reinterpret_cast<float4*>(smem);
   float4* P = QC + FK_MAXQ_2D;
@@ -262,11 +379,10 @@ __device__ __forceinline__ void masked_tile(const Step2D<float>& a, const float*
 
   stage_pairs(a, u_in, U, P, Yr, gi0, gk0);
 
-  // 3. one output node per thread and pass: column i0 + lane, row k0 + warp + 8 m
-  const int lane = tid & 31, warp = tid >> 5;
+  // 3. the output nodes: column i0 + lane of the tile, every row
+  const int lane = tid & 31;
   const int i = i0 + lane;
   if (i > a.nx - 2) return;  // (no barrier follows in the tile)
-  const int li = i - gi0;
   // no point of a node in this tile's columns can leave through an x face
   // (the halo exceeds the reach of every point)
   const bool xsafe = i0 - a.hx >= 0 && i0 + 31 + a.hx <= a.nx - 1;
@@ -278,88 +394,8 @@ __device__ __forceinline__ void masked_tile(const Step2D<float>& a, const float*
     fcx = a.A * ct[0] + e1 * ct[1];
     fcy = a.A * ct[2] + e2 * ct[3];
   }
-#pragma unroll 1
-  for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
-    const int k = k0 + ty;
-    if (k > a.ny - 2) break;
-    const int lk = k - gk0;
-    const float uj = U[lk * lx + li];
-    float dx, dy;
-    if (a.family == FK_CELLULAR_FLOW) {
-      const float* rt = a.row_tab + 2 * (int64_t)k;
-      dx = a.kx * rt[0] * fcx;
-      dy = a.ky * rt[1] * fcy;
-    } else {
-      dx = a.cdx * fcx;
-      dy = a.cdy * fcy;
-    }
-    // window origin F0: the cell of point 0 on each axis; positions after
-    // it are Z + g_q with Z = D - F0 (the points keep the rule's symmetric
-    // offsets g_q, so FP32 rounding of the offsets cannot add up to a drift),
-    // and a point exits when it leaves [LO, HI] (the box in the same
-    // coordinates)
-    const float fx0 = floorf(dx + a.gx[0]), fy0 = floorf(dy + a.gy[0]);
-    int wx = li + (int)fx0, wy = lk + (int)fy0;
-    if (wx < 1 || wx + 2 * NP - 1 > lx - 2 || wy < 1 || wy + W - 1 > ly - 2) {
-      bad = 1u;  // halo too small for this drift: flag, read an in-range window
-      wx = 1;
-      wy = 1;
-    }
-    const float2 Z = f2(dx - fx0, dy - fy0);
-    const float2 LO = f2(-(float)i - fx0, -(float)k - fy0);
-    const float2 HI = f2((float)(a.nx - 1 - i) - fx0, (float)(a.ny - 1 - k) - fy0);
-    const bool exits = !(xsafe && k - a.hy >= 0 && k + a.hy <= a.ny - 1);
-    // 1D weights, x in .x and y in .y: PH[s] = (phi_s, Phi_s), PS[s] = (psi_s, Psi_s)
-    // (slots 0 .. W-1 all receive a first contribution; the padding slot
-    // of an odd W stays 0)
-    float2 PH[2 * NP], PS[2 * NP];
-#pragma unroll
-    for (int r = W; r < 2 * NP; ++r) PH[r] = PS[r] = f2(0.f, 0.f);
-    float2 E = f2(0.f, 0.f);
-    weights_of<Q, W, 0>(a.mpat, exits, QC + opaque_zero(), Z, LO, HI, PH, PS, E);
-    // W x W record window, row by row, two columns per f32x2 operation:
-    //   (AE_r, AX_r) = sum_c (phi_c (u - u_j), psi_c h u_x),  B_r = sum_c phi_c h u_y,
-    //   acc += Phi_r (AE_r + AX_r) + Psi_r B_r
-    float2 XP[NP], XS[NP];  // (phi_c, phi_c+1), (psi_c, psi_c+1), c = 2 j
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      XP[j] = f2(PH[2 * j].x, PH[2 * j + 1].x);
-      XS[j] = f2(PS[2 * j].x, PS[2 * j + 1].x);
-    }
-    const float4* pwin = P + (wy * lx + wx);
-    const float2* ywin = Yr + (wy * lx + wx);
-    const float2 nuj = f2(-uj, -uj);
-    float acc = 0.f;
-#pragma unroll
-    for (int r = 0; r < W; ++r) {
-      const float4* pr = pwin + r * lx;
-      const float2* yr = ywin + r * lx;
-      float2 AE, AX, B;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        const float4 p = pr[2 * j];
-        const float2 y = yr[2 * j];
-        const float2 du = add2(f2(p.x, p.y), nuj);
-        if (j == 0) {
-          AE = mul2(XP[0], du);
-          AX = mul2(XS[0], f2(p.z, p.w));
-          B = mul2(XP[0], y);
-        } else {
-          AE = fma2(XP[j], du, AE);
-          AX = fma2(XS[j], f2(p.z, p.w), AX);
-          B = fma2(XP[j], y, B);
-        }
-      }
-      const float2 T = add2(AE, AX);
-      acc = fmaf(PH[r].y, T.x + T.y, fmaf(PS[r].y, B.x + B.y, acc));
-    }
-    const float ext = (1.f - uj) * (E.x + E.y - E.x * E.y);
-    const float un = uj + (acc + ext);
-    const int64_t j = (int64_t)k * a.nx + i;
-    u_out[j] = un;
-    if (a.snap) a.snap[j] = un;
-    boundary_ones(u_out, a.snap, a.nx, a.ny, i, k);
-  }
+  const MaskedTileRefs t = {QC, P, Yr, U, lx, ly, gi0, gk0};
+  masked_rows_of<Q, W, 0>(a.mpat, a, t, u_out, i, k0, xsafe, fcx, fcy, bad);
 }
 
 // MINB: CTAs of 256 threads per SM the register budget is sized for

@@ -207,6 +207,29 @@ def test_cellular_4097x2049_fp64_two_steps(fk, oracle):
     assert np.abs(got - want).max() <= TOL64
 
 
+@pytest.mark.parametrize("precision,tol", [("fp32", TOL32), ("fp64", TOL64)])
+def test_cellular_4097x2049_50_steps_vs_golden(fk, precision, tol):
+    """The large workload's mesh and rule (8 x 8 points, W about 19: the
+    direct kernel) over a 50-step march from chi, against the FP64 oracle's
+    u^0 at 20k+ sampled nodes (all nodes next to the boundary included),
+    written by tests/golden/make_oracle_golden.py."""
+    import torch
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden",
+                                "cellular_4097x2049_50steps_oracle_u0.npz"))
+    w = fk_inputs.workload("cellular_4097x2049", precision=precision, n_steps=50)
+    assert tuple(gold["n"]) == tuple(w["n"]) and int(gold["n_steps"]) == w["n_steps"]
+    plan = fk.Plan(_spec(fk, w))
+    out = plan.solve()
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    got = out.double().reshape(-1)[torch.tensor(gold["nodes"], device="cuda")].cpu().numpy()
+    plan.close()
+    assert float(gold["umax"]) == 1.0 and float(gold["umean"]) > 1e-3
+    err = np.abs(got - gold["u0"]).max()
+    print(f"cellular_4097x2049 {precision} vs fp64 oracle, 50 steps: max-abs {err:.3e}")
+    assert err <= tol
+
+
 def test_snapshots_and_resume(fk):
     """Snapshots equal the states reached by marching in chunks (fk_march)."""
     import torch
