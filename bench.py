@@ -755,7 +755,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                     "flop_per_launch": flops_launch, "launch_ms": launch_ms,
                     "window_rows": info.get("window_rows", 0),
                     "step_kernel": info.get("step_kernel"),
-                    "march_mode": info.get("march_mode")}
+                    "march_mode": info.get("march_mode"),
+                    "nodes_per_thread": info.get("nodes_per_thread", 1)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,

@@ -192,6 +192,11 @@ typedef struct fk_plan_info {
                                tiles wait on their 3 x 3 neighbourhood's
                                step counters, chosen at plan creation
                                when a timed 16-step march is faster)     */
+  int nodes_per_thread;     /* 2D FP32 masked kernel: 1, or 2 when each
+                               thread takes two nodes of a column and
+                               reads the rows their windows share once
+                               (W = 7; chosen by the timing at plan
+                               creation); 1 for every other kernel       */
 } fk_plan_info;
 
 /* ------------------------------------------------------------------------

@@ -59,7 +59,8 @@ class PlanInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64), ("window_rows", ctypes.c_int),
                 ("step_kernel", ctypes.c_int), ("batch_mode", ctypes.c_int),
                 ("adjoint_kernel", ctypes.c_int), ("periodic_x", ctypes.c_int),
-                ("nonuniform", ctypes.c_int), ("march_mode", ctypes.c_int)]
+                ("nonuniform", ctypes.c_int), ("march_mode", ctypes.c_int),
+                ("nodes_per_thread", ctypes.c_int)]
 
 
 _lib = None

@@ -49,7 +49,8 @@ struct Step2D {
   int nx, ny;
   int tx, ty;      // output tile (interior nodes) per CTA: tx = 32, ty = 8 m
   int variant;     // register-budget variant (FP32 direct and row window: 0 -> 4
-                   // CTAs/SM, 1 -> 3; masked window: 0 -> 3, 1 -> 2, 2 -> 4)
+                   // CTAs/SM, 1 -> 3; masked window: 0 -> 3, 1 -> 2, 2 -> 4,
+                   // 3 -> 2 with two nodes of a column per thread)
   int hx, hy;      // halo in cells
   int lx, ly;      // staged value tile: tx + 2 hx + 2, ty + 2 hy + 2
   int lyr;         // odd pitch of the record tiles: column pitch of the column-major

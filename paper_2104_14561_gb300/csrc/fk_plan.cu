@@ -506,6 +506,8 @@ bool kernel_eligible(const fk_plan* p, int kern) {
 bool cand_fits(const fk_plan* p, const TileCand& c, int dev_smem, int kern = kDirect) {
   if (p->elem == 8 && c.variant != 0) return false;
   if (c.variant == 2 && kern != kMasked) return false;  // (4 CTAs/SM: masked FP32 only)
+  // (two nodes per thread: masked FP32 with W = 7, even tile heights)
+  if (c.variant == 3 && (kern != kMasked || p->mwin != 7 || c.ty % 2 != 0)) return false;
   if (kern == kMasked) {
     const int lx = fk_step2dm_lx(p->mhalo[0], p->mwin), ly = c.ty + 2 * p->mhalo[1] + 2;
     const size_t bytes = p->elem == 8 ? fk_step2dm64_smem(ly, lx) : fk_step2dm_smem(ly, lx);
@@ -659,22 +661,25 @@ void refit_tile(fk_plan* p) {
 }
 
 // Tile candidates of the masked kernel: the fixed list, three heights of
-// variant 2, and tile heights that make the number of tiles just fit 1-4
-// waves of resident CTAs (3 per SM for variant 0, 2 for variant 1, 4 for
-// variant 2), so that the last wave is not short.
+// variant 2 and four of variant 3, and tile heights that make the number of
+// tiles just fit 1-4 waves of resident CTAs (3 per SM for variant 0, 2 for
+// variants 1 and 3, 4 for variant 2), so that the last wave is not short
+// (variant 3: rounded up to an even height).
 std::vector<TileCand> masked_cands(const fk_plan* p) {
   std::vector<TileCand> v(std::begin(kCands), std::end(kCands));
-  v.insert(v.end(), {TileCand{16, 2}, TileCand{24, 2}, TileCand{32, 2}});
+  v.insert(v.end(), {TileCand{16, 2}, TileCand{24, 2}, TileCand{32, 2}, TileCand{16, 3},
+                     TileCand{32, 3}, TileCand{48, 3}, TileCand{64, 3}});
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
     sms = 152;
   const int nxt = (p->grid.n[0] - 2 + 31) / 32, rows = p->grid.n[1] - 2;
-  for (int var = 0; var < 3; ++var) {
-    const int per_sm = var == 0 ? 3 : var == 1 ? 2 : 4;
+  for (int var = 0; var < 4; ++var) {
+    const int per_sm = var == 0 ? 3 : var == 2 ? 4 : 2;
     for (int waves = 1; waves <= 4; ++waves) {
       const int row_tiles = waves * sms * per_sm / nxt;
       if (row_tiles < 1) continue;
-      const int ty = (rows + row_tiles - 1) / row_tiles;
+      int ty = (rows + row_tiles - 1) / row_tiles;
+      if (var == 3) ty += ty & 1;
       if (ty < 4 || ty > 64) continue;
       bool seen = false;
       for (const TileCand& c : v) seen = seen || (c.ty == ty && c.variant == var);
@@ -684,6 +689,47 @@ std::vector<TileCand> masked_cands(const fk_plan* p) {
   return v;
 }
 
+// Mean time in ms of one replay of the work `enqueue` puts on stream s,
+// captured once into a CUDA graph (a warm-up replay, then `reps` timed):
+// fk_solve replays its march from a graph too, so host launch overhead,
+// which on a fast step exceeds the step itself, stays out of the
+// comparison.  1e30 when the capture, the instantiation or a replay fails
+// (a configuration the device refuses); the error is cleared.
+template <typename F>
+float graph_ms(cudaStream_t s, int reps, F&& enqueue) {
+  float ms = 1e30f;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return ms;
+  }
+  const fk_status es = enqueue();
+  const cudaError_t ec = cudaStreamEndCapture(s, &g);
+  if (es != FK_OK || ec != cudaSuccess || !g || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    return ms;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+      cudaGraphLaunch(ge, s) == cudaSuccess && cudaEventRecord(e0, s) == cudaSuccess) {
+    bool ok = true;
+    for (int r = 0; r < reps && ok; ++r) ok = cudaGraphLaunch(ge, s) == cudaSuccess;
+    float t = 0.f;
+    if (ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+        cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+      ms = t / reps;
+  }
+  cudaStreamSynchronize(s);
+  cudaGetLastError();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  return ms;
+}
+
 fk_status autotune(fk_plan* p) {
   if (p->grid.dim != 2 || p->path != FK_PATH_MATRIX_FREE) return FK_OK;
   // explicit choice (profiling runs, where timing is distorted):
@@ -691,7 +737,7 @@ fk_status autotune(fk_plan* p) {
   if (const char* t = getenv("FK_STEP_TILE")) {
     int ty = 0, var = 0, kern = 0;
     if (sscanf(t, "%d,%d,%d", &ty, &var, &kern) >= 1 && ty >= 4 && ty <= 64 &&
-        (var >= 0 && var <= 2) && kern >= 0 && kern <= 2) {
+        (var >= 0 && var <= 3) && kern >= 0 && kern <= 2) {
       if (kern != kMasked && ty % 8 != 0) ty = (ty + 7) / 8 * 8;
       int dev_smem = 0;
       cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
@@ -737,11 +783,9 @@ fk_status autotune(fk_plan* p) {
     return FK_OK;  // keep the default tile
   }
   cudaStream_t s = p->cap_stream;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
   fk_status st = cuda_status(
       fk_launch_fill_chi(p->scratch, 2, p->grid.n[0], p->grid.n[1], p->elem, s, p->periodic_x));
+  if (st == FK_OK) st = cuda_status(cudaStreamSynchronize(s));
   const bool log = getenv("FK_TUNE_LOG") != nullptr;
   if (log)
     fprintf(stderr,
@@ -761,17 +805,14 @@ fk_status autotune(fk_plan* p) {
       p->tile[1] = c.ty;
       p->variant = c.variant;
       set_kernel(p, kern);
-      st = fk_enqueue_step(p, p->n_steps - 1, p->scratch, tmp, nullptr, s);  // warm-up
-      if (st != FK_OK) break;
-      cudaEventRecord(e0, s);
-      const int reps = 4;
-      for (int r = 0; r < reps && st == FK_OK; ++r)
-        st = fk_enqueue_step(p, p->n_steps - 1, p->scratch, tmp, nullptr, s);
-      cudaEventRecord(e1, s);
-      if (cudaEventSynchronize(e1) != cudaSuccess) st = FK_ERR_CUDA;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= reps;
+      // 8 steps from chi per replay, 3 replays
+      const int steps = 8;
+      const float ms = graph_ms(s, 3, [&]() {
+        fk_status e = FK_OK;
+        for (int r = 0; r < steps && e == FK_OK; ++r)
+          e = fk_enqueue_step(p, p->n_steps - 1, p->scratch, tmp, nullptr, s);
+        return e;
+      }) / steps;
       if (log)
         fprintf(stderr, "fk autotune %dx%d q=%d elem=%d: ty=%d variant=%d kernel=%d  %.2f us\n",
                 p->grid.n[0], p->grid.n[1], p->q, p->elem, c.ty, c.variant, kern, ms * 1e3f);
@@ -783,8 +824,6 @@ fk_status autotune(fk_plan* p) {
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   cudaStreamSynchronize(s);
   cudaFree(tmp);
   p->tile[1] = best_ty;
@@ -845,39 +884,25 @@ fk_status tune_persist(fk_plan* p) {
     return FK_OK;
   }
   cudaStream_t s = p->cap_stream;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
   float ms[2] = {1e30f, 1e30f};
   fk_status st = FK_OK;
   const bool log = getenv("FK_TUNE_LOG") != nullptr;
-  for (int mode = 0; mode < 2 && st == FK_OK; ++mode) {
+  // each mode as fk_solve replays it: a graph of the march from chi (a
+  // persistent launch that the device refuses times as 1e30: the per-step
+  // launches stay)
+  for (int mode = 0; mode < 2; ++mode) {
     p->persist = mode;
-    for (int rep = 0; rep < 2 && st == FK_OK; ++rep) {  // the first is a warm-up
-      st = cuda_status(fk_launch_fill_chi(p->scratch, 2, p->grid.n[0], p->grid.n[1], p->elem, s));
-      cudaEventRecord(e0, s);
-      if (st == FK_OK) st = enqueue_march(p, p->n_steps, p->n_steps - steps, p->scratch, tmp, nullptr, 0, s);
-      cudaEventRecord(e1, s);
-      if (st == FK_OK && cudaEventSynchronize(e1) != cudaSuccess) st = FK_ERR_CUDA;
-      float t = 0.f;
-      cudaEventElapsedTime(&t, e0, e1);
-      if (rep == 1) ms[mode] = t;
-    }
-    if (st != FK_OK && mode == 1) {
-      // a persistent launch that the device refuses (resources): keep the
-      // per-step launches
-      const cudaError_t e = cudaGetLastError();
-      if (log) fprintf(stderr, "fk march tune: persistent march refused (%s)\n", cudaGetErrorString(e));
-      cudaStreamSynchronize(s);
-      st = FK_OK;
-      ms[1] = 1e30f;
-    }
+    ms[mode] = graph_ms(s, 2, [&]() {
+      fk_status e = cuda_status(
+          fk_launch_fill_chi(p->scratch, 2, p->grid.n[0], p->grid.n[1], p->elem, s));
+      if (e == FK_OK)
+        e = enqueue_march(p, p->n_steps, p->n_steps - steps, p->scratch, tmp, nullptr, 0, s);
+      return e;
+    });
   }
   if (log)
     fprintf(stderr, "fk march tune %dx%d: %d steps, per-step launches %.1f us, persistent %.1f us\n",
             p->grid.n[0], p->grid.n[1], steps, ms[0] * 1e3f, ms[1] * 1e3f);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   cudaStreamSynchronize(s);
   cudaFree(tmp);
   cudaMemset(p->d_err, 0, sizeof(unsigned));
@@ -1535,6 +1560,8 @@ fk_status fk_plan_get_info(const fk_plan* p, fk_plan_info* info) {
   info->batch_mode = fk_batch_mode(p);
   info->adjoint_kernel = p->adj_kernel;
   info->march_mode = p->persist ? 1 : 0;
+  info->nodes_per_thread =
+      p->grid.dim == 2 && p->use_masked && p->elem == 4 && p->variant == 3 ? 2 : 1;
   return FK_OK;
 }
 

@@ -235,18 +235,28 @@ struct MaskedTileRefs {
   int lx, ly, gi0, gk0;
 };
 
-// One output node (i, k) of pattern K of (Q, W): its 1D weights, the W x W
-// record window and the store.  Compiled per pattern and exit flag, so the
-// weights sit in fixed registers from their first contribution to the last
-// read, with no branch join in between.
+// What one output node carries from its 1D weights to the window sums: the
+// weights PH[s] = (phi_s, Phi_s), PS[s] = (psi_s, Psi_s) over slots s <
+// 2 NP (the padding slot of an odd W is 0), the dropped exit weights E,
+// u_j, and the window origin (wx, wy) in staged coordinates.
+template <int W>
+struct MaskedNode {
+  static constexpr int NP = (W + 1) / 2;  // column pairs of the window
+  float2 PH[2 * NP], PS[2 * NP];
+  float2 E;
+  float uj;
+  int wx, wy;
+};
+
+// The 1D weights of node (i, k) for pattern K of (Q, W).
 template <int Q, int W, int K, bool EXIT>
-__device__ __forceinline__ void masked_node(const Step2D<float>& a, const MaskedTileRefs& t,
-                                            float* u_out, int i, int k, float fcx, float fcy,
-                                            unsigned& bad) {
-  constexpr int NP = (W + 1) / 2;  // column pairs of the window
+__device__ __forceinline__ void masked_weights(const Step2D<float>& a, const MaskedTileRefs& t,
+                                               int i, int k, float fcx, float fcy,
+                                               MaskedNode<W>& n, unsigned& bad) {
+  constexpr int NP = MaskedNode<W>::NP;
   const int lx = t.lx, ly = t.ly;
   const int li = i - t.gi0, lk = k - t.gk0;
-  const float uj = t.U[lk * lx + li];
+  n.uj = t.U[lk * lx + li];
   float dx, dy;
   if (a.family == FK_CELLULAR_FLOW) {
     const float* rt = a.row_tab + 2 * (int64_t)k;
@@ -262,11 +272,12 @@ __device__ __forceinline__ void masked_node(const Step2D<float>& a, const Masked
   // and a point exits when it leaves [LO, HI] (the box in the same
   // coordinates)
   const float fx0 = floorf(dx + a.gx[0]), fy0 = floorf(dy + a.gy[0]);
-  int wx = li + (int)fx0, wy = lk + (int)fy0;
-  if (wx < 1 || wx + 2 * NP - 1 > lx - 2 || wy < 1 || wy + W - 1 > ly - 2) {
+  n.wx = li + (int)fx0;
+  n.wy = lk + (int)fy0;
+  if (n.wx < 1 || n.wx + 2 * NP - 1 > lx - 2 || n.wy < 1 || n.wy + W - 1 > ly - 2) {
     bad = 1u;  // halo too small for this drift: flag, read an in-range window
-    wx = 1;
-    wy = 1;
+    n.wx = 1;
+    n.wy = 1;
   }
   const float2 Z = f2(dx - fx0, dy - fy0);
   float2 LO = f2(0.f, 0.f), HI = f2(0.f, 0.f);
@@ -274,26 +285,35 @@ __device__ __forceinline__ void masked_node(const Step2D<float>& a, const Masked
     LO = f2(-(float)i - fx0, -(float)k - fy0);
     HI = f2((float)(a.nx - 1 - i) - fx0, (float)(a.ny - 1 - k) - fy0);
   }
-  // 1D weights, x in .x and y in .y: PH[s] = (phi_s, Phi_s), PS[s] = (psi_s, Psi_s)
-  // (slots 0 .. W-1 all receive a first contribution; the padding slot
-  // of an odd W stays 0)
-  float2 PH[2 * NP], PS[2 * NP];
+  // (slots 0 .. W-1 all receive a first contribution; the padding slot of
+  // an odd W stays 0)
 #pragma unroll
-  for (int r = W; r < 2 * NP; ++r) PH[r] = PS[r] = f2(0.f, 0.f);
-  float2 E = f2(0.f, 0.f);
-  PointWeights<Q, W, K, EXIT, 0>::run(t.QC + opaque_zero(), Z, LO, HI, PH, PS, E);
-  // W x W record window, row by row, two columns per f32x2 operation:
-  //   (AE_r, AX_r) = sum_c (phi_c (u - u_j), psi_c h u_x),  B_r = sum_c phi_c h u_y,
-  //   acc += Phi_r (AE_r + AX_r) + Psi_r B_r
+  for (int r = W; r < 2 * NP; ++r) n.PH[r] = n.PS[r] = f2(0.f, 0.f);
+  n.E = f2(0.f, 0.f);
+  PointWeights<Q, W, K, EXIT, 0>::run(t.QC + opaque_zero(), Z, LO, HI, n.PH, n.PS, n.E);
+}
+
+// The W x W record window of one node, row by row, two columns per f32x2
+// operation:
+//   (AE_r, AX_r) = sum_c (phi_c (u - u_j), psi_c h u_x),  B_r = sum_c phi_c h u_y,
+//   acc += Phi_r (AE_r + AX_r) + Psi_r B_r
+// (An odd W reads its last column as a whole pair whose second weight is
+// 0: reading it as three scalars instead halves its bytes but adds an
+// instruction per row, and the kernel is issue-bound: a GB300 ran the
+// 1025 x 513 march 0.5-5 % slower that way.)
+template <int W>
+__device__ __forceinline__ float masked_window(const MaskedTileRefs& t, const MaskedNode<W>& n) {
+  constexpr int NP = MaskedNode<W>::NP;
+  const int lx = t.lx;
   float2 XP[NP], XS[NP];  // (phi_c, phi_c+1), (psi_c, psi_c+1), c = 2 j
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
-    XP[j] = f2(PH[2 * j].x, PH[2 * j + 1].x);
-    XS[j] = f2(PS[2 * j].x, PS[2 * j + 1].x);
+    XP[j] = f2(n.PH[2 * j].x, n.PH[2 * j + 1].x);
+    XS[j] = f2(n.PS[2 * j].x, n.PS[2 * j + 1].x);
   }
-  const float4* pwin = t.P + (wy * lx + wx);
-  const float2* ywin = t.Yr + (wy * lx + wx);
-  const float2 nuj = f2(-uj, -uj);
+  const float4* pwin = t.P + (n.wy * lx + n.wx);
+  const float2* ywin = t.Yr + (n.wy * lx + n.wx);
+  const float2 nuj = f2(-n.uj, -n.uj);
   float acc = 0.f;
 #pragma unroll
   for (int r = 0; r < W; ++r) {
@@ -316,54 +336,228 @@ __device__ __forceinline__ void masked_node(const Step2D<float>& a, const Masked
       }
     }
     const float2 T = add2(AE, AX);
-    acc = fmaf(PH[r].y, T.x + T.y, fmaf(PS[r].y, B.x + B.y, acc));
+    acc = fmaf(n.PH[r].y, T.x + T.y, fmaf(n.PS[r].y, B.x + B.y, acc));
   }
-  const float ext = EXIT ? (1.f - uj) * (E.x + E.y - E.x * E.y) : 0.f;
-  const float un = uj + (acc + ext);
+  return acc;
+}
+
+// The exit term of node n: (1 - u_j) (E_x + E_y - E_x E_y).
+template <bool EXIT, int W>
+__device__ __forceinline__ float masked_exit(const MaskedNode<W>& n) {
+  return EXIT ? (1.f - n.uj) * (n.E.x + n.E.y - n.E.x * n.E.y) : 0.f;
+}
+
+// u^n of node (i, k) from its window sum and exit term: the increment
+// form, the store and the boundary nodes next to it.
+template <int W>
+__device__ __forceinline__ void masked_store(const Step2D<float>& a, float* u_out, int i, int k,
+                                             const MaskedNode<W>& n, float acc, float ext) {
+  const float un = n.uj + (acc + ext);
   const int64_t j = (int64_t)k * a.nx + i;
   u_out[j] = un;
   if (a.snap) a.snap[j] = un;
   boundary_ones(u_out, a.snap, a.nx, a.ny, i, k);
 }
 
+// One output node (i, k) of pattern K of (Q, W): its 1D weights, the W x W
+// record window and the store.  Compiled per pattern and exit flag, so the
+// weights sit in fixed registers from their first contribution to the last
+// read, with no branch join in between.
+template <int Q, int W, int K, bool EXIT>
+__device__ __forceinline__ void masked_node(const Step2D<float>& a, const MaskedTileRefs& t,
+                                            float* u_out, int i, int k, float fcx, float fcy,
+                                            unsigned& bad) {
+  MaskedNode<W> n;
+  masked_weights<Q, W, K, EXIT>(a, t, i, k, fcx, fcy, n, bad);
+  const float ext = masked_exit<EXIT>(n);
+  masked_store<W>(a, u_out, i, k, n, masked_window<W>(t, n), ext);
+}
+
+// Two nodes of one column, A = (i, k) and B = (i, k + 1), from one read of
+// the window rows they share (odd W).  B's window sits dy = wy_B - wy_A
+// rows below A's (1 for a smooth drift, 0 or 2 where floor(drift) steps
+// between the rows) and dx = wx_B - wx_A columns to the side (0, or +-1
+// where it steps).  The union of the two windows is then W + 1 rows (W + 2
+// when dy = 2) of the same 2 NP = W + 1 columns from ox = min(wx_A,
+// wx_B): each node's W columns start at offset 0 or 1 in it, so its weights
+// move up one slot when the offset is 1.  Rows read once serve both nodes:
+// (W + 1) NP pair records for two nodes instead of 2 W NP.  Slots outside a
+// node's window carry weight exactly 0, so each node's sum is its own
+// window's, up to the grouping of columns into pairs.  Other offsets (not
+// met by a drift that changes by less than a cell between rows) run the
+// two windows one after the other.
+template <int W>
+__device__ __forceinline__ void masked_pair_window(const MaskedTileRefs& t,
+                                                   const MaskedNode<W>& A,
+                                                   const MaskedNode<W>& B, float& acc_a,
+                                                   float& acc_b) {
+  constexpr int NP = MaskedNode<W>::NP;
+  static_assert(2 * NP == W + 1, "pairs of nodes need an odd window width");
+  const int lx = t.lx, ly = t.ly;
+  const int ox = min(A.wx, B.wx);
+  const bool sa = A.wx != ox, sb = B.wx != ox;  // window starts one column into the union
+  const int dy = B.wy - A.wy;                     // 0, 1 or 2
+  // x weights on the union's column pairs (2 j, 2 j + 1)
+  float2 XPA[NP], XSA[NP], XPB[NP], XSB[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const float pa0 = j > 0 ? A.PH[2 * j - 1].x : 0.f, sa0 = j > 0 ? A.PS[2 * j - 1].x : 0.f;
+    const float pb0 = j > 0 ? B.PH[2 * j - 1].x : 0.f, sb0 = j > 0 ? B.PS[2 * j - 1].x : 0.f;
+    XPA[j] = sa ? f2(pa0, A.PH[2 * j].x) : f2(A.PH[2 * j].x, A.PH[2 * j + 1].x);
+    XSA[j] = sa ? f2(sa0, A.PS[2 * j].x) : f2(A.PS[2 * j].x, A.PS[2 * j + 1].x);
+    XPB[j] = sb ? f2(pb0, B.PH[2 * j].x) : f2(B.PH[2 * j].x, B.PH[2 * j + 1].x);
+    XSB[j] = sb ? f2(sb0, B.PS[2 * j].x) : f2(B.PS[2 * j].x, B.PS[2 * j + 1].x);
+  }
+  // B's row weights on union rows 0 .. W (slot r - dy; slot W is the padding slot, 0)
+  float PHB[W + 1], PSB[W + 1];
+#pragma unroll
+  for (int r = 0; r <= W; ++r) {
+    const float ph1 = r >= 1 ? B.PH[r - 1].y : 0.f, ps1 = r >= 1 ? B.PS[r - 1].y : 0.f;
+    const float ph2 = r >= 2 ? B.PH[r - 2].y : 0.f, ps2 = r >= 2 ? B.PS[r - 2].y : 0.f;
+    PHB[r] = dy == 0 ? B.PH[r].y : (dy == 1 ? ph1 : ph2);
+    PSB[r] = dy == 0 ? B.PS[r].y : (dy == 1 ? ps1 : ps2);
+  }
+  const float4* pwin = t.P + (A.wy * lx + ox);
+  const float2* ywin = t.Yr + (A.wy * lx + ox);
+  // union row W is B's last row when dy >= 1; when dy = 0 it lies past both
+  // windows (weight 0) and may lie past the records: read an in-range row
+  const int rw = min(W, ly - 2 - A.wy);
+  const float2 nua = f2(-A.uj, -A.uj), nub = f2(-B.uj, -B.uj);
+  float accA = 0.f, accB = 0.f;
+#pragma unroll
+  for (int r = 0; r <= W; ++r) {
+    const int ro = r < W ? r : rw;
+    const float4* pr = pwin + ro * lx;
+    const float2* yr = ywin + ro * lx;
+    float2 Ta, Ba, Tb, Bb;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const float4 p = pr[2 * j];
+      const float2 y = yr[2 * j];
+      const float2 u = f2(p.x, p.y), ux = f2(p.z, p.w);
+      if (r < W) {
+        const float2 du = add2(u, nua);
+        if (j == 0) {
+          Ta = fma2(XSA[0], ux, mul2(XPA[0], du));
+          Ba = mul2(XPA[0], y);
+        } else {
+          Ta = fma2(XSA[j], ux, fma2(XPA[j], du, Ta));
+          Ba = fma2(XPA[j], y, Ba);
+        }
+      }
+      const float2 dub = add2(u, nub);
+      if (j == 0) {
+        Tb = fma2(XSB[0], ux, mul2(XPB[0], dub));
+        Bb = mul2(XPB[0], y);
+      } else {
+        Tb = fma2(XSB[j], ux, fma2(XPB[j], dub, Tb));
+        Bb = fma2(XPB[j], y, Bb);
+      }
+    }
+    if (r < W) accA = fmaf(A.PH[r].y, Ta.x + Ta.y, fmaf(A.PS[r].y, Ba.x + Ba.y, accA));
+    accB = fmaf(PHB[r], Tb.x + Tb.y, fmaf(PSB[r], Bb.x + Bb.y, accB));
+  }
+  if (dy == 2) {  // B's last row, union row W + 1
+    const float4* pr = pwin + (W + 1) * lx;
+    const float2* yr = ywin + (W + 1) * lx;
+    float2 Tb, Bb;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const float4 p = pr[2 * j];
+      const float2 y = yr[2 * j];
+      const float2 dub = add2(f2(p.x, p.y), nub);
+      if (j == 0) {
+        Tb = fma2(XSB[0], f2(p.z, p.w), mul2(XPB[0], dub));
+        Bb = mul2(XPB[0], y);
+      } else {
+        Tb = fma2(XSB[j], f2(p.z, p.w), fma2(XPB[j], dub, Tb));
+        Bb = fma2(XPB[j], y, Bb);
+      }
+    }
+    accB = fmaf(B.PH[W - 1].y, Tb.x + Tb.y, fmaf(B.PS[W - 1].y, Bb.x + Bb.y, accB));
+  }
+  acc_a = accA;
+  acc_b = accB;
+}
+
+// Nodes (i, k) and (i, k + 1) of pattern K of (Q, W); B = (i, k + 1) is
+// stored only when store_b (it may be the boundary row ny - 1, whose
+// window the halo still covers: it lies in the tile).
+template <int Q, int W, int K, bool EXIT>
+__device__ __forceinline__ void masked_pair(const Step2D<float>& a, const MaskedTileRefs& t,
+                                            float* u_out, int i, int k, bool store_b, float fcx,
+                                            float fcy, unsigned& bad) {
+  MaskedNode<W> A, B;
+  masked_weights<Q, W, K, EXIT>(a, t, i, k, fcx, fcy, A, bad);
+  masked_weights<Q, W, K, EXIT>(a, t, i, k + 1, fcx, fcy, B, bad);
+  // (the exit terms first: the dropped weights need not stay live across the window)
+  const float ext_a = masked_exit<EXIT>(A), ext_b = masked_exit<EXIT>(B);
+  float acc_a, acc_b;
+  const int dx = B.wx - A.wx, dy = B.wy - A.wy;
+  if (dx >= -1 && dx <= 1 && dy >= 0 && dy <= 2) {
+    masked_pair_window<W>(t, A, B, acc_a, acc_b);
+  } else {
+    acc_a = masked_window<W>(t, A);
+    acc_b = masked_window<W>(t, B);
+  }
+  masked_store<W>(a, u_out, i, k, A, acc_a, ext_a);
+  if (store_b) masked_store<W>(a, u_out, i, k + 1, B, acc_b, ext_b);
+}
+
 // The rows of one tile column (one output node per thread and pass: column
-// i, rows k0 + warp + 8 m) with pattern K; a row whose points can leave the
-// box takes the exit tests.
-template <int Q, int W, int K>
+// i, rows k0 + warp + 8 m; PAIR: two nodes per thread and pass, rows
+// k0 + 2 warp + 16 m and the row after it, the tile height being even)
+// with pattern K; a row whose points can leave the box takes the exit
+// tests.
+template <int Q, int W, int K, bool PAIR>
 __device__ __forceinline__ void masked_rows(const Step2D<float>& a, const MaskedTileRefs& t,
                                             float* u_out, int i, int k0, bool xsafe, float fcx,
                                             float fcy, unsigned& bad) {
   const int warp = threadIdx.x >> 5;
+  if constexpr (PAIR) {
 #pragma unroll 1
-  for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
-    const int k = k0 + ty;
-    if (k > a.ny - 2) break;
-    if (!(xsafe && k - a.hy >= 0 && k + a.hy <= a.ny - 1))
-      masked_node<Q, W, K, true>(a, t, u_out, i, k, fcx, fcy, bad);
-    else
-      masked_node<Q, W, K, false>(a, t, u_out, i, k, fcx, fcy, bad);
+    for (int ty = 2 * warp; ty < a.ty; ty += 2 * (FK_THREADS / 32)) {
+      const int k = k0 + ty;
+      if (k > a.ny - 2) break;
+      const bool store_b = k + 1 <= a.ny - 2;
+      if (!(xsafe && k - a.hy >= 0 && k + 1 + a.hy <= a.ny - 1))
+        masked_pair<Q, W, K, true>(a, t, u_out, i, k, store_b, fcx, fcy, bad);
+      else
+        masked_pair<Q, W, K, false>(a, t, u_out, i, k, store_b, fcx, fcy, bad);
+    }
+  } else {
+#pragma unroll 1
+    for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
+      const int k = k0 + ty;
+      if (k > a.ny - 2) break;
+      if (!(xsafe && k - a.hy >= 0 && k + a.hy <= a.ny - 1))
+        masked_node<Q, W, K, true>(a, t, u_out, i, k, fcx, fcy, bad);
+      else
+        masked_node<Q, W, K, false>(a, t, u_out, i, k, fcx, fcy, bad);
+    }
   }
 }
 
 // The plan's pattern `pat` of (Q, W), taken from K upwards: one uniform
 // branch per tile, ahead of the row loop.
-template <int Q, int W, int K>
+template <int Q, int W, int K, bool PAIR>
 __device__ __forceinline__ void masked_rows_of(int pat, const Step2D<float>& a,
                                                const MaskedTileRefs& t, float* u_out, int i,
                                                int k0, bool xsafe, float fcx, float fcy,
                                                unsigned& bad) {
   if constexpr (K < fk_npat(Q, W)) {
     if (pat == K)
-      masked_rows<Q, W, K>(a, t, u_out, i, k0, xsafe, fcx, fcy, bad);
+      masked_rows<Q, W, K, PAIR>(a, t, u_out, i, k0, xsafe, fcx, fcy, bad);
     else
-      masked_rows_of<Q, W, K + 1>(pat, a, t, u_out, i, k0, xsafe, fcx, fcy, bad);
+      masked_rows_of<Q, W, K + 1, PAIR>(pat, a, t, u_out, i, k0, xsafe, fcx, fcy, bad);
   }
 }
 
 // One tile (bx, by) of one step: u_in -> u_out (and a.snap), with the
 // per-step drift factors e1, e2 of the cellular flow.  MF: u_in and u_out
-// are the field of blockIdx.z.  Sets bad when a halo range check fires.
-template <int Q, int W, bool MF>
+// are the field of blockIdx.z.  PAIR: two nodes of a column per thread
+// (odd W, even tile height).  Sets bad when a halo range check fires.
+template <int Q, int W, bool MF, bool PAIR>
 __device__ __forceinline__ void masked_tile(const Step2D<float>& a, const float* u_in,
                                             float* u_out, float e1, float e2, int bx, int by,
                                             unsigned char* smem, unsigned& bad) {
@@ -395,18 +589,19 @@ __device__ __forceinline__ void masked_tile(const Step2D<float>& a, const float*
     fcy = a.A * ct[2] + e2 * ct[3];
   }
   const MaskedTileRefs t = {QC, P, Yr, U, lx, ly, gi0, gk0};
-  masked_rows_of<Q, W, 0>(a.mpat, a, t, u_out, i, k0, xsafe, fcx, fcy, bad);
+  masked_rows_of<Q, W, 0, PAIR>(a.mpat, a, t, u_out, i, k0, xsafe, fcx, fcy, bad);
 }
 
 // MINB: CTAs of 256 threads per SM the register budget is sized for
-// (3 -> 80 registers, 2 -> 128; variant 0 and 1 of the plan).
+// (3 -> 80 registers, 2 -> 128, 4 -> 64; variants 0, 1 and 2 of the plan;
+// variant 3 is PAIR with 2).
 // MF: several fields per launch (blockIdx.z), for Algorithm 1.
-template <int Q, int W, int MINB, bool MF>
+template <int Q, int W, int MINB, bool MF, bool PAIR = false>
 __global__ void __launch_bounds__(FK_THREADS, MINB) k_step2dm(const Step2D<float> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned bad = 0;
-  masked_tile<Q, W, MF>(a, field_in<MF>(a), field_out<MF>(a), a.e1, a.e2, blockIdx.x,
-                               blockIdx.y, smem, bad);
+  masked_tile<Q, W, MF, PAIR>(a, field_in<MF>(a), field_out<MF>(a), a.e1, a.e2, blockIdx.x,
+                              blockIdx.y, smem, bad);
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
 
@@ -438,7 +633,7 @@ __device__ __forceinline__ unsigned long long global_timer_ns() {
   return t;
 }
 
-template <int Q, int W, int MINB>
+template <int Q, int W, int MINB, bool PAIR = false>
 __global__ void __launch_bounds__(FK_THREADS, MINB) k_march2dm(const Step2D<float> a,
                                                                const MaskedMarch m) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -480,7 +675,7 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_march2dm(const Step2D<floa
     const float* src = s == 1 ? m.u_first : (odd ? m.buf[0] : m.buf[1]);
     float* dst = odd ? m.buf[1] : m.buf[0];
     const float2 e = m.e12[n];  // (e1, e2) at t_n
-    masked_tile<Q, W, false>(a, src, dst, e.x, e.y, bx, by, smem, bad);
+    masked_tile<Q, W, false, PAIR>(a, src, dst, e.x, e.y, bx, by, smem, bad);
     __syncthreads();  // every store of the tile is issued
     // the release is cumulative: it publishes the stores the barrier ordered before it
     if (threadIdx.x == 0 && by * tx + bx != m.silent) st_release(m.flags + by * tx + bx, (unsigned)s);
@@ -488,22 +683,37 @@ __global__ void __launch_bounds__(FK_THREADS, MINB) k_march2dm(const Step2D<floa
   if (bad) atomicOr(a.err, FK_DEVERR_RANGE);
 }
 
-// Several fields run the 3-CTA/SM register budget whatever the variant.
-template <int Q, int W, int MINB>
+// Variant 3 (two nodes per thread, 2 CTAs/SM) is built for W = 7 only, the
+// one width where a GB300 measured it ahead of one node per thread (the
+// 1025 x 513 march: 40.2 against 40.5 ms for the best other variant).  At
+// W = 5 the extra row's multiply-adds outweigh the shared reads saved
+// (the kernel is issue-bound: 33.5 against 32.4 ms), and at W = 9 the two
+// nodes' weights no longer fit 128 registers.  The plan offers it for
+// nothing else.
+template <int W>
+constexpr bool kPairs = W == 7;
+
+// Several fields run the 3-CTA/SM register budget, or the paired form of
+// variant 3.
+template <int Q, int W, int MINB, bool PAIR>
 cudaError_t launch_m(const Step2D<float>& a, cudaStream_t s) {
   const size_t smem = fk_step2dm_smem(a.ly, a.lx);
   const int nf = a.ncols > 1 ? a.ncols : 1;
   dim3 grid((a.nx - 2 + 31) / 32, (a.ny - 2 + a.ty - 1) / a.ty, nf);
-  if (nf > 1)
-    k_step2dm<Q, W, 3, true><<<grid, FK_THREADS, smem, s>>>(a);
-  else
-    k_step2dm<Q, W, MINB, false><<<grid, FK_THREADS, smem, s>>>(a);
+  if (nf > 1) {
+    if constexpr (PAIR)
+      k_step2dm<Q, W, 2, true, true><<<grid, FK_THREADS, smem, s>>>(a);
+    else
+      k_step2dm<Q, W, 3, true><<<grid, FK_THREADS, smem, s>>>(a);
+  } else {
+    k_step2dm<Q, W, MINB, false, PAIR><<<grid, FK_THREADS, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
 // The persistent march of a single-field plan (variant 0: 3 CTAs/SM, 1: 2,
-// 2: 4); cudaErrorCooperativeLaunchTooLarge when the tiles cannot all be
-// resident at once.
+// 2: 4, 3: pairs at 2); cudaErrorCooperativeLaunchTooLarge when the tiles
+// cannot all be resident at once.
 template <int Q, int W>
 cudaError_t launch_march_m(const Step2D<float>& a, const MaskedMarch& m, cudaStream_t s) {
   const size_t smem = fk_step2dm_smem(a.ly, a.lx);
@@ -520,17 +730,23 @@ cudaError_t launch_march_m(const Step2D<float>& a, const MaskedMarch& m, cudaStr
   cfg.numAttrs = 1;
   if (a.variant == 1) return cudaLaunchKernelEx(&cfg, k_march2dm<Q, W, 2>, a, m);
   if (a.variant == 2) return cudaLaunchKernelEx(&cfg, k_march2dm<Q, W, 4>, a, m);
+  if constexpr (kPairs<W>)
+    if (a.variant == 3) return cudaLaunchKernelEx(&cfg, k_march2dm<Q, W, 2, true>, a, m);
+  if (a.variant == 3) return cudaErrorInvalidValue;
   return cudaLaunchKernelEx(&cfg, k_march2dm<Q, W, 3>, a, m);
 }
 
 // The single-field step of register-budget variant a.variant (0: 3 CTAs/SM,
-// 1: 2, 2: 4).
+// 1: 2, 2: 4, 3: pairs at 2).
 template <int Q, int W>
 cudaError_t launch_v(const Step2D<float>& a, cudaStream_t s) {
   switch (a.variant) {
-    case 1: return launch_m<Q, W, 2>(a, s);
-    case 2: return launch_m<Q, W, 4>(a, s);
-    default: return launch_m<Q, W, 3>(a, s);
+    case 1: return launch_m<Q, W, 2, false>(a, s);
+    case 2: return launch_m<Q, W, 4, false>(a, s);
+    case 3:
+      if constexpr (kPairs<W>) return launch_m<Q, W, 2, true>(a, s);
+      else return cudaErrorInvalidValue;
+    default: return launch_m<Q, W, 3, false>(a, s);
   }
 }
 
@@ -543,13 +759,17 @@ bool march_fits_m(const Step2D<float>& a) {
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return false;
-  cudaError_t e =
-      a.variant == 1   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 2>,
-                                                                       FK_THREADS, smem)
-      : a.variant == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 4>,
-                                                                       FK_THREADS, smem)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 3>,
-                                                                       FK_THREADS, smem);
+  cudaError_t e = cudaErrorInvalidValue;
+  if (a.variant == 1)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 2>, FK_THREADS, smem);
+  else if (a.variant == 2)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 4>, FK_THREADS, smem);
+  else if (a.variant == 0)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 3>, FK_THREADS, smem);
+  if constexpr (kPairs<W>)
+    if (a.variant == 3)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march2dm<Q, W, 2, true>,
+                                                        FK_THREADS, smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -557,30 +777,28 @@ bool march_fits_m(const Step2D<float>& a) {
   return (int64_t)per * sms >= tiles;
 }
 
+template <typename F>
+cudaError_t big_smem(F* f, int bytes) {
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 template <int Q, int W>
 cudaError_t attr_m() {
   const int big = 227 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_step2dm<Q, W, 3, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_step2dm<Q, W, 2, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_step2dm<Q, W, 4, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_step2dm<Q, W, 3, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   // (the persistent march keeps a word of static shared memory beside the dynamic part)
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_march2dm<Q, W, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             big - 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_march2dm<Q, W, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             big - 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_march2dm<Q, W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             big - 1024);
+  const int bigm = big - 1024;
+  cudaError_t e = big_smem(k_step2dm<Q, W, 3, false>, big);
+  if (e == cudaSuccess) e = big_smem(k_step2dm<Q, W, 2, false>, big);
+  if (e == cudaSuccess) e = big_smem(k_step2dm<Q, W, 4, false>, big);
+  if (e == cudaSuccess) e = big_smem(k_step2dm<Q, W, 3, true>, big);
+  if (e == cudaSuccess) e = big_smem(k_march2dm<Q, W, 3>, bigm);
+  if (e == cudaSuccess) e = big_smem(k_march2dm<Q, W, 2>, bigm);
+  if (e == cudaSuccess) e = big_smem(k_march2dm<Q, W, 4>, bigm);
+  if constexpr (kPairs<W>) {
+    if (e == cudaSuccess) e = big_smem(k_step2dm<Q, W, 2, false, true>, big);
+    if (e == cudaSuccess) e = big_smem(k_step2dm<Q, W, 2, true, true>, big);
+    if (e == cudaSuccess) e = big_smem(k_march2dm<Q, W, 2, true>, bigm);
+  }
   return e;
 }
 

@@ -129,7 +129,8 @@ class Plan:
                 "batch_mode": ("none", "persistent", "streams")[i.batch_mode],
                 "adjoint_kernel": ("none", "scatter", "masked")[i.adjoint_kernel],
                 "periodic_x": bool(i.periodic_x), "nonuniform": bool(i.nonuniform),
-                "march_mode": ("steps", "persistent")[i.march_mode]}
+                "march_mode": ("steps", "persistent")[i.march_mode],
+                "nodes_per_thread": i.nodes_per_thread}
 
     def _check_field(self, t: torch.Tensor, name: str):
         if t.dtype != self.dtype or t.device.type != "cuda" or tuple(t.shape) != self.shape \
