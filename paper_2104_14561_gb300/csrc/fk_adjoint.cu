@@ -759,29 +759,31 @@ __device__ __forceinline__ void harm_grad(T dl, T dr, T& gl, T& gr) {
 // node 1 (the harmonic mean is symmetric), and node n-1 that of node n-2,
 // so mu of the end nodes is added to their neighbours' and only interior
 // three-point slopes remain.
+// Every load is made, at an offset clamped into the line, before any term
+// is chosen: the ten loads are then in flight together instead of each
+// waiting behind the range test that guards it (a clamped load reads a
+// real node, and the terms it feeds are dropped by the same tests as
+// before, in the same order).
 template <typename T>
 __device__ __forceinline__ T slope_line_t(const T* u, const T* mu, int64_t s, int n, int i) {
-  auto mu_f = [&](int d) {  // mu at node i + d, end nodes folded in
+  auto off = [&](int d) { return (int64_t)(min(max(i + d, 0), n - 1) - i) * s; };
+  const T um2 = u[off(-2)], um1 = u[off(-1)], u0 = u[0], up1 = u[off(1)], up2 = u[off(2)];
+  const T mm2 = mu[off(-2)], mm1 = mu[off(-1)], m0 = mu[0], mp1 = mu[off(1)], mp2 = mu[off(2)];
+  // mu of slope m = i + d (mc), end nodes folded in (mlo: node m - 1, mhi: node m + 1)
+  auto mu_f = [&](int d, T mlo, T mc, T mhi) {
     const int m = i + d;
-    if (m < 1 || m > n - 2) return T(0);
-    T v = mu[d * s];
-    if (m == 1) v += mu[(d - 1) * s];
-    if (m == n - 2) v += mu[(d + 1) * s];
-    return v;
+    T v = mc;
+    if (m == 1) v += mlo;
+    if (m == n - 2) v += mhi;
+    return (m < 1 || m > n - 2) ? T(0) : v;
   };
   T acc = T(0), gl, gr;
-  if (i >= 2) {  // slope i-1: u_i is its right node
-    harm_grad(u[-s] - u[-2 * s], u[0] - u[-s], gl, gr);
-    acc += mu_f(-1) * gr;
-  }
-  if (i >= 1 && i <= n - 2) {  // slope i
-    harm_grad(u[0] - u[-s], u[s] - u[0], gl, gr);
-    acc += mu_f(0) * (gl - gr);
-  }
-  if (i <= n - 3) {  // slope i+1: u_i is its left node
-    harm_grad(u[s] - u[0], u[2 * s] - u[s], gl, gr);
-    acc -= mu_f(1) * gl;
-  }
+  harm_grad(um1 - um2, u0 - um1, gl, gr);  // slope i-1: u_i is its right node
+  if (i >= 2) acc += mu_f(-1, mm2, mm1, m0) * gr;
+  harm_grad(u0 - um1, up1 - u0, gl, gr);  // slope i
+  if (i >= 1 && i <= n - 2) acc += mu_f(0, mm1, m0, mp1) * (gl - gr);
+  harm_grad(up1 - u0, up2 - up1, gl, gr);  // slope i+1: u_i is its left node
+  if (i <= n - 3) acc -= mu_f(1, m0, mp1, mp2) * gl;
   return acc;
 }
 

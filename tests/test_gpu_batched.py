@@ -7,7 +7,8 @@ the instances' own graph marches on concurrent side streams.
   to 1e-6) and, for small FP64 instances, the oracle (1e-12);
 * terminal fields given per instance, including one aliased with its output;
 * the 64-instance sweep's meshes and coefficients (fewer steps) against the
-  single-plan march;
+  single-plan march, and the whole 1000-step sweep's three smallest
+  instances against the FP64 oracle (1e-5);
 * the bounded grid barrier: with a phantom CTA that never arrives every wait
   runs into its 1 s limit, the launch ends, the host reads FK_ERR_TIMEOUT,
   and the context stays usable.
@@ -140,6 +141,39 @@ def test_batched_sweep_instances(fk, batch_mode):
         worst = max(worst, (o - ref).abs().max().item())
         p.close()
     assert worst <= 1e-6
+
+
+@pytest.fixture(scope="module")
+def sweep_oracle(oracle):
+    """The FP64 oracle's full 1000-step marches of the sweep's three
+    smallest instances (279 x 140 to 311 x 156 nodes), by instance index."""
+    ws = fk_inputs.batched_instances()
+    small = sorted(range(len(ws)), key=lambda m: ws[m]["n"][0] * ws[m]["n"][1])[:3]
+    out = {}
+    for m in small:
+        w = ws[m]
+        g = oracle.Grid(w["n"], w["lo"], w["hi"])
+        out[m] = oracle.march(g, 1, list(w["params"]), w["q"], w["dt"], w["n_steps"], 0,
+                              nthreads=NCPU)
+    return out
+
+
+def test_batched_sweep_full_march_vs_oracle(fk, sweep_oracle, batch_mode):
+    """The 64-instance sweep itself (1000 FP32 steps, every instance in one
+    batched call): its three smallest instances against the FP64 oracle's
+    whole marches, max-abs 1e-5 over every node."""
+    import torch
+    ws = fk_inputs.batched_instances()
+    plans = [_plan(fk, w) for w in ws]
+    outs = fk.solve_batched(plans)
+    torch.cuda.synchronize()
+    assert plans[0].info()["batch_mode"] == batch_mode
+    assert all(p.last_device_error() == 0 for p in plans)
+    for m, want in sweep_oracle.items():
+        err = np.abs(outs[m].double().cpu().numpy() - want).max()
+        assert err <= 1e-5, (m, ws[m]["n"], err)
+    for p in plans:
+        p.close()
 
 
 def test_barrier_timeout_is_reported(fk, monkeypatch):
