@@ -278,6 +278,29 @@ fk_status fk_solve(fk_plan *plan, const void *u_terminal, void *u_out,
                    void *snapshots, int snapshot_stride, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * fk_solve_host -- fk_solve (Scheme 1, Sec. 3.1.5) with the fields in host
+ * memory: copies u^N to the device, runs the march, copies u^0 back, all
+ * enqueued on `stream` in that order.
+ *   u_terminal_host  host pointer to u^N (J values of the plan's precision,
+ *                    laid out as fk_solve's fields), or NULL for the
+ *                    terminal indicator chi.  Read only.
+ *   u_out_host       host pointer, receives u^0 (J values).  May equal
+ *                    u_terminal_host.
+ *   stream           CUDA stream.  The call returns once the work is
+ *                    enqueued: u_out_host holds u^0 when the stream has
+ *                    passed it (cudaStreamSynchronize).  With page-locked
+ *                    buffers (cudaHostAlloc, cudaHostRegister) the copies
+ *                    are asynchronous; pageable buffers are staged by the
+ *                    CUDA driver and can block the calling thread.
+ * The device copy of the field is one plan-owned buffer of J values,
+ * allocated on the first call (FK_ERR_OOM if that fails; counted in
+ * workspace_bytes) and freed with the plan.  Calls on one plan whose work
+ * overlaps on the GPU share that buffer and race.
+ * ---------------------------------------------------------------------- */
+fk_status fk_solve_host(fk_plan *plan, const void *u_terminal_host, void *u_out_host,
+                        cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * fk_march -- the steps n = n_from-1, ..., n_to of Scheme 1 only:
  * u_out <- u^{n_to} given u_in = u^{n_from}, 0 <= n_to <= n_from <= N.
  * The march is Markov in (n, u^n), so this is also checkpoint / resume.

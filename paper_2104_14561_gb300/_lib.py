@@ -24,7 +24,8 @@ FK_PERIODIC_X = 0x3C
 
 # every symbol include/fk.h declares
 EXPORTS = ("fk_plan_create", "fk_plan_destroy", "fk_plan_get_info", "fk_gauss_hermite",
-           "fk_solve", "fk_march", "fk_solve_horizons", "fk_solve_batched", "fk_adjoint",
+           "fk_solve", "fk_solve_host", "fk_march", "fk_solve_horizons", "fk_solve_batched",
+           "fk_adjoint",
            "fk_status_string", "fk_last_device_error", "fk_solve_static",
            "fk_static_last_device_error", "fk_runaway_quench_params", "fk_measure_fma_rate",
            "fk_adjoint_kernel_times")
@@ -97,6 +98,8 @@ def load(build_if_missing: bool = False):
     lib.fk_runaway_quench_params.restype = st
     lib.fk_solve.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp]
     lib.fk_solve.restype = st
+    lib.fk_solve_host.argtypes = [vp, vp, vp, vp]
+    lib.fk_solve_host.restype = st
     lib.fk_march.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     lib.fk_march.restype = st
     lib.fk_solve_horizons.argtypes = [vp, vp, vp, vp]

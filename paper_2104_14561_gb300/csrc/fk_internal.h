@@ -388,6 +388,8 @@ struct fk_plan {
   void* rec3d;
   void* coef3d;      // the static runaway model's per-node coefficients (6 J values)
   int w3;
+  // fk_solve_host: the device copy of the host field (one field, on first use)
+  void* host_io;
   // fk_solve_horizons: the second buffer of the N horizon fields
   void* hz_ws;
   int64_t hz_bytes;

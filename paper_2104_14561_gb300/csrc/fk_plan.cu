@@ -1518,6 +1518,7 @@ fk_status fk_plan_destroy(fk_plan* p) {
   fk_dev_free(p->stack);
   fk_dev_free(p->batch_rec);
   fk_dev_free(p->hz_ws);
+  fk_dev_free(p->host_io);
   for (int m = 0; m < 3; ++m) {
     fk_dev_free(p->dcoord[m]);
     fk_dev_free(p->dcoord64[m]);
@@ -1611,6 +1612,29 @@ fk_status fk_solve(fk_plan* p, const void* u_terminal, void* u_out, void* snapsh
     p->g_persist = pers;
   }
   return cuda_status(cudaGraphLaunch(p->graph, stream));
+}
+
+fk_status fk_solve_host(fk_plan* p, const void* u_terminal_host, void* u_out_host,
+                        cudaStream_t stream) {
+  FkRange range("fk_solve_host");
+  if (!p || !u_out_host) return FK_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)(p->J * p->elem);
+  if (!p->host_io) {
+    fk_status st = fk_dev_alloc(p, &p->host_io, bytes);
+    if (st != FK_OK) return st;
+  }
+  if (u_terminal_host &&
+      cudaMemcpyAsync(p->host_io, u_terminal_host, bytes, cudaMemcpyHostToDevice, stream) !=
+          cudaSuccess)
+    return FK_ERR_CUDA;
+  // (in place on the device: fk_solve's march reads u^N before it writes u_out)
+  fk_status st =
+      fk_solve(p, u_terminal_host ? p->host_io : nullptr, p->host_io, nullptr, 0, stream);
+  if (st != FK_OK) return st;
+  if (cudaMemcpyAsync(u_out_host, p->host_io, bytes, cudaMemcpyDeviceToHost, stream) !=
+      cudaSuccess)
+    return FK_ERR_CUDA;
+  return FK_OK;
 }
 
 // Algorithm 1 (Sec. 3.2).  Field c (1-based) starts in buffer c mod 2 (odd:

@@ -161,6 +161,26 @@ class Plan:
                                                _stream(stream)))
         return out
 
+    def solve_host(self, u_terminal: torch.Tensor | None, out: torch.Tensor,
+                   stream=None) -> torch.Tensor:
+        """fk_solve_host: u^0 of Scheme 1 with the terminal field and the
+        result in host memory (CPU tensors; pinned ones keep the copies
+        asynchronous).  The copies and the march are enqueued on the stream:
+        out holds u^0 once the stream has passed them."""
+        for name, t in (("u_terminal", u_terminal), ("out", out)):
+            if t is None:
+                continue
+            if t.dtype != self.dtype or t.device.type != "cpu" or \
+                    tuple(t.shape) != self.shape or not t.is_contiguous():
+                raise ValueError(f"{name}: expected a contiguous {self.dtype} CPU tensor of "
+                                 f"shape {self.shape}, got {t.dtype} {tuple(t.shape)} on "
+                                 f"{t.device}")
+        if out is None:
+            raise ValueError("out: a host tensor is required")
+        L.check("fk_solve_host", self._lib.fk_solve_host(self._h, _ptr(u_terminal), _ptr(out),
+                                                         _stream(stream)))
+        return out
+
     def march(self, n_from: int, n_to: int, u_in: torch.Tensor,
               out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Steps n_from-1 .. n_to (resume from a checkpoint u^{n_from})."""

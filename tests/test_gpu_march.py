@@ -266,6 +266,41 @@ def test_in_place_terminal(fk, n_steps):
     plan.close()
 
 
+@pytest.mark.parametrize("precision,pinned", [("fp32", True), ("fp64", False)])
+def test_solve_host_buffers(fk, precision, pinned):
+    """fk_solve_host (fields in host memory, copies and march enqueued on
+    the stream) equals fk_solve on device buffers bit for bit: from chi, from
+    a terminal field, in place, and twice in a row on the same plan; pinned
+    and pageable host buffers."""
+    import torch
+    w = _small2d(6, precision, n_steps=30, n=(161, 81))
+    plan = fk.Plan(_spec(fk, w))
+    u0 = torch.tensor(fk_inputs.random_field(plan.shape, seed=5), dtype=plan.dtype)
+    ref_chi = plan.solve().cpu()
+    ref_u0 = plan.solve(u0.cuda()).cpu()
+    torch.cuda.synchronize()
+
+    def host(t):
+        return t.pin_memory() if pinned else t
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        out = host(torch.full(plan.shape, float("nan"), dtype=plan.dtype))
+        plan.solve_host(None, out, stream=stream)
+        stream.synchronize()
+        assert torch.equal(out, ref_chi)
+        out = host(torch.full(plan.shape, float("nan"), dtype=plan.dtype))
+        plan.solve_host(host(u0.clone()), out, stream=stream)
+        stream.synchronize()
+        assert torch.equal(out, ref_u0)
+        buf = host(u0.clone())
+        plan.solve_host(buf, buf, stream=stream)
+        stream.synchronize()
+        assert torch.equal(buf, ref_u0)
+    assert plan.last_device_error() == 0
+    assert plan.info()["workspace_bytes"] > 0
+    plan.close()
+
+
 @pytest.mark.parametrize("n,q,params", [
     ((3, 3), 3, (1.0, 0.2, 2 * math.pi, 0.01)),
     ((4, 3), 2, (1.0, 0.2, 2 * math.pi, 0.01)),
