@@ -1133,8 +1133,8 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
         cudaSuccess)
       return FK_ERR_CUDA;
   }
-  // workspace: checkpoints (M+1), a segment (K), lambda x2, mu (2 x 3 fields), dtheta
-  const int64_t need = (int64_t)(M + 1 + K + 2 + 6) * fb + 64;
+  // workspace: checkpoints (M+1), two segments (2K), lambda x2, mu (2 x 3 fields), dtheta
+  const int64_t need = (int64_t)(M + 1 + 2 * K + 2 + 6) * fb + 64;
   if (p->adj_bytes < need) {
     if (cudaStreamSynchronize(s) != cudaSuccess) return FK_ERR_CUDA;
     fk_dev_free(p->adj_ws);
@@ -1146,10 +1146,11 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
   }
   char* base = (char*)p->adj_ws;
   auto ckpt = [&](int m) { return (void*)(base + (int64_t)m * fb); };
-  char* seg = base + (int64_t)(M + 1) * fb;
-  void* lam[2] = {seg + (int64_t)K * fb, seg + (int64_t)(K + 1) * fb};
-  p->adj_mu = seg + (int64_t)(K + 2) * fb;
-  double* dth = dtheta ? dtheta : (double*)(seg + (int64_t)(K + 8) * fb);
+  char* seg = base + (int64_t)(M + 1) * fb;  // segment buffers 0 and 1, K fields each
+  char* rest = seg + (int64_t)(2 * K) * fb;
+  void* lam[2] = {rest, rest + fb};
+  p->adj_mu = rest + 2 * fb;
+  double* dth = dtheta ? dtheta : (double*)(rest + (int64_t)8 * fb);
   auto slot = [&](int n) { return n == N ? M : n / K; };  // n == N or n % K == 0
 
   // forward pass with checkpoints
@@ -1194,25 +1195,72 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
       ++p->adj_ev_cap;
     }
   }
+  // The recompute of a segment depends only on its checkpoint, so it runs
+  // on the plan's second stream, one segment ahead of the backward steps
+  // on s, into the other of two segment buffers: the forward steps and the
+  // backward kernels, which are bound by different units, share the SMs.
+  // Events order it: segment m + 1 is recomputed after the forward pass and
+  // after segment m - 1's backward steps have read that buffer; segment m's
+  // backward steps start after its recompute.  (Without the stream or the
+  // events, everything runs on s, one segment after the other.)
+  if (!p->adj_s2 && cudaStreamCreateWithFlags(&p->adj_s2, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    p->adj_s2 = nullptr;
+  }
+  while (p->adj_s2 && p->adj_sev_n < 5) {
+    if (cudaEventCreateWithFlags(&p->adj_sev[p->adj_sev_n], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    ++p->adj_sev_n;
+  }
+  const bool two = p->adj_s2 && p->adj_sev_n == 5;
+  cudaStream_t rs = two ? p->adj_s2 : s;  // the recompute's stream
+  cudaEvent_t* ev_rec = p->adj_sev + 1;     // per buffer: recomputed
+  cudaEvent_t* ev_bwd = p->adj_sev + 3;     // per buffer: backward steps done
+  if (two && (cudaEventRecord(p->adj_sev[0], s) != cudaSuccess ||
+              cudaStreamWaitEvent(rs, p->adj_sev[0], 0) != cudaSuccess))
+    return FK_ERR_CUDA;
+  auto segbuf = [&](int m) { return seg + (int64_t)(m & 1) * K * fb; };
+  // recompute u^{top-1} .. u^{lo+1} of segment m into its buffer
+  auto recompute = [&](int m) -> fk_status {
+    const int lo = m * K, top = (m + 1) * K < N ? (m + 1) * K : N;
+    if (two && m >= 2 && cudaStreamWaitEvent(rs, ev_bwd[m & 1], 0) != cudaSuccess)
+      return FK_ERR_CUDA;
+    const void* src = ckpt(slot(top));
+    for (int n = top - 1; n >= lo + 1; --n) {
+      void* dst = segbuf(m) + (int64_t)(n - lo - 1) * fb;
+      fk_status st = fk_enqueue_step(p, n, src, dst, nullptr, rs);
+      if (st != FK_OK) return st;
+      src = dst;
+    }
+    if (two && cudaEventRecord(ev_rec[m & 1], rs) != cudaSuccess) return FK_ERR_CUDA;
+    return FK_OK;
+  };
   // backward over segments [mK, top)
+  fk_status rst = recompute(0);
+  if (rst != FK_OK) return rst;
   for (int m = 0; m < M; ++m) {
     FkRange seg_range("fk_adjoint segment");
     const int lo = m * K, top = (m + 1) * K < N ? (m + 1) * K : N;
-    // recompute u^{top-1} .. u^{lo+1} into the segment buffer
-    const void* s2 = ckpt(slot(top));
-    for (int n = top - 1; n >= lo + 1; --n) {
-      void* dst = seg + (int64_t)(n - lo - 1) * fb;
-      fk_status st = fk_enqueue_step(p, n, s2, dst, nullptr, s);
-      if (st != FK_OK) return st;
-      s2 = dst;
+    if (two && m + 1 < M) {
+      rst = recompute(m + 1);
+      if (rst != FK_OK) return rst;
     }
+    if (two && cudaStreamWaitEvent(s, ev_rec[m & 1], 0) != cudaSuccess) return FK_ERR_CUDA;
     for (int n = lo; n < top; ++n) {
-      const void* u_in = (n + 1 == top) ? ckpt(slot(top)) : (const void*)(seg + (int64_t)(n - lo) * fb);
+      const void* u_in = (n + 1 == top) ? ckpt(slot(top))
+                                        : (const void*)(segbuf(m) + (int64_t)(n - lo) * fb);
       fk_status st = p->prec == FK_FP32
                          ? adj_step<float>(p, n, u_in, lam[cur], lam[cur ^ 1], dth, ty, s)
                          : adj_step<double>(p, n, u_in, lam[cur], lam[cur ^ 1], dth, ty, s);
       if (st != FK_OK) return st;
       cur ^= 1;
+    }
+    if (two && cudaEventRecord(ev_bwd[m & 1], s) != cudaSuccess) return FK_ERR_CUDA;
+    if (!two && m + 1 < M) {
+      rst = recompute(m + 1);
+      if (rst != FK_OK) return rst;
     }
   }
   if (du_terminal && fk_launch_copy(du_terminal, lam[cur], fb, s) != cudaSuccess) return FK_ERR_CUDA;

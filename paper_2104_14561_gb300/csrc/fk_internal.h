@@ -408,6 +408,12 @@ struct fk_plan {
   cudaEvent_t* adj_ev;
   int adj_ev_cap;     // events created
   int adj_ev_used;    // events recorded by the last fk_adjoint
+  // the segment recompute runs on its own stream (created on first use),
+  // ordered by events: forward pass done, segment recomputed (per buffer),
+  // segment's backward steps done (per buffer)
+  cudaStream_t adj_s2;
+  cudaEvent_t adj_sev[5];
+  int adj_sev_n;      // events of adj_sev created
 };
 
 void fk_batch_release(fk_plan* p);

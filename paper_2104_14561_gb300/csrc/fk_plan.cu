@@ -1530,6 +1530,8 @@ fk_status fk_plan_destroy(fk_plan* p) {
   fk_dev_free(p->me12);
   for (int i = 0; i < p->adj_ev_cap; ++i) cudaEventDestroy(p->adj_ev[i]);
   free(p->adj_ev);
+  for (int i = 0; i < p->adj_sev_n; ++i) cudaEventDestroy(p->adj_sev[i]);
+  if (p->adj_s2) cudaStreamDestroy(p->adj_s2);
   fk_batch_release(p);
   delete p;
   return FK_OK;
