@@ -76,15 +76,16 @@ def measure_alu_peaks(fk, stream, local_rank: int) -> dict:
 
 
 def csr_bytes_per_step(w, nnz: int) -> float:
-    """Algorithmic HBM bytes of one CSR step: the matrix stream (column index
-    + value per stored entry), row offsets, exit constants, the stacked
-    vector [u; h u_x; h u_y] written by the slope pass and read once, u^{n+1}
-    read and u^n written."""
+    """Algorithmic HBM bytes of one CSR step: the matrix stream (one record
+    of 16 B in FP32, 32 B in FP64, per three stored entries: a node and its
+    u, h u_x and h u_y weights), row offsets, exit constants, u^{n+1} read
+    by the slope pass, the interleaved {u, h u_x, h u_y, 0} written by it and
+    read once, and u^n written."""
     J = 1
     for n in w["n"]:
         J *= n
     e = 4 if w["precision"] == "fp32" else 8
-    return nnz * (4 + e) + 8.0 * (J + 1) + e * J * (1 + 3 + 3 + 1 + 1)
+    return (nnz // 3) * 4 * e + 8.0 * (J + 1) + e * J * (1 + 1 + 4 + 4 + 1)
 
 
 def parse():

@@ -20,6 +20,13 @@
 // The product is evaluated in increment form, u_j + sum A (X - u_j [u part])
 // + c_j (1 - u_j), which equals A X + c exactly (the u-part of each row sums
 // to 1 - c_j) but keeps FP32 rounding proportional to the per-step change.
+//
+// Storage: the three entries of a row that share a node ab (its u, h u_x and
+// h u_y columns) are one record {column ab, A[j, u_ab], A[j, hu_x,ab],
+// A[j, hu_y,ab]}: 16 B in FP32 (32 B in FP64) per three stored entries,
+// instead of a 4 B column index beside every value, and one aligned vector
+// load.  X is stored interleaved per node, {u, h u_x, h u_y, 0}, so that a
+// record needs one gather.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -114,12 +121,27 @@ __global__ void k_csr_count(const CsrAsm a, int64_t* counts) {
   AxisW ax, ay;
   axis_weights(a, 0, i, a.nx, dx, &ax);
   axis_weights(a, 1, k, a.ny, dy, &ay);
-  const int64_t nnz = 3 * (int64_t)ax.n * ay.n;
-  counts[j] = (nnz + 3) & ~(int64_t)3;  // rows padded to 4 entries (16 B vector loads)
+  counts[j] = (int64_t)ax.n * ay.n;  // records (three stored entries each)
 }
 
+// One record of a row: the column (a node index) and the weights of the
+// node's u, h u_x and h u_y.  FP32: 16 B; FP64: 32 B (the column in the
+// first 8 B).
 template <typename T>
-__global__ void k_csr_fill(const CsrAsm a, const int64_t* rowptr, int* col, T* val, T* cvec,
+struct CsrRec;
+template <>
+struct alignas(16) CsrRec<float> {
+  int col;
+  float vu, vx, vy;
+};
+template <>
+struct alignas(16) CsrRec<double> {
+  int col, pad;
+  double vu, vx, vy;
+};
+
+template <typename T>
+__global__ void k_csr_fill(const CsrAsm a, const int64_t* rowptr, CsrRec<T>* rec, T* cvec,
                            unsigned* err) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= a.J) return;
@@ -136,30 +158,21 @@ __global__ void k_csr_fill(const CsrAsm a, const int64_t* rowptr, int* col, T* v
   cvec[j] = (T)(1.0 - ax.inside * ay.inside);
   int64_t o = rowptr[j];
   const int64_t end = rowptr[j + 1];
-  for (int f = 0; f < 3; ++f) {
-    for (int mb = 0; mb < ay.n; ++mb) {
-      const int64_t rowoff = (int64_t)f * a.J + (int64_t)ay.node[mb] * a.nx;
-      for (int ma = 0; ma < ax.n; ++ma) {
-        double v;
-        if (f == 0)
-          v = ax.phi[ma] * ay.phi[mb];
-        else if (f == 1)
-          v = ax.psi[ma] * ay.phi[mb];
-        else
-          v = ax.phi[ma] * ay.psi[mb];
-        if (o >= end) {  // the count pass disagreed: never write past the row
-          atomicOr(err, FK_DEVERR_RANGE);
-          return;
-        }
-        col[o] = (int)(rowoff + ax.node[ma]);
-        val[o] = (T)v;
-        ++o;
+  for (int mb = 0; mb < ay.n; ++mb) {
+    for (int ma = 0; ma < ax.n; ++ma) {
+      if (o >= end) {  // the count pass disagreed: never write past the row
+        atomicOr(err, FK_DEVERR_RANGE);
+        return;
       }
+      CsrRec<T> r;
+      memset(&r, 0, sizeof(r));
+      r.col = (int)((int64_t)ay.node[mb] * a.nx + ax.node[ma]);
+      r.vu = (T)(ax.phi[ma] * ay.phi[mb]);
+      r.vx = (T)(ax.psi[ma] * ay.phi[mb]);
+      r.vy = (T)(ax.phi[ma] * ay.psi[mb]);
+      rec[o] = r;
+      ++o;
     }
-  }
-  for (; o < end; ++o) {  // padding: a zero weight on the row's own node
-    col[o] = (int)j;
-    val[o] = T(0);
   }
 }
 
@@ -169,14 +182,27 @@ __device__ __forceinline__ T pchip_exact(T dl, T dr) {
   return p > T(0) ? (T(2) * p) / (dl + dr) : T(0);
 }
 
-// F^n: X = [u; h u_x; h u_y] with the PCHIP rule of Eq. (e300) and its end
-// rule (node 0: (delta_0, delta_1); node n-1: (delta_{n-2}, delta_{n-3})).
 template <typename T>
-__global__ void k_csr_slopes(const T* __restrict__ u, T* __restrict__ X, int nx, int ny) {
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using type = float4;
+};
+template <>
+struct Vec4<double> {
+  using type = double4_16a;
+};
+
+// F^n: X = [u; h u_x; h u_y] with the PCHIP rule of Eq. (e300) and its end
+// rule (node 0: (delta_0, delta_1); node n-1: (delta_{n-2}, delta_{n-3})),
+// interleaved per node as {u, h u_x, h u_y, 0}.
+template <typename T>
+__global__ void k_csr_slopes(const T* __restrict__ u, typename Vec4<T>::type* __restrict__ X,
+                             int nx, int ny) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || k >= ny) return;
-  const int64_t J = (int64_t)nx * ny, j = (int64_t)k * nx + i;
+  const int64_t j = (int64_t)k * nx + i;
   const T* r = u + (int64_t)k * nx;
   T sx, sy;
   if (i == 0)
@@ -193,44 +219,48 @@ __global__ void k_csr_slopes(const T* __restrict__ u, T* __restrict__ X, int nx,
     sy = pchip_exact(c[(ny - 1) * s] - c[(ny - 2) * s], c[(ny - 2) * s] - c[(ny - 3) * s]);
   else
     sy = pchip_exact(c[k * s] - c[(k - 1) * s], c[(k + 1) * s] - c[k * s]);
-  X[j] = r[i];
-  X[J + j] = sx;
-  X[2 * J + j] = sy;
+  typename Vec4<T>::type x;
+  x.x = r[i];
+  x.y = sx;
+  x.z = sy;
+  x.w = T(0);
+  X[j] = x;
 }
 
-template <typename T>
-struct Vec4;
-template <>
-struct Vec4<float> {
-  using type = float4;
-};
-template <>
-struct Vec4<double> {
-  using type = double4_16a;
-};
-
-// One warp per row; each lane reads 4 consecutive entries per pass with
-// 16-byte column loads (rows are padded to multiples of 4 and start aligned).
+// One warp per row; each lane takes four records per pass (128 per warp,
+// about a whole row), all four record loads and then all four gathers of
+// their nodes from X in flight together: a record's gather depends on its
+// load, so one record per pass left each lane one L2 round trip at a time.
 template <typename T>
 __global__ void __launch_bounds__(256) k_csr_spmv(const int64_t* __restrict__ rowptr,
-                                                  const int* __restrict__ col,
-                                                  const T* __restrict__ val,
+                                                  const CsrRec<T>* __restrict__ rec,
                                                   const T* __restrict__ cvec,
-                                                  const T* __restrict__ X, T* __restrict__ y,
-                                                  T* __restrict__ snap, int64_t J) {
+                                                  const typename Vec4<T>::type* __restrict__ X,
+                                                  T* __restrict__ y, T* __restrict__ snap,
+                                                  int64_t J) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (row >= J) return;
   const int64_t b = rowptr[row], e = rowptr[row + 1];
-  const T uj = X[row];
+  const T uj = X[row].x;
   T acc = T(0);
-  for (int64_t o = b + 4 * lane; o < e; o += 128) {
-    const int4 c4 = *reinterpret_cast<const int4*>(col + o);
-    const typename Vec4<T>::type v4 = *reinterpret_cast<const typename Vec4<T>::type*>(val + o);
-    acc += v4.x * (X[c4.x] - (c4.x < J ? uj : T(0)));
-    acc += v4.y * (X[c4.y] - (c4.y < J ? uj : T(0)));
-    acc += v4.z * (X[c4.z] - (c4.z < J ? uj : T(0)));
-    acc += v4.w * (X[c4.w] - (c4.w < J ? uj : T(0)));
+  for (int64_t o0 = b + lane; o0 < e; o0 += 128) {
+    CsrRec<T> r[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int64_t o = o0 + 32 * m;
+      if (o < e) {
+        r[m] = rec[o];
+      } else {  // (a zero weight on the row's own node)
+        r[m].col = (int)row;
+        r[m].vu = r[m].vx = r[m].vy = T(0);
+      }
+    }
+    typename Vec4<T>::type x[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) x[m] = X[r[m].col];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc += r[m].vu * (x[m].x - uj) + r[m].vx * x[m].y + r[m].vy * x[m].z;
   }
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
@@ -296,21 +326,20 @@ fk_status fk_csr_assemble(fk_plan* p, cudaStream_t s) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? FK_ERR_OOM : FK_ERR_CUDA;
   }
-  if (3 * J >= ((int64_t)1 << 31)) return FK_ERR_UNSUPPORTED;  // int32 column indices
-  p->csr_nnz = nnz;
-  st = fk_dev_alloc(p, (void**)&p->csr_col, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
-  if (st == FK_OK) st = fk_dev_alloc(p, &p->csr_val, (size_t)p->elem * (nnz > 0 ? nnz : 1));
+  if (J >= ((int64_t)1 << 31)) return FK_ERR_UNSUPPORTED;  // int32 node indices
+  const int64_t nrec = nnz;  // (the scan counted records)
+  p->csr_nnz = 3 * nrec;     // stored entries of A: three per record
+  const size_t rec_bytes = p->prec == FK_FP32 ? sizeof(CsrRec<float>) : sizeof(CsrRec<double>);
+  st = fk_dev_alloc(p, &p->csr_val, rec_bytes * (size_t)(nrec > 0 ? nrec : 1));
   if (st == FK_OK) st = fk_dev_alloc(p, &p->csr_c, (size_t)p->elem * J);
-  if (st == FK_OK) st = fk_dev_alloc(p, &p->stack, (size_t)p->elem * 3 * J);
+  if (st == FK_OK) st = fk_dev_alloc(p, &p->stack, (size_t)p->elem * 4 * J);
   if (st != FK_OK) return st;
   if (p->prec == FK_FP32)
-    k_csr_fill<float><<<(unsigned)((J + tb - 1) / tb), tb, 0, s>>>(a, p->csr_rowptr, p->csr_col,
-                                                                  (float*)p->csr_val,
-                                                                  (float*)p->csr_c, p->d_err);
+    k_csr_fill<float><<<(unsigned)((J + tb - 1) / tb), tb, 0, s>>>(
+        a, p->csr_rowptr, (CsrRec<float>*)p->csr_val, (float*)p->csr_c, p->d_err);
   else
-    k_csr_fill<double><<<(unsigned)((J + tb - 1) / tb), tb, 0, s>>>(a, p->csr_rowptr, p->csr_col,
-                                                                   (double*)p->csr_val,
-                                                                   (double*)p->csr_c, p->d_err);
+    k_csr_fill<double><<<(unsigned)((J + tb - 1) / tb), tb, 0, s>>>(
+        a, p->csr_rowptr, (CsrRec<double>*)p->csr_val, (double*)p->csr_c, p->d_err);
   e = cudaGetLastError();
   return e == cudaSuccess ? FK_OK : FK_ERR_CUDA;
 }
@@ -321,15 +350,15 @@ fk_status fk_csr_step(fk_plan* p, const void* u_in, void* u_out, void* snap, cud
   const int64_t J = p->J;
   const unsigned blocks = (unsigned)((J * 32 + 255) / 256);
   if (p->prec == FK_FP32) {
-    k_csr_slopes<float><<<sg, sb, 0, s>>>((const float*)u_in, (float*)p->stack, nx, ny);
-    k_csr_spmv<float><<<blocks, 256, 0, s>>>(p->csr_rowptr, p->csr_col, (const float*)p->csr_val,
-                                             (const float*)p->csr_c, (const float*)p->stack,
+    k_csr_slopes<float><<<sg, sb, 0, s>>>((const float*)u_in, (float4*)p->stack, nx, ny);
+    k_csr_spmv<float><<<blocks, 256, 0, s>>>(p->csr_rowptr, (const CsrRec<float>*)p->csr_val,
+                                             (const float*)p->csr_c, (const float4*)p->stack,
                                              (float*)u_out, (float*)snap, J);
   } else {
-    k_csr_slopes<double><<<sg, sb, 0, s>>>((const double*)u_in, (double*)p->stack, nx, ny);
-    k_csr_spmv<double><<<blocks, 256, 0, s>>>(p->csr_rowptr, p->csr_col,
-                                              (const double*)p->csr_val, (const double*)p->csr_c,
-                                              (const double*)p->stack, (double*)u_out,
+    k_csr_slopes<double><<<sg, sb, 0, s>>>((const double*)u_in, (double4_16a*)p->stack, nx, ny);
+    k_csr_spmv<double><<<blocks, 256, 0, s>>>(p->csr_rowptr, (const CsrRec<double>*)p->csr_val,
+                                              (const double*)p->csr_c,
+                                              (const double4_16a*)p->stack, (double*)u_out,
                                               (double*)snap, J);
   }
   return cudaGetLastError() == cudaSuccess ? FK_OK : FK_ERR_CUDA;

@@ -369,12 +369,11 @@ struct fk_plan {
   void* g_snap;
   int g_stride;
   // CSR path (fk_csr.cu)
-  int64_t csr_nnz;
-  int64_t* csr_rowptr;  // J + 1 row offsets, multiples of 4
-  int* csr_col;      // nnz, column in the stacked vector [u; Dx; Dy]
-  void* csr_val;     // nnz
+  int64_t csr_nnz;       // stored entries of A = Q Psi: three per record
+  int64_t* csr_rowptr;  // J + 1 row offsets, in records
+  void* csr_val;     // csr_nnz / 3 records {node, weights of u, h u_x, h u_y}
   void* csr_c;       // J: exit weight constant per row
-  void* stack;       // 3 J: [u; Dx; Dy] for the CSR product
+  void* stack;       // 4 J: {u, h u_x, h u_y, 0} per node for the CSR product
   // batched persistent march (fk_batched.cu)
   void* batch_rec;   // 6 J values: slope records of this instance
   void* batch_work;  // BatchWork of a batch whose first plan is this one

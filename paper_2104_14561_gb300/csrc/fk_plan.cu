@@ -1512,7 +1512,6 @@ fk_status fk_plan_destroy(fk_plan* p) {
   fk_dev_free(p->row_tab);
   fk_dev_free(p->d_err);
   fk_dev_free(p->csr_rowptr);
-  fk_dev_free(p->csr_col);
   fk_dev_free(p->csr_val);
   fk_dev_free(p->csr_c);
   fk_dev_free(p->stack);
