@@ -716,7 +716,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         achieved = bytes_step / (launch_ms * 1e-3) / 1e9
         roofline = {"kernel": "k_csr_slopes + k_csr_spmv (one time step)", "bound": "hbm",
                     "achieved": achieved, "peak": peak, "peak_source": peak_kind,
-                    "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                    "unit": "GB/s", "frac": achieved / peak,
+                    # (the SpMV's DRAM bytes, the dominant kernel's, from its summary,
+                    # which covers the workload's own mesh only)
+                    "traffic": (None if args.grid else
+                                profile_traffic("k_csr_spmv", args.workload)),
                     "bytes_per_launch": bytes_step, "launch_ms": launch_ms,
                     "csr_nnz": info["csr_nnz"]}
     elif len(w["n"]) == 3:
