@@ -36,8 +36,16 @@ namespace {
 template <typename T>
 struct AdjArgs {
   Step2D<T> s;      // u_in = u^{n+1}; staging and drift as in the forward step
-  const T* lam;     // lambda^n
+  const T* lam;     // lambda^n, or nullptr: the masked kernel forms it (below)
   T* mu;            // 3 J accumulators (zero on entry): [u; h u_x; h u_y] parts
+  // lam == nullptr (masked form): lambda^n at the tile's nodes is the
+  // slope transpose of the previous backward step's accumulators mu_prev
+  // over u_prev, the field whose slopes that step took; the kernel also
+  // zeroes mu_clear at its nodes (and the boundary nodes next to them),
+  // the accumulators of the step after this one
+  const T* mu_prev;
+  const T* u_prev;
+  T* mu_clear;
   double* dth;      // 4 parameter derivatives (accumulated)
   // d(shift in cells)/d theta_k = ax_k + cn_k g (x) and ay_k + cn_k g (y):
   // cellular flow: ax_A = kx cy sx1, ax_eps = kx cy st sx2, ax_om = kx cy sw sx2
@@ -477,6 +485,93 @@ __device__ __forceinline__ AxisPos axis_pos(float d, float g0, int node, int n, 
   return P;
 }
 
+// Gradient of the slope rule H(dl, dr) = 2 dl dr / (dl + dr) (dl dr > 0,
+// else 0) of Eq. (e300): dH/d dl = 2 (dr / (dl + dr))^2 and
+// dH/d dr = 2 (dl / (dl + dr))^2, 0 on the zero branch.  Formed from the
+// ratios, which lie in [0, 1]: differences near the bottom of the exponent
+// range (a march from the indicator leaves such values far from the
+// boundary) would overflow 1 / (dl + dr)^2.
+template <typename T>
+__device__ __forceinline__ void harm_grad(T dl, T dr, T& gl, T& gr) {
+  if (dl * dr > T(0)) {
+    const T ql = dl / (dl + dr), qr = T(1) - ql;  // dr / (dl + dr)
+    gl = T(2) * qr * qr;
+    gr = T(2) * ql * ql;
+  } else {
+    gl = T(0);
+    gr = T(0);
+  }
+}
+
+// Transposed slope map along one grid line, at node i of n (u and mu point
+// at node i, s is the stride between neighbours): the sum over the slopes
+// m = i-1, i, i+1 that read u_i of mu_m dH_m/du_i, where slope m reads
+// dl = u_m - u_{m-1} and dr = u_{m+1} - u_m.  The end rule stated after
+// Eq. (e300) makes the slope of node 0 the same function of u as that of
+// node 1 (the harmonic mean is symmetric), and node n-1 that of node n-2,
+// so mu of the end nodes is added to their neighbours' and only interior
+// three-point slopes remain.
+// Every load is made, at an offset clamped into the line, before any term
+// is chosen: the ten loads are then in flight together instead of each
+// waiting behind the range test that guards it (a clamped load reads a
+// real node, and the terms it feeds are dropped by the same tests as
+// before, in the same order).
+template <typename T>
+__device__ __forceinline__ T slope_line_t(const T* u, const T* mu, int64_t s, int n, int i) {
+  auto off = [&](int d) { return (int64_t)(min(max(i + d, 0), n - 1) - i) * s; };
+  const T um2 = u[off(-2)], um1 = u[off(-1)], u0 = u[0], up1 = u[off(1)], up2 = u[off(2)];
+  const T mm2 = mu[off(-2)], mm1 = mu[off(-1)], m0 = mu[0], mp1 = mu[off(1)], mp2 = mu[off(2)];
+  // mu of slope m = i + d (mc), end nodes folded in (mlo: node m - 1, mhi: node m + 1)
+  auto mu_f = [&](int d, T mlo, T mc, T mhi) {
+    const int m = i + d;
+    T v = mc;
+    if (m == 1) v += mlo;
+    if (m == n - 2) v += mhi;
+    return (m < 1 || m > n - 2) ? T(0) : v;
+  };
+  T acc = T(0), gl, gr;
+  harm_grad(um1 - um2, u0 - um1, gl, gr);  // slope i-1: u_i is its right node
+  if (i >= 2) acc += mu_f(-1, mm2, mm1, m0) * gr;
+  harm_grad(u0 - um1, up1 - u0, gl, gr);  // slope i
+  if (i >= 1 && i <= n - 2) acc += mu_f(0, mm1, m0, mp1) * (gl - gr);
+  harm_grad(up1 - u0, up2 - up1, gl, gr);  // slope i+1: u_i is its left node
+  if (i <= n - 3) acc -= mu_f(1, m0, mp1, mp2) * gl;
+  return acc;
+}
+
+// Rows of a masked-adjoint tile whose lambda the kernel can form itself
+// (its tile height may not exceed this when lam == nullptr).
+constexpr int kAdjLamRows = 16;
+
+// lambda^n at interior node (i, k): read, or (lam == nullptr) the slope
+// transpose of the previous step's accumulators, as k_adj_slopes_t forms
+// it, after which the node's accumulators of the step after this one (and
+// those of the boundary nodes next to it, which no tile owns) are zeroed.
+__device__ __forceinline__ float node_lambda(const AdjArgs<float>& g, int i, int k) {
+  const int nx = g.s.nx, ny = g.s.ny;
+  const int64_t J = (int64_t)nx * ny, j = (int64_t)k * nx + i;
+  if (g.lam) return g.lam[j];
+  const float* mu = g.mu_prev;
+  const float lam = mu[j] + slope_line_t(g.u_prev + j, mu + J + j, (int64_t)1, nx, i) +
+                    slope_line_t(g.u_prev + j, mu + 2 * J + j, (int64_t)nx, ny, k);
+  auto clear = [&](int64_t m) {
+    g.mu_clear[m] = 0.f;
+    g.mu_clear[J + m] = 0.f;
+    g.mu_clear[2 * J + m] = 0.f;
+  };
+  clear(j);
+  const bool L = i == 1, R = i == nx - 2, B = k == 1, T = k == ny - 2;
+  if (L) clear(j - 1);
+  if (R) clear(j + 1);
+  if (B) clear(j - nx);
+  if (T) clear(j + nx);
+  if (L && B) clear(j - nx - 1);
+  if (R && B) clear(j - nx + 1);
+  if (L && T) clear(j + nx - 1);
+  if (R && T) clear(j + nx + 1);
+  return lam;
+}
+
 // Register budget for kAdjMinBlocks CTAs per SM (80 registers): the window
 // pass keeps only the 1D weights and the column sums in registers.
 #ifndef FK_ADJ_MINB
@@ -498,6 +593,7 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
   float* RS = reinterpret_cast<float*>(MU + 3 * ly * lp);  // per-thread row sums A_r, B_r
   __shared__ float lred[FK_THREADS / 32];
   __shared__ int fred[4][FK_THREADS / 32];
+  __shared__ float lam_s[kAdjLamRows][32];  // lambda^n of the thread's nodes (lam == nullptr)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = 1 + blockIdx.x * 32, k0 = 1 + blockIdx.y * a.ty;
   const int gi0 = i0 - a.hx - 1, gk0 = k0 - a.hy - 1;
@@ -518,7 +614,8 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
     for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
       const int k = k0 + ty;
       if (i > a.nx - 2 || k > a.ny - 2) break;
-      const float lam = g.lam[(int64_t)k * a.nx + i];
+      const float lam = node_lambda(g, i, k);
+      if (!g.lam) lam_s[ty][lane] = lam;
       if (lam == 0.f) continue;
       float dx, dy;
       node_drift(a, i, k, dx, dy);
@@ -579,8 +676,8 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
   for (int ty = warp; ty < a.ty; ty += FK_THREADS / 32) {
     const int k = k0 + ty;
     if (i > a.nx - 2 || k > a.ny - 2) break;
-    const float* lam_at = g.lam + (int64_t)k * a.nx + i;
-    const float lamS = ldexpf(*lam_at, s_exp);  // scaled to the accumulators' fixed point
+    const float lam = g.lam ? g.lam[(int64_t)k * a.nx + i] : lam_s[ty][lane];
+    const float lamS = ldexpf(lam, s_exp);  // scaled to the accumulators' fixed point
     if (lamS == 0.f) continue;
     const int lk = k - gk0;
     const float uj = U[lk * lp + li];
@@ -693,7 +790,6 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
       ax[1] = 0.f;   ay[1] = g.cby;
       ax[2] = 0.f;   ay[2] = 0.f;
     }
-    const float lam = *lam_at;
     DA[0] += lam * (ax[0] * Gx + ay[0] * Gy);
     DA[FK_THREADS] += lam * (ax[1] * Gx + ay[1] * Gy);
     DA[2 * FK_THREADS] += lam * (ax[2] * Gx + ay[2] * Gy);
@@ -731,60 +827,6 @@ __global__ void __launch_bounds__(FK_THREADS, kAdjMinBlocks) k_adj_masked(const 
     const double sum = warp_sum((double)part);
     if (lane == 0 && sum != 0.0) atomicAdd(&g.dth[warp], sum);
   }
-}
-
-// Gradient of the slope rule H(dl, dr) = 2 dl dr / (dl + dr) (dl dr > 0,
-// else 0) of Eq. (e300): dH/d dl = 2 (dr / (dl + dr))^2 and
-// dH/d dr = 2 (dl / (dl + dr))^2, 0 on the zero branch.  Formed from the
-// ratios, which lie in [0, 1]: differences near the bottom of the exponent
-// range (a march from the indicator leaves such values far from the
-// boundary) would overflow 1 / (dl + dr)^2.
-template <typename T>
-__device__ __forceinline__ void harm_grad(T dl, T dr, T& gl, T& gr) {
-  if (dl * dr > T(0)) {
-    const T ql = dl / (dl + dr), qr = T(1) - ql;  // dr / (dl + dr)
-    gl = T(2) * qr * qr;
-    gr = T(2) * ql * ql;
-  } else {
-    gl = T(0);
-    gr = T(0);
-  }
-}
-
-// Transposed slope map along one grid line, at node i of n (u and mu point
-// at node i, s is the stride between neighbours): the sum over the slopes
-// m = i-1, i, i+1 that read u_i of mu_m dH_m/du_i, where slope m reads
-// dl = u_m - u_{m-1} and dr = u_{m+1} - u_m.  The end rule stated after
-// Eq. (e300) makes the slope of node 0 the same function of u as that of
-// node 1 (the harmonic mean is symmetric), and node n-1 that of node n-2,
-// so mu of the end nodes is added to their neighbours' and only interior
-// three-point slopes remain.
-// Every load is made, at an offset clamped into the line, before any term
-// is chosen: the ten loads are then in flight together instead of each
-// waiting behind the range test that guards it (a clamped load reads a
-// real node, and the terms it feeds are dropped by the same tests as
-// before, in the same order).
-template <typename T>
-__device__ __forceinline__ T slope_line_t(const T* u, const T* mu, int64_t s, int n, int i) {
-  auto off = [&](int d) { return (int64_t)(min(max(i + d, 0), n - 1) - i) * s; };
-  const T um2 = u[off(-2)], um1 = u[off(-1)], u0 = u[0], up1 = u[off(1)], up2 = u[off(2)];
-  const T mm2 = mu[off(-2)], mm1 = mu[off(-1)], m0 = mu[0], mp1 = mu[off(1)], mp2 = mu[off(2)];
-  // mu of slope m = i + d (mc), end nodes folded in (mlo: node m - 1, mhi: node m + 1)
-  auto mu_f = [&](int d, T mlo, T mc, T mhi) {
-    const int m = i + d;
-    T v = mc;
-    if (m == 1) v += mlo;
-    if (m == n - 2) v += mhi;
-    return (m < 1 || m > n - 2) ? T(0) : v;
-  };
-  T acc = T(0), gl, gr;
-  harm_grad(um1 - um2, u0 - um1, gl, gr);  // slope i-1: u_i is its right node
-  if (i >= 2) acc += mu_f(-1, mm2, mm1, m0) * gr;
-  harm_grad(u0 - um1, up1 - u0, gl, gr);  // slope i
-  if (i >= 1 && i <= n - 2) acc += mu_f(0, mm1, m0, mp1) * (gl - gr);
-  harm_grad(up1 - u0, up2 - up1, gl, gr);  // slope i+1: u_i is its left node
-  if (i <= n - 3) acc -= mu_f(1, m0, mp1, mp2) * gl;
-  return acc;
 }
 
 // lambda^{n+1}_i = mu_u[i] + sum_m mu_x[m] dD^x_m/du_i + sum_m mu_y[m] dD^y_m/du_i;
@@ -989,8 +1031,9 @@ bool adj_use_masked(const fk_plan* p) {
 }
 int adj_masked_ty(const fk_plan* p, int smem_max) {
   const int lx = 32 + 2 * p->mhalo[0] + 2;
-  auto bytes = [&](int ty) {
-    return adj_masked_smem(ty + 2 * p->mhalo[1] + 2, lx | 1, p->mwin) + kAdjStatic;
+  auto bytes = [&](int ty) {  // (+ the kernel's static arrays: reductions and lam_s)
+    return adj_masked_smem(ty + 2 * p->mhalo[1] + 2, lx | 1, p->mwin) + kAdjStatic +
+           sizeof(float) * kAdjLamRows * 32;
   };
   // FK_ADJ_TILE=ty: an explicit tile height (profiling)
   if (const char* t = getenv("FK_ADJ_TILE")) {
@@ -1008,9 +1051,15 @@ int adj_masked_ty(const fk_plan* p, int smem_max) {
   return 0;
 }
 
+// One backward step (index n = 0, 1, ... in backward order).  fused (masked
+// form): the kernel forms lambda^n from the previous step's accumulators
+// over u_prev, and the accumulators rotate over three buffers (read n % 3,
+// accumulate into (n + 1) % 3, zero (n + 2) % 3); otherwise lambda^n comes
+// from lam, two buffers alternate, and the slope transpose writes
+// lambda^{n+1} into lam_out.
 template <typename T>
-fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* lam_out,
-                   double* dth, int ty, cudaStream_t s) {
+fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* u_prev, bool fused,
+                   const void* lam, void* lam_out, double* dth, int ty, cudaStream_t s) {
   AdjArgs<T> g;
   memset(&g, 0, sizeof(g));
   if (sizeof(T) == 4)
@@ -1028,11 +1077,21 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
   g.s.ly = ty + 2 * g.s.hy + 2;
   g.s.lyr = g.s.ly | 1;
   g.s.u_in = (const T*)u_in;
-  g.lam = (const T*)lam;
-  // two mu buffers of 3 J values: step n accumulates into buffer n % 2
-  // while its slope transpose clears the other one for step n + 1
-  g.mu = (T*)p->adj_mu + (n & 1) * 3 * p->J;
-  T* mu_next = (T*)p->adj_mu + ((n + 1) & 1) * 3 * p->J;
+  const int64_t J3 = 3 * p->J;
+  T* mu_next = nullptr;
+  if (fused) {
+    g.lam = nullptr;
+    g.mu = (T*)p->adj_mu + ((n + 1) % 3) * J3;
+    g.mu_prev = (const T*)p->adj_mu + (n % 3) * J3;
+    g.mu_clear = (T*)p->adj_mu + ((n + 2) % 3) * J3;
+    g.u_prev = (const T*)u_prev;
+  } else {
+    // two mu buffers of 3 J values: step n accumulates into buffer n % 2
+    // while its slope transpose clears the other one for step n + 1
+    g.lam = (const T*)lam;
+    g.mu = (T*)p->adj_mu + (n & 1) * J3;
+    mu_next = (T*)p->adj_mu + ((n + 1) & 1) * J3;
+  }
   g.dth = dth;
   const double tn = n * p->dt;
   if (p->coeffs.family == FK_CELLULAR_FLOW) {
@@ -1083,6 +1142,7 @@ fk_status adj_step(fk_plan* p, int n, const void* u_in, const void* lam, void* l
   }
   if (e != cudaSuccess) return FK_ERR_CUDA;
   if (ev && cudaEventRecord(ev[1], s) != cudaSuccess) return FK_ERR_CUDA;
+  if (fused) return FK_OK;
   const dim3 b(32, 8), gr((p->grid.n[0] + 31) / 32, (p->grid.n[1] + 7) / 8);
   k_adj_slopes_t<T><<<gr, b, 0, s>>>((const T*)u_in, (const T*)g.mu, (T*)lam_out, mu_next,
                                      p->grid.n[0], p->grid.n[1]);
@@ -1133,8 +1193,10 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
         cudaSuccess)
       return FK_ERR_CUDA;
   }
-  // workspace: checkpoints (M+1), two segments (2K), lambda x2, mu (2 x 3 fields), dtheta
-  const int64_t need = (int64_t)(M + 1 + 2 * K + 2 + 6) * fb + 64;
+  // the masked form forms lambda inside its kernel (three accumulator buffers)
+  const bool fused = p->adj_kernel == 2 && p->adj_ty <= kAdjLamRows;
+  // workspace: checkpoints (M+1), two segments (2K), lambda x2, mu (3 x 3 fields), dtheta
+  const int64_t need = (int64_t)(M + 1 + 2 * K + 2 + 9) * fb + 64;
   if (p->adj_bytes < need) {
     if (cudaStreamSynchronize(s) != cudaSuccess) return FK_ERR_CUDA;
     fk_dev_free(p->adj_ws);
@@ -1150,7 +1212,7 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
   char* rest = seg + (int64_t)(2 * K) * fb;
   void* lam[2] = {rest, rest + fb};
   p->adj_mu = rest + 2 * fb;
-  double* dth = dtheta ? dtheta : (double*)(rest + (int64_t)8 * fb);
+  double* dth = dtheta ? dtheta : (double*)(rest + (int64_t)11 * fb);
   auto slot = [&](int n) { return n == N ? M : n / K; };  // n == N or n % K == 0
 
   // forward pass with checkpoints
@@ -1170,17 +1232,19 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
       src = dst;
     }
   }
-  if (cudaMemsetAsync(p->adj_mu, 0, (size_t)6 * fb, s) != cudaSuccess ||
+  if (cudaMemsetAsync(p->adj_mu, 0, (size_t)9 * fb, s) != cudaSuccess ||
       cudaMemsetAsync(dth, 0, 4 * sizeof(double), s) != cudaSuccess)
     return FK_ERR_CUDA;
-  // lambda^0 = g
+  // lambda^0 = g (fused: as the u part of the accumulators step 0 reads, its
+  // slope parts zero)
   int cur = 0;
   {
     const int blocks = (int)((p->J + 255) / 256 < 152 * 16 ? (p->J + 255) / 256 : 152 * 16);
+    void* dst0 = fused ? p->adj_mu : lam[cur];
     if (p->prec == FK_FP32)
-      k_cast_in<float><<<blocks, 256, 0, s>>>(cotangent_u0, (float*)lam[cur], p->J);
+      k_cast_in<float><<<blocks, 256, 0, s>>>(cotangent_u0, (float*)dst0, p->J);
     else
-      k_cast_in<double><<<blocks, 256, 0, s>>>(cotangent_u0, (double*)lam[cur], p->J);
+      k_cast_in<double><<<blocks, 256, 0, s>>>(cotangent_u0, (double*)dst0, p->J);
     if (cudaGetLastError() != cudaSuccess) return FK_ERR_CUDA;
   }
   // events for the backward-step kernels (fk_adjoint_kernel_times)
@@ -1240,6 +1304,7 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
   // backward over segments [mK, top)
   fk_status rst = recompute(0);
   if (rst != FK_OK) return rst;
+  const void* u_prev = nullptr;  // the previous backward step's u_in
   for (int m = 0; m < M; ++m) {
     FkRange seg_range("fk_adjoint segment");
     const int lo = m * K, top = (m + 1) * K < N ? (m + 1) * K : N;
@@ -1251,17 +1316,31 @@ extern "C" fk_status fk_adjoint(fk_plan* p, const void* u_terminal, const double
     for (int n = lo; n < top; ++n) {
       const void* u_in = (n + 1 == top) ? ckpt(slot(top))
                                         : (const void*)(segbuf(m) + (int64_t)(n - lo) * fb);
-      fk_status st = p->prec == FK_FP32
-                         ? adj_step<float>(p, n, u_in, lam[cur], lam[cur ^ 1], dth, ty, s)
-                         : adj_step<double>(p, n, u_in, lam[cur], lam[cur ^ 1], dth, ty, s);
+      const void* up = u_prev ? u_prev : u_in;  // (step 0: the slope parts are 0)
+      fk_status st =
+          p->prec == FK_FP32
+              ? adj_step<float>(p, n, u_in, up, fused, lam[cur], lam[cur ^ 1], dth, ty, s)
+              : adj_step<double>(p, n, u_in, up, fused, lam[cur], lam[cur ^ 1], dth, ty, s);
       if (st != FK_OK) return st;
       cur ^= 1;
+      u_prev = u_in;
     }
     if (two && cudaEventRecord(ev_bwd[m & 1], s) != cudaSuccess) return FK_ERR_CUDA;
     if (!two && m + 1 < M) {
       rst = recompute(m + 1);
       if (rst != FK_OK) return rst;
     }
+  }
+  if (fused && du_terminal) {
+    // lambda^N: the slope transpose of the last step's accumulators
+    const dim3 b(32, 8), gr((p->grid.n[0] + 31) / 32, (p->grid.n[1] + 7) / 8);
+    const int64_t J3 = 3 * p->J;
+    k_adj_slopes_t<float><<<gr, b, 0, s>>>((const float*)u_prev,
+                                           (const float*)p->adj_mu + (N % 3) * J3,
+                                           (float*)lam[cur],
+                                           (float*)p->adj_mu + ((N + 1) % 3) * J3,
+                                           p->grid.n[0], p->grid.n[1]);
+    if (cudaGetLastError() != cudaSuccess) return FK_ERR_CUDA;
   }
   if (du_terminal && fk_launch_copy(du_terminal, lam[cur], fb, s) != cudaSuccess) return FK_ERR_CUDA;
   return FK_OK;
