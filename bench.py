@@ -776,9 +776,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "d2h_bytes_per_step": field_bytes},
         "gpu_launches": args.steps * (1 if info.get("step_kernel") in ("resident", "cluster") else
                                       2 if persistent else
-                                      # 3D: records + window (+ the quench's coefficients)
-                                      (3 if w["family"] == "runaway_quench" else
-                                       2 if w["path"] == "csr" or len(w["n"]) == 3 else 1)
+                                      # 3D: records (with the quench's coefficients) + window
+                                      (2 if w["path"] == "csr" or len(w["n"]) == 3 else 1)
                                       * w["n_steps"] + 1),
         "clocks": clocks,
         "wall_s_timed_region": wall,

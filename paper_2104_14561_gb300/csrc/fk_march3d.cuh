@@ -33,9 +33,9 @@
 //    reach, often far fewer than the W^3 the widest node needs.
 // The runaway model's per-node drift and sigma (Eq. (ex32d): erf, four
 // exponentials, square roots) go into a table of six values per node that
-// k_step3d reads: k_coef3d fills it once per plan for the static model and
-// before each step for the quench variant, whose constants depend on t_n
-// (a third launch per step there).
+// k_step3d reads: k_coef3d fills it once per plan for the static model, and
+// for the quench variant, whose constants depend on t_n, the record launch
+// fills it before each step (k_rec_coef3d).
 // Positions are taken relative to the node in cells: point p of axis m is
 // at i_m + rel_p with rel_p = b_m dt / h_m + sigma_m sqrt(2 dt) a_p / h_m.
 //
@@ -92,12 +92,9 @@ __device__ __forceinline__ T held_value(const Step3D<T>& a, int i, int j, int k)
   return on ? (one ? T(1) : T(0)) : T(-1);
 }
 
-// Records and boundary values of one field.
+// The record and the held boundary value of node (i, j, k).
 template <typename T>
-__global__ void __launch_bounds__(kRecThreads) k_rec3d(const Step3D<T> a) {
-  const int i = blockIdx.x * kRecThreads + threadIdx.x;
-  const int j = blockIdx.y, k = blockIdx.z;
-  if (i >= a.nx) return;
+__device__ __forceinline__ void rec3d_node(const Step3D<T>& a, int i, int j, int k) {
   const int64_t sy = a.nx, sz = (int64_t)a.nx * a.ny;
   const int64_t node = (int64_t)k * sz + (int64_t)j * sy + i;
   const T* u = a.u_in;
@@ -125,6 +122,14 @@ __global__ void __launch_bounds__(kRecThreads) k_rec3d(const Step3D<T> a) {
     a.u_out[node] = held;
     if (a.snap) a.snap[node] = held;
   }
+}
+
+// Records and boundary values of one field.
+template <typename T>
+__global__ void __launch_bounds__(kRecThreads) k_rec3d(const Step3D<T> a) {
+  const int i = blockIdx.x * kRecThreads + threadIdx.x;
+  if (i >= a.nx) return;
+  rec3d_node(a, i, (int)blockIdx.y, (int)blockIdx.z);
 }
 
 // Terminal indicator: 1 on the faces whose exit value is 1, 0 elsewhere.
@@ -517,6 +522,29 @@ __global__ void __launch_bounds__(kRecThreads) k_coef3d(const Step3D<T> a, T* co
   }
 }
 
+// The quench variant's step prologue in one launch: the records (as
+// k_rec3d) and, at the nodes the step updates, the coefficients of t_n (as
+// k_coef3d); two launches before.
+template <typename T, bool NU>
+__global__ void __launch_bounds__(kRecThreads) k_rec_coef3d(const Step3D<T> a, T* coef) {
+  const int i = blockIdx.x * kRecThreads + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  if (i >= a.nx) return;
+  rec3d_node(a, i, j, k);
+  if (i < a.first[0] || i >= a.first[0] + a.count[0] || j < a.first[1] ||
+      j >= a.first[1] + a.count[1] || k < a.first[2] || k >= a.first[2] + a.count[2])
+    return;
+  const int64_t J = (int64_t)a.nx * a.ny * a.nz;
+  const int64_t node = ((int64_t)k * a.ny + j) * a.nx + i;
+  T sh[3], gs[3];
+  runaway_coef<T, NU>(a, i, j, k, sh, gs);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    coef[m * J + node] = sh[m];
+    coef[(3 + m) * J + node] = gs[m];
+  }
+}
+
 template <typename T, int W>
 cudaError_t launch_w(const Step3D<T>& a, cudaStream_t s) {
   const int in = a.count[0];
@@ -540,14 +568,18 @@ cudaError_t launch_w(const Step3D<T>& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t fk_launch_step3d(const Step3D<T>& a, cudaStream_t s) {
-  if (a.family == FK_RUNAWAY_3D && a.coef_per_step) {
-    cudaError_t e = fk_launch_coef3d<T>(a, const_cast<T*>(a.coef), s);
-    if (e != cudaSuccess) return e;
-  }
   {
     const dim3 grid((unsigned)((a.nx + kRecThreads - 1) / kRecThreads), (unsigned)a.ny,
                     (unsigned)a.nz);
-    k_rec3d<T><<<grid, kRecThreads, 0, s>>>(a);
+    if (a.family == FK_RUNAWAY_3D && a.coef_per_step) {
+      T* coef = const_cast<T*>(a.coef);
+      if (a.nu)
+        k_rec_coef3d<T, true><<<grid, kRecThreads, 0, s>>>(a, coef);
+      else
+        k_rec_coef3d<T, false><<<grid, kRecThreads, 0, s>>>(a, coef);
+    } else {
+      k_rec3d<T><<<grid, kRecThreads, 0, s>>>(a);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
