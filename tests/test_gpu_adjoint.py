@@ -130,6 +130,26 @@ def test_adjoint_fp32_forms_vs_oracle(fk, oracle, monkeypatch, kernel):
     assert np.abs(du - odu).max() <= 1e-4 * np.abs(odu).max()
 
 
+@pytest.mark.parametrize("n,q,D", [((5, 3), 4, 0.01), ((9, 5), 4, 0.02), ((33, 17), 4, 0.02)])
+def test_adjoint_masked_small_meshes_vs_oracle(fk, oracle, monkeypatch, n, q, D):
+    """The masked form on meshes of one tile and of a few: every node is a
+    boundary node or next to one, so each tile's kernel forms lambda at its
+    nodes and also zeroes the accumulators of the boundary nodes next to
+    them, for the step after (three steps' buffers in turn, K = 2)."""
+    monkeypatch.setenv("FK_ADJ_KERNEL", "masked")
+    w = dict(SMALL, n=n, q=q, n_steps=7, dt=1e-2, params=(1.0, 0.2, 2 * math.pi, D))
+    shape = (n[1], n[0])
+    cot = np.random.default_rng(8).standard_normal(shape)
+    u0 = fk_inputs.random_field(shape, seed=9)
+    dth, du = _gpu_adjoint(fk, w, "fp32", cot, u0, K=2, kernel="masked")
+    g = oracle.Grid(w["n"], w["lo"], w["hi"])
+    odth, odu = oracle.adjoint(g, oracle.CELLULAR_FLOW, list(w["params"]), w["q"], w["dt"],
+                               w["n_steps"], cot, u0)
+    scale = np.abs(odth).max()
+    assert np.abs(dth - odth).max() <= 1e-3 * scale
+    assert np.abs(du - odu).max() <= 1e-4 * np.abs(odu).max()
+
+
 def test_adjoint_checkpoint_interval(fk):
     w = dict(SMALL, n_steps=23)
     shape = (w["n"][1], w["n"][0])
